@@ -1,0 +1,256 @@
+"""ORACLE -- test infrastructure only: ctypes binding of the C oracle.
+
+Functions mirror ``hweno_oracle.h``.  Arrays are float64 numpy arrays in the
+structure-of-arrays layout the header documents.
+"""
+
+import ctypes
+import glob
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libhweno_oracle.so")
+
+BURGERS, EULER = 0, 1
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+TROUBLED_HYBRID, TROUBLED_ALL, TROUBLED_NONE = 0, 1, 2
+
+_D = ctypes.c_double
+_I = ctypes.c_int
+_PD = ctypes.POINTER(ctypes.c_double)
+_PU8 = ctypes.POINTER(ctypes.c_uint8)
+_PL = ctypes.POINTER(ctypes.c_long)
+
+
+class Cfg1D(ctypes.Structure):
+    _fields_ = [
+        ("system", _I), ("nx", _I), ("x0", _D), ("x1", _D), ("bc", _I),
+        ("gas_gamma", _D), ("lin_w", _D * 3), ("eps", _D),
+        ("kxrcf_threshold", _D), ("troubled_mode", _I), ("limit_in_place", _I),
+    ]
+
+    @classmethod
+    def make(cls, system, nx, x0, x1, bc, lin_w=(0.98, 0.01, 0.01),
+             gas_gamma=1.4, eps=1e-6, threshold=1.0,
+             troubled_mode=TROUBLED_HYBRID, limit_in_place=1):
+        c = cls()
+        c.system, c.nx, c.x0, c.x1, c.bc = system, nx, x0, x1, bc
+        c.gas_gamma = gas_gamma
+        for k in range(3):
+            c.lin_w[k] = lin_w[k]
+        c.eps, c.kxrcf_threshold = eps, threshold
+        c.troubled_mode, c.limit_in_place = troubled_mode, limit_in_place
+        return c
+
+    @property
+    def ncomp(self):
+        return 3 if self.system == EULER else 1
+
+
+class Cfg2D(ctypes.Structure):
+    _fields_ = [
+        ("system", _I), ("nx", _I), ("ny", _I), ("x0", _D), ("x1", _D),
+        ("y0", _D), ("y1", _D), ("bc", _I), ("gas_gamma", _D),
+        ("lin_w", _D * 5), ("eps", _D), ("kxrcf_threshold", _D),
+        ("troubled_mode", _I), ("limit_in_place", _I), ("n_gauss", _I),
+    ]
+
+    @classmethod
+    def make(cls, system, nx, ny, x0, x1, y0, y1, bc,
+             lin_w=(0.96, 0.01, 0.01, 0.01, 0.01), gas_gamma=1.4, eps=1e-6,
+             threshold=1.0, troubled_mode=TROUBLED_HYBRID, limit_in_place=1,
+             n_gauss=3):
+        c = cls()
+        c.system, c.nx, c.ny = system, nx, ny
+        c.x0, c.x1, c.y0, c.y1, c.bc = x0, x1, y0, y1, bc
+        c.gas_gamma = gas_gamma
+        for k in range(5):
+            c.lin_w[k] = lin_w[k]
+        c.eps, c.kxrcf_threshold = eps, threshold
+        c.troubled_mode, c.limit_in_place, c.n_gauss = troubled_mode, limit_in_place, n_gauss
+        return c
+
+    @property
+    def ncomp(self):
+        return 4 if self.system == EULER else 1
+
+
+def build(force=False):
+    """Compile the C oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    srcs = sorted(glob.glob(os.path.join(_HERE, "*.c")))
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(p) for p in srcs + glob.glob(os.path.join(_HERE, "*.h")))
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P1 = ctypes.POINTER(Cfg1D)
+        L.hwo1d_alpha.restype = _D
+        L.hwo1d_alpha.argtypes = [P1, _PD]
+        L.hwo1d_rhs.restype = _I
+        L.hwo1d_rhs.argtypes = [P1, _PD, _D, _PD, _PD, _PU8, _PD]
+        L.hwo1d_rhs_ex.restype = _I
+        L.hwo1d_rhs_ex.argtypes = [P1, _PD, _D, _PD, _PD, _PU8, _PD, _PD]
+        L.hwo1d_step.restype = _I
+        L.hwo1d_step.argtypes = [P1, _PD, _D, _PL]
+        L.hwo1d_dt.restype = _D
+        L.hwo1d_dt.argtypes = [P1, _PD, _D, _D, _D]
+        L.hwo1d_run.restype = _I
+        L.hwo1d_run.argtypes = [P1, _PD, _I, _D, _D, _D, _D, _PD, _PD, _PL]
+        L.hwo1d_limiter_candidates.restype = None
+        L.hwo1d_limiter_candidates.argtypes = [_PD, _D, _D, _PD, _PD]
+        L.hwo1d_limit_scalar.restype = _D
+        L.hwo1d_limit_scalar.argtypes = [_PD, _D, _PD, _D, _D]
+        L.hwo1d_recon_candidates.restype = None
+        L.hwo1d_recon_candidates.argtypes = [_PD, _PD, _PD, _PD]
+        L.hwo1d_recon_scalar.restype = None
+        L.hwo1d_recon_scalar.argtypes = [_PD, _D, _PD, _PD, _I, _PD]
+        L.hwo_euler1d_eigen.restype = None
+        L.hwo_euler1d_eigen.argtypes = [_D, _PD, _PD, _PD]
+        L.hwo_euler1d_flux.restype = None
+        L.hwo_euler1d_flux.argtypes = [_D, _PD, _PD]
+        if hasattr(L, "hwo2d_rhs"):
+            P2 = ctypes.POINTER(Cfg2D)
+            L.hwo2d_rhs.restype = _I
+            L.hwo2d_rhs.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD]
+            L.hwo2d_alpha.restype = None
+            L.hwo2d_alpha.argtypes = [P2, _PD, _PD, _PD]
+            L.hwo2d_dt.restype = _D
+            L.hwo2d_dt.argtypes = [P2, _PD, _D, _D, _D]
+            L.hwo2d_step.restype = _I
+            L.hwo2d_step.argtypes = [P2, _PD, _D, _PL]
+            L.hwo2d_run.restype = _I
+            L.hwo2d_run.argtypes = [P2, _PD, _I, _D, _D, _D, _D, _PD, _PD, _PL]
+            L.hwo2d_recon_candidates.restype = _I
+            L.hwo2d_recon_candidates.argtypes = [_PD, _PD, _PD, _I, _PD, _PD]
+            L.hwo2d_linear_weights.restype = _I
+            L.hwo2d_linear_weights.argtypes = [_I, _PD]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_PD)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------- 1D
+
+def alpha1d(cfg, u):
+    u = _f64(u)
+    return lib().hwo1d_alpha(ctypes.byref(cfg), _p(u))
+
+
+def rhs1d(cfg, u, alpha=-1.0, faces=False):
+    """One evaluation of Eq. (odeH).  Returns (rhs, ulim, flags, indicator),
+    plus the interface values [C][2][nx] (u^+_{i-1/2}, u^-_{i+1/2}) if faces."""
+    u = _f64(u)
+    rhs = np.empty_like(u)
+    ulim = np.empty_like(u)
+    fc = np.empty_like(u)
+    flags = np.zeros(cfg.nx, dtype=np.uint8)
+    ind = np.zeros(cfg.nx, dtype=np.float64)
+    st = lib().hwo1d_rhs_ex(ctypes.byref(cfg), _p(u), alpha, _p(rhs), _p(ulim),
+                            flags.ctypes.data_as(_PU8), _p(ind), _p(fc))
+    if st != 0:
+        raise FloatingPointError("oracle rhs1d status %d" % st)
+    if faces:
+        return rhs, ulim, flags, ind, fc
+    return rhs, ulim, flags, ind
+
+
+def dt1d(cfg, u, cfl, t=0.0, t_final=-1.0):
+    u = _f64(u)
+    return lib().hwo1d_dt(ctypes.byref(cfg), _p(u), cfl, t, t_final)
+
+
+def step1d(cfg, u, dt):
+    """One SSP-RK3 step with the given dt; returns (u_new, troubled count)."""
+    u = _f64(u).copy()
+    nt = ctypes.c_long(0)
+    st = lib().hwo1d_step(ctypes.byref(cfg), _p(u), dt, ctypes.byref(nt))
+    if st != 0:
+        raise FloatingPointError("oracle step1d status %d" % st)
+    return u, nt.value
+
+
+def run1d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
+          lin_w_per_step=None):
+    """Repeated SSP-RK3 steps; returns (u, t, troubled cell-stage count)."""
+    u = _f64(u).copy()
+    t = ctypes.c_double(0.0)
+    nt = ctypes.c_long(0)
+    lw = None
+    if lin_w_per_step is not None:
+        lw_arr = _f64(lin_w_per_step)
+        assert nsteps >= 0 and lw_arr.size >= 3 * nsteps
+        lw = _p(lw_arr)
+    st = lib().hwo1d_run(ctypes.byref(cfg), _p(u), nsteps, cfl, t0, t_final,
+                         dt_fixed, lw, ctypes.byref(t), ctypes.byref(nt))
+    if st != 0:
+        raise FloatingPointError("oracle run1d status %d" % st)
+    return u, t.value, nt.value
+
+
+def limiter_candidates1d(ub3, v_m1, v_p1):
+    ub3 = _f64(ub3)
+    q = np.zeros(3)
+    beta = np.zeros(3)
+    lib().hwo1d_limiter_candidates(_p(ub3), v_m1, v_p1, _p(q), _p(beta))
+    return q, beta
+
+
+def limit_scalar1d(gam, eps, ub3, v_m1, v_p1):
+    gam = _f64(gam)
+    ub3 = _f64(ub3)
+    return lib().hwo1d_limit_scalar(_p(gam), eps, _p(ub3), v_m1, v_p1)
+
+
+def recon_candidates1d(ub3, vb3):
+    ub3, vb3 = _f64(ub3), _f64(vb3)
+    val = np.zeros(12)
+    beta = np.zeros(3)
+    lib().hwo1d_recon_candidates(_p(ub3), _p(vb3), _p(val), _p(beta))
+    return val.reshape(3, 4), beta
+
+
+def recon_scalar1d(gam, eps, ub3, vb3, hweno):
+    gam, ub3, vb3 = _f64(gam), _f64(ub3), _f64(vb3)
+    out = np.zeros(4)
+    lib().hwo1d_recon_scalar(_p(gam), eps, _p(ub3), _p(vb3), int(hweno), _p(out))
+    return out
+
+
+def euler1d_eigen(g, U):
+    U = _f64(U)
+    R = np.zeros(9)
+    L = np.zeros(9)
+    lib().hwo_euler1d_eigen(g, _p(U), _p(R), _p(L))
+    return R.reshape(3, 3), L.reshape(3, 3)
+
+
+def euler1d_flux(g, U):
+    U = _f64(U)
+    F = np.zeros(3)
+    lib().hwo_euler1d_flux(g, _p(U), _p(F))
+    return F

@@ -1,0 +1,402 @@
+"""Pins of the 1D oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows (Zhao & Qiu, arXiv:2002.08816).  None
+re-types the oracle's own code: the oracle derives every coefficient from the
+moment conditions by a linear solve, while these tests compare against the
+formulas printed in the paper (tests/golden/hweno1d_printed.txt), exact
+polynomial moments computed by numpy, closed-form invariants, and the error
+tables of Sec. 3.
+"""
+
+import numpy as np
+import pytest
+
+from helpers import burgers_exact_1d, eval_beta, load_printed_1d
+from oracle import oracle as O
+from paper_2002_08816_gb300 import workloads as W
+
+LIN, BETA = load_printed_1d()
+
+
+def _lin_oracle(name, d):
+    """The oracle's value of the printed linear functional on data d (6-vector)."""
+    um, u0, up, vm, v0, vp = d
+    if name.startswith("lim_q"):
+        q, _ = O.limiter_candidates1d([um, u0, up], vm, vp)
+        return q[int(name[-1])]
+    val, _ = O.recon_candidates1d([um, u0, up], [vm, v0, vp])
+    table = {"rec_p0_right": (0, 1), "rec_p1_right": (1, 1), "rec_p2_right": (2, 1),
+             "rec_p0_left": (0, 0), "rec_p0_gm": (0, 2), "rec_p0_gp": (0, 3)}
+    n, p = table[name]
+    return val[n, p]
+
+
+@pytest.mark.parametrize("name", sorted(LIN))
+def test_printed_linear_functionals(name):
+    """Sec. 2.1 Steps 1, 2.1-2.3: every printed coefficient, datum by datum."""
+    cite, coeffs = LIN[name]
+    if name.startswith("lim_q"):
+        assert coeffs[4] == 0.0  # Step 1 does not use v_i
+    got = np.array([_lin_oracle(name, np.eye(6)[k]) for k in range(6)])
+    np.testing.assert_allclose(got, coeffs, rtol=1e-12, atol=1e-13, err_msg=cite)
+
+
+def _beta_oracle(name, d):
+    um, u0, up, vm, v0, vp = d
+    if name.startswith("lim_"):
+        _, b = O.limiter_candidates1d([um, u0, up], vm, vp)
+    else:
+        _, b = O.recon_candidates1d([um, u0, up], [vm, v0, vp])
+    return b[int(name.split("beta")[1][0])]
+
+
+@pytest.mark.parametrize("name", sorted(k for k in BETA if not k.endswith("_printed")))
+def test_printed_smoothness_indicators(name):
+    """Eq. (GHYZ) as printed in Sec. 2.1 (Step 1 beta_0 with its corrected square)."""
+    cite, terms = BETA[name]
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        d = rng.normal(size=6)
+        if name.startswith("lim_"):
+            d[4] = 0.0
+        want = eval_beta(terms, d)
+        got = _beta_oracle(name, d)
+        assert abs(got - want) <= 1e-11 * max(1.0, abs(want)), (cite, got, want)
+
+
+def test_step1_beta0_as_printed_is_garbled():
+    """The printed last square of Step 1's beta_0 (v-coefficients +-1) does not
+    follow from Eq. (GHYZ); the corrected one (+-6) does (previous test)."""
+    _, terms = BETA["lim_beta0_printed"]
+    d = np.array([0.3, -0.1, 0.7, 0.05, 0.0, -0.02])
+    assert abs(_beta_oracle("lim_beta0", d) - eval_beta(terms, d)) > 1e-3
+
+
+# ----------------------------------------------------------------------------- exactness
+
+def _poly_moments(coef, j):
+    """Exact (average, first moment) of the polynomial sum c_k xi^k over
+    [j-1/2, j+1/2], via numpy's polynomial integration."""
+    P = np.polynomial.Polynomial(coef)
+    a, b = j - 0.5, j + 0.5
+    Pi = P.integ()
+    avg = Pi(b) - Pi(a)
+    Q = (P * np.polynomial.Polynomial([-j, 1.0])).integ()
+    return avg, Q(b) - Q(a)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3, 4, 5, 6])
+def test_reconstruction_polynomial_exactness(deg):
+    """Step 2: p0 reproduces polynomials of degree <= 5, p1 and p2 of degree <= 2."""
+    rng = np.random.default_rng(deg)
+    coef = rng.normal(size=deg + 1)
+    m = [_poly_moments(coef, j) for j in (-1, 0, 1)]
+    val, _ = O.recon_candidates1d([x[0] for x in m], [x[1] for x in m])
+    P = np.polynomial.Polynomial(coef)
+    exact = P(np.array([-0.5, 0.5, -np.sqrt(5) / 10, np.sqrt(5) / 10]))
+    err0 = np.max(np.abs(val[0] - exact))
+    err12 = max(np.max(np.abs(val[1] - exact)), np.max(np.abs(val[2] - exact)))
+    if deg <= 5:
+        assert err0 < 1e-12
+    else:
+        assert err0 > 1e-6
+    if deg <= 2:
+        assert err12 < 1e-12
+    else:
+        assert err12 > 1e-6
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3, 4, 5])
+def test_limiter_polynomial_exactness(deg):
+    """Step 1: q0 is exact for degree <= 4, q1 and q2 for degree <= 1."""
+    rng = np.random.default_rng(10 + deg)
+    coef = rng.normal(size=deg + 1)
+    m = [_poly_moments(coef, j) for j in (-1, 0, 1)]
+    q, _ = O.limiter_candidates1d([x[0] for x in m], m[0][1], m[2][1])
+    exact = m[1][1]
+    assert (abs(q[0] - exact) < 1e-12) == (deg <= 4)
+    assert (max(abs(q[1] - exact), abs(q[2] - exact)) < 1e-12) == (deg <= 1)
+
+
+# ----------------------------------------------------------------------------- weights
+
+def test_constant_data_gives_linear_weights():
+    """All beta vanish on constant data, so tau = 0, omega = gamma and the
+    combination returns p0 for any positive gamma (Eq. (p_big))."""
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        g = rng.uniform(0.01, 1.0, size=3)
+        g /= g.sum()
+        c = rng.normal()
+        out = O.recon_scalar1d(g, 1e-6, [c, c, c], [0, 0, 0], 1)
+        np.testing.assert_allclose(out, c, rtol=0, atol=1e-14)
+        assert abs(O.limit_scalar1d(g, 1e-6, [c, c, c], 0.0, 0.0)) < 1e-15
+
+
+def test_agreeing_candidates_are_reproduced_for_any_gamma():
+    """If every candidate gives the same value, the combination returns it
+    whatever the nonlinear weights (Step 1 and Step 2.1 formulas)."""
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        g = rng.uniform(0.01, 1.0, size=3)
+        g /= g.sum()
+        quad = rng.normal(size=3)
+        m = [_poly_moments(quad, j) for j in (-1, 0, 1)]
+        out = O.recon_scalar1d(g, 1e-6, [x[0] for x in m], [x[1] for x in m], 1)
+        P = np.polynomial.Polynomial(quad)
+        np.testing.assert_allclose(out[:2], P(np.array([-0.5, 0.5])), atol=1e-12)
+        lin = rng.normal(size=2)
+        m = [_poly_moments(lin, j) for j in (-1, 0, 1)]
+        v = O.limit_scalar1d(g, 1e-6, [x[0] for x in m], m[0][1], m[2][1])
+        assert abs(v - m[1][1]) < 1e-13
+
+
+def test_hweno_picks_the_smooth_side_at_a_jump():
+    """Essentially non-oscillatory: with a jump between I_i and I_{i+1}, the
+    HWENO value at x_{i+1/2} follows the left candidate p1, not p0."""
+    g = [0.98, 0.01, 0.01]
+    ub, vb = [0.0, 0.0, 1.0], [0.0, 0.0, 0.0]
+    val, beta = O.recon_candidates1d(ub, vb)
+    out = O.recon_scalar1d(g, 1e-6, ub, vb, 1)
+    assert abs(val[0, 1] - val[1, 1]) > 0.1            # p0 overshoots
+    assert abs(out[1] - val[1, 1]) < 1e-3 * abs(val[0, 1] - val[1, 1])
+
+
+# ----------------------------------------------------------------------------- physics
+
+def test_euler_eigenvectors_diagonalise_the_jacobian():
+    """Remark 2: R's columns are eigenvectors of dF/dU with eigenvalues
+    mu - c, mu, mu + c (Jacobian by central differences of the flux)."""
+    g = 1.4
+    U = W.euler_conserved_1d(np.array(0.8), np.array(-0.3), np.array(0.6))
+    R, L = O.euler1d_eigen(g, U)
+    h = 1e-6
+    J = np.zeros((3, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        J[:, k] = (O.euler1d_flux(g, U + e) - O.euler1d_flux(g, U - e)) / (2 * h)
+    rho, mu = U[0], U[1] / U[0]
+    p = (g - 1) * (U[2] - 0.5 * rho * mu * mu)
+    c = np.sqrt(g * p / rho)
+    lam = np.array([mu - c, mu, mu + c])
+    np.testing.assert_allclose(J @ R, R * lam[None, :], atol=1e-7)
+    np.testing.assert_allclose(L @ R, np.eye(3), atol=1e-13)
+
+
+@pytest.mark.parametrize("system", [O.BURGERS, O.EULER])
+def test_constant_state_is_steady(system):
+    """A constant state has zero right-hand side in Eq. (odeH)."""
+    nx = 16
+    if system == O.BURGERS:
+        u = np.zeros((1, 2, nx))
+        u[0, 0] = 0.7
+    else:
+        u = np.zeros((3, 2, nx))
+        u[:, 0, :] = W.euler_conserved_1d(np.array(0.9), np.array(0.4), np.array(0.7))[:, None]
+    for bc in (O.BC_PERIODIC, O.BC_OUTFLOW):
+        cfg = O.Cfg1D.make(system, nx, 0.0, 1.0, bc, troubled_mode=O.TROUBLED_ALL)
+        rhs, ulim, flags, _ = O.rhs1d(cfg, u)
+        assert np.max(np.abs(rhs)) < 1e-12
+        assert np.max(np.abs(ulim[:, 1])) < 1e-14
+
+
+@pytest.mark.parametrize("system", [O.BURGERS, O.EULER])
+def test_periodic_conservation_of_averages(system):
+    """Eq. (odeH): sum_i d(ubar_i)/dt telescopes to zero with periodic ends,
+    also through shocks, limiting and HWENO."""
+    if system == O.BURGERS:
+        nx = 80
+        u = W.burgers_sine_1d(nx)
+        cfg = O.Cfg1D.make(system, nx, -1.0, 1.0, O.BC_PERIODIC)
+        steps = 60
+    else:
+        nx = 128
+        u = W.euler_riemann_1d(nx, (1.0, 0.75, 1.0), (0.125, 0.0, 0.1), 0.0, 1.0, 0.5)
+        cfg = O.Cfg1D.make(system, nx, 0.0, 1.0, O.BC_PERIODIC)
+        steps = 40
+    s0 = u[:, 0].sum(axis=1)
+    u1, t, nt = O.run1d(cfg, u, nsteps=steps, cfl=0.5)
+    assert nt > 0  # the run went through troubled cells
+    np.testing.assert_allclose(u1[:, 0].sum(axis=1), s0, rtol=1e-13, atol=1e-12)
+
+
+def test_no_troubled_cells_on_smooth_burgers_and_some_after_the_shock():
+    """Example 3.1 is smooth (no cell flagged, as the paper states for the
+    hybrid scheme); Example 3.5 has a shock, flagged in a few cells."""
+    for nx in (40, 80, 160, 400):
+        u = W.burgers_sine_1d(nx)
+        cfg = O.Cfg1D.make(O.BURGERS, nx, -1.0, 1.0, O.BC_PERIODIC)
+        _, _, flags, _ = O.rhs1d(cfg, u)
+        assert flags.sum() == 0
+    nx = 80
+    u = W.burgers_sine_1d(nx)
+    cfg = O.Cfg1D.make(O.BURGERS, nx, -1.0, 1.0, O.BC_PERIODIC)
+    u1, t, _ = O.run1d(cfg, u, cfl=0.6, t_final=1.5 / np.pi)
+    _, _, flags, _ = O.rhs1d(cfg, u1)
+    assert 1 <= flags.sum() <= 0.15 * nx
+
+
+# ----------------------------------------------------------------------------- convergence
+
+TABLE1_NEW_HYBRID_L1 = {40: 8.51e-07, 80: 1.46e-08, 120: 1.39e-09, 160: 2.66e-10}
+TABLE1_NEW_HWENO_L1 = {80: 4.20e-07, 120: 3.97e-08, 160: 8.83e-09}
+
+
+def _burgers_error(nx, mode, lin_w_seed=None):
+    """Reading: dt = 0.6 dx^(5/3) so that RK3 does not hide the fifth order."""
+    T = 0.5 / np.pi
+    dx = 2.0 / nx
+    dt = 0.6 * dx ** (5.0 / 3.0)
+    cfg = O.Cfg1D.make(O.BURGERS, nx, -1.0, 1.0, O.BC_PERIODIC, troubled_mode=mode)
+    ns = int(np.ceil(T / dt)) + 1
+    lw = None if lin_w_seed is None else W.random_lin_weights(ns, 3, lin_w_seed)
+    u, t, nt = O.run1d(cfg, W.burgers_sine_1d(nx), nsteps=ns, t_final=T, dt_fixed=dt,
+                       lin_w_per_step=lw)
+    assert abs(t - T) < 1e-12
+    ex = W.cell_moments_1d(lambda x: burgers_exact_1d(x, T), nx, -1.0, 1.0, 8)[0, 0]
+    return np.mean(np.abs(u[0, 0] - ex)), nt
+
+
+def test_burgers_convergence_hybrid_table1():
+    """Table 1, new hybrid HWENO: fifth order, magnitudes within a factor 3."""
+    errs = {}
+    for nx in (40, 80, 120, 160):
+        errs[nx], nt = _burgers_error(nx, O.TROUBLED_HYBRID)
+        assert nt == 0
+        assert TABLE1_NEW_HYBRID_L1[nx] / 3 < errs[nx] < 3 * TABLE1_NEW_HYBRID_L1[nx]
+    for a, b in ((80, 120), (120, 160)):
+        assert np.log(errs[a] / errs[b]) / np.log(b / a) > 4.6
+
+
+def test_burgers_convergence_all_troubled_random_weights_table1():
+    """Table 1, new HWENO (every cell limited and HWENO-reconstructed, random
+    linear weights each step): fifth order, magnitudes within a factor 3."""
+    errs = {}
+    for nx in (80, 120, 160):
+        errs[nx], _ = _burgers_error(nx, O.TROUBLED_ALL, lin_w_seed=nx)
+        assert TABLE1_NEW_HWENO_L1[nx] / 3 < errs[nx] < 3 * TABLE1_NEW_HWENO_L1[nx]
+    for a, b in ((80, 120), (120, 160)):
+        assert np.log(errs[a] / errs[b]) / np.log(b / a) > 4.6
+
+
+def test_linear_weights_do_not_change_the_hybrid_scheme_on_smooth_data():
+    """Sec. 3.1: with no troubled cell the hybrid scheme is linear, so any
+    linear weights give identical results."""
+    nx = 60
+    u0 = W.burgers_sine_1d(nx)
+    a = O.run1d(O.Cfg1D.make(O.BURGERS, nx, -1.0, 1.0, O.BC_PERIODIC), u0,
+                nsteps=10, cfl=0.5)[0]
+    b = O.run1d(O.Cfg1D.make(O.BURGERS, nx, -1.0, 1.0, O.BC_PERIODIC,
+                             lin_w=(0.2, 0.5, 0.3)), u0, nsteps=10, cfl=0.5)[0]
+    assert np.array_equal(a, b)
+
+
+def test_euler_density_wave_table2():
+    """Table 2 (Example 3.2 on [0, 2]): fifth order; at a small CFL (spatial
+    error dominant) the N = 80 error lies within a factor 3 of the table."""
+    T = 2.0
+    errs = {}
+    for nx in (40, 80):
+        dx = 2.0 / nx
+        cfg = O.Cfg1D.make(O.EULER, nx, 0.0, 2.0, O.BC_PERIODIC)
+        u, t, nt = O.run1d(cfg, W.euler_density_wave_1d(nx), t_final=T,
+                           dt_fixed=0.6 * dx ** (5.0 / 3.0))
+        assert nt == 0
+        ex = W.cell_moments_1d(lambda x: 1 + 0.2 * np.sin(np.pi * (x - T)), nx, 0, 2, 8)[0, 0]
+        errs[nx] = np.mean(np.abs(u[0, 0] - ex))
+    assert np.log(errs[40] / errs[80]) / np.log(2) > 4.8
+    nx = 80
+    cfg = O.Cfg1D.make(O.EULER, nx, 0.0, 2.0, O.BC_PERIODIC)
+    u, t, _ = O.run1d(cfg, W.euler_density_wave_1d(nx), t_final=T, cfl=0.03)
+    ex = W.cell_moments_1d(lambda x: 1 + 0.2 * np.sin(np.pi * (x - T)), nx, 0, 2, 8)[0, 0]
+    e = np.mean(np.abs(u[0, 0] - ex))
+    assert 3.10e-11 / 3 < e < 3 * 3.10e-11
+
+
+# ----------------------------------------------------------------------------- hand-computed 5-cell values
+
+def _paper_weights(gam, beta, eps=1e-6):
+    """tau of Eq. (tao5) and the nonlinear weights of Sec. 2.1, computed here
+    by hand from the printed smoothness indicators."""
+    tau = ((abs(beta[0] - beta[1]) + abs(beta[0] - beta[2])) / 2.0) ** 2
+    wb = [g * (1.0 + tau / (b + eps)) for g, b in zip(gam, beta)]
+    return [w / sum(wb) for w in wb]
+
+
+def _paper_combine(gam, om, vals):
+    return (om[0] * (vals[0] / gam[0] - gam[1] / gam[0] * vals[1] - gam[2] / gam[0] * vals[2])
+            + om[1] * vals[1] + om[2] * vals[2])
+
+
+def test_hand_computed_hweno_on_five_cell_inputs():
+    """Step 1 and Step 2.1 evaluated by hand from the printed formulas (golden
+    file) on random 5-cell data, against the oracle's modified first moment
+    and u^-_{i+1/2}."""
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        # cells i-2..i+2; the limiter of I_i uses i-1..i+1
+        ub = rng.normal(size=5) * (1.0 if trial % 2 else 0.05)
+        vb = rng.normal(size=5) * 0.1
+        if trial % 3 == 0:
+            ub[3:] += 1.0  # a jump
+        gam = rng.uniform(0.01, 1.0, size=3)
+        gam /= gam.sum()
+        d = np.array([ub[1], ub[2], ub[3], vb[1], 0.0, vb[3]])
+        q = [LIN["lim_q%d" % n][1] @ d for n in range(3)]
+        beta = [eval_beta(BETA["lim_beta%d" % n][1], d) for n in range(3)]
+        want = _paper_combine(gam, _paper_weights(gam, beta), q)
+        got = O.limit_scalar1d(gam, 1e-6, ub[1:4], vb[1], vb[3])
+        assert abs(got - want) <= 1e-10 * max(1.0, abs(want))
+
+        d = np.array([ub[1], ub[2], ub[3], vb[1], vb[2], vb[3]])
+        p = [LIN["rec_p%d_right" % n][1] @ d for n in range(3)]
+        beta = [eval_beta(BETA["rec_beta%d" % n][1], d) for n in range(3)]
+        want = _paper_combine(gam, _paper_weights(gam, beta), p)
+        got = O.recon_scalar1d(gam, 1e-6, ub[1:4], vb[1:4], 1)[1]
+        assert abs(got - want) <= 1e-10 * max(1.0, abs(want))
+
+
+def test_hybrid_switch_uses_the_whole_big_stencil():
+    """Step 2: a cell takes the HWENO interface values when any cell of
+    S0 = {I_{i-1}, I_i, I_{i+1}} is troubled, the linear ones otherwise; the
+    interface values use the modified first moments."""
+    nx = 24
+    u = np.zeros((1, 2, nx))
+    u[0, 0, 8:15] = 1.0
+    u[0, 0] += 0.3
+    u[0, 1] = 0.001 * np.sin(np.arange(nx))
+    cfg = O.Cfg1D.make(O.BURGERS, nx, 0.0, float(nx), O.BC_PERIODIC, lin_w=(0.9, 0.04, 0.06))
+    _, ulim, flags, _, faces = O.rhs1d(cfg, u, faces=True)
+    assert 0 < flags.sum() < nx // 2
+    nhw = 0
+    for i in range(nx):
+        idx = [(i - 1) % nx, i, (i + 1) % nx]
+        hw = int(flags[idx].any())
+        nhw += hw
+        out = O.recon_scalar1d(cfg.lin_w, 1e-6, ulim[0, 0, idx], ulim[0, 1, idx], hw)
+        np.testing.assert_allclose(faces[0, :, i], out[:2], rtol=0, atol=1e-14)
+    assert nhw > flags.sum()
+
+
+TABLE2_NEW_HWENO_L1 = {40: 9.09e-07, 80: 7.89e-09}
+
+
+def test_euler_density_wave_all_troubled_table2():
+    """Table 2, new HWENO (Example 3.2, every cell limited and reconstructed in
+    characteristic fields, random linear weights each step): fifth order or
+    better, magnitudes within a factor 3."""
+    T = 2.0
+    errs = {}
+    for nx in (40, 80):
+        dx = 2.0 / nx
+        dt = 0.6 * dx ** (5.0 / 3.0)
+        ns = int(np.ceil(T / dt)) + 1
+        cfg = O.Cfg1D.make(O.EULER, nx, 0.0, 2.0, O.BC_PERIODIC, troubled_mode=O.TROUBLED_ALL)
+        u, t, _ = O.run1d(cfg, W.euler_density_wave_1d(nx), nsteps=ns, t_final=T, dt_fixed=dt,
+                          lin_w_per_step=W.random_lin_weights(ns, 3, nx))
+        assert abs(t - T) < 1e-12
+        ex = W.cell_moments_1d(lambda x: 1 + 0.2 * np.sin(np.pi * (x - T)), nx, 0, 2, 8)[0, 0]
+        errs[nx] = np.mean(np.abs(u[0, 0] - ex))
+        assert TABLE2_NEW_HWENO_L1[nx] / 3 < errs[nx] < 3 * TABLE2_NEW_HWENO_L1[nx], errs[nx]
+    assert np.log(errs[40] / errs[80]) / np.log(2) > 4.8
