@@ -1,0 +1,329 @@
+"""Benchmark of the hybrid HWENO time stepper on GB300.
+
+Workload (one bench step): the seeded two-state 1D Euler problem, gamma 1.4,
+65536 cells on [0, 1] with outflow ends, advanced 2000 third-order TVD
+Runge-Kutta steps (6000 stages, 3.93e8 cell-stages) at CFL 0.5, FP32 bulk
+arithmetic with FP64 alpha/dt.  The metric is cell-updates per second counted
+per Runge-Kutta stage.  The FP64 path is timed on the same workload and
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hweno|reference]
+
+--impl reference times the FP64 C oracle on the host cores on a bounded
+sample of the same workload.  Under torchrun each rank advances its own
+seeded instance (no data-path collective): weak scaling.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = 65536
+RK_STEPS = 2000
+CFL = 0.5
+SEED = 20250
+METRIC = "cell-updates/s (x RK stages) of the hybrid HWENO step"
+UNIT = "cell-stages/s"
+# algorithmic bytes per cell-stage: stage 1 reads u^n and writes u^(1) (2S),
+# stages 2 and 3 read u^n and u^(k) and write (3S); mean 8S/3 with
+# S = 3 components x 2 moments x sizeof(real)
+BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank):
+    from paper_2002_08816_gb300 import workloads as W
+    return W.euler_two_state_1d(NX, seed=SEED + rank)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                         "sw_power_cap"]
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_cpu_baseline(u0, budget_s=12.0, max_steps=400):
+    """The FP64 C oracle as it stands, single-threaded, on the full 65536-cell
+    state for as many RK steps as fit in about budget_s seconds."""
+    from oracle import oracle as O
+    cfg = O.Cfg1D.make(O.EULER, NX, 0.0, 1.0, O.BC_OUTFLOW)
+    u = u0.copy()
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        u, _, _ = O.run1d(cfg, u, nsteps=5, cfl=CFL)
+        steps += 5
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": NX * 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d RK steps of the 65536-cell workload, FP64, 1 thread, %.1f s"
+                      % (steps, RK_STEPS, el)}
+
+
+def bench_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    u0 = workload(0)
+    from oracle import oracle as O
+    cfg = O.Cfg1D.make(O.EULER, NX, 0.0, 1.0, O.BC_OUTFLOW)
+    sample_steps = 10
+    u = u0.copy()
+    for _ in range(args.warmup):
+        O.run1d(cfg, u, nsteps=sample_steps, cfl=CFL)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u, _, _ = O.run1d(cfg, u, nsteps=sample_steps, cfl=CFL)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = NX * 3 * sample_steps * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "1D Euler two-state, 65536 cells, outflow, CFL %.1f; each step "
+                               "%d of the %d RK steps (bounded sample)" % (CFL, sample_steps, RK_STEPS),
+                   "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d RK steps x %d timed steps on 65536 cells, 1 thread"
+                                   % (sample_steps, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def bench_hweno(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_08816_gb300 import hweno as H
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    u0 = workload(rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for prec_name, prec in (("fp32", H.HWENO_FP32), ("fp64", H.HWENO_FP64)):
+        cfg = H.make_config(1, H.HWENO_EULER, NX, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=CFL,
+                            precision=prec)
+        h = H.hweno_create(cfg, s)
+        dt = torch.float32 if prec == H.HWENO_FP32 else torch.float64
+        dev_in = torch.from_numpy(u0).to("cuda", dt).contiguous()
+        host_in = torch.from_numpy(u0).to(dt).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+
+        def one_step():
+            H.hweno_set_state(h, dev_in.data_ptr(), prec, True)
+            H.hweno_step(h, RK_STEPS, -1.0, wait=False)
+
+        for _ in range(args.warmup):
+            one_step()
+        torch.cuda.synchronize()
+        t_end = H.hweno_step(h, 0, -1.0)  # status check of the warm-up runs
+        assert t_end > 0.0
+        st_w = H.hweno_stats(h)
+        assert st_w["steps"] == RK_STEPS
+
+        # device-resident timing: L2 flushed between timed steps, events on the stream
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sampler = ClockSampler(local) if prec_name == "fp32" else None
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__enter__()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        H.hweno_step(h, 0, -1.0)  # raises on a non-physical run
+        stats = H.hweno_stats(h)
+        tot_s = max_over_ranks(sum(ms) / 1e3)
+
+        # end to end through the public API with host buffers (pinned)
+        e2e_ms = []
+        for k in range(max(1, min(args.steps, 3))):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            H.hweno_set_state(h, host_in.data_ptr(), prec, False)
+            H.hweno_step(h, RK_STEPS, -1.0, wait=False)
+            H.hweno_get_state(h, host_out.data_ptr(), prec, False)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        e2e_s = max_over_ranks(sum(e2e_ms) / 1e3)
+        H.hweno_destroy(h)
+        cells = NX * 3 * RK_STEPS
+        results[prec_name] = {
+            "value": ws * cells * args.steps / tot_s,
+            "ms_per_step": 1e3 * tot_s / args.steps,
+            "stage_us": 1e6 * tot_s / (args.steps * 3 * RK_STEPS),
+            "e2e": ws * cells * len(e2e_ms) / e2e_s,
+            "troubled_frac": stats["troubled"] / float(3 * RK_STEPS * NX),
+            "bytes_h2d": host_in.numel() * host_in.element_size(),
+            "clocks": sampler.summary() if sampler else None,
+        }
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(u0)
+    if rank != 0:
+        dist.destroy_process_group() if ws > 1 else None
+        return
+    r = results["fp32"]
+    peak, peak_kind = peaks()
+    per_launch = BYTES_PER_CELL_STAGE["fp32"] * NX
+    achieved = per_launch / (r["stage_us"] * 1e-6) / 1e9
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "1D Euler two-state, 65536 cells, outflow, 2000 SSP-RK3 steps, "
+                               "CFL 0.5, FP32 (FP64 alpha/dt)",
+                   "seed": SEED, "l2": "flushed (512 MiB write) between timed steps",
+                   "parallelism": "one independent instance per GPU"},
+        "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
+                 "e2e": results["fp64"]["e2e"]},
+        "troubled_frac": r["troubled_frac"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "stage1d_kernel<float,3>",
+                     "note": "avg stage-launch time = timed region / 6000 launches; peak %s" % peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["bytes_h2d"],
+                "d2h_bytes_per_step": r["bytes_h2d"]},
+        "gpu_launches": args.steps * (3 * RK_STEPS + 4),
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_hweno(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,132 @@
+/*
+ * hweno.h -- C ABI of the GB300 (sm_103a) hybrid Hermite WENO library.
+ *
+ * The library evolves the zeroth and first moments of 1D and 2D conservation
+ * laws (scalar Burgers, compressible Euler) with the fifth-order hybrid HWENO
+ * scheme with artificial linear weights of Zhao & Qiu, "A Hermite WENO scheme
+ * with artificial linear weights for hyperbolic conservation laws"
+ * (arXiv:2002.08816):
+ *   - semi-discrete moment scheme, Eq. (odeH) (1D) and Eq. (ode2) (2D);
+ *   - KXRCF troubled-cell detection and first-moment modification, Steps 1, 4;
+ *   - hybrid reconstruction: linear p0 on smooth stencils (Steps 2.2, 5.2),
+ *     HWENO nonlinear combination with any positive linear weights summing to
+ *     one on stencils holding a troubled cell (Steps 2.1, 5.1), linear values
+ *     at interior quadrature points (Steps 2.3, 5.3);
+ *   - global Lax-Friedrichs flux, Gauss(-Lobatto) quadratures, Sec. 2.1/2.2;
+ *   - third-order TVD Runge-Kutta, Eq. (RK), with a device-side CFL step.
+ *
+ * Every call takes plain pointers and sizes; no C++ or torch type crosses it.
+ * Errors are returned as hweno_status; no exception leaves the library.  A
+ * handle may be used from one host thread at a time.
+ *
+ * Layout of a state ("moments") buffer, structure of arrays, no padding:
+ *   1D: element (c, m, i)    at ((c*2 + m)*nx + i)
+ *   2D: element (c, m, j, i) at (((c*3 + m)*ny + j)*nx + i)
+ * with c the conserved component (Burgers: u; 1D Euler: rho, rho*mu, E;
+ * 2D Euler: rho, rho*mu, rho*nu, E) and m the moment: 0 the cell average
+ * (1/|I|) int u, 1 the x-moment (1/|I|) int u (x-x_i)/dx, 2 (2D) the
+ * y-moment (1/|I|) int u (y-y_j)/dy (Sec. 2.1 after Eq. (odeH); Sec. 2.2
+ * after Eq. (ode2)).
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HWENO_OK = 0,
+  HWENO_ERR_ARG = 1,           /* invalid argument or configuration */
+  HWENO_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  HWENO_ERR_NONPHYSICAL = 3,   /* non-finite value, rho <= 0 or p <= 0 seen */
+  HWENO_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+  HWENO_ERR_STATE = 5          /* call out of order (e.g. step before set_state) */
+} hweno_status;
+
+enum { HWENO_BURGERS = 0, HWENO_EULER = 1 };
+enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1 };
+enum { HWENO_TROUBLED_HYBRID = 0, HWENO_TROUBLED_ALL = 1, HWENO_TROUBLED_NONE = 2 };
+enum { HWENO_FP32 = 0, HWENO_FP64 = 1 };
+
+typedef struct {
+  int dim;                /* 1 or 2 */
+  int system;             /* HWENO_BURGERS or HWENO_EULER */
+  int nx, ny;             /* cells per direction (ny ignored for dim 1); nx, ny >= 4 */
+  double x0, x1, y0, y1;  /* domain [x0,x1] x [y0,y1] */
+  int bc;                 /* HWENO_BC_PERIODIC or HWENO_BC_OUTFLOW, all sides */
+  double gas_gamma;       /* ratio of specific heats (Euler), > 1 */
+  double lin_w[5];        /* linear weights gamma_0..gamma_2 (1D) or ..gamma_4 (2D):
+                             all > 0, |sum - 1| <= 1e-12 (Sec. 2.1 Step 1) */
+  double cfl;             /* CFL number of the time step, > 0 */
+  double eps;             /* epsilon of the nonlinear weights (paper: 1e-6), > 0 */
+  double kxrcf_threshold; /* troubled iff KXRCF indicator > threshold (1) */
+  int troubled_mode;      /* HWENO_TROUBLED_HYBRID (the paper's scheme), _ALL, _NONE */
+  int n_gauss;            /* 2D quadrature points per direction: 3 (paper) or 2 */
+  int precision;          /* HWENO_FP32 or HWENO_FP64 bulk arithmetic */
+} hweno_config;
+
+typedef struct hweno_ctx* hweno_handle;
+
+/* Fills cfg with the paper's defaults for the given dimension and system:
+ * gamma = 1.4, linear weights (0.98, 0.01, 0.01) in 1D and (0.96, 0.01 x 4)
+ * in 2D (Sec. 3.2), CFL 0.6 (Sec. 3), eps = 1e-6, threshold 1, hybrid mode,
+ * three Gauss points, FP32, periodic, unit domain.  Sizes are left at 0. */
+void hweno_default_config(hweno_config* cfg, int dim, int system);
+
+/* Validates cfg, allocates every device buffer the scheme needs (the library
+ * owns them) and binds the handle to cuda_stream (a cudaStream_t; NULL = the
+ * legacy default stream).  *out is set only on HWENO_OK.  Returns
+ * HWENO_ERR_ARG for an invalid configuration (see hweno_config). */
+hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_handle* out);
+
+/* Copies a state in the layout above into the handle and sets t = 0.
+ * moments: host (on_device = 0) or device (on_device = 1) pointer, caller
+ * owned, element type dtype (HWENO_FP32 / HWENO_FP64; converted when it
+ * differs from the configured precision).  Asynchronous with respect to the
+ * host for device sources; a host source is staged through a synchronous
+ * copy.  The state must hold the moments defined in Sec. 2 (the helper
+ * module workloads.py projects point data by Gauss quadrature). */
+hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int on_device);
+
+/* Enqueues nsteps third-order TVD Runge-Kutta steps (Eq. (RK)) on the bound
+ * stream.  dt = cfl * dx / alpha (1D) or cfl / (alpha_x/dx + alpha_y/dy) (2D)
+ * from the state at the start of each step, computed and kept on the device;
+ * with t_final > 0 the step is clipped so that t does not pass t_final and
+ * steps after t_final do nothing.  t_out NULL: returns without waiting.
+ * t_out non-NULL: waits for the stream, stores the time reached, and returns
+ * HWENO_ERR_NONPHYSICAL if any stage saw a non-finite or non-physical value. */
+hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_out);
+
+/* One evaluation of the right-hand side L of Eq. (odeH)/(ode2) on caller
+ * device buffers in the configured precision and the state layout: out =
+ * L(in) with alpha from in.  flags_out (nullable, nx*ny bytes) receives the
+ * troubled-cell flags (1 = troubled); ulim_out (nullable, state layout)
+ * receives in with the first moments of troubled cells modified (Step 1/4).
+ * in, out and ulim_out must not overlap.  Waits for the stream and returns
+ * HWENO_ERR_NONPHYSICAL on a non-finite result. */
+hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags_out,
+                       void* ulim_out);
+
+/* Copies the current state out (host or device pointer, caller owned, dtype
+ * as in set_state).  A host destination makes the call wait for the stream. */
+hweno_status hweno_get_state(hweno_handle h, void* out, int dtype, int on_device);
+
+/* Statistics since set_state: the time reached, the last dt, the number of
+ * completed steps and of troubled cell-stages.  Waits for the stream. */
+hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* steps,
+                         int64_t* troubled_cell_stages);
+
+/* Frees every device buffer of the handle; NULL is ignored. */
+void hweno_destroy(hweno_handle h);
+
+/* Text of the last error on this handle (or of the last failed create when
+ * h is NULL); valid until the next call on the handle. */
+const char* hweno_last_error(hweno_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,403 @@
+// One fused kernel per third-order TVD Runge-Kutta stage of the 1D hybrid
+// HWENO scheme (Zhao & Qiu, arXiv:2002.08816, Sec. 2.1).
+//
+// A CTA owns kTile1D consecutive cells.  It stages its cells plus a 3-cell
+// halo of the stage input in shared memory (coalesced loads of each
+// structure-of-arrays row), then, all on chip:
+//   1. alpha = max |f'(ubar)| from the per-tile partial maxima the producer
+//      of the stage input wrote (global Lax-Friedrichs flux); stage 1 also
+//      turns alpha into dt = CFL dx / alpha, clipped to t_final;
+//   2. KXRCF flags (FP64) and the modified first moments (Step 1) for the
+//      cells and 2 halo cells per side, in characteristic fields for Euler;
+//   3. interface values (Steps 2.1/2.2) for the cells and 1 halo cell per
+//      side: linear p0 unless a cell of S0 = {i-1, i, i+1} is troubled;
+//   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
+//      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
+//      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
+//   5. an FP64 partial maximum of the wave speed of the output for the next
+//      stage's alpha, and the status bits (non-finite, non-physical).
+// The limited stage input is what the RK combination uses (the first moment
+// of a troubled cell is modified in the state, as a DG limiter would).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hweno1d_recon.cuh"
+#include "hweno_device.cuh"
+#include "hweno_internal.h"
+
+namespace hw {
+namespace {
+
+constexpr int T = kTile1D;
+constexpr int H = 3;
+
+template <typename R, int C>
+struct Smem1D {
+  R u[C][2][T + 2 * H];  // stage input, cells base-3 .. base+T+2
+  R vl[C][T + 4];        // modified first moments, cells base-2 .. base+T+1
+  R fm[C][T + 2];        // u^+_{i-1/2}, cells base-1 .. base+T
+  R fp[C][T + 2];        // u^-_{i+1/2}
+  uint8_t fl[T + 4];     // flags, cells base-2 .. base+T+1
+  double red[T / 32];
+};
+
+template <typename R, int C>
+__device__ __forceinline__ void phys_flux(R gas, const R* U, R* F) {
+  if constexpr (C == 1) {
+    F[0] = R(0.5) * U[0] * U[0];
+  } else {
+    Euler1D<R>::flux(gas, U, F);
+  }
+}
+
+template <int C>
+__device__ __forceinline__ double wave_speed(double gas, const double* U) {
+  if constexpr (C == 1) {
+    return fabs(U[0]);
+  } else {
+    return euler1d_speed(gas, U[0], U[1], U[2]);
+  }
+}
+
+template <typename R, int C>
+__global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
+  __shared__ Smem1D<R, C> sm;
+  __shared__ double s_dt;
+  const int tid = threadIdx.x;
+  const int n = a.n;
+  const int base = blockIdx.x * T;
+  const R* __restrict__ w = static_cast<const R*>(a.w);
+
+  // 1. alpha of the stage input and the step size
+  double amax = 0.0;
+  for (int k = tid; k < a.ntile; k += T) amax = fmax(amax, a.a_in[k]);
+  const double alpha = block_max<T>(amax, sm.red);
+  double dt = 0.0;
+  if (a.stage == 1) {
+    if (tid == 0) {
+      double d = a.cfl * a.dx / alpha;
+      const double tf = a.sc->t_final;
+      if (tf > 0.0) {
+        const double rem = tf - a.sc->t;
+        d = rem <= 0.0 ? 0.0 : (d > rem ? rem : d);
+      }
+      if (!(alpha > 0.0) || !isfinite(d)) d = 0.0;
+      s_dt = d;
+      if (blockIdx.x == 0) a.sc->dt = d;
+    }
+    __syncthreads();
+    dt = s_dt;
+  } else if (a.stage > 1) {
+    dt = a.sc->dt;
+  }
+  if (a.stage > 0 && !(dt > 0.0)) return;  // uniform over the grid
+
+  // 2. stage the tile and its halo
+  for (int k = tid; k < T + 2 * H; k += T) {
+    const int g = bc_map(base - H + k, n, a.bc);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      sm.u[c][0][k] = w[(2 * c + 0) * n + g];
+      sm.u[c][1][k] = w[(2 * c + 1) * n + g];
+    }
+  }
+  __syncthreads();
+
+  const R gam[3] = {R(a.gam[0]), R(a.gam[1]), R(a.gam[2])};
+  const R eps = R(a.eps);
+  const R gas = R(a.gas);
+
+  // 3. troubled cells and modified first moments (Step 1)
+  for (int k = tid; k < T + 4; k += T) {
+    const int e = k + 1;
+    int flag;
+    if (a.mode == 1) {
+      flag = 1;
+    } else if (a.mode == 2) {
+      flag = 0;
+    } else {
+      const double h = 0.5 * a.dx;
+      double ind;
+      if constexpr (C == 1) {
+        const double u0 = sm.u[0][0][e];
+        ind = kxrcf1d(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
+                      sm.u[0][1][e], sm.u[0][1][e + 1], u0, h);
+      } else {
+        const double vel = (double)sm.u[1][0][e] / (double)sm.u[0][0][e];
+        const double ir = kxrcf1d(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
+                                  sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], vel, h);
+        const double ie = kxrcf1d(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
+                                  sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], vel, h);
+        ind = fmax(ir, ie);
+      }
+      flag = ind > a.thr;
+    }
+    sm.fl[k] = (uint8_t)flag;
+    if (!flag) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) sm.vl[c][k] = sm.u[c][1][e];
+    } else if constexpr (C == 1) {
+      sm.vl[0][k] = limit_first_moment(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
+                                       sm.u[0][1][e - 1], sm.u[0][1][e + 1], gam, eps);
+    } else {
+      // characteristic fields of the Jacobian at the cell average (Remark 2)
+      R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
+      R Rm[3][3], Lm[3][3];
+      Euler1D<R>::eigen(gas, U, Rm, Lm);
+      R q[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        R wv[5];
+        const int off[3] = {-1, 0, 1};
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+          wv[s] = Lm[f][0] * sm.u[0][0][e + off[s]] + Lm[f][1] * sm.u[1][0][e + off[s]] +
+                  Lm[f][2] * sm.u[2][0][e + off[s]];
+        wv[3] = Lm[f][0] * sm.u[0][1][e - 1] + Lm[f][1] * sm.u[1][1][e - 1] +
+                Lm[f][2] * sm.u[2][1][e - 1];
+        wv[4] = Lm[f][0] * sm.u[0][1][e + 1] + Lm[f][1] * sm.u[1][1][e + 1] +
+                Lm[f][2] * sm.u[2][1][e + 1];
+        q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sm.vl[c][k] = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2];
+    }
+  }
+  __syncthreads();
+
+  // 4. interface values (Steps 2.1, 2.2)
+  for (int k = tid; k < T + 2; k += T) {
+    const int e = k + 2;  // index into sm.u; sm.vl / sm.fl index of cell e is e - 1
+    const bool hw = sm.fl[k] | sm.fl[k + 1] | sm.fl[k + 2];
+    if (!hw) {
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                     sm.vl[c][e - 1], sm.vl[c][e], sm.fm[c][k], sm.fp[c][k]);
+    } else if constexpr (C == 1) {
+      hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
+                  sm.vl[0][e - 1], sm.vl[0][e], gam, eps, sm.fm[0][k], sm.fp[0][k]);
+    } else {
+      R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
+      R Rm[3][3], Lm[3][3];
+      Euler1D<R>::eigen(gas, U, Rm, Lm);
+      R cl[3], cr[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        R wu[3], wv[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          wu[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
+                  Lm[f][2] * sm.u[2][0][e - 1 + s];
+          wv[s] = Lm[f][0] * sm.vl[0][e - 2 + s] + Lm[f][1] * sm.vl[1][e - 2 + s] +
+                  Lm[f][2] * sm.vl[2][e - 2 + s];
+        }
+        hweno_faces(wu[0], wu[1], wu[2], wv[0], wv[1], wv[2], gam, eps, cl[f], cr[f]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sm.fm[c][k] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
+        sm.fp[c][k] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
+      }
+    }
+  }
+  __syncthreads();
+
+  // 5. own cells: fluxes, F_i, right-hand side, RK combination
+  const int i = base + tid;
+  const bool own = i < n;
+  int myflag = 0;
+  double speed = 0.0;
+  unsigned bad = 0;
+  if (own) {
+    const int e = tid + H;   // sm.u index
+    const int k = tid + 1;   // sm.fm/fp index of cell i
+    myflag = sm.fl[tid + 2];
+    const R alf = R(alpha);
+    R ql[C], qr[C], gm[C], gp[C], ra[C], rb[C], fa[C], fb[C];
+    // flux at x_{i-1/2}: u^- from cell i-1, u^+ from cell i
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      ra[c] = sm.fp[c][k - 1];
+      rb[c] = sm.fm[c][k];
+    }
+    phys_flux<R, C>(gas, ra, fa);
+    phys_flux<R, C>(gas, rb, fb);
+#pragma unroll
+    for (int c = 0; c < C; ++c) ql[c] = R(0.5) * (fa[c] + fb[c]) - R(0.5) * alf * (rb[c] - ra[c]);
+    // flux at x_{i+1/2}: u^- from cell i, u^+ from cell i+1
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      ra[c] = sm.fp[c][k];
+      rb[c] = sm.fm[c][k + 1];
+    }
+    phys_flux<R, C>(gas, ra, fa);
+    phys_flux<R, C>(gas, rb, fb);
+#pragma unroll
+    for (int c = 0; c < C; ++c) qr[c] = R(0.5) * (fa[c] + fb[c]) - R(0.5) * alf * (rb[c] - ra[c]);
+    // Gauss-Lobatto values: the cell's own traces and the interior points
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+      linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                      sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
+    R f1[C], f2[C], f3[C], f4[C], tr1[C], tr4[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      tr1[c] = sm.fm[c][k];
+      tr4[c] = sm.fp[c][k];
+    }
+    phys_flux<R, C>(gas, tr1, f1);
+    phys_flux<R, C>(gas, gm, f2);
+    phys_flux<R, C>(gas, gp, f3);
+    phys_flux<R, C>(gas, tr4, f4);
+    const R idx = R(1.0 / a.dx);
+    double Uo[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const R F = R(1.0 / 12.0) * (f1[c] + f4[c]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
+      const R Lu = -(qr[c] - ql[c]) * idx;
+      const R Lv = (F - R(0.5) * (ql[c] + qr[c])) * idx;
+      const R wu = sm.u[c][0][e];
+      const R wv = sm.vl[c][e - 1];
+      R ou, ov;
+      if (a.stage == 0) {
+        ou = Lu;
+        ov = Lv;
+      } else {
+        const R rdt = R(dt);
+        const R su = wu + rdt * Lu, sv = wv + rdt * Lv;
+        if (a.stage == 1) {
+          ou = su;
+          ov = sv;
+        } else {
+          const R* u0 = static_cast<const R*>(a.u0);
+          const R ca = a.stage == 2 ? R(0.75) : R(1.0 / 3.0);
+          const R cb = a.stage == 2 ? R(0.25) : R(2.0 / 3.0);
+          ou = ca * u0[(2 * c + 0) * n + i] + cb * su;
+          ov = ca * u0[(2 * c + 1) * n + i] + cb * sv;
+        }
+      }
+      R* out = static_cast<R*>(a.out);
+      out[(2 * c + 0) * n + i] = ou;
+      out[(2 * c + 1) * n + i] = ov;
+      if (a.lim_out) {
+        R* lo = static_cast<R*>(a.lim_out);
+        lo[(2 * c + 0) * n + i] = wu;
+        lo[(2 * c + 1) * n + i] = wv;
+      }
+      if (!isfinite(ou) || !isfinite(ov)) bad |= ST_NONFINITE;
+      Uo[c] = (double)ou;
+    }
+    if (a.flags_out) a.flags_out[i] = (uint8_t)myflag;
+    if (a.stage > 0) {
+      speed = wave_speed<C>(a.gas, Uo);
+      if (!(speed == speed)) {
+        bad |= ST_NONPHYSICAL;
+        speed = 0.0;
+      }
+    }
+  }
+  // 6. epilogue: partial max for the next alpha, counters, status
+  const int ntroubled = __syncthreads_count(myflag);
+  const double smax = block_max<T>(speed, sm.red);
+  if (tid == 0) {
+    if (a.a_out) a.a_out[blockIdx.x] = smax;
+    if (ntroubled) atomicAdd(&a.sc->troubled, (unsigned long long)ntroubled);
+    if (a.stage == 3 && blockIdx.x == 0) {
+      a.sc->t += dt;
+      a.sc->steps += 1;
+    }
+  }
+  if (bad) atomicOr(&a.sc->status, bad);
+}
+
+template <typename R, int C>
+__global__ void __launch_bounds__(T) alpha1d_kernel(const R* __restrict__ w, double* a_out,
+                                                   int n, double gas, DevScalars* sc) {
+  __shared__ double red[T / 32];
+  const int i = blockIdx.x * T + threadIdx.x;
+  double s = 0.0;
+  if (i < n) {
+    double U[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) U[c] = (double)w[(2 * c) * n + i];
+    s = wave_speed<C>(gas, U);
+    if (!(s == s)) {
+      atomicOr(&sc->status, (unsigned)ST_NONPHYSICAL);
+      s = 0.0;
+    }
+  }
+  s = block_max<T>(s, red);
+  if (threadIdx.x == 0) a_out[blockIdx.x] = s;
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, size_t count) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count;
+       k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = (D)src[k];
+}
+
+__global__ void set_scalars_kernel(DevScalars* sc, int reset, double t_final) {
+  if (reset) {
+    sc->t = 0.0;
+    sc->dt = 0.0;
+    sc->status = 0u;
+    sc->steps = 0ull;
+    sc->troubled = 0ull;
+  }
+  sc->t_final = t_final;
+}
+
+template <typename R, int C>
+cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
+  stage1d_kernel<R, C><<<a.ntile, T, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s) {
+  if (a.system == 0) return a.fp64 ? launch_stage1d_t<double, 1>(a, s) : launch_stage1d_t<float, 1>(a, s);
+  return a.fp64 ? launch_stage1d_t<double, 3>(a, s) : launch_stage1d_t<float, 3>(a, s);
+}
+
+cudaError_t launch_alpha1d(const void* w, double* a_out, int n, int ntile, int system, int fp64,
+                           double gas, DevScalars* sc, cudaStream_t s) {
+  if (system == 0) {
+    if (fp64)
+      alpha1d_kernel<double, 1><<<ntile, T, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
+    else
+      alpha1d_kernel<float, 1><<<ntile, T, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
+  } else {
+    if (fp64)
+      alpha1d_kernel<double, 3><<<ntile, T, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
+    else
+      alpha1d_kernel<float, 3><<<ntile, T, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* src, int src_fp64, void* dst, int dst_fp64, size_t count,
+                           cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int threads = 256;
+  size_t blocks = (count + threads - 1) / threads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (src_fp64 && dst_fp64)
+    convert_kernel<<<(unsigned)blocks, threads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), count);
+  else if (src_fp64)
+    convert_kernel<<<(unsigned)blocks, threads, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), count);
+  else if (dst_fp64)
+    convert_kernel<<<(unsigned)blocks, threads, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), count);
+  else
+    convert_kernel<<<(unsigned)blocks, threads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_scalars(DevScalars* sc, int reset, double t_final, cudaStream_t s) {
+  set_scalars_kernel<<<1, 1, 0, s>>>(sc, reset, t_final);
+  return cudaGetLastError();
+}
+
+}  // namespace hw

@@ -1,0 +1,130 @@
+// 1D reconstruction arithmetic of the hybrid HWENO scheme (Zhao & Qiu,
+// arXiv:2002.08816, Sec. 2.1), for one scalar field on the three cells
+// I_{i-1}, I_i, I_{i+1} (m, 0, p below).  The coefficients are the paper's
+// printed rationals:
+//   Step 1     q0, q1, q2 and beta_0..2 of the first-moment modification; the
+//              last square of beta_0 uses v-coefficients +6, -6 (the printed
+//              +1, -1 does not follow from Eq. (GHYZ));
+//   Step 2.1   p0, p1, p2 at x_{i+1/2} and beta_0..2; the values at x_{i-1/2}
+//              of p1 and p2 are their mirror images about x_i (p1 at
+//              x_{i-1/2}: u_m/6 + 5u_0/6 - 4v_0; p2: 5u_0/6 + u_p/6 - 8v_0);
+//   Step 2.2   p0 at x_{i-+1/2};   Step 2.3 p0 at x_{i-+sqrt5/10}.
+#pragma once
+
+namespace hw {
+
+// Nonlinear combination shared by Step 1 and Step 2.1:
+//   tau = ((|b0-b1| + |b0-b2|)/2)^2                          Eq. (tao5)
+//   wbar_n = gamma_n (1 + tau/(beta_n + eps)),  w_n = wbar_n / sum wbar
+//   out = w0 (v0/gamma0 - gamma1/gamma0 v1 - gamma2/gamma0 v2) + w1 v1 + w2 v2
+template <typename R>
+struct Weights3 {
+  R w0g, w1, w2, g1, g2;  // w0/gamma0, w1, w2, gamma1, gamma2
+  __device__ __forceinline__ Weights3(const R* gam, R eps, R b0, R b1, R b2) {
+    R s = R(0.5) * (fabs(b0 - b1) + fabs(b0 - b2));
+    R tau = s * s;
+    R a0 = gam[0] * (R(1) + tau / (b0 + eps));
+    R a1 = gam[1] * (R(1) + tau / (b1 + eps));
+    R a2 = gam[2] * (R(1) + tau / (b2 + eps));
+    R inv = R(1) / (a0 + a1 + a2);
+    w0g = a0 * inv / gam[0];
+    w1 = a1 * inv;
+    w2 = a2 * inv;
+    g1 = gam[1];
+    g2 = gam[2];
+  }
+  __device__ __forceinline__ R apply(R v0, R v1, R v2) const {
+    return w0g * (v0 - g1 * v1 - g2 * v2) + w1 * v1 + w2 * v2;
+  }
+};
+
+// Step 1: modified first moment of I_i from u_m, u_0, u_p, v_m, v_p.
+template <typename R>
+__device__ __forceinline__ R limit_first_moment(R um, R u0, R up, R vm, R vp, const R* gam,
+                                                R eps) {
+  const R q0 = R(5.0 / 76.0) * (up - um) - R(11.0 / 38.0) * (vm + vp);
+  const R q1 = R(1.0 / 12.0) * (u0 - um);
+  const R q2 = R(1.0 / 12.0) * (up - u0);
+  const R t1 = R(29.0 / 38.0) * (um - up) + R(60.0 / 19.0) * (vm + vp);
+  const R t2 = R(9.0 / 4.0) * (um + up) - R(9.0 / 2.0) * u0 + R(15.0 / 2.0) * (vm - vp);
+  const R t3 = (um - up) + R(12) * (vm + vp);
+  const R t4 = R(5.0 / 2.0) * (um + up) - R(5) * u0 + R(9) * (vm - vp);
+  const R t5 = (um - R(2) * u0 + up) + R(6) * (vm - vp);
+  const R b0 = t1 * t1 + t2 * t2 + R(3905.0 / 1444.0) * t3 * t3 + R(1.0 / 12.0) * t4 * t4 +
+               R(109341.0 / 448.0) * t5 * t5;
+  const R d1 = u0 - um, d2 = up - u0;
+  Weights3<R> w(gam, eps, b0, d1 * d1, d2 * d2);
+  return w.apply(q0, q1, q2);
+}
+
+// Step 2.2: linear p0 at x_{i-1/2} (left) and x_{i+1/2} (right).
+template <typename R>
+__device__ __forceinline__ void linear_faces(R um, R u0, R up, R vm, R v0, R vp, R& left,
+                                             R& right) {
+  left = R(8.0 / 27.0) * um + R(7.0 / 12.0) * u0 + R(13.0 / 108.0) * up + R(28.0 / 27.0) * vm -
+         R(241.0 / 54.0) * v0 - R(25.0 / 54.0) * vp;
+  right = R(13.0 / 108.0) * um + R(7.0 / 12.0) * u0 + R(8.0 / 27.0) * up + R(25.0 / 54.0) * vm +
+          R(241.0 / 54.0) * v0 - R(28.0 / 27.0) * vp;
+}
+
+// Step 2.3: linear p0 at x_{i-sqrt5/10} (gm) and x_{i+sqrt5/10} (gp).
+template <typename R>
+__device__ __forceinline__ void linear_interior(R um, R u0, R up, R vm, R v0, R vp, R& gm,
+                                                R& gp) {
+  constexpr double r5 = 2.2360679774997896964;
+  constexpr double a = 101.0 / 5400.0 * r5, b = 1.0 / 24.0;
+  constexpr double c = 3.0 / 20.0, d = 841.0 / 13500.0 * r5, e = 10289.0 / 6750.0 * r5;
+  gm = R(-(a + b)) * um + R(13.0 / 12.0) * u0 + R(a - b) * up - R(c + d) * vm - R(e) * v0 +
+       R(c - d) * vp;
+  gp = R(a - b) * um + R(13.0 / 12.0) * u0 - R(a + b) * up + R(d - c) * vm + R(e) * v0 +
+       R(c + d) * vp;
+}
+
+// Step 2.1: HWENO values at x_{i-1/2} (left) and x_{i+1/2} (right); one set of
+// nonlinear weights serves both points (same candidates, same beta on I_i).
+template <typename R>
+__device__ __forceinline__ void hweno_faces(R um, R u0, R up, R vm, R v0, R vp, const R* gam,
+                                            R eps, R& left, R& right) {
+  R p0l, p0r;
+  linear_faces(um, u0, up, vm, v0, vp, p0l, p0r);
+  const R p1r = R(1.0 / 6.0) * um + R(5.0 / 6.0) * u0 + R(8) * v0;
+  const R p1l = R(1.0 / 6.0) * um + R(5.0 / 6.0) * u0 - R(4) * v0;
+  const R p2r = R(5.0 / 6.0) * u0 + R(1.0 / 6.0) * up + R(4) * v0;
+  const R p2l = R(5.0 / 6.0) * u0 + R(1.0 / 6.0) * up - R(8) * v0;
+  const R dU = um - up, sV = vm + vp, cU = um - R(2) * u0 + up, dV = vm - vp;
+  const R s1 = R(19.0 / 108.0) * dU + R(31.0 / 54.0) * sV - R(241.0 / 27.0) * v0;
+  const R s2 = R(9.0 / 4.0) * cU + R(15.0 / 2.0) * dV;
+  const R s3 = R(70.0 / 9.0) * dU + R(200.0 / 9.0) * sV + R(1280.0 / 9.0) * v0;
+  const R s4 = R(5.0 / 2.0) * cU + R(9) * dV;
+  const R s5 = R(175.0 / 18.0) * dU + R(277.0 / 9.0) * sV + R(1546.0 / 9.0) * v0;
+  const R s6 = R(95.0 / 18.0) * dU + R(155.0 / 9.0) * sV + R(830.0 / 9.0) * v0;
+  const R s7 = R(5.0 / 8.0) * cU + R(15.0 / 4.0) * dV;
+  const R s8 = R(35.0 / 36.0) * dU + R(77.0 / 18.0) * sV + R(133.0 / 9.0) * v0;
+  const R b0 = s1 * s1 + s2 * s2 + s3 * s3 + R(1.0 / 12.0) * (s4 * s4 + s5 * s5) +
+               R(1.0 / 180.0) * s6 * s6 + R(109341.0 / 175.0) * s7 * s7 +
+               R(27553933.0 / 1764.0) * s8 * s8;
+  const R v2 = R(144) * v0 * v0;
+  const R e1 = um - u0 + R(12) * v0, e2 = u0 - up + R(12) * v0;
+  const R b1 = v2 + R(13.0 / 3.0) * e1 * e1;
+  const R b2 = v2 + R(13.0 / 3.0) * e2 * e2;
+  Weights3<R> w(gam, eps, b0, b1, b2);
+  left = w.apply(p0l, p1l, p2l);
+  right = w.apply(p0r, p1r, p2r);
+}
+
+// KXRCF indicator (reading of Sec. 2.1 Step 1 and Remark 1: Krivodonova et
+// al. with the degree-1 cell polynomial ubar + 12 vbar (x - x_i)/dx, h = dx/2,
+// the inflow face chosen by the sign of the velocity, normalised by
+// max(|ubar_i|, 1e-12)), evaluated in FP64 without contraction.
+__device__ __forceinline__ double kxrcf1d(double um, double u0, double up, double vm, double v0,
+                                          double vp, double vel, double h) {
+  double jump;
+  if (vel >= 0.0)
+    jump = __dsub_rn(__dsub_rn(u0, __dmul_rn(6.0, v0)), __dadd_rn(um, __dmul_rn(6.0, vm)));
+  else
+    jump = __dsub_rn(__dadd_rn(u0, __dmul_rn(6.0, v0)), __dsub_rn(up, __dmul_rn(6.0, vp)));
+  const double nrm = fmax(fabs(u0), 1e-12);
+  return fabs(jump) / __dmul_rn(h, nrm);
+}
+
+}  // namespace hw

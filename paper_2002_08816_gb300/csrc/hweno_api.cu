@@ -1,0 +1,361 @@
+// C ABI of the library (declared in include/hweno.h): validation, device
+// buffers owned by the handle, CUDA-graph-captured Runge-Kutta steps.
+//
+// One third-order TVD Runge-Kutta step (Eq. (RK)) is three stage launches
+// that rotate over the state buffers
+//   stage 1: U[0] -> U[1], writes the limited u^n to U0
+//   stage 2: U[1], U0 -> U[2]
+//   stage 3: U[2], U0 -> U[0]
+// and over three partial-maximum buffers P0 -> P1 -> P2 -> P0 that carry
+// alpha from each stage to the next.  dt, t and the status word live in
+// device memory, so a run of many steps needs no host synchronisation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "hweno.h"
+#include "hweno_internal.h"
+
+struct hweno_ctx {
+  hweno_config cfg;
+  cudaStream_t stream = nullptr;     // caller's stream (may be the legacy default)
+  cudaStream_t cap = nullptr;        // private stream used only to capture graphs
+  int C = 0, M = 0, n = 0, ntile = 0;
+  size_t elems = 0, esize = 0;
+  void* U[3] = {nullptr, nullptr, nullptr};
+  void* U0 = nullptr;
+  void* stage_buf = nullptr;         // conversion staging (other precision)
+  double* part[3] = {nullptr, nullptr, nullptr};
+  double* part_rhs = nullptr;
+  hw::DevScalars* sc = nullptr;
+  hw::DevScalars* sc_rhs = nullptr;
+  cudaGraphExec_t g_many = nullptr;  // kGraphSteps steps
+  cudaGraphExec_t g_one = nullptr;   // one step
+  bool has_state = false;
+  std::string err;
+};
+
+namespace {
+
+constexpr int kGraphSteps = 32;
+std::string g_create_error;
+
+hweno_status fail(hweno_ctx* h, hweno_status st, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+#define HW_CUDA(h, call)                                                            \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail((h), HWENO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+hw::Stage1DArgs base_args(const hweno_ctx* h) {
+  hw::Stage1DArgs a;
+  memset(&a, 0, sizeof(a));
+  const hweno_config& c = h->cfg;
+  a.n = h->n;
+  a.ntile = h->ntile;
+  a.bc = c.bc;
+  a.mode = c.troubled_mode;
+  a.system = c.system;
+  a.fp64 = c.precision == HWENO_FP64;
+  a.dx = (c.x1 - c.x0) / c.nx;
+  a.cfl = c.cfl;
+  a.eps = c.eps;
+  a.thr = c.kxrcf_threshold;
+  a.gas = c.gas_gamma;
+  for (int k = 0; k < 3; ++k) a.gam[k] = c.lin_w[k];
+  return a;
+}
+
+cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
+  hw::Stage1DArgs a = base_args(h);
+  a.sc = h->sc;
+  // stage 1
+  a.stage = 1;
+  a.w = h->U[0];
+  a.out = h->U[1];
+  a.lim_out = h->U0;
+  a.a_in = h->part[0];
+  a.a_out = h->part[1];
+  cudaError_t e = hw::launch_stage1d(a, s);
+  if (e != cudaSuccess) return e;
+  // stage 2
+  a.stage = 2;
+  a.w = h->U[1];
+  a.u0 = h->U0;
+  a.out = h->U[2];
+  a.lim_out = nullptr;
+  a.a_in = h->part[1];
+  a.a_out = h->part[2];
+  e = hw::launch_stage1d(a, s);
+  if (e != cudaSuccess) return e;
+  // stage 3
+  a.stage = 3;
+  a.w = h->U[2];
+  a.out = h->U[0];
+  a.a_in = h->part[2];
+  a.a_out = h->part[0];
+  return hw::launch_stage1d(a, s);
+}
+
+hweno_status build_graph(hweno_ctx* h, int steps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  HW_CUDA(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < steps && e == cudaSuccess; ++k) e = enqueue_step(h, h->cap);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(h, HWENO_ERR_CUDA, std::string("graph capture: ") +
+                                       cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, HWENO_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return HWENO_OK;
+}
+
+hweno_status validate(const hweno_config* c) {
+  if (!c) return fail(nullptr, HWENO_ERR_ARG, "cfg is NULL");
+  if (c->dim != 1) return fail(nullptr, HWENO_ERR_ARG, "dim must be 1 (2D is not built into this library yet)");
+  if (c->system != HWENO_BURGERS && c->system != HWENO_EULER)
+    return fail(nullptr, HWENO_ERR_ARG, "unknown system");
+  if (c->nx < 4) return fail(nullptr, HWENO_ERR_ARG, "nx must be >= 4");
+  if (c->nx > (1 << 28)) return fail(nullptr, HWENO_ERR_ARG, "nx too large");
+  if (!(c->x1 > c->x0)) return fail(nullptr, HWENO_ERR_ARG, "x1 must exceed x0");
+  if (c->bc != HWENO_BC_PERIODIC && c->bc != HWENO_BC_OUTFLOW)
+    return fail(nullptr, HWENO_ERR_ARG, "unknown boundary condition");
+  if (c->system == HWENO_EULER && !(c->gas_gamma > 1.0))
+    return fail(nullptr, HWENO_ERR_ARG, "gas_gamma must exceed 1");
+  const int ncand = c->dim == 1 ? 3 : 5;
+  double s = 0.0;
+  for (int k = 0; k < ncand; ++k) {
+    if (!(c->lin_w[k] > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "linear weights must be positive");
+    s += c->lin_w[k];
+  }
+  if (fabs(s - 1.0) > 1e-12) return fail(nullptr, HWENO_ERR_ARG, "linear weights must sum to one");
+  if (!(c->cfl > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "cfl must be positive");
+  if (!(c->eps > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "eps must be positive");
+  if (!(c->kxrcf_threshold >= 0.0)) return fail(nullptr, HWENO_ERR_ARG, "threshold must be >= 0");
+  if (c->troubled_mode < 0 || c->troubled_mode > 2) return fail(nullptr, HWENO_ERR_ARG, "unknown troubled_mode");
+  if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64)
+    return fail(nullptr, HWENO_ERR_ARG, "unknown precision");
+  return HWENO_OK;
+}
+
+hweno_status check_scalars(hweno_ctx* h, hw::DevScalars* dev, hw::DevScalars* host) {
+  HW_CUDA(h, cudaMemcpyAsync(host, dev, sizeof(*host), cudaMemcpyDeviceToHost, h->stream));
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (host->status & hw::ST_NONPHYSICAL)
+    return fail(h, HWENO_ERR_NONPHYSICAL, "non-physical state (rho <= 0 or p <= 0)");
+  if (host->status & hw::ST_NONFINITE) return fail(h, HWENO_ERR_NONPHYSICAL, "non-finite value");
+  if (host->status & hw::ST_TIMEOUT) return fail(h, HWENO_ERR_TIMEOUT, "device wait timed out");
+  return HWENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hweno_default_config(hweno_config* cfg, int dim, int system) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->dim = dim;
+  cfg->system = system;
+  cfg->x0 = 0.0;
+  cfg->x1 = 1.0;
+  cfg->y0 = 0.0;
+  cfg->y1 = 1.0;
+  cfg->bc = HWENO_BC_PERIODIC;
+  cfg->gas_gamma = 1.4;
+  if (dim == 2) {
+    cfg->lin_w[0] = 0.96;
+    for (int k = 1; k < 5; ++k) cfg->lin_w[k] = 0.01;
+  } else {
+    cfg->lin_w[0] = 0.98;
+    cfg->lin_w[1] = 0.01;
+    cfg->lin_w[2] = 0.01;
+  }
+  cfg->cfl = 0.6;
+  cfg->eps = 1e-6;
+  cfg->kxrcf_threshold = 1.0;
+  cfg->troubled_mode = HWENO_TROUBLED_HYBRID;
+  cfg->n_gauss = 3;
+  cfg->precision = HWENO_FP32;
+}
+
+hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_handle* out) {
+  if (!out) return fail(nullptr, HWENO_ERR_ARG, "out is NULL");
+  hweno_status st = validate(cfg);
+  if (st != HWENO_OK) return st;
+  hweno_ctx* h = new hweno_ctx();
+  h->cfg = *cfg;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->C = cfg->system == HWENO_EULER ? 3 : 1;
+  h->M = 2;
+  h->n = cfg->nx;
+  h->ntile = (h->n + hw::kTile1D - 1) / hw::kTile1D;
+  h->elems = (size_t)h->C * h->M * h->n;
+  h->esize = cfg->precision == HWENO_FP64 ? 8 : 4;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->U[k], h->elems * h->esize);
+  if (e == cudaSuccess) e = cudaMalloc(&h->U0, h->elems * h->esize);
+  if (e == cudaSuccess) e = cudaMalloc(&h->stage_buf, h->elems * 8);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * h->ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&h->part_rhs, sizeof(double) * h->ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&h->sc, sizeof(hw::DevScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&h->sc_rhs, sizeof(hw::DevScalars));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = hw::launch_set_scalars(h->sc, 1, -1.0, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("allocation: ") + cudaGetErrorString(e);
+    hweno_destroy(h);
+    return fail(nullptr, HWENO_ERR_CUDA, msg);
+  }
+  *out = h;
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int on_device) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (!moments) return fail(h, HWENO_ERR_ARG, "moments is NULL");
+  if (dtype != HWENO_FP32 && dtype != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "unknown dtype");
+  const int src64 = dtype == HWENO_FP64, dst64 = h->cfg.precision == HWENO_FP64;
+  const size_t sbytes = h->elems * (src64 ? 8 : 4);
+  const void* src = moments;
+  if (!on_device) {
+    if (src64 == dst64) {
+      HW_CUDA(h, cudaMemcpyAsync(h->U[0], moments, sbytes, cudaMemcpyHostToDevice, h->stream));
+      src = nullptr;
+    } else {
+      HW_CUDA(h, cudaMemcpyAsync(h->stage_buf, moments, sbytes, cudaMemcpyHostToDevice, h->stream));
+      src = h->stage_buf;
+    }
+  }
+  if (src) HW_CUDA(h, hw::launch_convert(src, src64, h->U[0], dst64, h->elems, h->stream));
+  HW_CUDA(h, hw::launch_set_scalars(h->sc, 1, -1.0, h->stream));
+  HW_CUDA(h, hw::launch_alpha1d(h->U[0], h->part[0], h->n, h->ntile, h->cfg.system, dst64,
+                                h->cfg.gas_gamma, h->sc, h->stream));
+  h->has_state = true;
+  return HWENO_OK;
+}
+
+hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_out) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_step before hweno_set_state");
+  if (nsteps < 0) return fail(h, HWENO_ERR_ARG, "nsteps must be >= 0");
+  HW_CUDA(h, hw::launch_set_scalars(h->sc, 0, t_final, h->stream));
+  int left = nsteps;
+  if (left >= kGraphSteps) {
+    if (!h->g_many) {
+      hweno_status st = build_graph(h, kGraphSteps, &h->g_many);
+      if (st != HWENO_OK) return st;
+    }
+    for (; left >= kGraphSteps; left -= kGraphSteps) HW_CUDA(h, cudaGraphLaunch(h->g_many, h->stream));
+  }
+  if (left > 0) {
+    if (!h->g_one) {
+      hweno_status st = build_graph(h, 1, &h->g_one);
+      if (st != HWENO_OK) return st;
+    }
+    for (; left > 0; --left) HW_CUDA(h, cudaGraphLaunch(h->g_one, h->stream));
+  }
+  if (t_out) {
+    hw::DevScalars s;
+    hweno_status st = check_scalars(h, h->sc, &s);
+    *t_out = s.t;
+    return st;
+  }
+  return HWENO_OK;
+}
+
+hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags_out, void* ulim_out) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (!in || !out) return fail(h, HWENO_ERR_ARG, "in and out must be device pointers");
+  if (in == out || (ulim_out && (ulim_out == in || ulim_out == out)))
+    return fail(h, HWENO_ERR_ARG, "in, out and ulim_out must not overlap");
+  HW_CUDA(h, hw::launch_set_scalars(h->sc_rhs, 1, -1.0, h->stream));
+  HW_CUDA(h, hw::launch_alpha1d(in, h->part_rhs, h->n, h->ntile, h->cfg.system,
+                                h->cfg.precision == HWENO_FP64, h->cfg.gas_gamma, h->sc_rhs,
+                                h->stream));
+  hw::Stage1DArgs a = base_args(h);
+  a.stage = 0;
+  a.w = in;
+  a.out = out;
+  a.lim_out = ulim_out;
+  a.a_in = h->part_rhs;
+  a.a_out = nullptr;
+  a.sc = h->sc_rhs;
+  a.flags_out = flags_out;
+  HW_CUDA(h, hw::launch_stage1d(a, h->stream));
+  hw::DevScalars s;
+  return check_scalars(h, h->sc_rhs, &s);
+}
+
+hweno_status hweno_get_state(hweno_handle h, void* out, int dtype, int on_device) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (!out) return fail(h, HWENO_ERR_ARG, "out is NULL");
+  if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_get_state before hweno_set_state");
+  if (dtype != HWENO_FP32 && dtype != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "unknown dtype");
+  const int dst64 = dtype == HWENO_FP64, src64 = h->cfg.precision == HWENO_FP64;
+  const size_t dbytes = h->elems * (dst64 ? 8 : 4);
+  if (on_device) {
+    HW_CUDA(h, hw::launch_convert(h->U[0], src64, out, dst64, h->elems, h->stream));
+    return HWENO_OK;
+  }
+  const void* src = h->U[0];
+  if (src64 != dst64) {
+    HW_CUDA(h, hw::launch_convert(h->U[0], src64, h->stage_buf, dst64, h->elems, h->stream));
+    src = h->stage_buf;
+  }
+  HW_CUDA(h, cudaMemcpyAsync(out, src, dbytes, cudaMemcpyDeviceToHost, h->stream));
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* steps,
+                         int64_t* troubled_cell_stages) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  hw::DevScalars s;
+  HW_CUDA(h, cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (t) *t = s.t;
+  if (last_dt) *last_dt = s.dt;
+  if (steps) *steps = (int64_t)s.steps;
+  if (troubled_cell_stages) *troubled_cell_stages = (int64_t)s.troubled;
+  return HWENO_OK;
+}
+
+void hweno_destroy(hweno_handle h) {
+  if (!h) return;
+  if (h->g_many) cudaGraphExecDestroy(h->g_many);
+  if (h->g_one) cudaGraphExecDestroy(h->g_one);
+  for (int k = 0; k < 3; ++k) {
+    if (h->U[k]) cudaFree(h->U[k]);
+    if (h->part[k]) cudaFree(h->part[k]);
+  }
+  if (h->U0) cudaFree(h->U0);
+  if (h->stage_buf) cudaFree(h->stage_buf);
+  if (h->part_rhs) cudaFree(h->part_rhs);
+  if (h->sc) cudaFree(h->sc);
+  if (h->sc_rhs) cudaFree(h->sc_rhs);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+const char* hweno_last_error(hweno_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Device helpers shared by the 1D and 2D kernels: ghost-cell index maps,
+// block reductions, status bits and the Euler physics (Eq. (euler1),
+// Eq. (euler2)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hw {
+
+// bits of the device status word
+enum : unsigned { ST_NONFINITE = 1u, ST_NONPHYSICAL = 2u, ST_TIMEOUT = 4u };
+
+// Scalars of one time integration, resident in device memory.
+struct DevScalars {
+  double t;          // time reached
+  double dt;         // dt of the step in flight (written by stage 1)
+  double t_final;    // clip time (<= 0: none)
+  unsigned status;   // ST_* bits
+  unsigned pad;
+  unsigned long long steps;     // completed steps
+  unsigned long long troubled;  // troubled cell-stages
+};
+
+// Ghost cells: periodic wraps, outflow copies the boundary cell.  Any g
+// (a tile's halo may span several periods when n is smaller than a tile).
+__device__ __forceinline__ int bc_map(int g, int n, int bc) {
+  if (bc == 0) {
+    if (g >= 0 && g < n) return g;
+    int r = g % n;
+    return r < 0 ? r + n : r;
+  }
+  return g < 0 ? 0 : (g >= n ? n - 1 : g);
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < NT / 32) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (threadIdx.x == 0) red[0] = v;
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ bool finite(R x) {
+  return isfinite(x);
+}
+
+// ---------------------------------------------------------------- physics
+
+template <typename R>
+struct Euler1D {
+  // flux of (rho, m, E)
+  static __device__ __forceinline__ void flux(R g, const R* U, R* F) {
+    const R rho = U[0], m = U[1], E = U[2];
+    const R mu = m / rho;
+    const R p = (g - R(1)) * (E - R(0.5) * m * mu);
+    F[0] = m;
+    F[1] = m * mu + p;
+    F[2] = mu * (E + p);
+  }
+  // Right (columns: mu-c, mu, mu+c) and left eigenvectors of dF/dU at U.
+  static __device__ __forceinline__ void eigen(R g, const R* U, R Rm[3][3], R Lm[3][3]) {
+    const R rho = U[0], mu = U[1] / U[0];
+    const R p = (g - R(1)) * (U[2] - R(0.5) * rho * mu * mu);
+    const R c = sqrt(g * p / rho);
+    const R H = (U[2] + p) / rho;
+    const R ic = R(1) / c;
+    const R b1 = (g - R(1)) * ic * ic;
+    const R b2 = R(0.5) * b1 * mu * mu;
+    Rm[0][0] = R(1);        Rm[0][1] = R(1);              Rm[0][2] = R(1);
+    Rm[1][0] = mu - c;      Rm[1][1] = mu;                Rm[1][2] = mu + c;
+    Rm[2][0] = H - mu * c;  Rm[2][1] = R(0.5) * mu * mu;  Rm[2][2] = H + mu * c;
+    Lm[0][0] = R(0.5) * (b2 + mu * ic);
+    Lm[0][1] = R(-0.5) * (b1 * mu + ic);
+    Lm[0][2] = R(0.5) * b1;
+    Lm[1][0] = R(1) - b2;
+    Lm[1][1] = b1 * mu;
+    Lm[1][2] = -b1;
+    Lm[2][0] = R(0.5) * (b2 - mu * ic);
+    Lm[2][1] = R(-0.5) * (b1 * mu - ic);
+    Lm[2][2] = R(0.5) * b1;
+  }
+};
+
+// |mu| + c from cell averages, in FP64; NaN marks a non-physical state.
+__device__ __forceinline__ double euler1d_speed(double g, double rho, double m, double E) {
+  if (!(rho > 0.0)) return __longlong_as_double(0x7ff8000000000000ll);
+  const double mu = m / rho;
+  const double p = (g - 1.0) * (E - 0.5 * m * mu);
+  if (!(p > 0.0)) return __longlong_as_double(0x7ff8000000000000ll);
+  return fabs(mu) + sqrt(g * p / rho);
+}
+
+}  // namespace hw

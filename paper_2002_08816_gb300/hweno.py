@@ -1,0 +1,147 @@
+"""Thin ctypes binding of libhweno.so (include/hweno.h), same names as the C ABI.
+
+Argument marshalling only: every step of the scheme runs in the library's
+CUDA kernels.  Device buffers are passed as integers (e.g. a torch tensor's
+``data_ptr()``), streams as integers (``torch.cuda.current_stream().cuda_stream``).
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhweno.so")
+
+HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL, HWENO_ERR_TIMEOUT, \
+    HWENO_ERR_STATE = range(6)
+HWENO_BURGERS, HWENO_EULER = 0, 1
+HWENO_BC_PERIODIC, HWENO_BC_OUTFLOW = 0, 1
+HWENO_TROUBLED_HYBRID, HWENO_TROUBLED_ALL, HWENO_TROUBLED_NONE = 0, 1, 2
+HWENO_FP32, HWENO_FP64 = 0, 1
+
+_D, _I, _VP = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+
+EXPORTED = ["hweno_default_config", "hweno_create", "hweno_set_state", "hweno_step",
+            "hweno_rhs", "hweno_get_state", "hweno_stats", "hweno_destroy",
+            "hweno_last_error"]
+
+
+class hweno_config(ctypes.Structure):
+    _fields_ = [
+        ("dim", _I), ("system", _I), ("nx", _I), ("ny", _I),
+        ("x0", _D), ("x1", _D), ("y0", _D), ("y1", _D),
+        ("bc", _I), ("gas_gamma", _D), ("lin_w", _D * 5), ("cfl", _D), ("eps", _D),
+        ("kxrcf_threshold", _D), ("troubled_mode", _I), ("n_gauss", _I), ("precision", _I),
+    ]
+
+
+class HwenoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("hweno status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libhweno.so is not built (run __graft_entry__.build()); "
+                              "this package has no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(hweno_config)
+        L.hweno_default_config.restype = None
+        L.hweno_default_config.argtypes = [P, _I, _I]
+        L.hweno_create.restype = _I
+        L.hweno_create.argtypes = [P, _VP, ctypes.POINTER(_VP)]
+        L.hweno_set_state.restype = _I
+        L.hweno_set_state.argtypes = [_VP, _VP, _I, _I]
+        L.hweno_step.restype = _I
+        L.hweno_step.argtypes = [_VP, _I, _D, ctypes.POINTER(_D)]
+        L.hweno_rhs.restype = _I
+        L.hweno_rhs.argtypes = [_VP, _VP, _VP, _VP, _VP]
+        L.hweno_get_state.restype = _I
+        L.hweno_get_state.argtypes = [_VP, _VP, _I, _I]
+        L.hweno_stats.restype = _I
+        L.hweno_stats.argtypes = [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.hweno_destroy.restype = None
+        L.hweno_destroy.argtypes = [_VP]
+        L.hweno_last_error.restype = ctypes.c_char_p
+        L.hweno_last_error.argtypes = [_VP]
+        _lib = L
+    return _lib
+
+
+def _check(st, h=None):
+    if st != HWENO_OK:
+        raise HwenoError(st, lib().hweno_last_error(h).decode())
+
+
+def hweno_default_config(dim, system):
+    cfg = hweno_config()
+    lib().hweno_default_config(ctypes.byref(cfg), dim, system)
+    return cfg
+
+
+def hweno_create(cfg, stream=0):
+    h = _VP()
+    _check(lib().hweno_create(ctypes.byref(cfg), _VP(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def hweno_set_state(h, ptr, dtype, on_device):
+    _check(lib().hweno_set_state(h, _VP(ptr), dtype, int(on_device)), h)
+
+
+def hweno_step(h, nsteps, t_final=-1.0, wait=True):
+    """Returns the time reached when wait, else None (asynchronous)."""
+    if wait:
+        t = _D()
+        _check(lib().hweno_step(h, int(nsteps), float(t_final), ctypes.byref(t)), h)
+        return t.value
+    _check(lib().hweno_step(h, int(nsteps), float(t_final), None), h)
+    return None
+
+
+def hweno_rhs(h, in_ptr, out_ptr, flags_ptr=0, ulim_ptr=0):
+    _check(lib().hweno_rhs(h, _VP(in_ptr), _VP(out_ptr), _VP(flags_ptr or None),
+                           _VP(ulim_ptr or None)), h)
+
+
+def hweno_get_state(h, ptr, dtype, on_device):
+    _check(lib().hweno_get_state(h, _VP(ptr), dtype, int(on_device)), h)
+
+
+def hweno_stats(h):
+    t, dt = _D(), _D()
+    steps, tr = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().hweno_stats(h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(steps),
+                             ctypes.byref(tr)), h)
+    return {"t": t.value, "dt": dt.value, "steps": steps.value, "troubled": tr.value}
+
+
+def hweno_destroy(h):
+    if h:
+        lib().hweno_destroy(h)
+
+
+def hweno_last_error(h=None):
+    return lib().hweno_last_error(h).decode()
+
+
+def make_config(dim, system, nx, ny=0, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=HWENO_BC_PERIODIC,
+                lin_w=None, cfl=0.6, precision=HWENO_FP32, troubled_mode=HWENO_TROUBLED_HYBRID,
+                gas_gamma=1.4, eps=1e-6, threshold=1.0, n_gauss=3):
+    cfg = hweno_default_config(dim, system)
+    cfg.nx, cfg.ny = nx, ny
+    cfg.x0, cfg.x1, cfg.y0, cfg.y1 = x0, x1, y0, y1
+    cfg.bc, cfg.cfl, cfg.precision, cfg.troubled_mode = bc, cfl, precision, troubled_mode
+    cfg.gas_gamma, cfg.eps, cfg.kxrcf_threshold, cfg.n_gauss = gas_gamma, eps, threshold, n_gauss
+    if lin_w is not None:
+        for k, v in enumerate(lin_w):
+            cfg.lin_w[k] = v
+    return cfg
