@@ -1,0 +1,54 @@
+"""Short run of the 1D stage kernels for profilers (ncu).
+
+  python -m paper_2002_08816_gb300.profile_stage [--nx 65536] [--rk-steps 10]
+                                                  [--precision fp32|fp64] [--system euler|burgers]
+
+Sets the seeded two-state 1D Euler state (or the Burgers sine wave), runs the
+requested number of Runge-Kutta steps through the C ABI (3 stage launches per
+step after one alpha launch) and checks the status word.
+"""
+
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    import torch
+
+    from paper_2002_08816_gb300 import build as B
+    from paper_2002_08816_gb300 import hweno as H
+    from paper_2002_08816_gb300 import workloads as W
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=65536)
+    ap.add_argument("--rk-steps", type=int, default=10)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--system", default="euler", choices=["euler", "burgers"])
+    ap.add_argument("--seed", type=int, default=20250)
+    args = ap.parse_args()
+    B.build()
+    prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
+    if args.system == "euler":
+        u = W.euler_two_state_1d(args.nx, args.seed)
+        cfg = H.make_config(1, H.HWENO_EULER, args.nx, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
+                            precision=prec)
+    else:
+        u = W.burgers_sine_1d(args.nx)
+        cfg = H.make_config(1, H.HWENO_BURGERS, args.nx, x0=-1.0, x1=1.0, cfl=0.5, precision=prec)
+    dt = torch.float32 if prec == H.HWENO_FP32 else torch.float64
+    dev = torch.from_numpy(u).to("cuda", dt).contiguous()
+    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        H.hweno_set_state(h, dev.data_ptr(), prec, True)
+        t = H.hweno_step(h, args.rk_steps)
+        st = H.hweno_stats(h)
+    finally:
+        H.hweno_destroy(h)
+    print("t=%.6g steps=%d troubled cell-stages=%d" % (t, st["steps"], st["troubled"]))
+
+
+if __name__ == "__main__":
+    main()
