@@ -43,7 +43,8 @@ typedef enum {
   HWENO_ERR_CUDA = 2,          /* a CUDA runtime call failed */
   HWENO_ERR_NONPHYSICAL = 3,   /* non-finite value, rho <= 0 or p <= 0 seen */
   HWENO_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
-  HWENO_ERR_STATE = 5          /* call out of order (e.g. step before set_state) */
+  HWENO_ERR_STATE = 5,         /* call out of order (e.g. step before set_state) */
+  HWENO_ERR_TOO_LARGE = 6      /* more cells than hweno_rhs1d_noalloc's fixed scratch holds */
 } hweno_status;
 
 enum { HWENO_BURGERS = 0, HWENO_EULER = 1 };
@@ -118,6 +119,35 @@ hweno_status hweno_get_state(hweno_handle h, void* out, int dtype, int on_device
  * completed steps and of troubled cell-stages.  Waits for the stream. */
 hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* steps,
                          int64_t* troubled_cell_stages);
+
+/* Largest nx that hweno_rhs1d_noalloc accepts: its scratch is a fixed array
+ * of one double per 256-cell tile (128 KiB) plus a 64-byte status block. */
+#define HWENO_NOALLOC_MAX_CELLS 4194304
+
+/* hweno_rhs for 1D without any device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot let a library call
+ * cudaMalloc: a framework whose device memory is owned by its own pool
+ * allocator (an allocation behind the pool's back is not accounted and can
+ * fail when the pool has reserved the memory), a process whose device memory
+ * is budgeted allocation by allocation, or a latency-bound loop that cannot
+ * afford the device synchronisation an allocation or a free may cause.
+ * It needs no handle: cfg (dim must be 1) is validated as hweno_create would
+ * and cuda_stream is the stream to run on (NULL: legacy default stream).
+ * in, out, flags_out and ulim_out mean exactly what they mean for hweno_rhs
+ * (caller-owned device buffers in cfg->precision; flags_out and ulim_out
+ * nullable; no overlap), and the result is the same L(in).
+ * Scratch: a file-scope __device__ array inside the library, which every GPU
+ * that loads the library holds until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the one array and each call resets the part
+ * that must start at zero, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Returns HWENO_ERR_TOO_LARGE when cfg->nx > HWENO_NOALLOC_MAX_CELLS,
+ * HWENO_ERR_ARG for any other invalid argument, HWENO_ERR_NONPHYSICAL for a
+ * non-finite or non-physical result; waits for the stream before returning. */
+hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, const void* in,
+                                 void* out, uint8_t* flags_out, void* ulim_out);
 
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);

@@ -1,0 +1,155 @@
+// hweno_rhs1d_noalloc: a 1D right-hand-side evaluation that allocates no
+// device memory.
+//
+// hweno_rhs needs scratch memory beside its inputs and outputs (the per-tile
+// partial maxima of the wave speed that give the Lax-Friedrichs alpha, and a
+// status word), which hweno_create obtains with cudaMalloc.  Some callers
+// cannot let a library call cudaMalloc: a framework that has handed the
+// device memory to its own pool allocator (a library allocation bypasses the
+// pool's accounting and can fail once the pool has reserved the memory), a
+// process whose device memory is budgeted allocation by allocation, or a
+// latency-bound loop that cannot afford the device synchronisation
+// cudaMalloc and cudaFree may imply.  For them this entry point keeps its
+// scratch in a fixed file-scope __device__ array instead.
+//
+// The array holds one partial maximum per 256-cell tile plus the status word,
+// so one call handles at most HWENO_NOALLOC_MAX_CELLS cells.  Every GPU that
+// loads the library holds the array (128 KiB + 64 B) until the process exits.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "hweno.h"
+#include "hweno_internal.h"
+
+namespace {
+
+constexpr int kNoallocMaxTiles = HWENO_NOALLOC_MAX_CELLS / hw::kTile1D;
+static_assert(HWENO_NOALLOC_MAX_CELLS % hw::kTile1D == 0, "whole tiles");
+// layout of the scratch, in doubles: [0, 8) the status word and counters of
+// one call (hw::DevScalars), [8, 8 + kNoallocMaxTiles) the per-tile maxima
+// of |f'(ubar)| that give alpha
+constexpr int kScalarSlots = 8;
+static_assert(sizeof(hw::DevScalars) <= kScalarSlots * sizeof(double), "scalars fit");
+constexpr int kNoallocScratchDoubles = kScalarSlots + kNoallocMaxTiles;
+
+}  // namespace
+
+// The scratch of every call, on every device that loads the library
+// (kNoallocScratchDoubles doubles = 128 KiB + 64 B).  In host code this name
+// is only a host-side stand-in: the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current) and cached.
+hweno_status scratch_on_current_device(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return HWENO_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return HWENO_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return HWENO_ERR_CUDA;
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return HWENO_OK;
+}
+
+hweno_status check_config(const hweno_config* c) {
+  if (!c) return HWENO_ERR_ARG;
+  if (c->dim != 1) return HWENO_ERR_ARG;
+  if (c->system != HWENO_BURGERS && c->system != HWENO_EULER)
+    return HWENO_ERR_ARG;
+  if (c->nx < 4) return HWENO_ERR_ARG;
+  if (c->nx > HWENO_NOALLOC_MAX_CELLS) return HWENO_ERR_TOO_LARGE;
+  if (!(c->x1 > c->x0)) return HWENO_ERR_ARG;
+  if (c->bc != HWENO_BC_PERIODIC && c->bc != HWENO_BC_OUTFLOW)
+    return HWENO_ERR_ARG;
+  if (c->system == HWENO_EULER && !(c->gas_gamma > 1.0))
+    return HWENO_ERR_ARG;
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    if (!(c->lin_w[k] > 0.0)) return HWENO_ERR_ARG;
+    s += c->lin_w[k];
+  }
+  if (fabs(s - 1.0) > 1e-12) return HWENO_ERR_ARG;
+  if (!(c->eps > 0.0)) return HWENO_ERR_ARG;
+  if (!(c->kxrcf_threshold >= 0.0)) return HWENO_ERR_ARG;
+  if (c->troubled_mode < 0 || c->troubled_mode > 2) return HWENO_ERR_ARG;
+  if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64)
+    return HWENO_ERR_ARG;
+  return HWENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, const void* in,
+                                 void* out, uint8_t* flags_out, void* ulim_out) {
+  hweno_status st = check_config(cfg);
+  if (st != HWENO_OK) return st;
+  if (!in || !out) return HWENO_ERR_ARG;
+  if (in == out || (ulim_out && (ulim_out == in || ulim_out == out)))
+    return HWENO_ERR_ARG;
+  double* scr = nullptr;
+  st = scratch_on_current_device(&scr);
+  if (st != HWENO_OK) return st;
+  hw::DevScalars* sc = reinterpret_cast<hw::DevScalars*>(scr);
+  double* partial = scr + kScalarSlots;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int n = cfg->nx;
+  const int ntile = (n + hw::kTile1D - 1) / hw::kTile1D;
+  const int fp64 = cfg->precision == HWENO_FP64;
+  // the previous call's status bits and counters must not leak into this one
+  cudaError_t e = hw::launch_set_scalars(sc, 1, -1.0, s);
+  if (e == cudaSuccess)
+    e = hw::launch_alpha1d(in, partial, n, ntile, cfg->system, fp64, cfg->gas_gamma, sc, s);
+  if (e == cudaSuccess) {
+    hw::Stage1DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.w = in;
+    a.out = out;
+    a.lim_out = ulim_out;
+    a.a_in = partial;
+    a.a_out = nullptr;
+    a.sc = sc;
+    a.flags_out = flags_out;
+    a.n = n;
+    a.ntile = ntile;
+    a.stage = 0;
+    a.bc = cfg->bc;
+    a.mode = cfg->troubled_mode;
+    a.system = cfg->system;
+    a.fp64 = fp64;
+    a.dx = (cfg->x1 - cfg->x0) / n;
+    a.cfl = cfg->cfl;
+    a.eps = cfg->eps;
+    a.thr = cfg->kxrcf_threshold;
+    a.gas = cfg->gas_gamma;
+    for (int k = 0; k < 3; ++k) a.gam[k] = cfg->lin_w[k];
+    e = hw::launch_stage1d(a, s);
+  }
+  unsigned status = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&status, &sc->status, sizeof(status), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return HWENO_ERR_CUDA;
+  if (status & hw::ST_NONPHYSICAL) return HWENO_ERR_NONPHYSICAL;
+  if (status & hw::ST_NONFINITE) return HWENO_ERR_NONPHYSICAL;
+  return HWENO_OK;
+}
+
+}  // extern "C"

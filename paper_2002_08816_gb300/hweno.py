@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhweno.so")
 
 HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL, HWENO_ERR_TIMEOUT, \
-    HWENO_ERR_STATE = range(6)
+    HWENO_ERR_STATE, HWENO_ERR_TOO_LARGE = range(7)
+HWENO_NOALLOC_MAX_CELLS = 4194304
 HWENO_BURGERS, HWENO_EULER = 0, 1
 HWENO_BC_PERIODIC, HWENO_BC_OUTFLOW = 0, 1
 HWENO_TROUBLED_HYBRID, HWENO_TROUBLED_ALL, HWENO_TROUBLED_NONE = 0, 1, 2
@@ -24,7 +25,7 @@ _D, _I, _VP = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
 
 EXPORTED = ["hweno_default_config", "hweno_create", "hweno_set_state", "hweno_step",
             "hweno_rhs", "hweno_get_state", "hweno_stats", "hweno_destroy",
-            "hweno_last_error"]
+            "hweno_last_error", "hweno_rhs1d_noalloc"]
 
 
 class hweno_config(ctypes.Structure):
@@ -72,6 +73,8 @@ def lib():
         L.hweno_destroy.argtypes = [_VP]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_last_error.argtypes = [_VP]
+        L.hweno_rhs1d_noalloc.restype = _I
+        L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
         _lib = L
     return _lib
 
@@ -110,6 +113,13 @@ def hweno_step(h, nsteps, t_final=-1.0, wait=True):
 def hweno_rhs(h, in_ptr, out_ptr, flags_ptr=0, ulim_ptr=0):
     _check(lib().hweno_rhs(h, _VP(in_ptr), _VP(out_ptr), _VP(flags_ptr or None),
                            _VP(ulim_ptr or None)), h)
+
+
+def hweno_rhs1d_noalloc(cfg, stream, in_ptr, out_ptr, flags_ptr=0, ulim_ptr=0):
+    """Allocation-free 1D right-hand side; returns the raw status code (no
+    handle, so no error text)."""
+    return lib().hweno_rhs1d_noalloc(ctypes.byref(cfg), _VP(stream or None), _VP(in_ptr),
+                                     _VP(out_ptr), _VP(flags_ptr or None), _VP(ulim_ptr or None))
 
 
 def hweno_get_state(h, ptr, dtype, on_device):
