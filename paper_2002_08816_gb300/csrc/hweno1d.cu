@@ -7,15 +7,17 @@
 //   1. alpha = max |f'(ubar)| from the per-tile partial maxima the producer
 //      of the stage input wrote (global Lax-Friedrichs flux); stage 1 also
 //      turns alpha into dt = CFL dx / alpha, clipped to t_final;
-//   2. KXRCF flags (FP64) and the modified first moments (Step 1) for the
-//      cells and 2 halo cells per side, in characteristic fields for Euler;
+//   2. KXRCF flags and the modified first moments (Step 1) for the cells and
+//      2 halo cells per side, in characteristic fields for Euler; an FP32
+//      kernel decides a flag in FP32 when its rounding-error bound allows and
+//      in FP64 otherwise, so flags equal the FP64 decision off the threshold;
 //   3. interface values (Steps 2.1/2.2) for the cells and 1 halo cell per
 //      side: linear p0 unless a cell of S0 = {i-1, i, i+1} is troubled;
 //   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
 //      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
 //      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
-//   5. an FP64 partial maximum of the wave speed of the output for the next
-//      stage's alpha, and the status bits (non-finite, non-physical).
+//   5. a partial maximum (reduced in FP64) of the output's wave speed for the
+//      next stage's alpha, and the status bits (non-finite, non-physical).
 // The limited stage input is what the RK combination uses (the first moment
 // of a troubled cell is modified in the state, as a DG limiter would).
 #include <cuda_runtime.h>
@@ -50,12 +52,14 @@ __device__ __forceinline__ void phys_flux(R gas, const R* U, R* F) {
   }
 }
 
-template <int C>
-__device__ __forceinline__ double wave_speed(double gas, const double* U) {
+// max |f'(u)| at a cell average, in the kernel's precision (NaN when the
+// state is not physical); the maxima are reduced in FP64.
+template <typename R, int C>
+__device__ __forceinline__ R wave_speed(R gas, const R* U) {
   if constexpr (C == 1) {
     return fabs(U[0]);
   } else {
-    return euler1d_speed(gas, U[0], U[1], U[2]);
+    return euler1d_speed_r<R>(gas, U[0], U[1], U[2]);
   }
 }
 
@@ -108,6 +112,8 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
   const R gas = R(a.gas);
 
   // 3. troubled cells and modified first moments (Step 1)
+  const double h = 0.5 * a.dx;
+  const float hthr = (float)(a.thr * h);
   for (int k = tid; k < T + 4; k += T) {
     const int e = k + 1;
     int flag;
@@ -116,21 +122,19 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
     } else if (a.mode == 2) {
       flag = 0;
     } else {
-      const double h = 0.5 * a.dx;
-      double ind;
       if constexpr (C == 1) {
-        const double u0 = sm.u[0][0][e];
-        ind = kxrcf1d(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
-                      sm.u[0][1][e], sm.u[0][1][e + 1], u0, h);
+        const R u0 = sm.u[0][0][e];
+        flag = kxrcf_troubled(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
+                              sm.u[0][1][e], sm.u[0][1][e + 1], u0 >= R(0), h, a.thr, hthr);
       } else {
-        const double vel = (double)sm.u[1][0][e] / (double)sm.u[0][0][e];
-        const double ir = kxrcf1d(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
-                                  sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], vel, h);
-        const double ie = kxrcf1d(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
-                                  sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], vel, h);
-        ind = fmax(ir, ie);
+        const bool left = inflow_left(sm.u[0][0][e], sm.u[1][0][e]);
+        flag = kxrcf_troubled(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
+                              sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left, h,
+                              a.thr, hthr) ||
+               kxrcf_troubled(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
+                              sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], left, h,
+                              a.thr, hthr);
       }
-      flag = ind > a.thr;
     }
     sm.fl[k] = (uint8_t)flag;
     if (!flag) {
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
     phys_flux<R, C>(gas, gp, f3);
     phys_flux<R, C>(gas, tr4, f4);
     const R idx = R(1.0 / a.dx);
-    double Uo[C];
+    R Uo[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const R F = R(1.0 / 12.0) * (f1[c] + f4[c]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
@@ -286,11 +290,11 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
         lo[(2 * c + 1) * n + i] = wv;
       }
       if (!isfinite(ou) || !isfinite(ov)) bad |= ST_NONFINITE;
-      Uo[c] = (double)ou;
+      Uo[c] = ou;
     }
     if (a.flags_out) a.flags_out[i] = (uint8_t)myflag;
     if (a.stage > 0) {
-      speed = wave_speed<C>(a.gas, Uo);
+      speed = (double)wave_speed<R, C>(gas, Uo);
       if (!(speed == speed)) {
         bad |= ST_NONPHYSICAL;
         speed = 0.0;
@@ -318,10 +322,10 @@ __global__ void __launch_bounds__(T) alpha1d_kernel(const R* __restrict__ w, dou
   const int i = blockIdx.x * T + threadIdx.x;
   double s = 0.0;
   if (i < n) {
-    double U[C];
+    R U[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) U[c] = (double)w[(2 * c) * n + i];
-    s = wave_speed<C>(gas, U);
+    for (int c = 0; c < C; ++c) U[c] = w[(2 * c) * n + i];
+    s = (double)wave_speed<R, C>(R(gas), U);
     if (!(s == s)) {
       atomicOr(&sc->status, (unsigned)ST_NONPHYSICAL);
       s = 0.0;

@@ -112,19 +112,56 @@ __device__ __forceinline__ void hweno_faces(R um, R u0, R up, R vm, R v0, R vp, 
   right = w.apply(p0r, p1r, p2r);
 }
 
-// KXRCF indicator (reading of Sec. 2.1 Step 1 and Remark 1: Krivodonova et
+// KXRCF decision (reading of Sec. 2.1 Step 1 and Remark 1: Krivodonova et
 // al. with the degree-1 cell polynomial ubar + 12 vbar (x - x_i)/dx, h = dx/2,
 // the inflow face chosen by the sign of the velocity, normalised by
-// max(|ubar_i|, 1e-12)), evaluated in FP64 without contraction.
-__device__ __forceinline__ double kxrcf1d(double um, double u0, double up, double vm, double v0,
-                                          double vp, double vel, double h) {
+// max(|ubar_i|, 1e-12)): troubled iff |jump| / (h max(|u0|, 1e-12)) > thr.
+// The FP64 form is evaluated without contraction.
+__device__ __forceinline__ bool kxrcf_troubled(double um, double u0, double up, double vm,
+                                               double v0, double vp, bool left, double h,
+                                               double thr, float /*hthr*/) {
   double jump;
-  if (vel >= 0.0)
+  if (left)
     jump = __dsub_rn(__dsub_rn(u0, __dmul_rn(6.0, v0)), __dadd_rn(um, __dmul_rn(6.0, vm)));
   else
     jump = __dsub_rn(__dadd_rn(u0, __dmul_rn(6.0, v0)), __dsub_rn(up, __dmul_rn(6.0, vp)));
   const double nrm = fmax(fabs(u0), 1e-12);
-  return fabs(jump) / __dmul_rn(h, nrm);
+  return fabs(jump) / __dmul_rn(h, nrm) > thr;
+}
+
+// FP32 inputs: decide in FP32 when the rounding-error bound allows, else fall
+// back to the FP64 form, so the decision equals the FP64 one away from the
+// threshold.  With S = |u0| + 6|v0| + |u_nb| + 6|v_nb|, the FP32 jump (four
+// roundings) is within 3 * 2^-24 * S of the exact one (bounded here by
+// 6e-7 S), and r = thr*h*max(|u0|,1e-12) (three roundings) within a relative
+// 4.8e-7; hthr = (float)(thr*h).
+__device__ __forceinline__ bool kxrcf_troubled(float um, float u0, float up, float vm, float v0,
+                                               float vp, bool left, double h, double thr,
+                                               float hthr) {
+  float a, b, s;
+  if (left) {
+    a = u0 - 6.0f * v0;
+    b = um + 6.0f * vm;
+    s = fabsf(u0) + 6.0f * fabsf(v0) + fabsf(um) + 6.0f * fabsf(vm);
+  } else {
+    a = u0 + 6.0f * v0;
+    b = up - 6.0f * vp;
+    s = fabsf(u0) + 6.0f * fabsf(v0) + fabsf(up) + 6.0f * fabsf(vp);
+  }
+  const float j = fabsf(a - b);
+  const float e = 6.0e-7f * s;
+  const float r = hthr * fmaxf(fabsf(u0), 1e-12f);
+  if (j - e > r * (1.0f + 4.8e-7f)) return true;
+  if (j + e < r * (1.0f - 4.8e-7f)) return false;
+  return kxrcf_troubled((double)um, (double)u0, (double)up, (double)vm, (double)v0, (double)vp,
+                        left, h, thr, hthr);
+}
+
+// Side of the inflow face: left when the velocity m/rho is >= 0 (its sign
+// without the division when rho > 0).
+template <typename R>
+__device__ __forceinline__ bool inflow_left(R rho, R m) {
+  return rho > R(0) ? (m >= R(0)) : (m / rho >= R(0));
 }
 
 }  // namespace hw

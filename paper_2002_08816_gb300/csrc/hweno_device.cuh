@@ -92,12 +92,13 @@ struct Euler1D {
   }
 };
 
-// |mu| + c from cell averages, in FP64; NaN marks a non-physical state.
-__device__ __forceinline__ double euler1d_speed(double g, double rho, double m, double E) {
-  if (!(rho > 0.0)) return __longlong_as_double(0x7ff8000000000000ll);
-  const double mu = m / rho;
-  const double p = (g - 1.0) * (E - 0.5 * m * mu);
-  if (!(p > 0.0)) return __longlong_as_double(0x7ff8000000000000ll);
+// |mu| + c from cell averages; NaN marks a non-physical state.
+template <typename R>
+__device__ __forceinline__ R euler1d_speed_r(R g, R rho, R m, R E) {
+  if (!(rho > R(0))) return R(NAN);
+  const R mu = m / rho;
+  const R p = (g - R(1)) * (E - R(0.5) * m * mu);
+  if (!(p > R(0))) return R(NAN);
   return fabs(mu) + sqrt(g * p / rho);
 }
 
