@@ -121,7 +121,7 @@ hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* st
                          int64_t* troubled_cell_stages);
 
 /* Largest nx that hweno_rhs1d_noalloc accepts: its scratch is a fixed array
- * of one double per 256-cell tile (128 KiB) plus a 64-byte status block. */
+ * of one double per 250-cell tile (about 131 KiB) plus a 64-byte status block. */
 #define HWENO_NOALLOC_MAX_CELLS 4194304
 
 /* hweno_rhs for 1D without any device allocation.  The paper has no

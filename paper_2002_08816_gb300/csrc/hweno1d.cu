@@ -30,8 +30,11 @@
 namespace hw {
 namespace {
 
-constexpr int T = kTile1D;
+constexpr int T = kTile1D;      // cells per CTA
+constexpr int NT = kThreads1D;  // threads per CTA
 constexpr int H = 3;
+static_assert(T + 2 * H <= NT, "every phase is one pass over the threads");
+constexpr int NW = NT / 32;
 
 template <typename R, int C>
 struct Smem1D {
@@ -39,16 +42,34 @@ struct Smem1D {
   R vl[C][T + 4];        // modified first moments, cells base-2 .. base+T+1
   R fm[C][T + 2];        // u^+_{i-1/2}, cells base-1 .. base+T
   R fp[C][T + 2];        // u^-_{i+1/2}
+  R ffm[C][T + 2];       // f(u^+_{i-1/2})
+  R ffp[C][T + 2];       // f(u^-_{i+1/2})
   uint8_t fl[T + 4];     // flags, cells base-2 .. base+T+1
-  double red[T / 32];
+  R red[NW];
+  int cnt[NW];
 };
+
+template <typename R>
+__device__ __forceinline__ R recip(R x) {
+  if constexpr (sizeof(R) == 4) {
+    return __frcp_rn(x);
+  } else {
+    return R(1) / x;
+  }
+}
 
 template <typename R, int C>
 __device__ __forceinline__ void phys_flux(R gas, const R* U, R* F) {
   if constexpr (C == 1) {
     F[0] = R(0.5) * U[0] * U[0];
   } else {
-    Euler1D<R>::flux(gas, U, F);
+    // f(rho, m, E) of Eq. (euler1); FP32 uses a rounded reciprocal of rho
+    const R rho = U[0], m = U[1], E = U[2];
+    const R mu = sizeof(R) == 4 ? m * recip(rho) : m / rho;
+    const R p = (gas - R(1)) * (E - R(0.5) * m * mu);
+    F[0] = m;
+    F[1] = m * mu + p;
+    F[2] = mu * (E + p);
   }
 }
 
@@ -64,77 +85,91 @@ __device__ __forceinline__ R wave_speed(R gas, const R* U) {
 }
 
 template <typename R, int C>
-__global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
+__global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
   __shared__ Smem1D<R, C> sm;
   __shared__ double s_dt;
+  __shared__ R s_half_alpha, s_rdt;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
   const int base = blockIdx.x * T;
   const R* __restrict__ w = static_cast<const R*>(a.w);
 
-  // 1. alpha of the stage input and the step size
-  double amax = 0.0;
-  for (int k = tid; k < a.ntile; k += T) amax = fmax(amax, a.a_in[k]);
-  const double alpha = block_max<T>(amax, sm.red);
-  double dt = 0.0;
-  if (a.stage == 1) {
-    if (tid == 0) {
-      double d = a.cfl * a.dx / alpha;
-      const double tf = a.sc->t_final;
-      if (tf > 0.0) {
-        const double rem = tf - a.sc->t;
-        d = rem <= 0.0 ? 0.0 : (d > rem ? rem : d);
+  // 1. alpha of the stage input (warp 0 reduces the producer's partials) and,
+  //    in stage 1, the step size
+  if (warp == 0) {
+    double amax = 0.0;
+    for (int k = lane; k < a.ntile; k += 32) amax = fmax(amax, a.a_in[k]);
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane == 0) {
+      double d = 0.0;
+      if (a.stage == 1) {
+        d = a.cfl * a.dx / amax;
+        const double tf = a.sc->t_final;
+        if (tf > 0.0) {
+          const double rem = tf - a.sc->t;
+          d = rem <= 0.0 ? 0.0 : (d > rem ? rem : d);
+        }
+        if (!(amax > 0.0) || !isfinite(d)) d = 0.0;
+        if (blockIdx.x == 0) a.sc->dt = d;
+      } else if (a.stage > 1) {
+        d = a.sc->dt;
       }
-      if (!(alpha > 0.0) || !isfinite(d)) d = 0.0;
       s_dt = d;
-      if (blockIdx.x == 0) a.sc->dt = d;
+      s_half_alpha = R(0.5 * amax);
+      s_rdt = R(d);
     }
-    __syncthreads();
-    dt = s_dt;
-  } else if (a.stage > 1) {
-    dt = a.sc->dt;
   }
-  if (a.stage > 0 && !(dt > 0.0)) return;  // uniform over the grid
-
-  // 2. stage the tile and its halo
-  for (int k = tid; k < T + 2 * H; k += T) {
-    const int g = bc_map(base - H + k, n, a.bc);
+  // 2. stage the tile and its halo (one element per thread); stages 2 and 3
+  //    also fetch the modified u^n of their own cell now, so that its latency
+  //    overlaps the tile's
+  R u0c[C][2];
+  if (a.stage >= 2 && tid < T && base + tid < n) {
+    const R* u0 = static_cast<const R*>(a.u0);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      sm.u[c][0][k] = w[(2 * c + 0) * n + g];
-      sm.u[c][1][k] = w[(2 * c + 1) * n + g];
+      u0c[c][0] = u0[(2 * c + 0) * n + base + tid];
+      u0c[c][1] = u0[(2 * c + 1) * n + base + tid];
+    }
+  }
+  if (tid < T + 2 * H) {
+    const int g = bc_map(base - H + tid, n, a.bc);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      sm.u[c][0][tid] = w[(2 * c + 0) * n + g];
+      sm.u[c][1][tid] = w[(2 * c + 1) * n + g];
     }
   }
   __syncthreads();
+  const double dt = s_dt;
+  if (a.stage > 0 && !(dt > 0.0)) return;  // uniform over the grid
 
   const R gam[3] = {R(a.gam[0]), R(a.gam[1]), R(a.gam[2])};
   const R eps = R(a.eps);
   const R gas = R(a.gas);
 
-  // 3. troubled cells and modified first moments (Step 1)
-  const double h = 0.5 * a.dx;
-  const float hthr = (float)(a.thr * h);
-  for (int k = tid; k < T + 4; k += T) {
-    const int e = k + 1;
+  // 3. troubled cells and modified first moments (Step 1), cells base-2 ..
+  if (tid < T + 4) {
+    const int k = tid, e = k + 1;
+    const double h = a.h;
+    const float hthr = a.hthr;
     int flag;
     if (a.mode == 1) {
       flag = 1;
     } else if (a.mode == 2) {
       flag = 0;
+    } else if constexpr (C == 1) {
+      const R u0 = sm.u[0][0][e];
+      flag = kxrcf_troubled(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
+                            sm.u[0][1][e], sm.u[0][1][e + 1], u0 >= R(0), h, a.thr, hthr);
     } else {
-      if constexpr (C == 1) {
-        const R u0 = sm.u[0][0][e];
-        flag = kxrcf_troubled(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
-                              sm.u[0][1][e], sm.u[0][1][e + 1], u0 >= R(0), h, a.thr, hthr);
-      } else {
-        const bool left = inflow_left(sm.u[0][0][e], sm.u[1][0][e]);
-        flag = kxrcf_troubled(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
-                              sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left, h,
-                              a.thr, hthr) ||
-               kxrcf_troubled(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
-                              sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], left, h,
-                              a.thr, hthr);
-      }
+      const bool left = inflow_left(sm.u[0][0][e], sm.u[1][0][e]);
+      flag = kxrcf_troubled(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
+                            sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left, h, a.thr,
+                            hthr) ||
+             kxrcf_troubled(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
+                            sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], left, h, a.thr,
+                            hthr);
     }
     sm.fl[k] = (uint8_t)flag;
     if (!flag) {
@@ -152,11 +187,10 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
         R wv[5];
-        const int off[3] = {-1, 0, 1};
 #pragma unroll
         for (int s = 0; s < 3; ++s)
-          wv[s] = Lm[f][0] * sm.u[0][0][e + off[s]] + Lm[f][1] * sm.u[1][0][e + off[s]] +
-                  Lm[f][2] * sm.u[2][0][e + off[s]];
+          wv[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
+                  Lm[f][2] * sm.u[2][0][e - 1 + s];
         wv[3] = Lm[f][0] * sm.u[0][1][e - 1] + Lm[f][1] * sm.u[1][1][e - 1] +
                 Lm[f][2] * sm.u[2][1][e - 1];
         wv[4] = Lm[f][0] * sm.u[0][1][e + 1] + Lm[f][1] * sm.u[1][1][e + 1] +
@@ -169,18 +203,19 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
   }
   __syncthreads();
 
-  // 4. interface values (Steps 2.1, 2.2)
-  for (int k = tid; k < T + 2; k += T) {
-    const int e = k + 2;  // index into sm.u; sm.vl / sm.fl index of cell e is e - 1
+  // 4. interface values (Steps 2.1, 2.2) and their physical fluxes, cells base-1 ..
+  if (tid < T + 2) {
+    const int k = tid, e = k + 2;  // sm.u index e; sm.vl / sm.fl index of cell e is e - 1
     const bool hw = sm.fl[k] | sm.fl[k + 1] | sm.fl[k + 2];
+    R L[C], Rt[C];
     if (!hw) {
 #pragma unroll
       for (int c = 0; c < C; ++c)
         linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                     sm.vl[c][e - 1], sm.vl[c][e], sm.fm[c][k], sm.fp[c][k]);
+                     sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
     } else if constexpr (C == 1) {
       hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
-                  sm.vl[0][e - 1], sm.vl[0][e], gam, eps, sm.fm[0][k], sm.fp[0][k]);
+                  sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
     } else {
       R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
       R Rm[3][3], Lm[3][3];
@@ -200,67 +235,55 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        sm.fm[c][k] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
-        sm.fp[c][k] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
+        L[c] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
+        Rt[c] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
       }
+    }
+    R fL[C], fR[C];
+    phys_flux<R, C>(gas, L, fL);
+    phys_flux<R, C>(gas, Rt, fR);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      sm.fm[c][k] = L[c];
+      sm.fp[c][k] = Rt[c];
+      sm.ffm[c][k] = fL[c];
+      sm.ffp[c][k] = fR[c];
     }
   }
   __syncthreads();
 
   // 5. own cells: fluxes, F_i, right-hand side, RK combination
   const int i = base + tid;
-  const bool own = i < n;
+  const bool own = tid < T && i < n;
   int myflag = 0;
-  double speed = 0.0;
+  R speed = R(0);
   unsigned bad = 0;
   if (own) {
-    const int e = tid + H;   // sm.u index
-    const int k = tid + 1;   // sm.fm/fp index of cell i
+    const int e = tid + H;  // sm.u index
+    const int k = tid + 1;  // sm.fm/fp index of cell i
     myflag = sm.fl[tid + 2];
-    const R alf = R(alpha);
-    R ql[C], qr[C], gm[C], gp[C], ra[C], rb[C], fa[C], fb[C];
-    // flux at x_{i-1/2}: u^- from cell i-1, u^+ from cell i
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      ra[c] = sm.fp[c][k - 1];
-      rb[c] = sm.fm[c][k];
-    }
-    phys_flux<R, C>(gas, ra, fa);
-    phys_flux<R, C>(gas, rb, fb);
-#pragma unroll
-    for (int c = 0; c < C; ++c) ql[c] = R(0.5) * (fa[c] + fb[c]) - R(0.5) * alf * (rb[c] - ra[c]);
-    // flux at x_{i+1/2}: u^- from cell i, u^+ from cell i+1
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      ra[c] = sm.fp[c][k];
-      rb[c] = sm.fm[c][k + 1];
-    }
-    phys_flux<R, C>(gas, ra, fa);
-    phys_flux<R, C>(gas, rb, fb);
-#pragma unroll
-    for (int c = 0; c < C; ++c) qr[c] = R(0.5) * (fa[c] + fb[c]) - R(0.5) * alf * (rb[c] - ra[c]);
-    // Gauss-Lobatto values: the cell's own traces and the interior points
+    const R half_alpha = s_half_alpha;
+    R gm[C], gp[C], f2[C], f3[C];
 #pragma unroll
     for (int c = 0; c < C; ++c)
       linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
                       sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
-    R f1[C], f2[C], f3[C], f4[C], tr1[C], tr4[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      tr1[c] = sm.fm[c][k];
-      tr4[c] = sm.fp[c][k];
-    }
-    phys_flux<R, C>(gas, tr1, f1);
     phys_flux<R, C>(gas, gm, f2);
     phys_flux<R, C>(gas, gp, f3);
-    phys_flux<R, C>(gas, tr4, f4);
-    const R idx = R(1.0 / a.dx);
+    const R idx = R(a.inv_dx);
     R Uo[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const R F = R(1.0 / 12.0) * (f1[c] + f4[c]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
-      const R Lu = -(qr[c] - ql[c]) * idx;
-      const R Lv = (F - R(0.5) * (ql[c] + qr[c])) * idx;
+      // Lax-Friedrichs fluxes at x_{i-1/2} (u^- of cell i-1, u^+ of cell i)
+      // and at x_{i+1/2} (u^- of cell i, u^+ of cell i+1)
+      const R ql = R(0.5) * (sm.ffp[c][k - 1] + sm.ffm[c][k]) -
+                   half_alpha * (sm.fm[c][k] - sm.fp[c][k - 1]);
+      const R qr = R(0.5) * (sm.ffp[c][k] + sm.ffm[c][k + 1]) -
+                   half_alpha * (sm.fm[c][k + 1] - sm.fp[c][k]);
+      // four-point Gauss-Lobatto F_i; the end points are the cell's own traces
+      const R F = R(1.0 / 12.0) * (sm.ffm[c][k] + sm.ffp[c][k]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
+      const R Lu = -(qr - ql) * idx;
+      const R Lv = (F - R(0.5) * (ql + qr)) * idx;
       const R wu = sm.u[c][0][e];
       const R wv = sm.vl[c][e - 1];
       R ou, ov;
@@ -268,17 +291,16 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
         ou = Lu;
         ov = Lv;
       } else {
-        const R rdt = R(dt);
+        const R rdt = s_rdt;
         const R su = wu + rdt * Lu, sv = wv + rdt * Lv;
         if (a.stage == 1) {
           ou = su;
           ov = sv;
         } else {
-          const R* u0 = static_cast<const R*>(a.u0);
           const R ca = a.stage == 2 ? R(0.75) : R(1.0 / 3.0);
           const R cb = a.stage == 2 ? R(0.25) : R(2.0 / 3.0);
-          ou = ca * u0[(2 * c + 0) * n + i] + cb * su;
-          ov = ca * u0[(2 * c + 1) * n + i] + cb * sv;
+          ou = ca * u0c[c][0] + cb * su;
+          ov = ca * u0c[c][1] + cb * sv;
         }
       }
       R* out = static_cast<R*>(a.out);
@@ -294,34 +316,49 @@ __global__ void __launch_bounds__(T) stage1d_kernel(Stage1DArgs a) {
     }
     if (a.flags_out) a.flags_out[i] = (uint8_t)myflag;
     if (a.stage > 0) {
-      speed = (double)wave_speed<R, C>(gas, Uo);
+      speed = wave_speed<R, C>(gas, Uo);
       if (!(speed == speed)) {
         bad |= ST_NONPHYSICAL;
-        speed = 0.0;
+        speed = R(0);
       }
     }
   }
-  // 6. epilogue: partial max for the next alpha, counters, status
-  const int ntroubled = __syncthreads_count(myflag);
-  const double smax = block_max<T>(speed, sm.red);
-  if (tid == 0) {
-    if (a.a_out) a.a_out[blockIdx.x] = smax;
-    if (ntroubled) atomicAdd(&a.sc->troubled, (unsigned long long)ntroubled);
-    if (a.stage == 3 && blockIdx.x == 0) {
-      a.sc->t += dt;
-      a.sc->steps += 1;
-    }
+  // 6. epilogue: partial max for the next alpha (a max is exact in any
+  //    precision; the tile's maximum is stored as FP64), troubled count, status
+  R wmax = speed;
+  for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  const int wcnt = __popc(__ballot_sync(0xffffffffu, myflag));
+  if (lane == 0) {
+    sm.red[warp] = wmax;
+    sm.cnt[warp] = wcnt;
   }
   if (bad) atomicOr(&a.sc->status, bad);
+  __syncthreads();
+  if (warp == 0) {
+    R m = lane < NW ? sm.red[lane] : R(0);
+    int c = lane < NW ? sm.cnt[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+      if (a.a_out) a.a_out[blockIdx.x] = (double)m;
+      if (c) atomicAdd(&a.sc->troubled, (unsigned long long)c);
+      if (a.stage == 3 && blockIdx.x == 0) {
+        a.sc->t += dt;
+        a.sc->steps += 1;
+      }
+    }
+  }
 }
 
 template <typename R, int C>
-__global__ void __launch_bounds__(T) alpha1d_kernel(const R* __restrict__ w, double* a_out,
-                                                   int n, double gas, DevScalars* sc) {
-  __shared__ double red[T / 32];
+__global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, double* a_out,
+                                                    int n, double gas, DevScalars* sc) {
+  __shared__ double red[NW];
   const int i = blockIdx.x * T + threadIdx.x;
   double s = 0.0;
-  if (i < n) {
+  if (threadIdx.x < T && i < n) {
     R U[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) U[c] = w[(2 * c) * n + i];
@@ -331,7 +368,7 @@ __global__ void __launch_bounds__(T) alpha1d_kernel(const R* __restrict__ w, dou
       s = 0.0;
     }
   }
-  s = block_max<T>(s, red);
+  s = block_max<NT>(s, red);
   if (threadIdx.x == 0) a_out[blockIdx.x] = s;
 }
 
@@ -355,7 +392,7 @@ __global__ void set_scalars_kernel(DevScalars* sc, int reset, double t_final) {
 
 template <typename R, int C>
 cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
-  stage1d_kernel<R, C><<<a.ntile, T, 0, s>>>(a);
+  stage1d_kernel<R, C><<<a.ntile, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -370,14 +407,14 @@ cudaError_t launch_alpha1d(const void* w, double* a_out, int n, int ntile, int s
                            double gas, DevScalars* sc, cudaStream_t s) {
   if (system == 0) {
     if (fp64)
-      alpha1d_kernel<double, 1><<<ntile, T, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<double, 1><<<ntile, NT, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
     else
-      alpha1d_kernel<float, 1><<<ntile, T, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<float, 1><<<ntile, NT, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
   } else {
     if (fp64)
-      alpha1d_kernel<double, 3><<<ntile, T, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<double, 3><<<ntile, NT, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
     else
-      alpha1d_kernel<float, 3><<<ntile, T, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<float, 3><<<ntile, NT, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
   }
   return cudaGetLastError();
 }

@@ -74,6 +74,9 @@ hw::Stage1DArgs base_args(const hweno_ctx* h) {
   a.thr = c.kxrcf_threshold;
   a.gas = c.gas_gamma;
   for (int k = 0; k < 3; ++k) a.gam[k] = c.lin_w[k];
+  a.inv_dx = 1.0 / a.dx;
+  a.h = 0.5 * a.dx;
+  a.hthr = (float)(a.thr * a.h);
   return a;
 }
 

@@ -28,9 +28,14 @@ struct Stage1DArgs {
   int fp64;              // 0 FP32, 1 FP64
   double dx, cfl, eps, thr, gas;
   double gam[3];
+  // derived on the host so that no thread spends FP64 work on them
+  double inv_dx;         // 1 / dx
+  double h;              // dx / 2, the KXRCF cell size
+  float hthr;            // (float)(thr * h)
 };
 
-constexpr int kTile1D = 256;  // cells per CTA = threads per CTA
+constexpr int kTile1D = 250;     // cells per CTA of the 1D kernels
+constexpr int kThreads1D = 256;  // threads per CTA (tile + 3-cell halo per side)
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
 cudaError_t launch_alpha1d(const void* w, double* a_out, int n, int ntile, int system, int fp64,

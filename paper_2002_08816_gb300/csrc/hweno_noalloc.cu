@@ -12,9 +12,10 @@
 // cudaMalloc and cudaFree may imply.  For them this entry point keeps its
 // scratch in a fixed file-scope __device__ array instead.
 //
-// The array holds one partial maximum per 256-cell tile plus the status word,
-// so one call handles at most HWENO_NOALLOC_MAX_CELLS cells.  Every GPU that
-// loads the library holds the array (128 KiB + 64 B) until the process exits.
+// The array holds one partial maximum per tile of the 1D stage kernel plus
+// the status word, so one call handles at most HWENO_NOALLOC_MAX_CELLS cells.
+// Every GPU that loads the library holds the array (about 131 KiB) until the
+// process exits.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -26,8 +27,7 @@
 
 namespace {
 
-constexpr int kNoallocMaxTiles = HWENO_NOALLOC_MAX_CELLS / hw::kTile1D;
-static_assert(HWENO_NOALLOC_MAX_CELLS % hw::kTile1D == 0, "whole tiles");
+constexpr int kNoallocMaxTiles = (HWENO_NOALLOC_MAX_CELLS + hw::kTile1D - 1) / hw::kTile1D;
 // layout of the scratch, in doubles: [0, 8) the status word and counters of
 // one call (hw::DevScalars), [8, 8 + kNoallocMaxTiles) the per-tile maxima
 // of |f'(ubar)| that give alpha
@@ -38,7 +38,7 @@ constexpr int kNoallocScratchDoubles = kScalarSlots + kNoallocMaxTiles;
 }  // namespace
 
 // The scratch of every call, on every device that loads the library
-// (kNoallocScratchDoubles doubles = 128 KiB + 64 B).  In host code this name
+// (kNoallocScratchDoubles doubles, about 131 KiB).  In host code this name
 // is only a host-side stand-in: the device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles];
@@ -140,6 +140,9 @@ hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, con
     a.thr = cfg->kxrcf_threshold;
     a.gas = cfg->gas_gamma;
     for (int k = 0; k < 3; ++k) a.gam[k] = cfg->lin_w[k];
+    a.inv_dx = 1.0 / a.dx;
+    a.h = 0.5 * a.dx;
+    a.hthr = (float)(a.thr * a.h);
     e = hw::launch_stage1d(a, s);
   }
   unsigned status = 0;
