@@ -3,7 +3,7 @@
 Workload (one bench step): the seeded two-state 1D Euler problem, gamma 1.4,
 65536 cells on [0, 1] with outflow ends, advanced 2000 third-order TVD
 Runge-Kutta steps (6000 stages, 3.93e8 cell-stages) at CFL 0.5, FP32 bulk
-arithmetic with FP64 alpha/dt.  The metric is cell-updates per second counted
+arithmetic (the time itself accumulated in FP64).  The metric is cell-updates per second counted
 per Runge-Kutta stage.  The FP64 path is timed on the same workload and
 reported beside it.
 
@@ -290,7 +290,7 @@ def bench_hweno(args):
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "1D Euler two-state, 65536 cells, outflow, 2000 SSP-RK3 steps, "
-                               "CFL 0.5, FP32 (FP64 alpha/dt)",
+                               "CFL 0.5, FP32 (time accumulated in FP64)",
                    "seed": SEED, "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": "one independent instance per GPU"},
         "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],

@@ -557,29 +557,35 @@ int hwo1d_step(const hwo1d_cfg* cfg, double* u, double dt, long* n_troubled) {
   return st;
 }
 
+/* Reading of the final step: a step clipped to t_final (dt >= t_final - t)
+ * is the last one and ends exactly at t_final.  Without it, rounding of t
+ * can leave a remainder of a few ulps and one more, vanishing, step, which
+ * would still modify the first moments of troubled cells once more. */
 int hwo1d_run(const hwo1d_cfg* cfg, double* u, int nsteps, double cfl,
               double t0, double t_final, double dt_fixed,
               const double* lin_w_per_step, double* t_out, long* n_troubled) {
+  const double dx = (cfg->x1 - cfg->x0) / cfg->nx;
   double t = t0;
   int st = 0;
   hwo1d_cfg c = *cfg;
   for (int s = 0; nsteps < 0 || s < nsteps; ++s) {
-    double dt;
-    if (dt_fixed > 0.0) {
-      dt = dt_fixed;
-      if (t_final > 0.0) {
-        double rem = t_final - t;
-        dt = rem <= 0.0 ? 0.0 : (dt > rem ? rem : dt);
+    double dt = dt_fixed > 0.0 ? dt_fixed : cfl * dx / hwo1d_alpha(&c, u);
+    int last = 0;
+    if (t_final > 0.0) {
+      double rem = t_final - t;
+      if (rem <= 0.0) break;
+      if (dt >= rem) {
+        dt = rem;
+        last = 1;
       }
-    } else {
-      dt = hwo1d_dt(&c, u, cfl, t, t_final);
     }
     if (!(dt > 0.0)) break;
     if (lin_w_per_step)
       for (int k = 0; k < 3; ++k) c.lin_w[k] = lin_w_per_step[3 * s + k];
     st = hwo1d_step(&c, u, dt, n_troubled);
     if (st) break;
-    t += dt;
+    t = last ? t_final : t + dt;
+    if (last) break;
   }
   if (t_out) *t_out = t;
   return st;

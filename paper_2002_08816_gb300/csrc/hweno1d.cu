@@ -4,9 +4,12 @@
 // A CTA owns kTile1D consecutive cells.  It stages its cells plus a 3-cell
 // halo of the stage input in shared memory (coalesced loads of each
 // structure-of-arrays row), then, all on chip:
-//   1. alpha = max |f'(ubar)| from the per-tile partial maxima the producer
-//      of the stage input wrote (global Lax-Friedrichs flux); stage 1 also
-//      turns alpha into dt = CFL dx / alpha, clipped to t_final;
+//   1. alpha = max |f'(ubar)| from the maxima the producer of the stage
+//      input left in kAlphaSlots slots (global Lax-Friedrichs flux); stage 1
+//      also turns alpha into dt = CFL dx / alpha, clipped to t_final.  All of
+//      it runs in the kernel's precision: on GB300 each dependent FP64
+//      operation costs tens of cycles, so the FP32 kernel keeps FP64 off its
+//      critical path (the time itself is accumulated in FP64 by an idle thread);
 //   2. KXRCF flags and the modified first moments (Step 1) for the cells and
 //      2 halo cells per side, in characteristic fields for Euler; an FP32
 //      kernel decides a flag in FP32 when its rounding-error bound allows and
@@ -16,8 +19,9 @@
 //   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
 //      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
 //      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
-//   5. a partial maximum (reduced in FP64) of the output's wave speed for the
-//      next stage's alpha, and the status bits (non-finite, non-physical).
+//   5. the tile's maximum wave speed of the output, folded by an FP64 atomic
+//      max into one of kAlphaSlots slots that the next stage reads for its
+//      alpha, and the status bits (non-finite, non-physical).
 // The limited stage input is what the RK combination uses (the first moment
 // of a troubled cell is modified in the state, as a DG limiter would).
 #include <cuda_runtime.h>
@@ -47,6 +51,7 @@ struct Smem1D {
   uint8_t fl[T + 4];     // flags, cells base-2 .. base+T+1
   R red[NW];
   int cnt[NW];
+  R amax[NW];
 };
 
 template <typename R>
@@ -87,42 +92,37 @@ __device__ __forceinline__ R wave_speed(R gas, const R* U) {
 template <typename R, int C>
 __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
   __shared__ Smem1D<R, C> sm;
-  __shared__ double s_dt;
-  __shared__ R s_half_alpha, s_rdt;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int n = a.n;
   const int base = blockIdx.x * T;
   const R* __restrict__ w = static_cast<const R*>(a.w);
 
-  // 1. alpha of the stage input (warp 0 reduces the producer's partials) and,
-  //    in stage 1, the step size
-  if (warp == 0) {
-    double amax = 0.0;
-    for (int k = lane; k < a.ntile; k += 32) amax = fmax(amax, a.a_in[k]);
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (lane == 0) {
-      double d = 0.0;
-      if (a.stage == 1) {
-        d = a.cfl * a.dx / amax;
-        const double tf = a.sc->t_final;
-        if (tf > 0.0) {
-          const double rem = tf - a.sc->t;
-          d = rem <= 0.0 ? 0.0 : (d > rem ? rem : d);
-        }
-        if (!(amax > 0.0) || !isfinite(d)) d = 0.0;
-        if (blockIdx.x == 0) a.sc->dt = d;
-      } else if (a.stage > 1) {
-        d = a.sc->dt;
-      }
-      s_dt = d;
-      s_half_alpha = R(0.5 * amax);
-      s_rdt = R(d);
-    }
+  // The producer of the stage input may still be finishing (programmatic
+  // dependent launch): wait for its completion and memory before any read.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  // Parameters in the kernel's precision (FP32 copies made on the host).
+  R gam[3], eps, gas, inv_dx, cfl_dx;
+  if constexpr (sizeof(R) == 4) {
+    gam[0] = a.f32[0]; gam[1] = a.f32[1]; gam[2] = a.f32[2];
+    eps = a.f32[3]; gas = a.f32[4]; inv_dx = a.f32[5]; cfl_dx = a.f32[6];
+  } else {
+    gam[0] = a.gam[0]; gam[1] = a.gam[1]; gam[2] = a.gam[2];
+    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx; cfl_dx = a.cfl_dx;
   }
-  // 2. stage the tile and its halo (one element per thread); stages 2 and 3
-  //    also fetch the modified u^n of their own cell now, so that its latency
-  //    overlaps the tile's
+
+  // 1-2. in one round trip: every thread fetches its share of the producer's
+  //      wave-speed maxima (for alpha), its tile-plus-halo element, the time
+  //      bookkeeping, and in stages 2 and 3 the modified u^n of its own cell
+  const R* a_in = static_cast<const R*>(a.a_in);
+  R amax = R(0);
+  for (int k = tid; k < a.nin; k += NT) amax = fmax(amax, a_in[k]);
+  R rem = R(0), dt_prev = R(0);
+  if (a.stage == 1)
+    rem = sc_rem<R>(a.sc);
+  else if (a.stage > 1)
+    dt_prev = sc_dt<R>(a.sc);
   R u0c[C][2];
   if (a.stage >= 2 && tid < T && base + tid < n) {
     const R* u0 = static_cast<const R*>(a.u0);
@@ -140,13 +140,35 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
       sm.u[c][1][tid] = w[(2 * c + 1) * n + g];
     }
   }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (lane == 0) sm.amax[warp] = amax;
   __syncthreads();
-  const double dt = s_dt;
-  if (a.stage > 0 && !(dt > 0.0)) return;  // uniform over the grid
-
-  const R gam[3] = {R(a.gam[0]), R(a.gam[1]), R(a.gam[2])};
-  const R eps = R(a.eps);
-  const R gas = R(a.gas);
+  // the next stage's CTAs may be scheduled now; they wait for this grid above
+  asm volatile("griddepcontrol.launch_dependents;");
+  // alpha (every thread reads the warps' maxima) and dt: CFL dx / alpha in
+  // stage 1, clipped to the remaining time; 0 once t_final is reached
+  R alpha = sm.amax[0];
+#pragma unroll
+  for (int k = 1; k < NW; ++k) alpha = fmax(alpha, sm.amax[k]);
+  R dt = dt_prev;
+  if (a.stage == 1) {
+    dt = cfl_dx / alpha;
+    unsigned last = 0;
+    if (rem <= R(0)) {
+      dt = R(0);
+    } else if (dt >= rem) {  // clipped: this step ends exactly at t_final
+      dt = rem;
+      last = 1;
+    }
+    if (!(alpha > R(0)) || !isfinite(dt)) dt = R(0);
+    if (blockIdx.x == 0 && tid == 0) {
+      sc_dt<R>(a.sc) = dt;
+      a.sc->last = last;
+    }
+  }
+  if (a.stage > 0 && !(dt > R(0))) return;  // uniform over the grid
+  // the slots of the stage after next (read two stages ago, now free)
+  if (a.a_zero && blockIdx.x == 0 && tid < kAlphaSlots) static_cast<R*>(a.a_zero)[tid] = R(0);
 
   // 3. troubled cells and modified first moments (Step 1), cells base-2 ..
   if (tid < T + 4) {
@@ -252,6 +274,20 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
   }
   __syncthreads();
 
+  // time bookkeeping (FP64) by a thread that has no cell in phase 5
+  if (a.stage == 3 && blockIdx.x == 0 && tid == NT - 1) {
+    DevScalars* sc = a.sc;
+    const double tf = sc->t_final;
+    const double t = sc->last ? tf : sc->t + (double)dt;
+    const double r = tf > 0.0 ? tf - t : (double)INFINITY;
+    sc->t = t;
+    sc->dt = (double)dt;
+    sc->rem = r;
+    sc->rem_f = (float)r;
+    sc->steps += 1;
+  }
+  static_assert(T < NT, "a thread without a cell keeps the time");
+
   // 5. own cells: fluxes, F_i, right-hand side, RK combination
   const int i = base + tid;
   const bool own = tid < T && i < n;
@@ -262,7 +298,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
     const int e = tid + H;  // sm.u index
     const int k = tid + 1;  // sm.fm/fp index of cell i
     myflag = sm.fl[tid + 2];
-    const R half_alpha = s_half_alpha;
+    const R half_alpha = R(0.5) * alpha;
     R gm[C], gp[C], f2[C], f3[C];
 #pragma unroll
     for (int c = 0; c < C; ++c)
@@ -270,7 +306,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
                       sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
     phys_flux<R, C>(gas, gm, f2);
     phys_flux<R, C>(gas, gp, f3);
-    const R idx = R(a.inv_dx);
+    const R idx = inv_dx;
     R Uo[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -291,7 +327,7 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
         ou = Lu;
         ov = Lv;
       } else {
-        const R rdt = s_rdt;
+        const R rdt = dt;
         const R su = wu + rdt * Lu, sv = wv + rdt * Lv;
         if (a.stage == 1) {
           ou = su;
@@ -342,34 +378,38 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
       c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-      if (a.a_out) a.a_out[blockIdx.x] = (double)m;
+      if (a.a_out) atomic_max_nonneg(static_cast<R*>(a.a_out) + blockIdx.x % kAlphaSlots, m);
       if (c) atomicAdd(&a.sc->troubled, (unsigned long long)c);
-      if (a.stage == 3 && blockIdx.x == 0) {
-        a.sc->t += dt;
-        a.sc->steps += 1;
-      }
     }
   }
 }
 
 template <typename R, int C>
-__global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, double* a_out,
-                                                    int n, double gas, DevScalars* sc) {
-  __shared__ double red[NW];
+__global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, R* a_out, int n,
+                                                    double gas, DevScalars* sc, int slots) {
+  __shared__ R red[NW];
   const int i = blockIdx.x * T + threadIdx.x;
-  double s = 0.0;
+  R s = R(0);
   if (threadIdx.x < T && i < n) {
     R U[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) U[c] = w[(2 * c) * n + i];
-    s = (double)wave_speed<R, C>(R(gas), U);
+    s = wave_speed<R, C>(R(gas), U);
     if (!(s == s)) {
       atomicOr(&sc->status, (unsigned)ST_NONPHYSICAL);
-      s = 0.0;
+      s = R(0);
     }
   }
-  s = block_max<NT>(s, red);
-  if (threadIdx.x == 0) a_out[blockIdx.x] = s;
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NW; ++k) s = fmax(s, red[k]);
+    if (slots)
+      atomic_max_nonneg(a_out + blockIdx.x % kAlphaSlots, s);
+    else
+      a_out[blockIdx.x] = s;
+  }
 }
 
 template <typename S, typename D>
@@ -383,17 +423,33 @@ __global__ void set_scalars_kernel(DevScalars* sc, int reset, double t_final) {
   if (reset) {
     sc->t = 0.0;
     sc->dt = 0.0;
+    sc->dt_f = 0.0f;
+    sc->last = 0u;
     sc->status = 0u;
     sc->steps = 0ull;
     sc->troubled = 0ull;
   }
   sc->t_final = t_final;
+  const double r = t_final > 0.0 ? t_final - sc->t : (double)INFINITY;
+  sc->rem = r;
+  sc->rem_f = (float)r;
 }
 
+// Stage launches allow programmatic dependent launch: a stage's CTAs can be
+// resident before the previous stage ends and start at its completion.
 template <typename R, int C>
 cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
-  stage1d_kernel<R, C><<<a.ntile, NT, 0, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)a.ntile);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C>, a);
 }
 
 }  // namespace
@@ -403,18 +459,22 @@ cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s) {
   return a.fp64 ? launch_stage1d_t<double, 3>(a, s) : launch_stage1d_t<float, 3>(a, s);
 }
 
-cudaError_t launch_alpha1d(const void* w, double* a_out, int n, int ntile, int system, int fp64,
-                           double gas, DevScalars* sc, cudaStream_t s) {
+cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int system, int fp64,
+                           double gas, DevScalars* sc, int slots, cudaStream_t s) {
+  const double* wd = static_cast<const double*>(w);
+  const float* wf = static_cast<const float*>(w);
+  double* od = static_cast<double*>(a_out);
+  float* of = static_cast<float*>(a_out);
   if (system == 0) {
     if (fp64)
-      alpha1d_kernel<double, 1><<<ntile, NT, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<double, 1><<<ntile, NT, 0, s>>>(wd, od, n, gas, sc, slots);
     else
-      alpha1d_kernel<float, 1><<<ntile, NT, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<float, 1><<<ntile, NT, 0, s>>>(wf, of, n, gas, sc, slots);
   } else {
     if (fp64)
-      alpha1d_kernel<double, 3><<<ntile, NT, 0, s>>>(static_cast<const double*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<double, 3><<<ntile, NT, 0, s>>>(wd, od, n, gas, sc, slots);
     else
-      alpha1d_kernel<float, 3><<<ntile, NT, 0, s>>>(static_cast<const float*>(w), a_out, n, gas, sc);
+      alpha1d_kernel<float, 3><<<ntile, NT, 0, s>>>(wf, of, n, gas, sc, slots);
   }
   return cudaGetLastError();
 }

@@ -6,8 +6,9 @@
 //   stage 1: U[0] -> U[1], writes the limited u^n to U0
 //   stage 2: U[1], U0 -> U[2]
 //   stage 3: U[2], U0 -> U[0]
-// and over three partial-maximum buffers P0 -> P1 -> P2 -> P0 that carry
-// alpha from each stage to the next.  dt, t and the status word live in
+// and over three buffers of kAlphaSlots wave-speed maxima P0 -> P1 -> P2 -> P0
+// that carry alpha from each stage to the next (each stage also zeroes the
+// buffer the stage after next fills).  dt, t and the status word live in
 // device memory, so a run of many steps needs no host synchronisation.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -28,8 +29,8 @@ struct hweno_ctx {
   void* U[3] = {nullptr, nullptr, nullptr};
   void* U0 = nullptr;
   void* stage_buf = nullptr;         // conversion staging (other precision)
-  double* part[3] = {nullptr, nullptr, nullptr};
-  double* part_rhs = nullptr;
+  double* part[3] = {nullptr, nullptr, nullptr};  // kAlphaSlots slots (float or double)
+  double* part_rhs = nullptr;                      // one maximum per tile
   hw::DevScalars* sc = nullptr;
   hw::DevScalars* sc_rhs = nullptr;
   cudaGraphExec_t g_many = nullptr;  // kGraphSteps steps
@@ -74,9 +75,7 @@ hw::Stage1DArgs base_args(const hweno_ctx* h) {
   a.thr = c.kxrcf_threshold;
   a.gas = c.gas_gamma;
   for (int k = 0; k < 3; ++k) a.gam[k] = c.lin_w[k];
-  a.inv_dx = 1.0 / a.dx;
-  a.h = 0.5 * a.dx;
-  a.hthr = (float)(a.thr * a.h);
+  hw::finish_stage_args(a);
   return a;
 }
 
@@ -89,7 +88,9 @@ cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
   a.out = h->U[1];
   a.lim_out = h->U0;
   a.a_in = h->part[0];
+  a.nin = hw::kAlphaSlots;
   a.a_out = h->part[1];
+  a.a_zero = h->part[2];
   cudaError_t e = hw::launch_stage1d(a, s);
   if (e != cudaSuccess) return e;
   // stage 2
@@ -100,6 +101,7 @@ cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
   a.lim_out = nullptr;
   a.a_in = h->part[1];
   a.a_out = h->part[2];
+  a.a_zero = h->part[0];
   e = hw::launch_stage1d(a, s);
   if (e != cudaSuccess) return e;
   // stage 3
@@ -108,6 +110,7 @@ cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
   a.out = h->U[0];
   a.a_in = h->part[2];
   a.a_out = h->part[0];
+  a.a_zero = h->part[1];
   return hw::launch_stage1d(a, s);
 }
 
@@ -214,7 +217,7 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->U[k], h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->U0, h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_buf, h->elems * 8);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * h->ntile);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * hw::kAlphaSlots);
   if (e == cudaSuccess) e = cudaMalloc(&h->part_rhs, sizeof(double) * h->ntile);
   if (e == cudaSuccess) e = cudaMalloc(&h->sc, sizeof(hw::DevScalars));
   if (e == cudaSuccess) e = cudaMalloc(&h->sc_rhs, sizeof(hw::DevScalars));
@@ -248,8 +251,10 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
   }
   if (src) HW_CUDA(h, hw::launch_convert(src, src64, h->U[0], dst64, h->elems, h->stream));
   HW_CUDA(h, hw::launch_set_scalars(h->sc, 1, -1.0, h->stream));
+  for (int k = 0; k < 3; ++k)
+    HW_CUDA(h, cudaMemsetAsync(h->part[k], 0, sizeof(double) * hw::kAlphaSlots, h->stream));
   HW_CUDA(h, hw::launch_alpha1d(h->U[0], h->part[0], h->n, h->ntile, h->cfg.system, dst64,
-                                h->cfg.gas_gamma, h->sc, h->stream));
+                                h->cfg.gas_gamma, h->sc, 1, h->stream));
   h->has_state = true;
   return HWENO_OK;
 }
@@ -290,7 +295,7 @@ hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags
     return fail(h, HWENO_ERR_ARG, "in, out and ulim_out must not overlap");
   HW_CUDA(h, hw::launch_set_scalars(h->sc_rhs, 1, -1.0, h->stream));
   HW_CUDA(h, hw::launch_alpha1d(in, h->part_rhs, h->n, h->ntile, h->cfg.system,
-                                h->cfg.precision == HWENO_FP64, h->cfg.gas_gamma, h->sc_rhs,
+                                h->cfg.precision == HWENO_FP64, h->cfg.gas_gamma, h->sc_rhs, 0,
                                 h->stream));
   hw::Stage1DArgs a = base_args(h);
   a.stage = 0;
@@ -298,6 +303,7 @@ hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags
   a.out = out;
   a.lim_out = ulim_out;
   a.a_in = h->part_rhs;
+  a.nin = h->ntile;
   a.a_out = nullptr;
   a.sc = h->sc_rhs;
   a.flags_out = flags_out;

@@ -16,11 +16,35 @@ struct DevScalars {
   double t;          // time reached
   double dt;         // dt of the step in flight (written by stage 1)
   double t_final;    // clip time (<= 0: none)
+  double rem;        // t_final - t (+inf without clipping)
+  float dt_f;        // dt as the FP32 kernels use it
+  float rem_f;       // rem rounded to FP32
   unsigned status;   // ST_* bits
-  unsigned pad;
+  unsigned last;     // 1: the step in flight was clipped to t_final (its last)
   unsigned long long steps;     // completed steps
   unsigned long long troubled;  // troubled cell-stages
 };
+static_assert(sizeof(DevScalars) == 64, "one 64-byte block");
+
+// dt and rem in the kernel's precision
+template <typename R>
+__device__ __forceinline__ R& sc_dt(DevScalars* s) {
+  if constexpr (sizeof(R) == 4) return s->dt_f; else return s->dt;
+}
+template <typename R>
+__device__ __forceinline__ R sc_rem(const DevScalars* s) {
+  if constexpr (sizeof(R) == 4) return s->rem_f; else return s->rem;
+}
+
+// Maximum of a non-negative value into a slot: for x >= 0 the order of the
+// IEEE bit patterns is the numeric order.
+__device__ __forceinline__ void atomic_max_nonneg(float* slot, float x) {
+  atomicMax(reinterpret_cast<unsigned int*>(slot), __float_as_uint(x));
+}
+__device__ __forceinline__ void atomic_max_nonneg(double* slot, double x) {
+  atomicMax(reinterpret_cast<unsigned long long*>(slot),
+            (unsigned long long)__double_as_longlong(x));
+}
 
 // Ghost cells: periodic wraps, outflow copies the boundary cell.  Any g
 // (a tile's halo may span several periods when n is smaller than a tile).

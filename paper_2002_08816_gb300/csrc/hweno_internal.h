@@ -15,8 +15,13 @@ struct Stage1DArgs {
   const void* u0;        // limited u^n (stages 2, 3)
   void* out;             // stage output (or L in rhs mode)
   void* lim_out;         // stage 1: limited u^n; rhs mode: limited input (nullable)
-  const double* a_in;    // per-tile partial maxima of the wave speed of w
-  double* a_out;         // per-tile partial maxima of the wave speed of out (nullable)
+  // Wave-speed maxima travel between launches in the kernel's precision
+  // (float or double elements): a max is exact in any precision.
+  const void* a_in;      // maxima of the wave speed of w (nin entries)
+  int nin;               // entries of a_in
+  void* a_out;           // kAlphaSlots zeroed slots that receive, by atomic max, the
+                         // wave-speed maxima of out's tiles (nullable)
+  void* a_zero;          // kAlphaSlots slots this launch zeroes for a later stage (nullable)
   DevScalars* sc;        // t, dt, t_final, status, counters
   uint8_t* flags_out;    // troubled flags of the own cells (nullable)
   int n;                 // cells
@@ -28,18 +33,39 @@ struct Stage1DArgs {
   int fp64;              // 0 FP32, 1 FP64
   double dx, cfl, eps, thr, gas;
   double gam[3];
-  // derived on the host so that no thread spends FP64 work on them
+  // derived on the host so that no thread spends FP64 work on them (on
+  // GB300 a dependent FP64 operation or conversion costs ~80 cycles)
   double inv_dx;         // 1 / dx
   double h;              // dx / 2, the KXRCF cell size
+  double cfl_dx;         // cfl * dx
   float hthr;            // (float)(thr * h)
+  float f32[7];          // FP32 copies: gamma_0..2, eps, gas_gamma, 1/dx, cfl*dx
 };
 
+// Fills the derived fields of a from its primary ones.
+inline void finish_stage_args(Stage1DArgs& a) {
+  a.inv_dx = 1.0 / a.dx;
+  a.h = 0.5 * a.dx;
+  a.cfl_dx = a.cfl * a.dx;
+  a.hthr = (float)(a.thr * a.h);
+  a.f32[0] = (float)a.gam[0];
+  a.f32[1] = (float)a.gam[1];
+  a.f32[2] = (float)a.gam[2];
+  a.f32[3] = (float)a.eps;
+  a.f32[4] = (float)a.gas;
+  a.f32[5] = (float)a.inv_dx;
+  a.f32[6] = (float)a.cfl_dx;
+}
+
+constexpr int kAlphaSlots = 64;  // slots that carry alpha between stages
 constexpr int kTile1D = 250;     // cells per CTA of the 1D kernels
 constexpr int kThreads1D = 256;  // threads per CTA (tile + 3-cell halo per side)
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
-cudaError_t launch_alpha1d(const void* w, double* a_out, int n, int ntile, int system, int fp64,
-                           double gas, DevScalars* sc, cudaStream_t s);
+// Wave-speed maxima of w, in the kernel's precision: one per tile (slots = 0)
+// or folded into kAlphaSlots zeroed slots by atomic max (slots = 1).
+cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int system, int fp64,
+                           double gas, DevScalars* sc, int slots, cudaStream_t s);
 cudaError_t launch_convert(const void* src, int src_fp64, void* dst, int dst_fp64, size_t count,
                            cudaStream_t s);
 cudaError_t launch_set_scalars(DevScalars* sc, int reset, double t_final, cudaStream_t s);

@@ -116,7 +116,7 @@ hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, con
   // the previous call's status bits and counters must not leak into this one
   cudaError_t e = hw::launch_set_scalars(sc, 1, -1.0, s);
   if (e == cudaSuccess)
-    e = hw::launch_alpha1d(in, partial, n, ntile, cfg->system, fp64, cfg->gas_gamma, sc, s);
+    e = hw::launch_alpha1d(in, partial, n, ntile, cfg->system, fp64, cfg->gas_gamma, sc, 0, s);
   if (e == cudaSuccess) {
     hw::Stage1DArgs a;
     memset(&a, 0, sizeof(a));
@@ -124,6 +124,7 @@ hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, con
     a.out = out;
     a.lim_out = ulim_out;
     a.a_in = partial;
+    a.nin = ntile;
     a.a_out = nullptr;
     a.sc = sc;
     a.flags_out = flags_out;
@@ -140,9 +141,7 @@ hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, con
     a.thr = cfg->kxrcf_threshold;
     a.gas = cfg->gas_gamma;
     for (int k = 0; k < 3; ++k) a.gam[k] = cfg->lin_w[k];
-    a.inv_dx = 1.0 / a.dx;
-    a.h = 0.5 * a.dx;
-    a.hthr = (float)(a.thr * a.h);
+    hw::finish_stage_args(a);
     e = hw::launch_stage1d(a, s);
   }
   unsigned status = 0;
