@@ -91,6 +91,9 @@ int hwo2d_ncomp(int system);
 int hwo2d_rhs(const hwo2d_cfg* cfg, const double* u, double alpha_x,
               double alpha_y, double* rhs, double* ulim, unsigned char* flags,
               double* indicator);
+int hwo2d_rhs_ex(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alpha_y,
+                 double* rhs, double* ulim, unsigned char* flags, double* indicator,
+                 double* points);
 void hwo2d_alpha(const hwo2d_cfg* cfg, const double* u, double* ax, double* ay);
 double hwo2d_dt(const hwo2d_cfg* cfg, const double* u, double cfl, double t,
                 double t_final);
@@ -102,6 +105,11 @@ int hwo2d_recon_candidates(const double ub[9], const double vb[9],
                            const double wb[9], int n_gauss, double* val,
                            double beta[5]);
 int hwo2d_linear_weights(int n_gauss, double* W);
+void hwo2d_p0_coeffs(const double* d19, double* c15);
+void hwo2d_quad_coeffs(int n, const double* d19, double* c6);
+double hwo2d_beta_of_coeffs(int degree, const double* c, double ratio);
+void hwo_euler2d_flux(double g, const double* U, int dir, double* F);
+void hwo_euler2d_eigen(double g, const double* U, int dir, double R[16], double L[16]);
 
 #ifdef __cplusplus
 }

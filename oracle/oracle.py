@@ -130,6 +130,8 @@ def lib():
             P2 = ctypes.POINTER(Cfg2D)
             L.hwo2d_rhs.restype = _I
             L.hwo2d_rhs.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD]
+            L.hwo2d_rhs_ex.restype = _I
+            L.hwo2d_rhs_ex.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD, _PD]
             L.hwo2d_alpha.restype = None
             L.hwo2d_alpha.argtypes = [P2, _PD, _PD, _PD]
             L.hwo2d_dt.restype = _D
@@ -142,6 +144,16 @@ def lib():
             L.hwo2d_recon_candidates.argtypes = [_PD, _PD, _PD, _I, _PD, _PD]
             L.hwo2d_linear_weights.restype = _I
             L.hwo2d_linear_weights.argtypes = [_I, _PD]
+            L.hwo2d_p0_coeffs.restype = None
+            L.hwo2d_p0_coeffs.argtypes = [_PD, _PD]
+            L.hwo2d_quad_coeffs.restype = None
+            L.hwo2d_quad_coeffs.argtypes = [_I, _PD, _PD]
+            L.hwo2d_beta_of_coeffs.restype = _D
+            L.hwo2d_beta_of_coeffs.argtypes = [_I, _PD, _D]
+            L.hwo_euler2d_flux.restype = None
+            L.hwo_euler2d_flux.argtypes = [_D, _PD, _I, _PD]
+            L.hwo_euler2d_eigen.restype = None
+            L.hwo_euler2d_eigen.argtypes = [_D, _PD, _I, _PD, _PD]
         _lib = L
     return _lib
 
@@ -254,3 +266,111 @@ def euler1d_flux(g, U):
     F = np.zeros(3)
     lib().hwo_euler1d_flux(g, _p(U), _p(F))
     return F
+
+
+# ----------------------------------------------------------------------------- 2D
+
+# monomials xi^a eta^b, a + b <= 4, by total degree then descending a
+MONO2D = [(a, d - a) for d in range(5) for a in range(d, -1, -1)]
+
+
+def alpha2d(cfg, u):
+    u = _f64(u)
+    ax, ay = ctypes.c_double(), ctypes.c_double()
+    lib().hwo2d_alpha(ctypes.byref(cfg), _p(u), ctypes.byref(ax), ctypes.byref(ay))
+    return ax.value, ay.value
+
+
+def rhs2d(cfg, u, alpha_x=-1.0, alpha_y=-1.0, points=False):
+    """One evaluation of Eq. (ode2).  Returns (rhs, ulim, flags, indicator),
+    plus the reconstructed point values [C][np][ny][nx] if points."""
+    u = _f64(u)
+    rhs = np.empty_like(u)
+    ulim = np.empty_like(u)
+    flags = np.zeros((cfg.ny, cfg.nx), dtype=np.uint8)
+    ind = np.zeros((cfg.ny, cfg.nx), dtype=np.float64)
+    ng = 2 if cfg.n_gauss == 2 else 3
+    pts = np.zeros((u.shape[0], 4 * ng + ng * ng, cfg.ny, cfg.nx))
+    st = lib().hwo2d_rhs_ex(ctypes.byref(cfg), _p(u), alpha_x, alpha_y, _p(rhs), _p(ulim),
+                            flags.ctypes.data_as(_PU8), _p(ind), _p(pts))
+    if st != 0:
+        raise FloatingPointError("oracle rhs2d status %d" % st)
+    if points:
+        return rhs, ulim, flags, ind, pts
+    return rhs, ulim, flags, ind
+
+
+def step2d(cfg, u, dt):
+    u = _f64(u).copy()
+    nt = ctypes.c_long(0)
+    st = lib().hwo2d_step(ctypes.byref(cfg), _p(u), dt, ctypes.byref(nt))
+    if st != 0:
+        raise FloatingPointError("oracle step2d status %d" % st)
+    return u, nt.value
+
+
+def run2d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
+          lin_w_per_step=None):
+    u = _f64(u).copy()
+    t = ctypes.c_double(0.0)
+    nt = ctypes.c_long(0)
+    lw = None
+    if lin_w_per_step is not None:
+        lw_arr = _f64(lin_w_per_step)
+        assert nsteps >= 0 and lw_arr.size >= 5 * nsteps
+        lw = _p(lw_arr)
+    st = lib().hwo2d_run(ctypes.byref(cfg), _p(u), nsteps, cfl, t0, t_final, dt_fixed, lw,
+                         ctypes.byref(t), ctypes.byref(nt))
+    if st != 0:
+        raise FloatingPointError("oracle run2d status %d" % st)
+    return u, t.value, nt.value
+
+
+def recon_candidates2d(ub9, vb9, wb9, n_gauss=3):
+    ub9, vb9, wb9 = _f64(ub9), _f64(vb9), _f64(wb9)
+    np_ = 4 * n_gauss + n_gauss * n_gauss
+    val = np.zeros(5 * 21)
+    beta = np.zeros(5)
+    lib().hwo2d_recon_candidates(_p(ub9), _p(vb9), _p(wb9), n_gauss, _p(val), _p(beta))
+    return val[:5 * np_].reshape(5, np_), beta
+
+
+def linear_weights2d(n_gauss=3):
+    np_ = 4 * n_gauss + n_gauss * n_gauss
+    W = np.zeros(21 * 19)
+    lib().hwo2d_linear_weights(n_gauss, _p(W))
+    return W[:np_ * 19].reshape(np_, 19)
+
+
+def p0_coeffs2d(d19):
+    d19 = _f64(d19)
+    c = np.zeros(15)
+    lib().hwo2d_p0_coeffs(_p(d19), _p(c))
+    return c
+
+
+def quad_coeffs2d(n, d19):
+    d19 = _f64(d19)
+    c = np.zeros(6)
+    lib().hwo2d_quad_coeffs(int(n), _p(d19), _p(c))
+    return c
+
+
+def beta_of_coeffs2d(degree, c, ratio=1.0):
+    c = _f64(c)
+    return lib().hwo2d_beta_of_coeffs(int(degree), _p(c), ratio)
+
+
+def euler2d_flux(g, U, direction):
+    U = _f64(U)
+    F = np.zeros(4)
+    lib().hwo_euler2d_flux(g, _p(U), int(direction), _p(F))
+    return F
+
+
+def euler2d_eigen(g, U, direction):
+    U = _f64(U)
+    R = np.zeros(16)
+    L = np.zeros(16)
+    lib().hwo_euler2d_eigen(g, _p(U), int(direction), _p(R), _p(L))
+    return R.reshape(4, 4), L.reshape(4, 4)
