@@ -55,7 +55,8 @@ enum { HWENO_FP32 = 0, HWENO_FP64 = 1 };
 typedef struct {
   int dim;                /* 1 or 2 */
   int system;             /* HWENO_BURGERS or HWENO_EULER */
-  int nx, ny;             /* cells per direction (ny ignored for dim 1); nx, ny >= 4 */
+  int nx, ny;             /* cells per direction (ny ignored for dim 1); nx, ny >= 4;
+                             2D cells must be square: (x1-x0)/nx = (y1-y0)/ny */
   double x0, x1, y0, y1;  /* domain [x0,x1] x [y0,y1] */
   int bc;                 /* HWENO_BC_PERIODIC or HWENO_BC_OUTFLOW, all sides */
   double gas_gamma;       /* ratio of specific heats (Euler), > 1 */

@@ -166,17 +166,31 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _state1d(cfg, u):
+    u = _f64(u)
+    if u.size != cfg.ncomp * 2 * cfg.nx:
+        raise ValueError("state of %d values does not match the 1D configuration" % u.size)
+    return u
+
+
+def _state2d(cfg, u):
+    u = _f64(u)
+    if u.size != cfg.ncomp * 3 * cfg.nx * cfg.ny:
+        raise ValueError("state of %d values does not match the 2D configuration" % u.size)
+    return u
+
+
 # ----------------------------------------------------------------------------- 1D
 
 def alpha1d(cfg, u):
-    u = _f64(u)
+    u = _state1d(cfg, u)
     return lib().hwo1d_alpha(ctypes.byref(cfg), _p(u))
 
 
 def rhs1d(cfg, u, alpha=-1.0, faces=False):
     """One evaluation of Eq. (odeH).  Returns (rhs, ulim, flags, indicator),
     plus the interface values [C][2][nx] (u^+_{i-1/2}, u^-_{i+1/2}) if faces."""
-    u = _f64(u)
+    u = _state1d(cfg, u)
     rhs = np.empty_like(u)
     ulim = np.empty_like(u)
     fc = np.empty_like(u)
@@ -192,13 +206,13 @@ def rhs1d(cfg, u, alpha=-1.0, faces=False):
 
 
 def dt1d(cfg, u, cfl, t=0.0, t_final=-1.0):
-    u = _f64(u)
+    u = _state1d(cfg, u)
     return lib().hwo1d_dt(ctypes.byref(cfg), _p(u), cfl, t, t_final)
 
 
 def step1d(cfg, u, dt):
     """One SSP-RK3 step with the given dt; returns (u_new, troubled count)."""
-    u = _f64(u).copy()
+    u = _state1d(cfg, u).copy()
     nt = ctypes.c_long(0)
     st = lib().hwo1d_step(ctypes.byref(cfg), _p(u), dt, ctypes.byref(nt))
     if st != 0:
@@ -209,7 +223,7 @@ def step1d(cfg, u, dt):
 def run1d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
           lin_w_per_step=None):
     """Repeated SSP-RK3 steps; returns (u, t, troubled cell-stage count)."""
-    u = _f64(u).copy()
+    u = _state1d(cfg, u).copy()
     t = ctypes.c_double(0.0)
     nt = ctypes.c_long(0)
     lw = None
@@ -275,7 +289,7 @@ MONO2D = [(a, d - a) for d in range(5) for a in range(d, -1, -1)]
 
 
 def alpha2d(cfg, u):
-    u = _f64(u)
+    u = _state2d(cfg, u)
     ax, ay = ctypes.c_double(), ctypes.c_double()
     lib().hwo2d_alpha(ctypes.byref(cfg), _p(u), ctypes.byref(ax), ctypes.byref(ay))
     return ax.value, ay.value
@@ -284,7 +298,7 @@ def alpha2d(cfg, u):
 def rhs2d(cfg, u, alpha_x=-1.0, alpha_y=-1.0, points=False):
     """One evaluation of Eq. (ode2).  Returns (rhs, ulim, flags, indicator),
     plus the reconstructed point values [C][np][ny][nx] if points."""
-    u = _f64(u)
+    u = _state2d(cfg, u)
     rhs = np.empty_like(u)
     ulim = np.empty_like(u)
     flags = np.zeros((cfg.ny, cfg.nx), dtype=np.uint8)
@@ -301,7 +315,7 @@ def rhs2d(cfg, u, alpha_x=-1.0, alpha_y=-1.0, points=False):
 
 
 def step2d(cfg, u, dt):
-    u = _f64(u).copy()
+    u = _state2d(cfg, u).copy()
     nt = ctypes.c_long(0)
     st = lib().hwo2d_step(ctypes.byref(cfg), _p(u), dt, ctypes.byref(nt))
     if st != 0:
@@ -311,7 +325,7 @@ def step2d(cfg, u, dt):
 
 def run2d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
           lin_w_per_step=None):
-    u = _f64(u).copy()
+    u = _state2d(cfg, u).copy()
     t = ctypes.c_double(0.0)
     nt = ctypes.c_long(0)
     lw = None

@@ -1,0 +1,823 @@
+// One fused kernel per third-order TVD Runge-Kutta stage of the 2D hybrid
+// HWENO scheme (Zhao & Qiu, arXiv:2002.08816, Sec. 2.2).
+//
+// A CTA owns a TX x TY tile of cells.  It stages the tile and a 3-cell halo
+// of the stage input in shared memory, then, on chip:
+//   1. alpha_x, alpha_y from the slots the producer of the stage input left
+//      (global Lax-Friedrichs fluxes); stage 1 turns them into
+//      dt = CFL / (alpha_x/dx + alpha_y/dy), clipped to t_final;
+//   2. Step 4 for the tile and 2 halo cells: KXRCF flags (FP32 kernels decide
+//      in FP32 when the rounding-error bound allows, else in FP64) and the
+//      first moments of troubled cells modified dimension by dimension with
+//      the 1D Step 1 formula (Euler: characteristic fields of the x- and of
+//      the y-Jacobian at the cell average);
+//   3. Step 5.1/5.2 at the interface Gauss points of the tile's cells and of
+//      the one-cell cross halo: linear p0 (the quartic on the 3x3 stencil),
+//      or HWENO when the 3x3 stencil holds a troubled cell (Euler: x-faces in
+//      the x characteristic fields, y-faces in the y fields);
+//   4. own cells: Step 5.3 at the interior Gauss points, Lax-Friedrichs
+//      fluxes at the 4 ng interface points, Eq. (ode2) and Eq. (RK);
+//   5. the tile's wave-speed maxima (x and y) into the slots for the next
+//      stage, the troubled count and the status bits.
+// The reconstruction arithmetic is the generated straight-line code of
+// hweno2d_coef.cuh (square cells).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hweno1d_recon.cuh"
+#include "hweno2d_coef.cuh"
+#include "hweno_device.cuh"
+#include "hweno_internal.h"
+
+namespace hw {
+namespace {
+
+constexpr int TX = kTile2DX, TY = kTile2DY;
+constexpr int NT = kThreads2D;
+constexpr int NW = NT / 32;
+constexpr int RX = TX + 6, RY = TY + 6;  // raw tile, 3-cell halo
+constexpr int LX = TX + 4, LY = TY + 4;  // flags and modified moments, 2-cell halo
+static_assert(TX * TY == NT, "one own cell per thread");
+
+template <typename R, int C, int NG>
+struct Smem2D {
+  R u[C][3][RY][RX];            // stage input
+  R vl[C][LY][LX];              // modified x-moments
+  R wl[C][LY][LX];              // modified y-moments
+  R xf[C][2 * NG][TY][TX + 2];  // x-face values (left NG, right NG) of cells -1..TX
+  R yf[C][2 * NG][TY + 2][TX];  // y-face values (bottom NG, top NG) of cells -1..TY
+  uint8_t fl[LY][LX];
+  R red[2][NW];
+  int cnt[NW];
+  R amax[2][NW];
+};
+
+// ------------------------------------------------------------ physics (2D)
+
+template <typename R>
+struct Euler2D {
+  static __device__ __forceinline__ void flux(R g, const R* U, int dir, R* F) {
+    const R rho = U[0], m = U[1], n = U[2], E = U[3];
+    const R ir = sizeof(R) == 4 ? R(__frcp_rn((float)rho)) : R(1) / rho;
+    const R mu = sizeof(R) == 4 ? m * ir : m / rho;
+    const R nu = sizeof(R) == 4 ? n * ir : n / rho;
+    const R p = (g - R(1)) * (E - R(0.5) * (m * mu + n * nu));
+    const R vn = dir == 0 ? mu : nu;
+    F[0] = dir == 0 ? m : n;
+    F[1] = m * vn + (dir == 0 ? p : R(0));
+    F[2] = n * vn + (dir == 1 ? p : R(0));
+    F[3] = vn * (E + p);
+  }
+  // Right (columns: v-c, v, v, v+c with v the normal velocity) and left
+  // eigenvectors of dF/dU (dir 0) or dG/dU (dir 1) at U.
+  static __device__ __forceinline__ void eigen(R g, const R* U, int dir, R Rm[4][4], R Lm[4][4]) {
+    const R rho = U[0], mu = U[1] / rho, nu = U[2] / rho;
+    const R q2 = mu * mu + nu * nu;
+    const R p = (g - R(1)) * (U[3] - R(0.5) * rho * q2);
+    const R c = sqrt(g * p / rho);
+    const R H = (U[3] + p) / rho;
+    const R ic = R(1) / c;
+    const R b1 = (g - R(1)) * ic * ic;
+    const R b2 = R(0.5) * b1 * q2;
+    const R vn = dir == 0 ? mu : nu;
+    // columns
+    Rm[0][0] = R(1); Rm[0][1] = R(1); Rm[0][3] = R(1);
+    Rm[3][0] = H - vn * c; Rm[3][1] = R(0.5) * q2; Rm[3][3] = H + vn * c;
+    if (dir == 0) {
+      Rm[1][0] = mu - c; Rm[1][1] = mu; Rm[1][3] = mu + c;
+      Rm[2][0] = nu;     Rm[2][1] = nu; Rm[2][3] = nu;
+      Rm[0][2] = R(0); Rm[1][2] = R(0); Rm[2][2] = R(1); Rm[3][2] = nu;
+    } else {
+      Rm[1][0] = mu;     Rm[1][1] = mu; Rm[1][3] = mu;
+      Rm[2][0] = nu - c; Rm[2][1] = nu; Rm[2][3] = nu + c;
+      Rm[0][2] = R(0); Rm[1][2] = R(1); Rm[2][2] = R(0); Rm[3][2] = mu;
+    }
+    // rows
+    const R ex = dir == 0 ? ic : R(0), ey = dir == 1 ? ic : R(0);
+    Lm[0][0] = R(0.5) * (b2 + vn * ic);
+    Lm[0][1] = R(-0.5) * (b1 * mu + ex);
+    Lm[0][2] = R(-0.5) * (b1 * nu + ey);
+    Lm[0][3] = R(0.5) * b1;
+    Lm[1][0] = R(1) - b2;
+    Lm[1][1] = b1 * mu;
+    Lm[1][2] = b1 * nu;
+    Lm[1][3] = -b1;
+    if (dir == 0) {
+      Lm[2][0] = -nu; Lm[2][1] = R(0); Lm[2][2] = R(1); Lm[2][3] = R(0);
+    } else {
+      Lm[2][0] = -mu; Lm[2][1] = R(1); Lm[2][2] = R(0); Lm[2][3] = R(0);
+    }
+    Lm[3][0] = R(0.5) * (b2 - vn * ic);
+    Lm[3][1] = R(-0.5) * (b1 * mu - ex);
+    Lm[3][2] = R(-0.5) * (b1 * nu - ey);
+    Lm[3][3] = R(0.5) * b1;
+  }
+};
+
+template <typename R, int C>
+__device__ __forceinline__ void phys_flux2(R gas, const R* U, int dir, R* F) {
+  if constexpr (C == 1) {
+    F[0] = R(0.5) * U[0] * U[0];
+  } else {
+    Euler2D<R>::flux(gas, U, dir, F);
+  }
+}
+
+// max |f'| (dir 0) and |g'| (dir 1) at a cell average; NaN when not physical
+template <typename R, int C>
+__device__ __forceinline__ void wave_speeds2(R gas, const R* U, R& sx, R& sy) {
+  if constexpr (C == 1) {
+    sx = sy = fabs(U[0]);
+  } else {
+    const R rho = U[0];
+    if (!(rho > R(0))) {
+      sx = sy = R(NAN);
+      return;
+    }
+    const R mu = U[1] / rho, nu = U[2] / rho;
+    const R p = (gas - R(1)) * (U[3] - R(0.5) * rho * (mu * mu + nu * nu));
+    if (!(p > R(0))) {
+      sx = sy = R(NAN);
+      return;
+    }
+    const R c = sqrt(gas * p / rho);
+    sx = fabs(mu) + c;
+    sy = fabs(nu) + c;
+  }
+}
+
+// --------------------------------------------------------- KXRCF (2D)
+// Reading: I = |dy jx + dx jy| / (h (dx + dy) max(|u0|, 1e-12)), h =
+// sqrt(dx^2 + dy^2)/2, jx / jy the degree-1 trace jumps across the inflow x-
+// and y-faces (left / bottom when the velocity component is >= 0).
+
+__device__ __forceinline__ double jump64(double u0, double v0, double unb, double vnb, bool low) {
+  return low ? __dsub_rn(__dsub_rn(u0, __dmul_rn(6.0, v0)), __dadd_rn(unb, __dmul_rn(6.0, vnb)))
+             : __dsub_rn(__dadd_rn(u0, __dmul_rn(6.0, v0)), __dsub_rn(unb, __dmul_rn(6.0, vnb)));
+}
+
+// u0/v0/w0 the cell, (uxn, vxn) its inflow x-neighbour, (uyn, wyn) its inflow
+// y-neighbour; lowx / lowy: the inflow faces are the left / bottom ones.
+__device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0, double uxn,
+                                                double vxn, double uyn, double wyn, bool lowx,
+                                                bool lowy, const Kx2& k) {
+  const double jx = jump64(u0, v0, uxn, vxn, lowx);
+  const double jy = jump64(u0, w0, uyn, wyn, lowy);
+  const double num = __dadd_rn(__dmul_rn(k.dy, jx), __dmul_rn(k.dx, jy));
+  const double nrm = fmax(fabs(u0), 1e-12);
+  return fabs(num) / __dmul_rn(k.den_h, nrm) > k.thr;
+}
+
+__device__ __forceinline__ bool kxrcf2_troubled(float u0, float v0, float w0, float uxn, float vxn,
+                                                float uyn, float wyn, bool lowx, bool lowy,
+                                                const Kx2& k) {
+  const float jx = lowx ? (u0 - 6.0f * v0) - (uxn + 6.0f * vxn) : (u0 + 6.0f * v0) - (uxn - 6.0f * vxn);
+  const float jy = lowy ? (u0 - 6.0f * w0) - (uyn + 6.0f * wyn) : (u0 + 6.0f * w0) - (uyn - 6.0f * wyn);
+  const float sx = fabsf(u0) + 6.0f * fabsf(v0) + fabsf(uxn) + 6.0f * fabsf(vxn);
+  const float sy = fabsf(u0) + 6.0f * fabsf(w0) + fabsf(uyn) + 6.0f * fabsf(wyn);
+  const float num = fabsf(k.fdy * jx + k.fdx * jy);
+  // |num - exact| <= 2^-24 (3 dy sx + 3 dx sy + 3 |num|) to first order
+  const float e = 1.0e-6f * (k.fdy * sx + k.fdx * sy);
+  const float r = k.fthr_den * fmaxf(fabsf(u0), 1e-12f);
+  if (num - e > r * (1.0f + 4.8e-7f)) return true;
+  if (num + e < r * (1.0f - 4.8e-7f)) return false;
+  return kxrcf2_troubled((double)u0, (double)v0, (double)w0, (double)uxn, (double)vxn,
+                         (double)uyn, (double)wyn, lowx, lowy, k);
+}
+
+// ------------------------------------------------------ HWENO helpers (2D)
+
+template <int NG, typename R>
+__device__ __forceinline__ void p0_faces(const R* d, R* o) {
+  if constexpr (NG == 3) hw2::p0_faces_ng3(d, o); else hw2::p0_faces_ng2(d, o);
+}
+template <int NG, typename R>
+__device__ __forceinline__ void p0_interior(const R* d, R* o) {
+  if constexpr (NG == 3) hw2::p0_interior_ng3(d, o); else hw2::p0_interior_ng2(d, o);
+}
+template <int NG, typename R>
+__device__ __forceinline__ void q_faces(int n, const R* d, R* o) {
+  if constexpr (NG == 3) {
+    if (n == 1) hw2::q1_faces_ng3(d, o);
+    else if (n == 2) hw2::q2_faces_ng3(d, o);
+    else if (n == 3) hw2::q3_faces_ng3(d, o);
+    else hw2::q4_faces_ng3(d, o);
+  } else {
+    if (n == 1) hw2::q1_faces_ng2(d, o);
+    else if (n == 2) hw2::q2_faces_ng2(d, o);
+    else if (n == 3) hw2::q3_faces_ng2(d, o);
+    else hw2::q4_faces_ng2(d, o);
+  }
+}
+
+// HWENO values (Step 5.1) at the interface points [p_lo, p_hi) of one scalar
+// field from its 19 data: tau of Eq. (tao4), weights of Eq. (99), and the
+// combination omega_0 (p0/gamma_0 - sum gamma_n/gamma_0 p_n) + sum omega_n p_n
+// accumulated candidate by candidate (it is linear in the candidates).
+template <int NG, typename R>
+__device__ __forceinline__ void hweno2d_faces(const R* d, const R* gam, R eps, int p_lo,
+                                              int p_hi, R* out) {
+  constexpr int NF = 4 * NG;
+  R b[5];
+  b[0] = hw2::beta_p0(d);
+  b[1] = hw2::beta_q1(d);
+  b[2] = hw2::beta_q2(d);
+  b[3] = hw2::beta_q3(d);
+  b[4] = hw2::beta_q4(d);
+  const R s = R(0.25) * (fabs(b[0] - b[1]) + fabs(b[0] - b[2]) + fabs(b[0] - b[3]) + fabs(b[0] - b[4]));
+  const R tau = s * s;
+  R a[5], sum = R(0);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) {
+    a[n] = gam[n] * (R(1) + tau / (b[n] + eps));
+    sum += a[n];
+  }
+  const R inv = R(1) / sum;
+  const R c0 = a[0] * inv / gam[0];
+  R tmp[NF];
+  p0_faces<NG>(d, tmp);
+#pragma unroll
+  for (int p = 0; p < NF; ++p)
+    if (p >= p_lo && p < p_hi) out[p] = c0 * tmp[p];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const R cn = a[n + 1] * inv - c0 * gam[n + 1];
+    q_faces<NG>(n + 1, d, tmp);
+#pragma unroll
+    for (int p = 0; p < NF; ++p)
+      if (p >= p_lo && p < p_hi) out[p] += cn * tmp[p];
+  }
+}
+
+// The 19 data of component c of the cell at own-tile coordinates (ci, cj):
+// ubar of cells 1..9, vbar and wbar (modified) of cells 2, 4, 5, 6, 8.
+template <typename S, typename R>
+__device__ __forceinline__ void gather19(const S& sm, int c, int ci, int cj, R* d) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d[k] = sm.u[c][0][cj + 3 + k / 3 - 1][ci + 3 + k % 3 - 1];
+  const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    d[9 + k] = sm.vl[c][cj + 2 + my[k]][ci + 2 + mx[k]];
+    d[14 + k] = sm.wl[c][cj + 2 + my[k]][ci + 2 + mx[k]];
+  }
+}
+
+template <typename R, int C, int NG>
+__global__ void __launch_bounds__(NT) stage2d_kernel(Stage2DArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem2D<R, C, NG>& sm = *reinterpret_cast<Smem2D<R, C, NG>*>(smem_raw);
+  constexpr int NF = 4 * NG, NI = NG * NG;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nx = a.nx, ny = a.ny;
+  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+  const size_t plane = (size_t)nx * ny;
+  const R* __restrict__ w = static_cast<const R*>(a.w);
+
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  R gam[5], eps, gas, inv_dx, inv_dy, cfl;
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) gam[k] = a.f32[k];
+    eps = a.f32[5]; gas = a.f32[6]; inv_dx = a.f32[7]; inv_dy = a.f32[8]; cfl = a.f32[9];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) gam[k] = a.gam[k];
+    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx; inv_dy = a.inv_dy; cfl = a.cfl;
+  }
+
+  // ---- 1. alpha_x, alpha_y, the time bookkeeping, the tile and its halo
+  const R* a_in = static_cast<const R*>(a.a_in);
+  R ax = R(0), ay = R(0);
+  for (int k = tid; k < a.nin; k += NT) {
+    ax = fmax(ax, a_in[k]);
+    ay = fmax(ay, a_in[a.nin + k]);
+  }
+  R rem = R(0), dt_prev = R(0);
+  if (a.stage == 1) rem = sc_rem<R>(a.sc);
+  else if (a.stage > 1) dt_prev = sc_dt<R>(a.sc);
+  const int ox = tid % TX, oy = tid / TX;  // own cell of this thread
+  const int gi = bx0 + ox, gj = by0 + oy;
+  const bool own = gi < nx && gj < ny;
+  R u0c[C][3];
+  if (a.stage >= 2 && own) {
+    const R* u0 = static_cast<const R*>(a.u0);
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) u0c[c][m] = u0[(3 * c + m) * plane + (size_t)gj * nx + gi];
+  }
+  for (int k = tid; k < RX * RY; k += NT) {
+    const int rx = k % RX, ry = k / RX;
+    const int si = bc_map(bx0 - 3 + rx, nx, a.bc), sj = bc_map(by0 - 3 + ry, ny, a.bc);
+    const size_t s = (size_t)sj * nx + si;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax = fmax(ax, __shfl_xor_sync(0xffffffffu, ax, o));
+    ay = fmax(ay, __shfl_xor_sync(0xffffffffu, ay, o));
+  }
+  if (lane == 0) {
+    sm.amax[0][warp] = ax;
+    sm.amax[1][warp] = ay;
+  }
+  __syncthreads();
+  asm volatile("griddepcontrol.launch_dependents;");
+  R alx = sm.amax[0][0], aly = sm.amax[1][0];
+#pragma unroll
+  for (int k = 1; k < NW; ++k) {
+    alx = fmax(alx, sm.amax[0][k]);
+    aly = fmax(aly, sm.amax[1][k]);
+  }
+  R dt = dt_prev;
+  if (a.stage == 1) {
+    dt = cfl / (alx * inv_dx + aly * inv_dy);
+    unsigned last = 0;
+    if (rem <= R(0)) {
+      dt = R(0);
+    } else if (dt >= rem) {
+      dt = rem;
+      last = 1;
+    }
+    if (!(alx + aly > R(0)) || !isfinite(dt)) dt = R(0);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+      sc_dt<R>(a.sc) = dt;
+      a.sc->last = last;
+    }
+  }
+  if (a.stage > 0 && !(dt > R(0))) return;  // uniform over the grid
+  if (a.a_zero && blockIdx.x == 0 && blockIdx.y == 0 && tid < 2 * kAlphaSlots)
+    static_cast<R*>(a.a_zero)[tid] = R(0);
+
+  // ---- 2. Step 4 on the tile plus 2 halo cells
+  for (int k = tid; k < LX * LY; k += NT) {
+    const int lx = k % LX, ly = k / LX;
+    const int rx = lx + 1, ry = ly + 1;  // raw index of the cell
+    int flag;
+    if (a.mode == 1) {
+      flag = 1;
+    } else if (a.mode == 2) {
+      flag = 0;
+    } else {
+      bool lowx, lowy;
+      if constexpr (C == 1) {
+        lowx = lowy = sm.u[0][0][ry][rx] >= R(0);
+      } else {
+        lowx = inflow_left(sm.u[0][0][ry][rx], sm.u[1][0][ry][rx]);
+        lowy = inflow_left(sm.u[0][0][ry][rx], sm.u[2][0][ry][rx]);
+      }
+      const int nxx = lowx ? rx - 1 : rx + 1, nyy = lowy ? ry - 1 : ry + 1;
+      const int ci = 0;
+      flag = kxrcf2_troubled(sm.u[ci][0][ry][rx], sm.u[ci][1][ry][rx], sm.u[ci][2][ry][rx],
+                             sm.u[ci][0][ry][nxx], sm.u[ci][1][ry][nxx], sm.u[ci][0][nyy][rx],
+                             sm.u[ci][2][nyy][rx], lowx, lowy, a.kx);
+      if constexpr (C == 4) {
+        flag = flag || kxrcf2_troubled(sm.u[3][0][ry][rx], sm.u[3][1][ry][rx], sm.u[3][2][ry][rx],
+                                       sm.u[3][0][ry][nxx], sm.u[3][1][ry][nxx],
+                                       sm.u[3][0][nyy][rx], sm.u[3][2][nyy][rx], lowx, lowy, a.kx);
+      }
+    }
+    sm.fl[ly][lx] = (uint8_t)flag;
+    if (!flag) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        sm.vl[c][ly][lx] = sm.u[c][1][ry][rx];
+        sm.wl[c][ly][lx] = sm.u[c][2][ry][rx];
+      }
+    } else if constexpr (C == 1) {
+      sm.vl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx],
+                                            sm.u[0][0][ry][rx + 1], sm.u[0][1][ry][rx - 1],
+                                            sm.u[0][1][ry][rx + 1], gam, eps);
+      sm.wl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx],
+                                            sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
+                                            sm.u[0][2][ry + 1][rx], gam, eps);
+    } else {
+      R U[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][ry][rx];
+#pragma unroll 1
+      for (int dir = 0; dir < 2; ++dir) {
+        R Rm[4][4], Lm[4][4];
+        Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+        const int sx = dir == 0 ? 1 : 0, sy = dir == 0 ? 0 : 1;
+        const int mom = dir == 0 ? 1 : 2;
+        R q[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          R wv[5];
+#pragma unroll
+          for (int s = 0; s < 3; ++s) {
+            wv[s] = R(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) wv[s] += Lm[f][c] * sm.u[c][0][ry + (s - 1) * sy][rx + (s - 1) * sx];
+          }
+          wv[3] = R(0);
+          wv[4] = R(0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            wv[3] += Lm[f][c] * sm.u[c][mom][ry - sy][rx - sx];
+            wv[4] += Lm[f][c] * sm.u[c][mom][ry + sy][rx + sx];
+          }
+          q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const R v = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2] + Rm[c][3] * q[3];
+          if (dir == 0) sm.vl[c][ly][lx] = v; else sm.wl[c][ly][lx] = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. interface values of the own cells (all faces) and of the cross
+  //         halo (left column: right face, right column: left face, bottom
+  //         row: top face, top row: bottom face)
+  for (int item = tid; item < TX * TY + 2 * TX + 2 * TY; item += NT) {
+    int ci, cj, p_lo, p_hi;  // own-tile coordinates of the cell, point range
+    if (item < TX * TY) {
+      ci = item % TX; cj = item / TX; p_lo = 0; p_hi = NF;
+    } else {
+      const int h = item - TX * TY;
+      if (h < TY) { ci = -1; cj = h; p_lo = NG; p_hi = 2 * NG; }
+      else if (h < 2 * TY) { ci = TX; cj = h - TY; p_lo = 0; p_hi = NG; }
+      else if (h < 2 * TY + TX) { ci = h - 2 * TY; cj = -1; p_lo = 3 * NG; p_hi = 4 * NG; }
+      else { ci = h - 2 * TY - TX; cj = TY; p_lo = 2 * NG; p_hi = 3 * NG; }
+    }
+    bool hw = false;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 2 + dj][ci + 2 + di] != 0;
+    // point p of component c of this cell into the face arrays
+    auto store = [&](int c, int p, R v) {
+      if (p < NG) {
+        sm.xf[c][p][cj][ci + 1] = v;  // left face
+      } else if (p < 2 * NG) {
+        sm.xf[c][p][cj][ci + 1] = v;  // right face
+      } else if (p < 3 * NG) {
+        sm.yf[c][p - 2 * NG][cj + 1][ci] = v;  // bottom face
+      } else {
+        sm.yf[c][p - 2 * NG][cj + 1][ci] = v;  // top face
+      }
+    };
+    if (!hw || C == 1) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        R d[19], v[NF];
+        gather19(sm, c, ci, cj, d);
+        if (!hw)
+          p0_faces<NG>(d, v);
+        else
+          hweno2d_faces<NG>(d, gam, eps, p_lo, p_hi, v);
+#pragma unroll
+        for (int p = 0; p < NF; ++p)
+          if (p >= p_lo && p < p_hi) store(c, p, v[p]);
+      }
+    } else if constexpr (C == 4) {
+      R U[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][cj + 3][ci + 3];
+#pragma unroll 1
+      for (int dir = 0; dir < 2; ++dir) {
+        const int lo = dir == 0 ? 0 : 2 * NG, hi = dir == 0 ? 2 * NG : 4 * NG;
+        const int plo = p_lo > lo ? p_lo : lo, phi = p_hi < hi ? p_hi : hi;
+        if (plo >= phi) continue;
+        R Rm[4][4], Lm[4][4];
+        Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+        R acc[4][NF];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int p = 0; p < NF; ++p) acc[c][p] = R(0);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          // characteristic field f of the 19 data (Remark 4)
+          R e[19], t[19];
+#pragma unroll
+          for (int k = 0; k < 19; ++k) e[k] = R(0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            gather19(sm, c, ci, cj, t);
+#pragma unroll
+            for (int k = 0; k < 19; ++k) e[k] += Lm[f][c] * t[k];
+          }
+          R chv[NF];
+          hweno2d_faces<NG>(e, gam, eps, plo, phi, chv);
+#pragma unroll
+          for (int p = 0; p < NF; ++p)
+            if (p >= plo && p < phi)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[c][p] += Rm[c][f] * chv[p];
+        }
+#pragma unroll
+        for (int p = 0; p < NF; ++p)
+          if (p >= plo && p < phi)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) store(c, p, acc[c][p]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 4. own cells: interior points, fluxes, Eq. (ode2), Eq. (RK)
+  constexpr double r15 = 0.38729833462074168852;  // sqrt(15)/10
+  constexpr double r3 = 0.28867513459481288225;   // sqrt(3)/6
+  const R gw[3] = {NG == 3 ? R(5.0 / 18.0) : R(0.5), NG == 3 ? R(4.0 / 9.0) : R(0.5), R(5.0 / 18.0)};
+  const R gx[3] = {NG == 3 ? R(-r15) : R(-r3), NG == 3 ? R(0) : R(r3), R(r15)};
+  const int ci = ox, cj = oy;
+  int myflag = 0;
+  R spx = R(0), spy = R(0);
+  unsigned bad = 0;
+  {
+    myflag = sm.fl[cj + 2][ci + 2];
+    const R hax = R(0.5) * alx, hay = R(0.5) * aly;
+    R Fv[C], Gv[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) Fv[c] = Gv[c] = R(0);
+    {
+      R inter[C][NI];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        R d[19];
+        gather19(sm, c, ci, cj, d);
+        p0_interior<NG>(d, inter[c]);
+      }
+#pragma unroll
+      for (int l = 0; l < NG; ++l)
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          R U[C], f[C], g[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) U[c] = inter[c][l * NG + k];
+          phys_flux2<R, C>(gas, U, 0, f);
+          phys_flux2<R, C>(gas, U, 1, g);
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            Fv[c] += gw[k] * gw[l] * f[c];
+            Gv[c] += gw[k] * gw[l] * g[c];
+          }
+        }
+    }
+    R sfx[C], sfs[C], sfxe[C], sgy[C], sgs[C], sgyx[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) sfx[c] = sfs[c] = sfxe[c] = sgy[c] = sgs[c] = sgyx[c] = R(0);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      R am[C], ap[C], fa[C], fb[C], FLk[C], FRk[C], GBk[C], GTk[C];
+      // x_{i-1/2}: u^- = right face of cell i-1, u^+ = own left face
+#pragma unroll
+      for (int c = 0; c < C; ++c) { am[c] = sm.xf[c][NG + k][cj][ci]; ap[c] = sm.xf[c][k][cj][ci + 1]; }
+      phys_flux2<R, C>(gas, am, 0, fa); phys_flux2<R, C>(gas, ap, 0, fb);
+#pragma unroll
+      for (int c = 0; c < C; ++c) FLk[c] = R(0.5) * (fa[c] + fb[c]) - hax * (ap[c] - am[c]);
+      // x_{i+1/2}: u^- = own right face, u^+ = left face of cell i+1
+#pragma unroll
+      for (int c = 0; c < C; ++c) { am[c] = sm.xf[c][NG + k][cj][ci + 1]; ap[c] = sm.xf[c][k][cj][ci + 2]; }
+      phys_flux2<R, C>(gas, am, 0, fa); phys_flux2<R, C>(gas, ap, 0, fb);
+#pragma unroll
+      for (int c = 0; c < C; ++c) FRk[c] = R(0.5) * (fa[c] + fb[c]) - hax * (ap[c] - am[c]);
+      // y_{j-1/2}: u^- = top face of cell j-1, u^+ = own bottom face
+#pragma unroll
+      for (int c = 0; c < C; ++c) { am[c] = sm.yf[c][NG + k][cj][ci]; ap[c] = sm.yf[c][k][cj + 1][ci]; }
+      phys_flux2<R, C>(gas, am, 1, fa); phys_flux2<R, C>(gas, ap, 1, fb);
+#pragma unroll
+      for (int c = 0; c < C; ++c) GBk[c] = R(0.5) * (fa[c] + fb[c]) - hay * (ap[c] - am[c]);
+      // y_{j+1/2}: u^- = own top face, u^+ = bottom face of cell j+1
+#pragma unroll
+      for (int c = 0; c < C; ++c) { am[c] = sm.yf[c][NG + k][cj + 1][ci]; ap[c] = sm.yf[c][k][cj + 2][ci]; }
+      phys_flux2<R, C>(gas, am, 1, fa); phys_flux2<R, C>(gas, ap, 1, fb);
+#pragma unroll
+      for (int c = 0; c < C; ++c) GTk[c] = R(0.5) * (fa[c] + fb[c]) - hay * (ap[c] - am[c]);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        sfx[c] += gw[k] * (FRk[c] - FLk[c]);
+        sfs[c] += gw[k] * (FLk[c] + FRk[c]);
+        sfxe[c] += gw[k] * gx[k] * (FRk[c] - FLk[c]);
+        sgy[c] += gw[k] * (GTk[c] - GBk[c]);
+        sgs[c] += gw[k] * (GBk[c] + GTk[c]);
+        sgyx[c] += gw[k] * gx[k] * (GTk[c] - GBk[c]);
+      }
+    }
+    R Uo[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const R L0 = -sfx[c] * inv_dx - sgy[c] * inv_dy;
+      const R L1 = -R(0.5) * sfs[c] * inv_dx + Fv[c] * inv_dx - sgyx[c] * inv_dy;
+      const R L2 = -sfxe[c] * inv_dx - R(0.5) * sgs[c] * inv_dy + Gv[c] * inv_dy;
+      const R W[3] = {sm.u[c][0][cj + 3][ci + 3], sm.vl[c][cj + 2][ci + 2], sm.wl[c][cj + 2][ci + 2]};
+      const R Lm[3] = {L0, L1, L2};
+      R o[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        if (a.stage == 0) {
+          o[m] = Lm[m];
+        } else {
+          const R s = W[m] + dt * Lm[m];
+          if (a.stage == 1) o[m] = s;
+          else {
+            const R ca = a.stage == 2 ? R(0.75) : R(1.0 / 3.0);
+            const R cb = a.stage == 2 ? R(0.25) : R(2.0 / 3.0);
+            o[m] = ca * u0c[c][m] + cb * s;
+          }
+        }
+        if (!isfinite(o[m])) bad |= ST_NONFINITE;
+      }
+      if (own) {
+        R* out = static_cast<R*>(a.out);
+        const size_t s = (size_t)gj * nx + gi;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) out[(3 * c + m) * plane + s] = o[m];
+        if (a.lim_out) {
+          R* lo = static_cast<R*>(a.lim_out);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) lo[(3 * c + m) * plane + s] = W[m];
+        }
+      }
+      Uo[c] = o[0];
+    }
+    if (own) {
+      if (a.flags_out) a.flags_out[(size_t)gj * nx + gi] = (uint8_t)myflag;
+      if (a.stage > 0) {
+        wave_speeds2<R, C>(gas, Uo, spx, spy);
+        if (!(spx == spx) || !(spy == spy)) {
+          bad |= ST_NONPHYSICAL;
+          spx = spy = R(0);
+        }
+      }
+    } else {
+      myflag = 0;
+      bad = 0;
+    }
+  }
+
+  // ---- 5. epilogue
+  for (int o = 16; o > 0; o >>= 1) {
+    spx = fmax(spx, __shfl_xor_sync(0xffffffffu, spx, o));
+    spy = fmax(spy, __shfl_xor_sync(0xffffffffu, spy, o));
+  }
+  const int wcnt = __popc(__ballot_sync(0xffffffffu, myflag));
+  if (lane == 0) {
+    sm.red[0][warp] = spx;
+    sm.red[1][warp] = spy;
+    sm.cnt[warp] = wcnt;
+  }
+  if (bad) atomicOr(&a.sc->status, bad);
+  __syncthreads();
+  if (warp == 0) {
+    R mx = lane < NW ? sm.red[0][lane] : R(0);
+    R my = lane < NW ? sm.red[1][lane] : R(0);
+    int cn = lane < NW ? sm.cnt[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+      cn += __shfl_xor_sync(0xffffffffu, cn, o);
+    }
+    if (lane == 0) {
+      const int slot = (blockIdx.y * gridDim.x + blockIdx.x) % kAlphaSlots;
+      if (a.a_out) {
+        atomic_max_nonneg(static_cast<R*>(a.a_out) + slot, mx);
+        atomic_max_nonneg(static_cast<R*>(a.a_out) + kAlphaSlots + slot, my);
+      }
+      if (cn) atomicAdd(&a.sc->troubled, (unsigned long long)cn);
+      if (a.stage == 3 && blockIdx.x == 0 && blockIdx.y == 0) {
+        DevScalars* sc = a.sc;
+        const double tf = sc->t_final;
+        const double t = sc->last ? tf : sc->t + (double)dt;
+        const double r = tf > 0.0 ? tf - t : (double)INFINITY;
+        sc->t = t;
+        sc->dt = (double)dt;
+        sc->rem = r;
+        sc->rem_f = (float)r;
+        sc->steps += 1;
+      }
+    }
+  }
+}
+
+template <typename R, int C>
+__global__ void __launch_bounds__(NT) alpha2d_kernel(const R* __restrict__ w, R* a_out, int nx,
+                                                    int ny, double gas, DevScalars* sc,
+                                                    int slots) {
+  __shared__ R red[2][NW];
+  const int gi = blockIdx.x * TX + threadIdx.x % TX, gj = blockIdx.y * TY + threadIdx.x / TX;
+  const size_t plane = (size_t)nx * ny;
+  R sx = R(0), sy = R(0);
+  if (gi < nx && gj < ny) {
+    R U[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) U[c] = w[(3 * c) * plane + (size_t)gj * nx + gi];
+    wave_speeds2<R, C>(R(gas), U, sx, sy);
+    if (!(sx == sx) || !(sy == sy)) {
+      atomicOr(&sc->status, (unsigned)ST_NONPHYSICAL);
+      sx = sy = R(0);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx = fmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
+    sy = fmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sx;
+    red[1][threadIdx.x >> 5] = sy;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NW; ++k) {
+      sx = fmax(sx, red[0][k]);
+      sy = fmax(sy, red[1][k]);
+    }
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    if (slots) {
+      atomic_max_nonneg(a_out + b % kAlphaSlots, sx);
+      atomic_max_nonneg(a_out + kAlphaSlots + b % kAlphaSlots, sy);
+    } else {
+      const int nt = gridDim.x * gridDim.y;
+      a_out[b] = sx;
+      a_out[nt + b] = sy;
+    }
+  }
+}
+
+template <typename R, int C, int NG>
+cudaError_t launch_stage2d_t(const Stage2DArgs& a, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sizeof(Smem2D<R, C, NG>);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, stage2d_kernel<R, C, NG>, a);
+}
+
+template <typename R, int C, int NG>
+cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(stage2d_kernel<R, C, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(Smem2D<R, C, NG>));
+}
+
+}  // namespace
+
+void finish_stage2d_args(Stage2DArgs& a) {
+  a.inv_dx = 1.0 / a.dx;
+  a.inv_dy = 1.0 / a.dy;
+  const double h = 0.5 * sqrt(a.dx * a.dx + a.dy * a.dy);
+  a.kx.dx = a.dx;
+  a.kx.dy = a.dy;
+  a.kx.den_h = h * (a.dx + a.dy);
+  a.kx.thr = a.thr;
+  a.kx.fdx = (float)a.dx;
+  a.kx.fdy = (float)a.dy;
+  a.kx.fthr_den = (float)(a.thr * a.kx.den_h);
+  for (int k = 0; k < 5; ++k) a.f32[k] = (float)a.gam[k];
+  a.f32[5] = (float)a.eps;
+  a.f32[6] = (float)a.gas;
+  a.f32[7] = (float)a.inv_dx;
+  a.f32[8] = (float)a.inv_dy;
+  a.f32[9] = (float)a.cfl;
+}
+
+cudaError_t prepare_stage2d(int system, int fp64, int ng) {
+  if (system == 0) {
+    if (fp64) return ng == 2 ? prepare_t<double, 1, 2>() : prepare_t<double, 1, 3>();
+    return ng == 2 ? prepare_t<float, 1, 2>() : prepare_t<float, 1, 3>();
+  }
+  if (fp64) return ng == 2 ? prepare_t<double, 4, 2>() : prepare_t<double, 4, 3>();
+  return ng == 2 ? prepare_t<float, 4, 2>() : prepare_t<float, 4, 3>();
+}
+
+cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s) {
+  if (a.system == 0) {
+    if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 1, 2>(a, s) : launch_stage2d_t<double, 1, 3>(a, s);
+    return a.ng == 2 ? launch_stage2d_t<float, 1, 2>(a, s) : launch_stage2d_t<float, 1, 3>(a, s);
+  }
+  if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 4, 2>(a, s) : launch_stage2d_t<double, 4, 3>(a, s);
+  return a.ng == 2 ? launch_stage2d_t<float, 4, 2>(a, s) : launch_stage2d_t<float, 4, 3>(a, s);
+}
+
+cudaError_t launch_alpha2d(const void* w, void* a_out, int nx, int ny, int system, int fp64,
+                           double gas, DevScalars* sc, int slots, cudaStream_t s) {
+  dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
+  if (system == 0) {
+    if (fp64)
+      alpha2d_kernel<double, 1><<<grid, NT, 0, s>>>(static_cast<const double*>(w), static_cast<double*>(a_out), nx, ny, gas, sc, slots);
+    else
+      alpha2d_kernel<float, 1><<<grid, NT, 0, s>>>(static_cast<const float*>(w), static_cast<float*>(a_out), nx, ny, gas, sc, slots);
+  } else {
+    if (fp64)
+      alpha2d_kernel<double, 4><<<grid, NT, 0, s>>>(static_cast<const double*>(w), static_cast<double*>(a_out), nx, ny, gas, sc, slots);
+    else
+      alpha2d_kernel<float, 4><<<grid, NT, 0, s>>>(static_cast<const float*>(w), static_cast<float*>(a_out), nx, ny, gas, sc, slots);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hw

@@ -24,7 +24,8 @@ struct hweno_ctx {
   hweno_config cfg;
   cudaStream_t stream = nullptr;     // caller's stream (may be the legacy default)
   cudaStream_t cap = nullptr;        // private stream used only to capture graphs
-  int C = 0, M = 0, n = 0, ntile = 0;
+  int C = 0, M = 0, n = 0, ntile = 0;  // n = cells; ntile = CTAs of one stage
+  int dim = 1;
   size_t elems = 0, esize = 0;
   void* U[3] = {nullptr, nullptr, nullptr};
   void* U0 = nullptr;
@@ -79,7 +80,62 @@ hw::Stage1DArgs base_args(const hweno_ctx* h) {
   return a;
 }
 
+hw::Stage2DArgs base_args2d(const hweno_ctx* h) {
+  hw::Stage2DArgs a;
+  memset(&a, 0, sizeof(a));
+  const hweno_config& c = h->cfg;
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.bc = c.bc;
+  a.mode = c.troubled_mode;
+  a.system = c.system;
+  a.fp64 = c.precision == HWENO_FP64;
+  a.ng = c.n_gauss;
+  a.dx = (c.x1 - c.x0) / c.nx;
+  a.dy = (c.y1 - c.y0) / c.ny;
+  a.cfl = c.cfl;
+  a.eps = c.eps;
+  a.thr = c.kxrcf_threshold;
+  a.gas = c.gas_gamma;
+  for (int k = 0; k < 5; ++k) a.gam[k] = c.lin_w[k];
+  hw::finish_stage2d_args(a);
+  return a;
+}
+
+cudaError_t enqueue_step2d(hweno_ctx* h, cudaStream_t s) {
+  hw::Stage2DArgs a = base_args2d(h);
+  a.sc = h->sc;
+  a.nin = hw::kAlphaSlots;
+  a.stage = 1;
+  a.w = h->U[0];
+  a.out = h->U[1];
+  a.lim_out = h->U0;
+  a.a_in = h->part[0];
+  a.a_out = h->part[1];
+  a.a_zero = h->part[2];
+  cudaError_t e = hw::launch_stage2d(a, s);
+  if (e != cudaSuccess) return e;
+  a.stage = 2;
+  a.w = h->U[1];
+  a.u0 = h->U0;
+  a.out = h->U[2];
+  a.lim_out = nullptr;
+  a.a_in = h->part[1];
+  a.a_out = h->part[2];
+  a.a_zero = h->part[0];
+  e = hw::launch_stage2d(a, s);
+  if (e != cudaSuccess) return e;
+  a.stage = 3;
+  a.w = h->U[2];
+  a.out = h->U[0];
+  a.a_in = h->part[2];
+  a.a_out = h->part[0];
+  a.a_zero = h->part[1];
+  return hw::launch_stage2d(a, s);
+}
+
 cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
+  if (h->dim == 2) return enqueue_step2d(h, s);
   hw::Stage1DArgs a = base_args(h);
   a.sc = h->sc;
   // stage 1
@@ -133,7 +189,16 @@ hweno_status build_graph(hweno_ctx* h, int steps, cudaGraphExec_t* out) {
 
 hweno_status validate(const hweno_config* c) {
   if (!c) return fail(nullptr, HWENO_ERR_ARG, "cfg is NULL");
-  if (c->dim != 1) return fail(nullptr, HWENO_ERR_ARG, "dim must be 1 (2D is not built into this library yet)");
+  if (c->dim != 1 && c->dim != 2) return fail(nullptr, HWENO_ERR_ARG, "dim must be 1 or 2");
+  if (c->dim == 2) {
+    if (c->ny < 4) return fail(nullptr, HWENO_ERR_ARG, "ny must be >= 4");
+    if (!(c->y1 > c->y0)) return fail(nullptr, HWENO_ERR_ARG, "y1 must exceed y0");
+    if ((double)c->nx * c->ny > (double)(1u << 30)) return fail(nullptr, HWENO_ERR_ARG, "too many cells");
+    const double dx = (c->x1 - c->x0) / c->nx, dy = (c->y1 - c->y0) / c->ny;
+    if (fabs(dx - dy) > 1e-12 * (dx > dy ? dx : dy))
+      return fail(nullptr, HWENO_ERR_ARG, "2D cells must be square (dx = dy)");
+    if (c->n_gauss != 2 && c->n_gauss != 3) return fail(nullptr, HWENO_ERR_ARG, "n_gauss must be 2 or 3");
+  }
   if (c->system != HWENO_BURGERS && c->system != HWENO_EULER)
     return fail(nullptr, HWENO_ERR_ARG, "unknown system");
   if (c->nx < 4) return fail(nullptr, HWENO_ERR_ARG, "nx must be >= 4");
@@ -207,18 +272,28 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
   hweno_ctx* h = new hweno_ctx();
   h->cfg = *cfg;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
-  h->C = cfg->system == HWENO_EULER ? 3 : 1;
-  h->M = 2;
-  h->n = cfg->nx;
-  h->ntile = (h->n + hw::kTile1D - 1) / hw::kTile1D;
+  h->dim = cfg->dim;
+  if (cfg->dim == 2) {
+    h->C = cfg->system == HWENO_EULER ? 4 : 1;
+    h->M = 3;
+    h->n = cfg->nx * cfg->ny;
+    h->ntile = ((cfg->nx + hw::kTile2DX - 1) / hw::kTile2DX) * ((cfg->ny + hw::kTile2DY - 1) / hw::kTile2DY);
+  } else {
+    h->C = cfg->system == HWENO_EULER ? 3 : 1;
+    h->M = 2;
+    h->n = cfg->nx;
+    h->ntile = (h->n + hw::kTile1D - 1) / hw::kTile1D;
+  }
   h->elems = (size_t)h->C * h->M * h->n;
   h->esize = cfg->precision == HWENO_FP64 ? 8 : 4;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->U[k], h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->U0, h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_buf, h->elems * 8);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * hw::kAlphaSlots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->part_rhs, sizeof(double) * h->ntile);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * 2 * hw::kAlphaSlots);
+  if (e == cudaSuccess) e = cudaMalloc(&h->part_rhs, sizeof(double) * 2 * h->ntile);
+  if (e == cudaSuccess && cfg->dim == 2)
+    e = hw::prepare_stage2d(cfg->system, cfg->precision == HWENO_FP64, cfg->n_gauss);
   if (e == cudaSuccess) e = cudaMalloc(&h->sc, sizeof(hw::DevScalars));
   if (e == cudaSuccess) e = cudaMalloc(&h->sc_rhs, sizeof(hw::DevScalars));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
@@ -252,9 +327,13 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
   if (src) HW_CUDA(h, hw::launch_convert(src, src64, h->U[0], dst64, h->elems, h->stream));
   HW_CUDA(h, hw::launch_set_scalars(h->sc, 1, -1.0, h->stream));
   for (int k = 0; k < 3; ++k)
-    HW_CUDA(h, cudaMemsetAsync(h->part[k], 0, sizeof(double) * hw::kAlphaSlots, h->stream));
-  HW_CUDA(h, hw::launch_alpha1d(h->U[0], h->part[0], h->n, h->ntile, h->cfg.system, dst64,
-                                h->cfg.gas_gamma, h->sc, 1, h->stream));
+    HW_CUDA(h, cudaMemsetAsync(h->part[k], 0, sizeof(double) * 2 * hw::kAlphaSlots, h->stream));
+  if (h->dim == 2)
+    HW_CUDA(h, hw::launch_alpha2d(h->U[0], h->part[0], h->cfg.nx, h->cfg.ny, h->cfg.system, dst64,
+                                  h->cfg.gas_gamma, h->sc, 1, h->stream));
+  else
+    HW_CUDA(h, hw::launch_alpha1d(h->U[0], h->part[0], h->n, h->ntile, h->cfg.system, dst64,
+                                  h->cfg.gas_gamma, h->sc, 1, h->stream));
   h->has_state = true;
   return HWENO_OK;
 }
@@ -294,6 +373,23 @@ hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags
   if (in == out || (ulim_out && (ulim_out == in || ulim_out == out)))
     return fail(h, HWENO_ERR_ARG, "in, out and ulim_out must not overlap");
   HW_CUDA(h, hw::launch_set_scalars(h->sc_rhs, 1, -1.0, h->stream));
+  if (h->dim == 2) {
+    HW_CUDA(h, hw::launch_alpha2d(in, h->part_rhs, h->cfg.nx, h->cfg.ny, h->cfg.system,
+                                  h->cfg.precision == HWENO_FP64, h->cfg.gas_gamma, h->sc_rhs, 0,
+                                  h->stream));
+    hw::Stage2DArgs a = base_args2d(h);
+    a.stage = 0;
+    a.w = in;
+    a.out = out;
+    a.lim_out = ulim_out;
+    a.a_in = h->part_rhs;
+    a.nin = h->ntile;
+    a.sc = h->sc_rhs;
+    a.flags_out = flags_out;
+    HW_CUDA(h, hw::launch_stage2d(a, h->stream));
+    hw::DevScalars s2;
+    return check_scalars(h, h->sc_rhs, &s2);
+  }
   HW_CUDA(h, hw::launch_alpha1d(in, h->part_rhs, h->n, h->ntile, h->cfg.system,
                                 h->cfg.precision == HWENO_FP64, h->cfg.gas_gamma, h->sc_rhs, 0,
                                 h->stream));

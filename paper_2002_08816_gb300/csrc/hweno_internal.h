@@ -61,6 +61,46 @@ constexpr int kAlphaSlots = 64;  // slots that carry alpha between stages
 constexpr int kTile1D = 250;     // cells per CTA of the 1D kernels
 constexpr int kThreads1D = 256;  // threads per CTA (tile + 3-cell halo per side)
 
+// KXRCF constants of the 2D reading, derived on the host
+struct Kx2 {
+  double dx, dy, den_h;      // den_h = h (dx + dy), h = sqrt(dx^2 + dy^2) / 2
+  double thr;
+  float fdx, fdy, fthr_den;  // FP32 copies: dx, dy, thr * den_h
+};
+
+// Everything one 2D stage launch needs.  Pointers are device pointers.
+// Wave-speed maxima: x values in [0, nin), y values in [nin, 2 nin).
+struct Stage2DArgs {
+  const void* w;
+  const void* u0;
+  void* out;
+  void* lim_out;
+  const void* a_in;
+  int nin;
+  void* a_out;           // 2 * kAlphaSlots slots (x, then y), zeroed, atomic max
+  void* a_zero;          // 2 * kAlphaSlots slots to zero (nullable)
+  DevScalars* sc;
+  uint8_t* flags_out;
+  int nx, ny, stage, bc, mode, system, fp64, ng;
+  double dx, dy, cfl, eps, thr, gas;
+  double gam[5];
+  double inv_dx, inv_dy;  // derived
+  Kx2 kx;                 // derived
+  float f32[10];          // FP32 copies: gamma_0..4, eps, gas, 1/dx, 1/dy, cfl
+};
+
+constexpr int kTile2DX = 16, kTile2DY = 16;  // cells per CTA of the 2D kernels
+constexpr int kThreads2D = 256;
+
+void finish_stage2d_args(Stage2DArgs& a);
+// Allows the 2D stage kernel of this configuration its dynamic shared memory.
+cudaError_t prepare_stage2d(int system, int fp64, int ng);
+cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s);
+// Wave-speed maxima (x then y) of a 2D state, per tile (slots = 0, 2 ntile
+// entries) or into 2 * kAlphaSlots zeroed slots (slots = 1).
+cudaError_t launch_alpha2d(const void* w, void* a_out, int nx, int ny, int system, int fp64,
+                           double gas, DevScalars* sc, int slots, cudaStream_t s);
+
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
 // Wave-speed maxima of w, in the kernel's precision: one per tile (slots = 0)
 // or folded into kAlphaSlots zeroed slots by atomic max (slots = 1).

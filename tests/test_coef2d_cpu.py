@@ -1,0 +1,71 @@
+"""The 2D coefficient tables the CUDA kernels compile in
+(csrc/hweno2d_coef.cuh, generated in exact arithmetic by sympy) against the
+oracle's own numerical derivation of the same moment conditions (a KKT solve
+in FP64).  The two derivations share no code; this compares their outputs."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_2002_08816_gb300", "csrc", "hweno2d_coef.cuh")
+
+
+def _parse():
+    txt = open(HDR).read()
+    maps, betas = {}, {}
+    for m in re.finditer(r"void (\w+)\(const R\* d, R\* o\) \{(.*?)\n\}", txt, re.S):
+        rows = {}
+        for line in m.group(2).strip().splitlines():
+            mm = re.match(r"\s*o\[(\d+)\] = (.*);", line)
+            coef = {int(j): float(c) for c, j in re.findall(r"R\(([-0-9.eE+]+)\) \* d\[(\d+)\]", mm.group(2))}
+            rows[int(mm.group(1))] = coef
+        maps[m.group(1)] = rows
+    for m in re.finditer(r"R (beta_\w+)\(const R\* d\) \{(.*?)\n\}", txt, re.S):
+        terms, cur = [], None
+        for line in m.group(2).splitlines():
+            if line.strip().startswith("t ="):
+                cur = {int(j): float(c) for c, j in re.findall(r"R\(([-0-9.eE+]+)\) \* d\[(\d+)\]", line)}
+            elif line.strip().startswith("b +="):
+                w = float(re.search(r"R\(([-0-9.eE+]+)\)", line).group(1))
+                terms.append((w, cur))
+        betas[m.group(1)] = terms
+    return maps, betas
+
+
+MAPS, BETAS = _parse()
+
+
+def _apply(rows, d):
+    return np.array([sum(c * d[j] for j, c in rows[p].items()) for p in range(len(rows))])
+
+
+def _split(d):
+    ub = d[:9]
+    vb = np.zeros(9)
+    wb = np.zeros(9)
+    for k, cell in enumerate([2, 4, 5, 6, 8]):
+        vb[cell - 1] = d[9 + k]
+        wb[cell - 1] = d[14 + k]
+    return ub, vb, wb
+
+
+@pytest.mark.parametrize("ng", [2, 3])
+def test_generated_maps_match_the_oracle(ng):
+    rng = np.random.default_rng(ng)
+    nf = 4 * ng
+    for _ in range(6):
+        d = rng.normal(size=19)
+        val, beta = O.recon_candidates2d(*_split(d), ng)
+        np.testing.assert_allclose(_apply(MAPS["p0_faces_ng%d" % ng], d), val[0, :nf], atol=1e-12)
+        np.testing.assert_allclose(_apply(MAPS["p0_interior_ng%d" % ng], d), val[0, nf:], atol=1e-12)
+        for n in (1, 2, 3, 4):
+            np.testing.assert_allclose(_apply(MAPS["q%d_faces_ng%d" % (n, ng)], d), val[n, :nf],
+                                       atol=1e-12)
+        got = [sum(w * sum(c * d[j] for j, c in f.items()) ** 2 for w, f in BETAS[name])
+               for name in ("beta_p0", "beta_q1", "beta_q2", "beta_q3", "beta_q4")]
+        np.testing.assert_allclose(got, beta, rtol=1e-11)
