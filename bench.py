@@ -311,6 +311,142 @@ def bench_hweno(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- 2D workload
+
+NX2 = 4096
+RK_STEPS_2D = 100
+SEED_2D = 2026
+CFL_2D = 0.5
+COEF_HDR = os.path.join(ROOT, "paper_2002_08816_gb300", "csrc", "hweno2d_coef.cuh")
+
+
+def flops_per_cell_stage_2d(ng, ncomp=4):
+    """FP32 operations of one smooth 2D Euler cell-stage, counted on the
+    operations the method needs (halo recomputation excluded): the linear p0
+    maps of the generated code (one FMA = 2 flops per nonzero coefficient) for
+    the 4 ng interface and ng^2 interior points of every component, the
+    Lax-Friedrichs flux of each of the cell's own 2 ng interface points (two
+    Euler fluxes of 15 flops and 16 for the combination), f and g at the
+    interior points (2 x 15 + 16), the right-hand-side sums (6 per quadrature
+    point and component plus 10) and the Runge-Kutta combination (4 per
+    moment)."""
+    import re
+    txt = open(COEF_HDR).read()
+    nnz = 0
+    for name in ("p0_faces_ng%d" % ng, "p0_interior_ng%d" % ng):
+        body = re.search(r"void %s\(const R\* d, R\* o\) \{(.*?)\n\}" % name, txt, re.S).group(1)
+        nnz += len(re.findall(r"\* d\[", body))
+    return (2 * ncomp * nnz + 2 * ng * 46 + ng * ng * 46 + ncomp * (6 * 3 * ng + 10)
+            + 4 * 3 * ncomp)
+
+
+def bench_euler2d(args):
+    """2D Euler, 4096 x 4096 periodic [0, 10]^2, isentropic vortex plus seeded
+    density modes, FP32, RK_STEPS_2D steps per bench step (state > L2)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_08816_gb300 import hweno as H
+    from paper_2002_08816_gb300 import workloads as W
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    ng = args.n_gauss
+    u0 = W.euler_vortex_modes_2d(NX2, NX2, seed=SEED_2D + rank, npts=2).astype(np.float32)
+    cfg = H.make_config(2, H.HWENO_EULER, NX2, NX2, x0=0.0, x1=10.0, y0=0.0, y1=10.0,
+                        bc=H.HWENO_BC_PERIODIC, cfl=CFL_2D, precision=H.HWENO_FP32, n_gauss=ng)
+    h = H.hweno_create(cfg, stream.cuda_stream)
+    dev = torch.from_numpy(u0).to("cuda")
+    host_in = torch.from_numpy(u0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+
+    def one_step():
+        H.hweno_set_state(h, dev.data_ptr(), H.HWENO_FP32, True)
+        H.hweno_step(h, RK_STEPS_2D, -1.0, wait=False)
+
+    for _ in range(args.warmup):
+        one_step()
+    H.hweno_step(h, 0, -1.0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        one_step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.__exit__(None, None, None)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    H.hweno_step(h, 0, -1.0)
+    st = H.hweno_stats(h)
+    tot = sum(ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    # end to end from pinned host buffers
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    H.hweno_set_state(h, host_in.data_ptr(), H.HWENO_FP32, False)
+    H.hweno_step(h, RK_STEPS_2D, -1.0, wait=False)
+    H.hweno_get_state(h, host_out.data_ptr(), H.HWENO_FP32, False)
+    b.record(stream)
+    b.synchronize()
+    e2e_s = a.elapsed_time(b) / 1e3
+    H.hweno_destroy(h)
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    cells = NX2 * NX2 * 3 * RK_STEPS_2D
+    stage_s = tot / (args.steps * 3 * RK_STEPS_2D)
+    clocks = sampler.summary()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
+    flops = flops_per_cell_stage_2d(ng) * NX2 * NX2
+    byts = 128.0 * NX2 * NX2
+    hbm, peak_kind = peaks()
+    t_alu = flops / (fp32_peak * 1e12)
+    t_hbm = byts / (hbm * 1e9)
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": t_alu / stage_s, "traffic": None,
+                "note": "FP32 peak = 152 SMs x 128 lanes x 2 flops x sampled SM clock; "
+                        "%d flops per smooth cell-stage" % flops_per_cell_stage_2d(ng)}
+    else:
+        roof = {"bound": "hbm", "achieved": byts / stage_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": t_hbm / stage_s, "traffic": None, "note": "peak %s" % peak_kind}
+    roof["kernel"] = "stage2d_kernel<float,4,%d>" % ng
+    line = {
+        "metric": METRIC, "value": ws * cells * args.steps / tot, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "2D Euler 4096x4096 periodic, vortex + 8 density modes, %d RK3 "
+                               "steps, %d Gauss points, CFL %.1f, FP32" % (RK_STEPS_2D, ng, CFL_2D),
+                   "seed": SEED_2D, "l2": "state (805 MB) larger than L2"},
+        "stage_ms": stage_s * 1e3,
+        "troubled_frac": st["troubled"] / float(cells * (args.steps + args.warmup)),
+        "roofline": roof,
+        "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": host_in.numel() * 4,
+                "d2h_bytes_per_step": host_in.numel() * 4},
+        "gpu_launches": args.steps * (3 * RK_STEPS_2D + 4),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,9 +454,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="euler1d", choices=["euler1d", "euler2d"],
+                    help="euler1d: the headline 65536-cell 1D workload; euler2d: the "
+                         "4096 x 4096 2D Euler workload")
+    ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "euler2d":
+        bench_euler2d(args)
     else:
         bench_hweno(args)
 

@@ -158,9 +158,9 @@ __device__ __forceinline__ double jump64(double u0, double v0, double unb, doubl
 
 // u0/v0/w0 the cell, (uxn, vxn) its inflow x-neighbour, (uyn, wyn) its inflow
 // y-neighbour; lowx / lowy: the inflow faces are the left / bottom ones.
-__device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0, double uxn,
-                                                double vxn, double uyn, double wyn, bool lowx,
-                                                bool lowy, const Kx2& k) {
+__device__ __noinline__ bool kxrcf2_troubled64(double u0, double v0, double w0, double uxn,
+                                               double vxn, double uyn, double wyn, bool lowx,
+                                               bool lowy, const Kx2& k) {
   const double jx = jump64(u0, v0, uxn, vxn, lowx);
   const double jy = jump64(u0, w0, uyn, wyn, lowy);
   const double num = __dadd_rn(__dmul_rn(k.dy, jx), __dmul_rn(k.dx, jy));
@@ -181,8 +181,14 @@ __device__ __forceinline__ bool kxrcf2_troubled(float u0, float v0, float w0, fl
   const float r = k.fthr_den * fmaxf(fabsf(u0), 1e-12f);
   if (num - e > r * (1.0f + 4.8e-7f)) return true;
   if (num + e < r * (1.0f - 4.8e-7f)) return false;
-  return kxrcf2_troubled((double)u0, (double)v0, (double)w0, (double)uxn, (double)vxn,
-                         (double)uyn, (double)wyn, lowx, lowy, k);
+  return kxrcf2_troubled64((double)u0, (double)v0, (double)w0, (double)uxn, (double)vxn,
+                           (double)uyn, (double)wyn, lowx, lowy, k);
+}
+
+__device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0, double uxn,
+                                                double vxn, double uyn, double wyn, bool lowx,
+                                                bool lowy, const Kx2& k) {
+  return kxrcf2_troubled64(u0, v0, w0, uxn, vxn, uyn, wyn, lowx, lowy, k);
 }
 
 // ------------------------------------------------------ HWENO helpers (2D)
@@ -263,8 +269,111 @@ __device__ __forceinline__ void gather19(const S& sm, int c, int ci, int cj, R* 
   }
 }
 
+// Value v of point p (order of hweno2d_coef.cuh) of component c of the cell at
+// own-tile coordinates (ci, cj) into the face arrays.
+template <typename S, typename R>
+__device__ __forceinline__ void store_point(S& sm, int c, int p, int ci, int cj, R v) {
+  constexpr int NG2 = sizeof(sm.xf[0]) / sizeof(sm.xf[0][0]);  // 2 NG
+  if (p < NG2)
+    sm.xf[c][p][cj][ci + 1] = v;        // left and right faces
+  else
+    sm.yf[c][p - NG2][cj + 1][ci] = v;  // bottom and top faces
+}
+
+// Step 4 for a troubled Euler cell (lx, ly) of the flag grid: vbar from the
+// x-neighbours in the x characteristic fields, wbar from the y-neighbours in
+// the y fields, with the 1D Step 1 formula.  Rare: kept out of line so that
+// its registers do not weigh on the common path.
+template <typename S, typename R>
+__device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, const R* gam, R eps, R gas) {
+  const int rx = lx + 1, ry = ly + 1;
+  R U[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][ry][rx];
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    R Rm[4][4], Lm[4][4];
+    Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+    const int sx = dir == 0 ? 1 : 0, sy = dir == 0 ? 0 : 1;
+    const int mom = dir == 0 ? 1 : 2;
+    R q[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      R wv[5];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        wv[s] = R(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) wv[s] += Lm[f][c] * sm.u[c][0][ry + (s - 1) * sy][rx + (s - 1) * sx];
+      }
+      wv[3] = R(0);
+      wv[4] = R(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        wv[3] += Lm[f][c] * sm.u[c][mom][ry - sy][rx - sx];
+        wv[4] += Lm[f][c] * sm.u[c][mom][ry + sy][rx + sx];
+      }
+      q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const R v = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2] + Rm[c][3] * q[3];
+      if (dir == 0) sm.vl[c][ly][lx] = v; else sm.wl[c][ly][lx] = v;
+    }
+  }
+}
+
+// Step 5.1 for an Euler cell whose 3x3 stencil holds a troubled cell: the
+// interface points [p_lo, p_hi) by HWENO in the x (x-faces) and y (y-faces)
+// characteristic fields of the cell average (Remark 4).  Rare: out of line.
+template <int NG, typename S, typename R>
+__device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo, int p_hi,
+                                                 const R* gam, R eps, R gas) {
+  constexpr int NF = 4 * NG;
+  R U[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][cj + 3][ci + 3];
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const int lo = dir == 0 ? 0 : 2 * NG, hi = dir == 0 ? 2 * NG : 4 * NG;
+    const int plo = p_lo > lo ? p_lo : lo, phi = p_hi < hi ? p_hi : hi;
+    if (plo >= phi) continue;
+    R Rm[4][4], Lm[4][4];
+    Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+    R acc[4][NF];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int p = 0; p < NF; ++p) acc[c][p] = R(0);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      R e[19], t[19];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) e[k] = R(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        gather19(sm, c, ci, cj, t);
+#pragma unroll
+        for (int k = 0; k < 19; ++k) e[k] += Lm[f][c] * t[k];
+      }
+      R chv[NF];
+      hweno2d_faces<NG>(e, gam, eps, plo, phi, chv);
+#pragma unroll
+      for (int p = 0; p < NF; ++p)
+        if (p >= plo && p < phi)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[c][p] += Rm[c][f] * chv[p];
+    }
+#pragma unroll
+    for (int p = 0; p < NF; ++p)
+      if (p >= plo && p < phi)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) store_point(sm, c, p, ci, cj, acc[c][p]);
+  }
+}
+
 template <typename R, int C, int NG>
-__global__ void __launch_bounds__(NT) stage2d_kernel(Stage2DArgs a) {
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(Stage2DArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem2D<R, C, NG>& sm = *reinterpret_cast<Smem2D<R, C, NG>*>(smem_raw);
   constexpr int NF = 4 * NG, NI = NG * NG;
@@ -396,40 +505,7 @@ __global__ void __launch_bounds__(NT) stage2d_kernel(Stage2DArgs a) {
                                             sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
                                             sm.u[0][2][ry + 1][rx], gam, eps);
     } else {
-      R U[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][ry][rx];
-#pragma unroll 1
-      for (int dir = 0; dir < 2; ++dir) {
-        R Rm[4][4], Lm[4][4];
-        Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
-        const int sx = dir == 0 ? 1 : 0, sy = dir == 0 ? 0 : 1;
-        const int mom = dir == 0 ? 1 : 2;
-        R q[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          R wv[5];
-#pragma unroll
-          for (int s = 0; s < 3; ++s) {
-            wv[s] = R(0);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) wv[s] += Lm[f][c] * sm.u[c][0][ry + (s - 1) * sy][rx + (s - 1) * sx];
-          }
-          wv[3] = R(0);
-          wv[4] = R(0);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            wv[3] += Lm[f][c] * sm.u[c][mom][ry - sy][rx - sx];
-            wv[4] += Lm[f][c] * sm.u[c][mom][ry + sy][rx + sx];
-          }
-          q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const R v = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2] + Rm[c][3] * q[3];
-          if (dir == 0) sm.vl[c][ly][lx] = v; else sm.wl[c][ly][lx] = v;
-        }
-      }
+      limit_euler2d(sm, lx, ly, gam, eps, gas);
     }
   }
   __syncthreads();
@@ -453,18 +529,6 @@ __global__ void __launch_bounds__(NT) stage2d_kernel(Stage2DArgs a) {
     for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
       for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 2 + dj][ci + 2 + di] != 0;
-    // point p of component c of this cell into the face arrays
-    auto store = [&](int c, int p, R v) {
-      if (p < NG) {
-        sm.xf[c][p][cj][ci + 1] = v;  // left face
-      } else if (p < 2 * NG) {
-        sm.xf[c][p][cj][ci + 1] = v;  // right face
-      } else if (p < 3 * NG) {
-        sm.yf[c][p - 2 * NG][cj + 1][ci] = v;  // bottom face
-      } else {
-        sm.yf[c][p - 2 * NG][cj + 1][ci] = v;  // top face
-      }
-    };
     if (!hw || C == 1) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
@@ -476,50 +540,10 @@ __global__ void __launch_bounds__(NT) stage2d_kernel(Stage2DArgs a) {
           hweno2d_faces<NG>(d, gam, eps, p_lo, p_hi, v);
 #pragma unroll
         for (int p = 0; p < NF; ++p)
-          if (p >= p_lo && p < p_hi) store(c, p, v[p]);
+          if (p >= p_lo && p < p_hi) store_point(sm, c, p, ci, cj, v[p]);
       }
     } else if constexpr (C == 4) {
-      R U[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][cj + 3][ci + 3];
-#pragma unroll 1
-      for (int dir = 0; dir < 2; ++dir) {
-        const int lo = dir == 0 ? 0 : 2 * NG, hi = dir == 0 ? 2 * NG : 4 * NG;
-        const int plo = p_lo > lo ? p_lo : lo, phi = p_hi < hi ? p_hi : hi;
-        if (plo >= phi) continue;
-        R Rm[4][4], Lm[4][4];
-        Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
-        R acc[4][NF];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int p = 0; p < NF; ++p) acc[c][p] = R(0);
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          // characteristic field f of the 19 data (Remark 4)
-          R e[19], t[19];
-#pragma unroll
-          for (int k = 0; k < 19; ++k) e[k] = R(0);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            gather19(sm, c, ci, cj, t);
-#pragma unroll
-            for (int k = 0; k < 19; ++k) e[k] += Lm[f][c] * t[k];
-          }
-          R chv[NF];
-          hweno2d_faces<NG>(e, gam, eps, plo, phi, chv);
-#pragma unroll
-          for (int p = 0; p < NF; ++p)
-            if (p >= plo && p < phi)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) acc[c][p] += Rm[c][f] * chv[p];
-        }
-#pragma unroll
-        for (int p = 0; p < NF; ++p)
-          if (p >= plo && p < phi)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) store(c, p, acc[c][p]);
-      }
+      hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam, eps, gas);
     }
   }
   __syncthreads();
@@ -760,8 +784,12 @@ cudaError_t launch_stage2d_t(const Stage2DArgs& a, cudaStream_t s) {
 
 template <typename R, int C, int NG>
 cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(stage2d_kernel<R, C, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(Smem2D<R, C, NG>));
+  cudaError_t e = cudaFuncSetAttribute(stage2d_kernel<R, C, NG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem2D<R, C, NG>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(stage2d_kernel<R, C, NG>,
+                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 }  // namespace

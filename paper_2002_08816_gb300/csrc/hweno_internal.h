@@ -89,7 +89,7 @@ struct Stage2DArgs {
   float f32[10];          // FP32 copies: gamma_0..4, eps, gas, 1/dx, 1/dy, cfl
 };
 
-constexpr int kTile2DX = 16, kTile2DY = 16;  // cells per CTA of the 2D kernels
+constexpr int kTile2DX = 32, kTile2DY = 8;  // cells per CTA of the 2D kernels (a warp per row)
 constexpr int kThreads2D = 256;
 
 void finish_stage2d_args(Stage2DArgs& a);

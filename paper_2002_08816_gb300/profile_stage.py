@@ -2,8 +2,10 @@
 
   python -m paper_2002_08816_gb300.profile_stage [--nx 65536] [--rk-steps 10]
                                                   [--precision fp32|fp64] [--system euler|burgers]
+                                                  [--dim 1|2] [--n-gauss 2|3]
 
-Sets the seeded two-state 1D Euler state (or the Burgers sine wave), runs the
+Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
+--dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
 requested number of Runge-Kutta steps through the C ABI (3 stage launches per
 step after one alpha launch) and checks the status word.
 """
@@ -28,10 +30,17 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--system", default="euler", choices=["euler", "burgers"])
     ap.add_argument("--seed", type=int, default=20250)
+    ap.add_argument("--dim", type=int, default=1, choices=[1, 2])
+    ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
     args = ap.parse_args()
     B.build()
     prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
-    if args.system == "euler":
+    if args.dim == 2:
+        # 2D Euler, nx x nx periodic on [0, 10]^2, vortex plus density modes
+        u = W.euler_vortex_modes_2d(args.nx, args.nx, seed=args.seed, npts=2)
+        cfg = H.make_config(2, H.HWENO_EULER, args.nx, args.nx, x0=0.0, x1=10.0, y0=0.0,
+                            y1=10.0, cfl=0.5, precision=prec, n_gauss=args.n_gauss)
+    elif args.system == "euler":
         u = W.euler_two_state_1d(args.nx, args.seed)
         cfg = H.make_config(1, H.HWENO_EULER, args.nx, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
                             precision=prec)
