@@ -447,6 +447,104 @@ def bench_euler2d(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- batched 1D workload
+
+N_BATCH = 512
+RK_STEPS_BATCH = 500
+SEED_BATCH = 77
+
+
+def bench_batch1d(args):
+    """512 independent 1D Euler instances, cell counts log-uniform in
+    [256, 16384], two-state data, FP32, RK_STEPS_BATCH steps each, advanced in
+    shared launches; compared with one handle per instance on an evenly spread
+    subset of 32 instances (the per-instance time is launch-bound, so it is
+    scaled to 512 instances by their count)."""
+    import torch
+
+    from paper_2002_08816_gb300 import hweno as H
+    from paper_2002_08816_gb300 import workloads as W
+    import __graft_entry__
+
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    sizes = [int(v) for v in W.batch_sizes_1d(N_BATCH, seed=SEED_BATCH)]
+    states = [W.euler_two_state_1d(n, seed=SEED_BATCH + b).astype(np.float32)
+              for b, n in enumerate(sizes)]
+    cells = sum(sizes)
+    cfg = H.make_config(1, H.HWENO_EULER, 4, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=CFL,
+                        precision=H.HWENO_FP32)
+    h = H.hweno_create_batch(cfg, sizes, stream.cuda_stream)
+    dev = torch.from_numpy(np.concatenate([s.reshape(-1) for s in states])).to("cuda")
+
+    def one_step():
+        H.hweno_set_state(h, dev.data_ptr(), H.HWENO_FP32, True)
+        H.hweno_step(h, RK_STEPS_BATCH, -1.0, wait=False)
+
+    for _ in range(args.warmup):
+        one_step()
+    H.hweno_step(h, 0, -1.0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.__enter__()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        one_step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.__exit__(None, None, None)
+    H.hweno_step(h, 0, -1.0)
+    H.hweno_destroy(h)
+    tot = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    # one handle per instance, on 32 instances spread over the size range
+    order = np.argsort(sizes)
+    pick = [int(order[k]) for k in np.linspace(0, N_BATCH - 1, 32).round().astype(int)]
+    handles = []
+    for b in pick:
+        c1 = H.make_config(1, H.HWENO_EULER, sizes[b], x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW,
+                           cfl=CFL, precision=H.HWENO_FP32)
+        hb = H.hweno_create(c1, stream.cuda_stream)
+        d = torch.from_numpy(states[b]).to("cuda")
+        handles.append((hb, d))
+    for hb, d in handles:  # warm-up (graph capture)
+        H.hweno_set_state(hb, d.data_ptr(), H.HWENO_FP32, True)
+        H.hweno_step(hb, 40, -1.0, wait=False)
+    torch.cuda.synchronize()
+    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for hb, d in handles:
+        H.hweno_set_state(hb, d.data_ptr(), H.HWENO_FP32, True)
+        H.hweno_step(hb, RK_STEPS_BATCH, -1.0, wait=False)
+    b2.record(stream)
+    b2.synchronize()
+    sub_s = a.elapsed_time(b2) / 1e3
+    for hb, _ in handles:
+        H.hweno_destroy(hb)
+    per_inst_s = sub_s * N_BATCH / len(pick)
+    value = cells * 3 * RK_STEPS_BATCH * args.steps / tot
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched 1D Euler: 512 instances, cells log-uniform in "
+                               "[256, 16384] (%d cells), two-state data, %d RK3 steps each, "
+                               "CFL %.1f, FP32, one launch per stage for all instances"
+                               % (cells, RK_STEPS_BATCH, CFL),
+                   "seed": SEED_BATCH, "l2": "flushed (512 MiB write) between timed steps"},
+        "per_instance": {"ms_per_step_estimate": 1e3 * per_inst_s,
+                         "value_estimate": cells * 3 * RK_STEPS_BATCH / per_inst_s,
+                         "how": "one handle per instance (CUDA graphs of 32 steps), 32 instances "
+                                "spread over the sizes, %.1f ms, scaled by 512/32" % (1e3 * sub_s)},
+        "speedup_vs_per_instance": per_inst_s / (tot / args.steps),
+        "gpu_launches": args.steps * (3 * RK_STEPS_BATCH + 5),
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,15 +552,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="euler1d", choices=["euler1d", "euler2d"],
+    ap.add_argument("--workload", default="euler1d", choices=["euler1d", "euler2d", "batch1d"],
                     help="euler1d: the headline 65536-cell 1D workload; euler2d: the "
-                         "4096 x 4096 2D Euler workload")
+                         "4096 x 4096 2D Euler workload; batch1d: 512 uneven 1D instances")
     ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
     elif args.workload == "euler2d":
         bench_euler2d(args)
+    elif args.workload == "batch1d":
+        bench_batch1d(args)
     else:
         bench_hweno(args)
 

@@ -150,6 +150,21 @@ hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* st
 hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, const void* in,
                                  void* out, uint8_t* flags_out, void* ulim_out);
 
+/* A batch of n_batch independent 1D problems of nx[b] cells each (nx[b] >= 4),
+ * sharing every other field of cfg (dim must be 1; cfg->nx is ignored); each
+ * instance covers [x0, x1] with its own dx, alpha, dt and time (the scheme of
+ * Sec. 2.1 applied to each instance separately).  All instances advance in
+ * the same launches.  The state layout is the instances' 1D states one after
+ * the other (instance b at offset 2 C sum_{b'<b} nx[b']).  set_state,
+ * get_state, step and stats work as for one instance (stats report instance
+ * 0's time); hweno_rhs is not available on a batch. */
+hweno_status hweno_create_batch(const hweno_config* cfg, int n_batch, const int* nx,
+                                void* cuda_stream, hweno_handle* out);
+
+/* The time reached by every instance of a batch (t: n_batch doubles).  Waits
+ * for the stream. */
+hweno_status hweno_batch_times(hweno_handle h, double* t);
+
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);
 

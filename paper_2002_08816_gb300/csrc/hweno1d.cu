@@ -89,13 +89,37 @@ __device__ __forceinline__ R wave_speed(R gas, const R* U) {
   }
 }
 
-template <typename R, int C>
+template <typename R, int C, bool BATCH>
 __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
   __shared__ Smem1D<R, C> sm;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int n = a.n;
-  const int base = blockIdx.x * T;
+  int n = a.n;
+  int base = blockIdx.x * T;
+  int inst = 0;
+  bool lead = blockIdx.x == 0;  // the tile that keeps the (instance's) time
+  if constexpr (BATCH) {
+    // a batch of independent instances: this tile's instance and first cell
+    inst = a.tile_inst[blockIdx.x];
+    base = a.tile_base[blockIdx.x];
+    const BatchInst& bi = a.binst[inst];
+    n = bi.n;
+    lead = base == 0;
+    const long long off = bi.off;
+    a.w = static_cast<const R*>(a.w) + off;
+    if (a.u0) a.u0 = static_cast<const R*>(a.u0) + off;
+    a.out = static_cast<R*>(a.out) + off;
+    if (a.lim_out) a.lim_out = static_cast<R*>(a.lim_out) + off;
+    if (a.flags_out) a.flags_out += off / (2 * C);
+    a.a_in = static_cast<const R*>(a.a_in) + inst;
+    a.nin = 1;
+    a.inv_dx = bi.inv_dx;
+    a.h = bi.h;
+    a.cfl_dx = bi.cfl_dx;
+    a.hthr = bi.hthr_f;
+    a.f32[5] = bi.inv_dx_f;
+    a.f32[6] = bi.cfl_dx_f;
+  }
   const R* __restrict__ w = static_cast<const R*>(a.w);
 
   // The producer of the stage input may still be finishing (programmatic
@@ -119,10 +143,18 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
   R amax = R(0);
   for (int k = tid; k < a.nin; k += NT) amax = fmax(amax, a_in[k]);
   R rem = R(0), dt_prev = R(0);
-  if (a.stage == 1)
-    rem = sc_rem<R>(a.sc);
-  else if (a.stage > 1)
-    dt_prev = sc_dt<R>(a.sc);
+  if constexpr (BATCH) {
+    const BatchScalars& bs = a.bsc[inst];
+    if (a.stage == 1)
+      rem = sizeof(R) == 4 ? R(bs.rem_f) : R(bs.rem);
+    else if (a.stage > 1)
+      dt_prev = sizeof(R) == 4 ? R(bs.dt_f) : R(bs.dt);
+  } else {
+    if (a.stage == 1)
+      rem = sc_rem<R>(a.sc);
+    else if (a.stage > 1)
+      dt_prev = sc_dt<R>(a.sc);
+  }
   R u0c[C][2];
   if (a.stage >= 2 && tid < T && base + tid < n) {
     const R* u0 = static_cast<const R*>(a.u0);
@@ -161,14 +193,24 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
       last = 1;
     }
     if (!(alpha > R(0)) || !isfinite(dt)) dt = R(0);
-    if (blockIdx.x == 0 && tid == 0) {
-      sc_dt<R>(a.sc) = dt;
-      a.sc->last = last;
+    if (lead && tid == 0) {
+      if constexpr (BATCH) {
+        BatchScalars& bs = a.bsc[inst];
+        if (sizeof(R) == 4) bs.dt_f = (float)dt; else bs.dt = (double)dt;
+        bs.last = last;
+      } else {
+        sc_dt<R>(a.sc) = dt;
+        a.sc->last = last;
+      }
     }
   }
-  if (a.stage > 0 && !(dt > R(0))) return;  // uniform over the grid
+  if (a.stage > 0 && !(dt > R(0))) return;  // uniform over the grid (the instance)
   // the slots of the stage after next (read two stages ago, now free)
-  if (a.a_zero && blockIdx.x == 0 && tid < kAlphaSlots) static_cast<R*>(a.a_zero)[tid] = R(0);
+  if constexpr (BATCH) {
+    if (a.a_zero && lead && tid == 0) static_cast<R*>(a.a_zero)[inst] = R(0);
+  } else {
+    if (a.a_zero && blockIdx.x == 0 && tid < kAlphaSlots) static_cast<R*>(a.a_zero)[tid] = R(0);
+  }
 
   // 3. troubled cells and modified first moments (Step 1), cells base-2 ..
   if (tid < T + 4) {
@@ -275,16 +317,27 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
   __syncthreads();
 
   // time bookkeeping (FP64) by a thread that has no cell in phase 5
-  if (a.stage == 3 && blockIdx.x == 0 && tid == NT - 1) {
+  if (a.stage == 3 && lead && tid == NT - 1) {
     DevScalars* sc = a.sc;
     const double tf = sc->t_final;
-    const double t = sc->last ? tf : sc->t + (double)dt;
-    const double r = tf > 0.0 ? tf - t : (double)INFINITY;
-    sc->t = t;
-    sc->dt = (double)dt;
-    sc->rem = r;
-    sc->rem_f = (float)r;
-    sc->steps += 1;
+    if constexpr (BATCH) {
+      BatchScalars& bs = a.bsc[inst];
+      const double t = bs.last ? tf : bs.t + (double)dt;
+      const double r = tf > 0.0 ? tf - t : (double)INFINITY;
+      bs.t = t;
+      bs.dt = (double)dt;
+      bs.rem = r;
+      bs.rem_f = (float)r;
+      if (inst == 0) sc->steps += 1;
+    } else {
+      const double t = sc->last ? tf : sc->t + (double)dt;
+      const double r = tf > 0.0 ? tf - t : (double)INFINITY;
+      sc->t = t;
+      sc->dt = (double)dt;
+      sc->rem = r;
+      sc->rem_f = (float)r;
+      sc->steps += 1;
+    }
   }
   static_assert(T < NT, "a thread without a cell keeps the time");
 
@@ -378,7 +431,8 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
       c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-      if (a.a_out) atomic_max_nonneg(static_cast<R*>(a.a_out) + blockIdx.x % kAlphaSlots, m);
+      if (a.a_out)
+        atomic_max_nonneg(static_cast<R*>(a.a_out) + (BATCH ? inst : blockIdx.x % kAlphaSlots), m);
       if (c) atomicAdd(&a.sc->troubled, (unsigned long long)c);
     }
   }
@@ -409,6 +463,50 @@ __global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, R*
       atomic_max_nonneg(a_out + blockIdx.x % kAlphaSlots, s);
     else
       a_out[blockIdx.x] = s;
+  }
+}
+
+// Wave-speed maxima of every instance of a batch, one slot per instance.
+template <typename R, int C>
+__global__ void __launch_bounds__(NT) alpha1d_batch_kernel(Stage1DArgs a) {
+  __shared__ R red[NW];
+  const int inst = a.tile_inst[blockIdx.x];
+  const BatchInst& bi = a.binst[inst];
+  const int i = a.tile_base[blockIdx.x] + threadIdx.x;
+  const R* w = static_cast<const R*>(a.w) + bi.off;
+  const int n = bi.n;
+  R s = R(0);
+  if (threadIdx.x < T && i < n) {
+    R U[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) U[c] = w[(2 * c) * n + i];
+    s = wave_speed<R, C>(R(a.gas), U);
+    if (!(s == s)) {
+      atomicOr(&a.sc->status, (unsigned)ST_NONPHYSICAL);
+      s = R(0);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NW; ++k) s = fmax(s, red[k]);
+    atomic_max_nonneg(static_cast<R*>(a.a_out) + inst, s);
+  }
+}
+
+__global__ void batch_scalars_kernel(BatchScalars* bsc, int n_inst, int reset, double t_final) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_inst; b += gridDim.x * blockDim.x) {
+    BatchScalars& s = bsc[b];
+    if (reset) {
+      s.t = 0.0;
+      s.dt = 0.0;
+      s.dt_f = 0.0f;
+      s.last = 0u;
+    }
+    const double r = t_final > 0.0 ? t_final - s.t : (double)INFINITY;
+    s.rem = r;
+    s.rem_f = (float)r;
   }
 }
 
@@ -449,7 +547,8 @@ cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C>, a);
+  if (a.tile_inst) return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C, true>, a);
+  return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C, false>, a);
 }
 
 }  // namespace
@@ -476,6 +575,25 @@ cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int sys
     else
       alpha1d_kernel<float, 3><<<ntile, NT, 0, s>>>(wf, of, n, gas, sc, slots);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alpha1d_batch(const Stage1DArgs& a, cudaStream_t s) {
+  if (a.system == 0) {
+    if (a.fp64) alpha1d_batch_kernel<double, 1><<<a.ntile, NT, 0, s>>>(a);
+    else alpha1d_batch_kernel<float, 1><<<a.ntile, NT, 0, s>>>(a);
+  } else {
+    if (a.fp64) alpha1d_batch_kernel<double, 3><<<a.ntile, NT, 0, s>>>(a);
+    else alpha1d_batch_kernel<float, 3><<<a.ntile, NT, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scalars(BatchScalars* bsc, int n_inst, int reset, double t_final,
+                                 cudaStream_t s) {
+  int blocks = (n_inst + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  batch_scalars_kernel<<<blocks, 256, 0, s>>>(bsc, n_inst, reset, t_final);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,12 @@ struct hweno_ctx {
   cudaGraphExec_t g_one = nullptr;   // one step
   bool has_state = false;
   std::string err;
+  // batches of independent 1D instances
+  int n_batch = 0;
+  int* d_tile_inst = nullptr;
+  int* d_tile_base = nullptr;
+  hw::BatchInst* d_binst = nullptr;
+  hw::BatchScalars* d_bsc = nullptr;
 };
 
 namespace {
@@ -77,6 +83,12 @@ hw::Stage1DArgs base_args(const hweno_ctx* h) {
   a.gas = c.gas_gamma;
   for (int k = 0; k < 3; ++k) a.gam[k] = c.lin_w[k];
   hw::finish_stage_args(a);
+  if (h->n_batch > 0) {
+    a.tile_inst = h->d_tile_inst;
+    a.tile_base = h->d_tile_base;
+    a.binst = h->d_binst;
+    a.bsc = h->d_bsc;
+  }
   return a;
 }
 
@@ -326,9 +338,17 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
   }
   if (src) HW_CUDA(h, hw::launch_convert(src, src64, h->U[0], dst64, h->elems, h->stream));
   HW_CUDA(h, hw::launch_set_scalars(h->sc, 1, -1.0, h->stream));
+  const size_t nslot = h->n_batch > 2 * hw::kAlphaSlots ? (size_t)h->n_batch : 2 * hw::kAlphaSlots;
   for (int k = 0; k < 3; ++k)
-    HW_CUDA(h, cudaMemsetAsync(h->part[k], 0, sizeof(double) * 2 * hw::kAlphaSlots, h->stream));
-  if (h->dim == 2)
+    HW_CUDA(h, cudaMemsetAsync(h->part[k], 0, sizeof(double) * nslot, h->stream));
+  if (h->n_batch > 0) {
+    HW_CUDA(h, hw::launch_batch_scalars(h->d_bsc, h->n_batch, 1, -1.0, h->stream));
+    hw::Stage1DArgs a = base_args(h);
+    a.w = h->U[0];
+    a.a_out = h->part[0];
+    a.sc = h->sc;
+    HW_CUDA(h, hw::launch_alpha1d_batch(a, h->stream));
+  } else if (h->dim == 2)
     HW_CUDA(h, hw::launch_alpha2d(h->U[0], h->part[0], h->cfg.nx, h->cfg.ny, h->cfg.system, dst64,
                                   h->cfg.gas_gamma, h->sc, 1, h->stream));
   else
@@ -343,6 +363,8 @@ hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_ou
   if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_step before hweno_set_state");
   if (nsteps < 0) return fail(h, HWENO_ERR_ARG, "nsteps must be >= 0");
   HW_CUDA(h, hw::launch_set_scalars(h->sc, 0, t_final, h->stream));
+  if (h->n_batch > 0)
+    HW_CUDA(h, hw::launch_batch_scalars(h->d_bsc, h->n_batch, 0, t_final, h->stream));
   int left = nsteps;
   if (left >= kGraphSteps) {
     if (!h->g_many) {
@@ -369,6 +391,7 @@ hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_ou
 
 hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags_out, void* ulim_out) {
   if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (h->n_batch > 0) return fail(h, HWENO_ERR_ARG, "hweno_rhs takes a single-instance handle");
   if (!in || !out) return fail(h, HWENO_ERR_ARG, "in and out must be device pointers");
   if (in == out || (ulim_out && (ulim_out == in || ulim_out == out)))
     return fail(h, HWENO_ERR_ARG, "in, out and ulim_out must not overlap");
@@ -435,6 +458,12 @@ hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* st
   hw::DevScalars s;
   HW_CUDA(h, cudaMemcpyAsync(&s, h->sc, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
   HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->n_batch > 0) {  // the time of instance 0
+    hw::BatchScalars b0;
+    HW_CUDA(h, cudaMemcpy(&b0, h->d_bsc, sizeof(b0), cudaMemcpyDeviceToHost));
+    s.t = b0.t;
+    s.dt = b0.dt;
+  }
   if (t) *t = s.t;
   if (last_dt) *last_dt = s.dt;
   if (steps) *steps = (int64_t)s.steps;
@@ -455,8 +484,98 @@ void hweno_destroy(hweno_handle h) {
   if (h->part_rhs) cudaFree(h->part_rhs);
   if (h->sc) cudaFree(h->sc);
   if (h->sc_rhs) cudaFree(h->sc_rhs);
+  if (h->d_tile_inst) cudaFree(h->d_tile_inst);
+  if (h->d_tile_base) cudaFree(h->d_tile_base);
+  if (h->d_binst) cudaFree(h->d_binst);
+  if (h->d_bsc) cudaFree(h->d_bsc);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
+}
+
+hweno_status hweno_create_batch(const hweno_config* cfg, int n_batch, const int* nx,
+                                void* cuda_stream, hweno_handle* out) {
+  if (!out) return fail(nullptr, HWENO_ERR_ARG, "out is NULL");
+  if (!cfg || cfg->dim != 1) return fail(nullptr, HWENO_ERR_ARG, "batches are of 1D instances");
+  if (n_batch < 1 || !nx) return fail(nullptr, HWENO_ERR_ARG, "n_batch must be >= 1 with sizes");
+  hweno_config c = *cfg;
+  long long total = 0;
+  for (int b = 0; b < n_batch; ++b) {
+    if (nx[b] < 4) return fail(nullptr, HWENO_ERR_ARG, "every instance needs nx >= 4");
+    total += nx[b];
+  }
+  if (total > (1ll << 28)) return fail(nullptr, HWENO_ERR_ARG, "batch too large");
+  c.nx = nx[0];
+  hweno_status st = validate(&c);
+  if (st != HWENO_OK) return st;
+  c.nx = (int)total;
+  hweno_handle h = nullptr;
+  st = hweno_create(&c, cuda_stream, &h);
+  if (st != HWENO_OK) return st;
+  h->cfg.nx = (int)total;
+  h->n_batch = n_batch;
+  // tiles of every instance, and each instance's geometry
+  std::string msg;
+  const int C = h->C;
+  long long ntile = 0;
+  for (int b = 0; b < n_batch; ++b) ntile += (nx[b] + hw::kTile1D - 1) / hw::kTile1D;
+  int* tinst = new int[ntile];
+  int* tbase = new int[ntile];
+  hw::BatchInst* bi = new hw::BatchInst[n_batch];
+  long long k = 0, cells = 0;
+  for (int b = 0; b < n_batch; ++b) {
+    const double dx = (c.x1 - c.x0) / nx[b];
+    bi[b].off = (long long)C * 2 * cells;
+    bi[b].n = nx[b];
+    bi[b].first_tile = (int)k;
+    bi[b].inv_dx = 1.0 / dx;
+    bi[b].h = 0.5 * dx;
+    bi[b].cfl_dx = c.cfl * dx;
+    bi[b].inv_dx_f = (float)bi[b].inv_dx;
+    bi[b].hthr_f = (float)(c.kxrcf_threshold * bi[b].h);
+    bi[b].cfl_dx_f = (float)bi[b].cfl_dx;
+    bi[b].pad = 0.0f;
+    for (int base = 0; base < nx[b]; base += hw::kTile1D, ++k) {
+      tinst[k] = b;
+      tbase[k] = base;
+    }
+    cells += nx[b];
+  }
+  h->ntile = (int)ntile;
+  cudaError_t e = cudaMalloc(&h->d_tile_inst, sizeof(int) * ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tile_base, sizeof(int) * ntile);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_binst, sizeof(hw::BatchInst) * n_batch);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_bsc, sizeof(hw::BatchScalars) * n_batch);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tile_inst, tinst, sizeof(int) * ntile, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tile_base, tbase, sizeof(int) * ntile, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_binst, bi, sizeof(hw::BatchInst) * n_batch, cudaMemcpyHostToDevice);
+  // one alpha slot per instance in each of the three rotating buffers
+  for (int r = 0; r < 3 && e == cudaSuccess && n_batch > 2 * hw::kAlphaSlots; ++r) {
+    cudaFree(h->part[r]);
+    h->part[r] = nullptr;
+    e = cudaMalloc(&h->part[r], sizeof(double) * n_batch);
+  }
+  delete[] tinst;
+  delete[] tbase;
+  delete[] bi;
+  if (e != cudaSuccess) {
+    msg = std::string("batch allocation: ") + cudaGetErrorString(e);
+    hweno_destroy(h);
+    return fail(nullptr, HWENO_ERR_CUDA, msg);
+  }
+  *out = h;
+  return HWENO_OK;
+}
+
+hweno_status hweno_batch_times(hweno_handle h, double* t) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (h->n_batch < 1 || !t) return fail(h, HWENO_ERR_ARG, "not a batch handle, or t is NULL");
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  hw::BatchScalars* b = new hw::BatchScalars[h->n_batch];
+  cudaError_t e = cudaMemcpy(b, h->d_bsc, sizeof(hw::BatchScalars) * h->n_batch, cudaMemcpyDeviceToHost);
+  for (int k = 0; k < h->n_batch && e == cudaSuccess; ++k) t[k] = b[k].t;
+  delete[] b;
+  if (e != cudaSuccess) return fail(h, HWENO_ERR_CUDA, cudaGetErrorString(e));
+  return HWENO_OK;
 }
 
 const char* hweno_last_error(hweno_handle h) {

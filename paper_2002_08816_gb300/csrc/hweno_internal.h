@@ -9,6 +9,22 @@
 
 namespace hw {
 
+// One instance of a batch of independent 1D problems.
+struct BatchInst {
+  long long off;           // element offset of the instance's state in the batch buffer
+  int n;                   // cells
+  int first_tile;          // first tile of the instance
+  double inv_dx, h, cfl_dx;
+  float inv_dx_f, hthr_f, cfl_dx_f, pad;
+};
+
+// Time bookkeeping of one instance.
+struct BatchScalars {
+  double t, rem, dt;
+  float dt_f, rem_f;
+  unsigned last, pad;
+};
+
 // Everything one 1D stage launch needs.  Pointers are device pointers.
 struct Stage1DArgs {
   const void* w;         // stage input [C][2][n]
@@ -40,6 +56,11 @@ struct Stage1DArgs {
   double cfl_dx;         // cfl * dx
   float hthr;            // (float)(thr * h)
   float f32[7];          // FP32 copies: gamma_0..2, eps, gas_gamma, 1/dx, cfl*dx
+  // batches of independent instances (nullable): tile -> instance, first cell
+  const int* tile_inst;
+  const int* tile_base;
+  const BatchInst* binst;
+  BatchScalars* bsc;
 };
 
 // Fills the derived fields of a from its primary ones.
@@ -102,6 +123,11 @@ cudaError_t launch_alpha2d(const void* w, void* a_out, int nx, int ny, int syste
                            double gas, DevScalars* sc, int slots, cudaStream_t s);
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
+// Batched variants: one launch over all instances (a.tile_inst != nullptr);
+// alpha slots are one per instance.
+cudaError_t launch_alpha1d_batch(const Stage1DArgs& a, cudaStream_t s);
+cudaError_t launch_batch_scalars(BatchScalars* bsc, int n_inst, int reset, double t_final,
+                                 cudaStream_t s);
 // Wave-speed maxima of w, in the kernel's precision: one per tile (slots = 0)
 // or folded into kAlphaSlots zeroed slots by atomic max (slots = 1).
 cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int system, int fp64,

@@ -25,7 +25,8 @@ _D, _I, _VP = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
 
 EXPORTED = ["hweno_default_config", "hweno_create", "hweno_set_state", "hweno_step",
             "hweno_rhs", "hweno_get_state", "hweno_stats", "hweno_destroy",
-            "hweno_last_error", "hweno_rhs1d_noalloc"]
+            "hweno_last_error", "hweno_rhs1d_noalloc", "hweno_create_batch",
+            "hweno_batch_times"]
 
 
 class hweno_config(ctypes.Structure):
@@ -73,6 +74,10 @@ def lib():
         L.hweno_destroy.argtypes = [_VP]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_last_error.argtypes = [_VP]
+        L.hweno_create_batch.restype = _I
+        L.hweno_create_batch.argtypes = [P, _I, ctypes.POINTER(_I), _VP, ctypes.POINTER(_VP)]
+        L.hweno_batch_times.restype = _I
+        L.hweno_batch_times.argtypes = [_VP, ctypes.POINTER(_D)]
         L.hweno_rhs1d_noalloc.restype = _I
         L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
         _lib = L
@@ -94,6 +99,20 @@ def hweno_create(cfg, stream=0):
     h = _VP()
     _check(lib().hweno_create(ctypes.byref(cfg), _VP(stream or None), ctypes.byref(h)))
     return h.value
+
+
+def hweno_create_batch(cfg, nx_list, stream=0):
+    n = len(nx_list)
+    arr = (_I * n)(*[int(v) for v in nx_list])
+    h = _VP()
+    _check(lib().hweno_create_batch(ctypes.byref(cfg), n, arr, _VP(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def hweno_batch_times(h, n):
+    t = (_D * n)()
+    _check(lib().hweno_batch_times(h, t), h)
+    return list(t)
 
 
 def hweno_set_state(h, ptr, dtype, on_device):
