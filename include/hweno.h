@@ -48,7 +48,7 @@ typedef enum {
 } hweno_status;
 
 enum { HWENO_BURGERS = 0, HWENO_EULER = 1 };
-enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1 };
+enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECTIVE = 2 };
 enum { HWENO_TROUBLED_HYBRID = 0, HWENO_TROUBLED_ALL = 1, HWENO_TROUBLED_NONE = 2 };
 enum { HWENO_FP32 = 0, HWENO_FP64 = 1 };
 
@@ -58,7 +58,10 @@ typedef struct {
   int nx, ny;             /* cells per direction (ny ignored for dim 1); nx, ny >= 4;
                              2D cells must be square: (x1-x0)/nx = (y1-y0)/ny */
   double x0, x1, y0, y1;  /* domain [x0,x1] x [y0,y1] */
-  int bc;                 /* HWENO_BC_PERIODIC or HWENO_BC_OUTFLOW, all sides */
+  int bc;                 /* HWENO_BC_PERIODIC or HWENO_BC_OUTFLOW on all sides, or
+                             HWENO_BC_REFLECTIVE (solid walls; 1D Euler only): a ghost
+                             is the mirror image of an interior cell, density and
+                             energy even, momentum odd */
   double gas_gamma;       /* ratio of specific heats (Euler), > 1 */
   double lin_w[5];        /* linear weights gamma_0..gamma_2 (1D) or ..gamma_4 (2D):
                              all > 0, |sum - 1| <= 1e-12 (Sec. 2.1 Step 1) */

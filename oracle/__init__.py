@@ -11,6 +11,7 @@ code with it.
 from .oracle import (  # noqa: F401
     BC_OUTFLOW,
     BC_PERIODIC,
+    BC_REFLECTIVE,
     BURGERS,
     EULER,
     TROUBLED_ALL,

@@ -27,6 +27,7 @@ extern "C" {
 
 #define HWO_BC_PERIODIC 0
 #define HWO_BC_OUTFLOW 1
+#define HWO_BC_REFLECTIVE 2 /* 1D Euler: a solid wall at each end */
 
 #define HWO_TROUBLED_HYBRID 0 /* KXRCF decides (the "new hybrid HWENO" scheme) */
 #define HWO_TROUBLED_ALL 1    /* every cell troubled (the "new HWENO" scheme, Sec. 3) */

@@ -275,11 +275,25 @@ double hwo1d_alpha(const hwo1d_cfg* cfg, const double* u) {
 #define G1 3 /* ghost cells per side: the stencil of one stage reaches 3 cells */
 
 /* Reading: periodic ghosts wrap; outflow ghosts copy the boundary cell's
- * average and first moment. */
-static int ghost_src(const hwo1d_cfg* cfg, int i) {
+ * average and first moment; reflective ghosts (1D Euler) are the mirror images
+ * of the interior cells (*mirror = 1). */
+static int ghost_src(const hwo1d_cfg* cfg, int i, int* mirror) {
   int N = cfg->nx;
+  *mirror = 0;
   if (cfg->bc == HWO_BC_PERIODIC) return ((i % N) + N) % N;
+  if (cfg->bc == HWO_BC_REFLECTIVE && (i < 0 || i >= N)) {
+    *mirror = 1;
+    return i < 0 ? -1 - i : 2 * N - 1 - i;
+  }
   return i < 0 ? 0 : (i >= N ? N - 1 : i);
+}
+
+/* Sign of a mirrored ghost's moment: q(x) -> s q(2 x_w - x) keeps the average
+ * times s and the first moment times -s; s = -1 for the momentum, +1 for the
+ * density and the energy. */
+static double mirror_sign(int c, int m) {
+  double s = c == 1 ? -1.0 : 1.0;
+  return m == 0 ? s : -s;
 }
 
 /* Reading of the KXRCF indicator (Krivodonova et al., with the degree-1 cell
@@ -327,11 +341,13 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   double* fh = (double*)malloc(sizeof(double) * C * NE); /* flux at e+1/2 */
   int status = 0;
 
+  if (cfg->bc == HWO_BC_REFLECTIVE && !euler) return -1;
   for (int e = 0; e < NE; ++e) {
-    int s = ghost_src(cfg, e - G1);
+    int mir;
+    int s = ghost_src(cfg, e - G1, &mir);
     for (int c = 0; c < C; ++c) {
-      ub[c * NE + e] = u[(c * 2 + 0) * N + s];
-      vb[c * NE + e] = u[(c * 2 + 1) * N + s];
+      ub[c * NE + e] = u[(c * 2 + 0) * N + s] * (mir ? mirror_sign(c, 0) : 1.0);
+      vb[c * NE + e] = u[(c * 2 + 1) * N + s] * (mir ? mirror_sign(c, 1) : 1.0);
     }
   }
 

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libhweno_oracle.so")
 
 BURGERS, EULER = 0, 1
-BC_PERIODIC, BC_OUTFLOW = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_REFLECTIVE = 0, 1, 2
 TROUBLED_HYBRID, TROUBLED_ALL, TROUBLED_NONE = 0, 1, 2
 
 _D = ctypes.c_double

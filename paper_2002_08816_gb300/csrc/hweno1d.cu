@@ -165,11 +165,21 @@ __global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
     }
   }
   if (tid < T + 2 * H) {
-    const int g = bc_map(base - H + tid, n, a.bc);
+    if (a.bc == 2) {
+      bool mir;
+      const int g = bc_map_wall(base - H + tid, n, &mir);
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      sm.u[c][0][tid] = w[(2 * c + 0) * n + g];
-      sm.u[c][1][tid] = w[(2 * c + 1) * n + g];
+      for (int c = 0; c < C; ++c) {
+        sm.u[c][0][tid] = w[(2 * c + 0) * n + g] * (mir ? R(mirror_sign(c, 0)) : R(1));
+        sm.u[c][1][tid] = w[(2 * c + 1) * n + g] * (mir ? R(mirror_sign(c, 1)) : R(1));
+      }
+    } else {
+      const int g = bc_map(base - H + tid, n, a.bc);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        sm.u[c][0][tid] = w[(2 * c + 0) * n + g];
+        sm.u[c][1][tid] = w[(2 * c + 1) * n + g];
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));

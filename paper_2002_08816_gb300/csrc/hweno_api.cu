@@ -216,8 +216,10 @@ hweno_status validate(const hweno_config* c) {
   if (c->nx < 4) return fail(nullptr, HWENO_ERR_ARG, "nx must be >= 4");
   if (c->nx > (1 << 28)) return fail(nullptr, HWENO_ERR_ARG, "nx too large");
   if (!(c->x1 > c->x0)) return fail(nullptr, HWENO_ERR_ARG, "x1 must exceed x0");
-  if (c->bc != HWENO_BC_PERIODIC && c->bc != HWENO_BC_OUTFLOW)
+  if (c->bc != HWENO_BC_PERIODIC && c->bc != HWENO_BC_OUTFLOW && c->bc != HWENO_BC_REFLECTIVE)
     return fail(nullptr, HWENO_ERR_ARG, "unknown boundary condition");
+  if (c->bc == HWENO_BC_REFLECTIVE && (c->dim != 1 || c->system != HWENO_EULER))
+    return fail(nullptr, HWENO_ERR_ARG, "reflective walls are available for 1D Euler");
   if (c->system == HWENO_EULER && !(c->gas_gamma > 1.0))
     return fail(nullptr, HWENO_ERR_ARG, "gas_gamma must exceed 1");
   const int ncand = c->dim == 1 ? 3 : 5;

@@ -57,6 +57,24 @@ __device__ __forceinline__ int bc_map(int g, int n, int bc) {
   return g < 0 ? 0 : (g >= n ? n - 1 : g);
 }
 
+// Reflective walls (1D Euler): a ghost is the mirror image of an interior
+// cell; *mirror tells the caller to apply mirror_sign.  Tiles may stage cells
+// far beyond the domain when n is small; those (never used by an own cell) are
+// clamped into range.
+__device__ __forceinline__ int bc_map_wall(int g, int n, bool* mirror) {
+  *mirror = g < 0 || g >= n;
+  if (g < 0) return min(-1 - g, n - 1);
+  if (g >= n) return max(2 * n - 1 - g, 0);
+  return g;
+}
+
+// q(x) -> s q(2 x_w - x) keeps the average times s and the first moment times
+// -s; s = -1 for the momentum (component 1), +1 for density and energy.
+__device__ __forceinline__ float mirror_sign(int c, int m) {
+  const float s = c == 1 ? -1.0f : 1.0f;
+  return m == 0 ? s : -s;
+}
+
 template <int NT>
 __device__ __forceinline__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

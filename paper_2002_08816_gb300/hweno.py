@@ -17,7 +17,7 @@ HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL, HWENO_ERR_TIMEOU
     HWENO_ERR_STATE, HWENO_ERR_TOO_LARGE = range(7)
 HWENO_NOALLOC_MAX_CELLS = 4194304
 HWENO_BURGERS, HWENO_EULER = 0, 1
-HWENO_BC_PERIODIC, HWENO_BC_OUTFLOW = 0, 1
+HWENO_BC_PERIODIC, HWENO_BC_OUTFLOW, HWENO_BC_REFLECTIVE = 0, 1, 2
 HWENO_TROUBLED_HYBRID, HWENO_TROUBLED_ALL, HWENO_TROUBLED_NONE = 0, 1, 2
 HWENO_FP32, HWENO_FP64 = 0, 1
 

@@ -57,7 +57,7 @@ def test_rhs_burgers(prec, bc, nx):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("bc", [H.HWENO_BC_PERIODIC, H.HWENO_BC_OUTFLOW])
+@pytest.mark.parametrize("bc", [H.HWENO_BC_PERIODIC, H.HWENO_BC_OUTFLOW, H.HWENO_BC_REFLECTIVE])
 @pytest.mark.parametrize("nx", SIZES)
 def test_rhs_euler(prec, bc, nx):
     _compare_rhs(H.HWENO_EULER, nx, bc, prec, H.HWENO_TROUBLED_HYBRID, seed=nx)
@@ -200,3 +200,17 @@ def test_step_before_set_state_is_an_error():
         assert ei.value.status == H.HWENO_ERR_STATE
     finally:
         H.hweno_destroy(h)
+
+
+@pytest.mark.parametrize("prec,tol", [(H.HWENO_FP64, 1e-12), (H.HWENO_FP32, 1e-4)])
+def test_run_blast_waves_between_walls(prec, tol):
+    """Example 3.8's data (two blast waves, reflective walls), 800 cells, 40 steps."""
+    nx = 800
+
+    def g(x):
+        p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+        return W.euler_conserved_1d(np.ones_like(x), np.zeros_like(x), p)
+    u = W.cell_moments_1d(g, nx, 0.0, 1.0)
+    stats, nt = _compare_run(H.HWENO_EULER, nx, H.HWENO_BC_REFLECTIVE, prec, 40, u, 0.0, 1.0, tol,
+                             cfl=0.6)
+    assert nt > 0
