@@ -95,6 +95,9 @@ int hwo2d_rhs(const hwo2d_cfg* cfg, const double* u, double alpha_x,
 int hwo2d_rhs_ex(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alpha_y,
                  double* rhs, double* ulim, unsigned char* flags, double* indicator,
                  double* points);
+int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alpha_y,
+                 const unsigned char* flags_in, double* rhs, double* ulim,
+                 unsigned char* flags, double* indicator, double* points);
 void hwo2d_alpha(const hwo2d_cfg* cfg, const double* u, double* ax, double* ay);
 double hwo2d_dt(const hwo2d_cfg* cfg, const double* u, double cfl, double t,
                 double t_final);

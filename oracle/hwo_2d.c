@@ -421,7 +421,7 @@ static void tau_weights5(const double* gam, double eps, const double beta[5], do
 
 int hwo2d_rhs(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alpha_y,
               double* rhs, double* ulim, unsigned char* flags, double* indicator) {
-  return hwo2d_rhs_ex(cfg, u, alpha_x, alpha_y, rhs, ulim, flags, indicator, NULL);
+  return hwo2d_rhs_fx(cfg, u, alpha_x, alpha_y, NULL, rhs, ulim, flags, indicator, NULL);
 }
 
 /* As hwo2d_rhs; points (nullable, [C][4 ng + ng^2][ny][nx]) receives the
@@ -430,6 +430,17 @@ int hwo2d_rhs(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alph
 int hwo2d_rhs_ex(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alpha_y,
                  double* rhs, double* ulim, unsigned char* flags, double* indicator,
                  double* points) {
+  return hwo2d_rhs_fx(cfg, u, alpha_x, alpha_y, NULL, rhs, ulim, flags, indicator, points);
+}
+
+/* As hwo2d_rhs_ex with the troubled cells given (flags_in, [ny][nx], nullable)
+ * instead of decided by KXRCF: the operator with its switch held fixed, whose
+ * derivative the adjoint computes.  Periodic boundaries only (a ghost cell is
+ * troubled iff the cell it wraps to is); -1 otherwise. */
+int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double alpha_y,
+                 const unsigned char* flags_in, double* rhs, double* ulim,
+                 unsigned char* flags, double* indicator, double* points) {
+  if (flags_in && cfg->bc != HWO_BC_PERIODIC) return -1;
   const int NX = cfg->nx, NY = cfg->ny, N = NX * NY;
   const int C = hwo2d_ncomp(cfg->system);
   const int EX = NX + 2 * G2, EY = NY + 2 * G2, NE = EX * EY;
@@ -483,6 +494,10 @@ int hwo2d_rhs_ex(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
         I = kxrcf2d(ub, vb, wb, e, 1, EX, ub[e], ub[e], dx, dy);
       }
       ind[e] = I;
+      if (flags_in) {
+        fl[e] = flags_in[map1(ej - G2, NY, cfg->bc) * NX + map1(ei - G2, NX, cfg->bc)] != 0;
+        continue;
+      }
       fl[e] = cfg->troubled_mode == HWO_TROUBLED_ALL ? 1
               : cfg->troubled_mode == HWO_TROUBLED_NONE ? 0
               : I > cfg->kxrcf_threshold;

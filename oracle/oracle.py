@@ -132,6 +132,8 @@ def lib():
             L.hwo2d_rhs.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD]
             L.hwo2d_rhs_ex.restype = _I
             L.hwo2d_rhs_ex.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD, _PD]
+            L.hwo2d_rhs_fx.restype = _I
+            L.hwo2d_rhs_fx.argtypes = [P2, _PD, _D, _D, _PU8, _PD, _PD, _PU8, _PD, _PD]
             L.hwo2d_alpha.restype = None
             L.hwo2d_alpha.argtypes = [P2, _PD, _PD, _PD]
             L.hwo2d_dt.restype = _D
