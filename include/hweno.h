@@ -168,6 +168,43 @@ hweno_status hweno_create_batch(const hweno_config* cfg, int n_batch, const int*
  * for the stream. */
 hweno_status hweno_batch_times(hweno_handle h, double* t);
 
+/* ---- Adjoint (2D, periodic boundaries) --------------------------------
+ * The derivative of the Runge-Kutta map with the scheme's switches held
+ * fixed: the troubled cells of every stage, the Lax-Friedrichs speeds
+ * (alpha_x, alpha_y) of every stage and the dt of every step are those of the
+ * recorded forward run (Sec. 2.2 Steps 4-6 with Eq. (ode2) and Eq. (RK)).  The
+ * paper defines no adjoint; the derivative is of the discrete scheme as it
+ * runs.  Where an absolute value in tau (Eq. (tao4), Eq. (tao5)) has a kink,
+ * the derivative with sign(0) = 0 is taken. */
+
+/* Like hweno_step (from the current state, t_final as there), and records
+ * the switches and every checkpoint_every-th state for hweno_backward.  The
+ * tape (3 nsteps nx ny bytes of flags, ceil(nsteps / checkpoint_every)
+ * states, a few scalars per step) belongs to the handle and is replaced by
+ * the next hweno_record.  Waits for the stream; returns HWENO_ERR_ARG unless
+ * dim == 2, bc == HWENO_BC_PERIODIC, nsteps >= 1 and checkpoint_every >= 1,
+ * HWENO_ERR_STATE before set_state, HWENO_ERR_NONPHYSICAL as hweno_step. */
+hweno_status hweno_record(hweno_handle h, int nsteps, int checkpoint_every, double t_final,
+                          double* t_out);
+
+/* Vector-Jacobian product of the recorded run: grad_in = (d u_N / d u_0)^T
+ * grad_out, with u_0 the state hweno_record started from and u_N the state
+ * it ended at (state layout, element type dtype, host or device pointers as
+ * in set_state; caller owned).  Recomputes each checkpoint segment forward
+ * (3 checkpoint_every + 1 states of scratch) and runs the adjoint stages
+ * backwards through it.  The current state is not changed.  Waits for the
+ * stream; HWENO_ERR_STATE without a recorded run. */
+hweno_status hweno_backward(hweno_handle h, const void* grad_out, void* grad_in, int dtype,
+                            int on_device);
+
+/* Vector-Jacobian product of one operator evaluation: grad = (d L(in)/d in)^T
+ * lam, L as in hweno_rhs (Step 4 included) but with the troubled cells given
+ * (flags, nx*ny bytes, 1 = troubled) and alpha_x, alpha_y given.  Device
+ * pointers in the configured precision; grad must not overlap in or lam.
+ * Waits for the stream. */
+hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags, double alpha_x,
+                           double alpha_y, const void* lam, void* grad);
+
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);
 

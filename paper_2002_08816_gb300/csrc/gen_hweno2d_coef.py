@@ -1,9 +1,14 @@
 """Generates hweno2d_coef.cuh: the 2D reconstruction of Zhao & Qiu,
 arXiv:2002.08816, Sec. 2.2 Step 5, as straight-line device code.
 
-Run once (needs sympy); the output is committed:
+Run once (needs sympy); the outputs are committed:
 
     python gen_hweno2d_coef.py > hweno2d_coef.cuh
+    python gen_hweno2d_coef.py adjoint > hweno2d_adj_coef.cuh
+
+The second file holds what the adjoint kernels need: the transposes of the
+point maps (g[j] += sum_p M[p][j] l[p]) and the gradients of the smoothness
+indicators (g += s grad beta(d), from the same LDL^T forms).
 
 Everything is derived in exact arithmetic from the moment conditions the paper
 states, in the reference coordinates xi = (x - x_i)/dx, eta = (y - y_j)/dy:
@@ -182,6 +187,64 @@ def emit_beta(name, D, forms):
     return "\n".join(lines)
 
 
+def emit_map_T(name, rows):
+    lines = ["template <typename R>",
+             "__device__ __forceinline__ void %s(const R* l, R* g) {" % name]
+    for j in range(19):
+        terms = []
+        for p, row in enumerate(rows):
+            s = lit(row[j])
+            if s is not None:
+                terms.append("%s * l[%d]" % (s, p))
+        if terms:
+            lines.append("  g[%d] += %s;" % (j, " + ".join(terms)))
+    lines.append("}")
+    return "\n".join(lines)
+
+
+def emit_beta_grad(name, D, forms):
+    lines = ["template <typename R>",
+             "__device__ __forceinline__ void %s(const R* d, R s, R* g) {" % name,
+             "  R t;"]
+    for k in range(forms.shape[0]):
+        idx = [(j, lit(forms[k, j])) for j in range(19)]
+        idx = [(j, c) for j, c in idx if c is not None]
+        if not idx:
+            continue
+        lines.append("  t = %s * s * (%s);" % (lit(2 * D[k]), " + ".join("%s * d[%d]" % (c, j) for j, c in idx)))
+        for j, c in idx:
+            lines.append("  g[%d] += %s * t;" % (j, c))
+    lines.append("}")
+    return "\n".join(lines)
+
+
+def main_adjoint():
+    out = ["// Generated by gen_hweno2d_coef.py (adjoint) from the moment conditions of\n"
+           "// Zhao & Qiu, arXiv:2002.08816, Sec. 2.2 Step 5: transposed point maps and\n"
+           "// smoothness-indicator gradients.  Do not edit: rerun the generator.\n"
+           "#pragma once\n"
+           "namespace hw2 {"]
+    M0 = p0_map()
+    MQ = {n: quad_map(n) for n in (1, 2, 3, 4)}
+    B4, B2 = gram(4), gram(2)
+    for ng in (2, 3):
+        pts = points(ng)
+        nf = 4 * ng
+        out.append("// ---- %d Gauss points per direction" % ng)
+        out.append(emit_map_T("p0_faces_ng%d_T" % ng, value_map(M0, 4, pts[:nf])))
+        out.append(emit_map_T("p0_interior_ng%d_T" % ng, value_map(M0, 4, pts[nf:])))
+        for n in (1, 2, 3, 4):
+            out.append(emit_map_T("q%d_faces_ng%d_T" % (n, ng), value_map(MQ[n], 2, pts[:nf])))
+    D0, F0 = ldl_forms(B4, M0)
+    out.append("// gradients of the smoothness indicators of Eq. (2dGHYZ), dx = dy")
+    out.append(emit_beta_grad("beta_p0_grad", D0, F0))
+    for n in (1, 2, 3, 4):
+        Dn, Fn = ldl_forms(B2, MQ[n])
+        out.append(emit_beta_grad("beta_q%d_grad" % n, Dn, Fn))
+    out.append("}  // namespace hw2")
+    sys.stdout.write("\n\n".join(out) + "\n")
+
+
 def main():
     out = ["// Generated by gen_hweno2d_coef.py from the moment conditions of Zhao & Qiu,\n"
            "// arXiv:2002.08816, Sec. 2.2 Step 5 (exact rationals, printed to 20 digits).\n"
@@ -211,4 +274,7 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "adjoint":
+        main_adjoint()
+    else:
+        main()

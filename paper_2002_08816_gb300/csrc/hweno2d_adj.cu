@@ -1,0 +1,629 @@
+// Adjoint of one third-order TVD Runge-Kutta stage of the 2D hybrid HWENO
+// scheme (Zhao & Qiu, arXiv:2002.08816, Sec. 2.2) with the switches of the
+// forward run held fixed: the troubled cells of the stage (recorded in the
+// forward pass), its Lax-Friedrichs speeds (alpha_x, alpha_y) and the step's
+// dt.  Periodic boundaries.
+//
+// Forward, a stage maps its raw input w to W = Step 4(w) (first moments of
+// troubled cells modified), to the values P_i = Step 5(D_i) at the 4 ng + ng^2
+// Gauss points of every cell i (D_i: the 19 data of its 3x3 stencil), to the
+// Lax-Friedrichs fluxes and L = Eq. (ode2), and to u_out = a W0 + b (W + dt L).
+// Backward, lam being the adjoint of u_out:
+//   kernel A, per cell i: the adjoints of the fluxes at its faces (from lam of
+//     i and of its four neighbours, times b dt), of its point values (through
+//     the flux Jacobians), and G_i = (dP_i/dD_i)^T lam_P, the adjoints of its
+//     19 data (transposed linear p0, or the reverse of Step 5.1's nonlinear
+//     combination where the stencil holds a troubled cell);
+//   kernel B, per cell j: mu_j = b lam_j + the entries of G_i that belong to
+//     j, over the cells i whose stencil holds j (+ the adjoint of W0 at stage
+//     1): the adjoint of W; then the reverse of Step 4, where mu passes
+//     through unmodified moments and each troubled cell sends the adjoint of
+//     its modified moments back to the five data Step 1 read.
+// Reverse-mode arithmetic: hweno_adj.cuh; transposed maps and smoothness-
+// indicator gradients: the generated hweno2d_adj_coef.cuh.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hweno2d_adj_coef.cuh"
+#include "hweno_adj.cuh"
+#include "hweno_device.cuh"
+#include "hweno_internal.h"
+
+namespace hw {
+namespace {
+
+constexpr int TX = kTile2DX, TY = kTile2DY;
+constexpr int NT = kThreads2D;
+constexpr int AX = TX + 4, AY = TY + 4;  // raw input, 2-cell halo
+constexpr int BX = TX + 2, BY = TY + 2;  // 1-cell halo
+static_assert(TX * TY == NT, "one own cell per thread");
+
+template <typename R, int C>
+struct SmemA {
+  R u[C][3][AY][AX];    // raw stage input
+  R lam[C][3][BY][BX];  // b dt lam (the adjoint of L)
+  R vl[C][BY][BX];      // Step 4 moments
+  R wl[C][BY][BX];
+  uint8_t fl[BY][BX];
+};
+
+template <typename R, int C>
+struct SmemB {
+  R mu[C][3][BY][BX];   // adjoint of W
+  R u[C][3][AY][AX];    // raw stage input (tiles near a troubled cell)
+  R cx[C][5][BY][BX];   // x-direction Step 1 of a troubled cell: adjoints of
+  R cy[C][5][BY][BX];   // u_{i-1}, u_i, u_{i+1}, v_{i-1}, v_{i+1} (y: w)
+  uint8_t fl[BY][BX];
+};
+
+// scalar parameters in the kernel's precision
+template <typename R>
+struct AdjParams {
+  R gam[5], eps, gas, inv_dx, inv_dy;
+  __device__ __forceinline__ explicit AdjParams(const Adj2DArgs& a) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gam[k] = a.f32[k];
+      eps = a.f32[5]; gas = a.f32[6]; inv_dx = a.f32[7]; inv_dy = a.f32[8];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) gam[k] = a.gam[k];
+      eps = a.eps; gas = a.gas; inv_dx = 1.0 / a.dx; inv_dy = 1.0 / a.dy;
+    }
+  }
+};
+
+// Eq. (RK) weight b of the stage's W + dt L
+template <typename R>
+__device__ __forceinline__ R stage_b(int stage) {
+  return stage == 1 ? R(1) : stage == 2 ? R(0.25) : stage == 3 ? R(2.0 / 3.0) : R(0);
+}
+
+// The 19 data of component c of the cell at own-tile coordinates (ci, cj),
+// ci, cj in [-1, TX] x [-1, TY]: averages of cells 1..9, Step 4 x- and
+// y-moments of cells 2, 4, 5, 6, 8 (Fig. 1).
+template <typename S, typename R>
+__device__ __forceinline__ void gather19a(const S& sm, int c, int ci, int cj, R* d) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d[k] = sm.u[c][0][cj + 2 + k / 3 - 1][ci + 2 + k % 3 - 1];
+  const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    d[9 + k] = sm.vl[c][cj + 1 + my[k]][ci + 1 + mx[k]];
+    d[14 + k] = sm.wl[c][cj + 1 + my[k]][ci + 1 + mx[k]];
+  }
+}
+
+// Step 5.1 interface values of an Euler cell next to a troubled cell (x-faces
+// in the x characteristic fields, y-faces in the y fields of the average).
+template <int NG, typename S, typename R>
+__device__ __noinline__ void hw_faces_euler_vals(const S& sm, int ci, int cj, const R* gam, R eps,
+                                                 R gas, R (*out)[4 * NG]) {
+  constexpr int NF = 4 * NG;
+  R D[4][19];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) gather19a(sm, c, ci, cj, D[c]);
+  R U[4] = {D[0][4], D[1][4], D[2][4], D[3][4]};
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const int lo = dir == 0 ? 0 : 2 * NG, hi = lo + 2 * NG;
+    R Rm[4][4], Lm[4][4];
+    Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int p = 0; p < NF; ++p)
+        if (p >= lo && p < hi) out[c][p] = R(0);
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+      R e[19], chv[NF];
+#pragma unroll
+      for (int k = 0; k < 19; ++k)
+        e[k] = Lm[f][0] * D[0][k] + Lm[f][1] * D[1][k] + Lm[f][2] * D[2][k] + Lm[f][3] * D[3][k];
+      hweno2d_faces<NG>(e, gam, eps, lo, hi, chv);
+#pragma unroll
+      for (int p = 0; p < NF; ++p)
+        if (p >= lo && p < hi)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) out[c][p] += Rm[c][f] * chv[p];
+    }
+  }
+}
+
+// Reverse of hw_faces_euler_vals: G[c][k] += the adjoint of datum k of
+// component c, given the adjoints lam[c][p] of the interface values.
+template <int NG, typename S, typename R>
+__device__ __noinline__ void hw_faces_euler_vjp(const S& sm, int ci, int cj, const R* gam, R eps,
+                                                R gas, R (*lam)[4 * NG], R (*G)[19]) {
+  constexpr int NF = 4 * NG;
+  R D[4][19];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) gather19a(sm, c, ci, cj, D[c]);
+  R U[4] = {D[0][4], D[1][4], D[2][4], D[3][4]};
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const int lo = dir == 0 ? 0 : 2 * NG, hi = lo + 2 * NG;
+    R Rm[4][4], Lm[4][4], lR[4][4], lL[4][4];
+    Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lR[r][q] = lL[r][q] = R(0);
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+      R e[19], chv[NF], lch[NF], ge[19];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) {
+        e[k] = Lm[f][0] * D[0][k] + Lm[f][1] * D[1][k] + Lm[f][2] * D[2][k] + Lm[f][3] * D[3][k];
+        ge[k] = R(0);
+      }
+      hweno2d_faces<NG>(e, gam, eps, lo, hi, chv);
+#pragma unroll
+      for (int p = 0; p < NF; ++p) {
+        lch[p] = R(0);
+        if (p >= lo && p < hi) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            lch[p] += Rm[c][f] * lam[c][p];
+            lR[c][f] += chv[p] * lam[c][p];
+          }
+        }
+      }
+      hweno2d_faces_vjp<NG>(e, gam, eps, lch, ge);
+#pragma unroll
+      for (int k = 0; k < 19; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          G[c][k] += Lm[f][c] * ge[k];
+          lL[f][c] += ge[k] * D[c][k];
+        }
+    }
+    R gU[4] = {R(0), R(0), R(0), R(0)};
+    euler2d_eigen_vjp(gas, U, dir, lR, lL, gU);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) G[c][4] += gU[c];
+  }
+}
+
+// Reverse of Step 4 for a troubled Euler cell (lx, ly) of the 1-halo grid:
+// the adjoints mu of its modified x- and y-moments go back to the five data
+// of each direction (cx, cy), including through the eigen-system of the
+// cell's average.
+template <typename S, typename R>
+__device__ __noinline__ void limit_euler2d_vjp(S& sm, int lx, int ly, const R* gam, R eps, R gas) {
+  const int rx = lx + 1, ry = ly + 1;
+  R U[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][ry][rx];
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    const int sx = dir == 0 ? 1 : 0, sy = dir == 0 ? 0 : 1;
+    const int mom = dir == 0 ? 1 : 2;
+    R Rm[4][4], Lm[4][4], lR[4][4], lL[4][4], src[5][4], out[5][4], mu[4];
+    Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      src[0][c] = sm.u[c][0][ry - sy][rx - sx];
+      src[1][c] = U[c];
+      src[2][c] = sm.u[c][0][ry + sy][rx + sx];
+      src[3][c] = sm.u[c][mom][ry - sy][rx - sx];
+      src[4][c] = sm.u[c][mom][ry + sy][rx + sx];
+      mu[c] = sm.mu[c][mom][ly][lx];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) out[k][c] = R(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lR[c][q] = lL[c][q] = R(0);
+    }
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+      R wv[5], g5[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        wv[k] = Lm[f][0] * src[k][0] + Lm[f][1] * src[k][1] + Lm[f][2] * src[k][2] +
+                Lm[f][3] * src[k][3];
+        g5[k] = R(0);
+      }
+      const R lq = Rm[0][f] * mu[0] + Rm[1][f] * mu[1] + Rm[2][f] * mu[2] + Rm[3][f] * mu[3];
+      const R q = limit_first_moment_vjp(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps, lq, g5);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        lR[c][f] += mu[c] * q;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          out[k][c] += Lm[f][c] * g5[k];
+          lL[f][c] += g5[k] * src[k][c];
+        }
+      }
+    }
+    R gU[4] = {R(0), R(0), R(0), R(0)};
+    euler2d_eigen_vjp(gas, U, dir, lR, lL, gU);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      out[1][c] += gU[c];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        if (dir == 0) sm.cx[c][k][ly][lx] = out[k][c]; else sm.cy[c][k][ly][lx] = out[k][c];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- kernel A
+
+template <typename R, int C, int NG>
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_kernel(Adj2DArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemA<R, C>& sm = *reinterpret_cast<SmemA<R, C>*>(smem_raw);
+  constexpr int NF = 4 * NG, NI = NG * NG, NP = NF + NI;
+  const int tid = threadIdx.x;
+  const int nx = a.nx, ny = a.ny;
+  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+  const size_t plane = (size_t)nx * ny;
+  const AdjParams<R> P_(a);
+  const R* __restrict__ w = static_cast<const R*>(a.w);
+  const R* __restrict__ lam = static_cast<const R*>(a.lam);
+  const R ax = static_cast<const R*>(a.alpha)[0], ay = static_cast<const R*>(a.alpha)[1];
+  const R scale = a.stage == 0 ? R(1) : stage_b<R>(a.stage) * *static_cast<const R*>(a.dt);
+
+  for (int k = tid; k < AX * AY; k += NT) {
+    const int rx = k % AX, ry = k / AX;
+    const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 2 + rx, nx, 0);
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+  }
+  for (int k = tid; k < BX * BY; k += NT) {
+    const int lx = k % BX, ly = k / BX;
+    const size_t s = (size_t)bc_map(by0 - 1 + ly, ny, 0) * nx + bc_map(bx0 - 1 + lx, nx, 0);
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) sm.lam[c][m][ly][lx] = scale * lam[(3 * c + m) * plane + s];
+    sm.fl[ly][lx] = a.flags[s] != 0;
+  }
+  __syncthreads();
+
+  // Step 4 on the tile and its 1-cell halo (the forward values)
+  for (int k = tid; k < BX * BY; k += NT) {
+    const int lx = k % BX, ly = k / BX;
+    const int rx = lx + 1, ry = ly + 1;
+    if (!sm.fl[ly][lx]) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        sm.vl[c][ly][lx] = sm.u[c][1][ry][rx];
+        sm.wl[c][ly][lx] = sm.u[c][2][ry][rx];
+      }
+    } else if constexpr (C == 1) {
+      sm.vl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx],
+                                            sm.u[0][0][ry][rx + 1], sm.u[0][1][ry][rx - 1],
+                                            sm.u[0][1][ry][rx + 1], P_.gam, P_.eps);
+      sm.wl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx],
+                                            sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
+                                            sm.u[0][2][ry + 1][rx], P_.gam, P_.eps);
+    } else {
+      limit_euler2d(sm, lx, ly, P_.gam, P_.eps, P_.gas);
+    }
+  }
+  __syncthreads();
+
+  const int ci = tid % TX, cj = tid / TX;
+  const int gi = bx0 + ci, gj = by0 + cj;
+  if (gi >= nx || gj >= ny) return;  // no barrier below
+  bool hw = false;
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 1 + dj][ci + 1 + di] != 0;
+
+  // point values (the forward's)
+  R P[C][NP];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    R d[19];
+    gather19a(sm, c, ci, cj, d);
+    p0_faces<NG>(d, P[c]);
+    p0_interior<NG>(d, &P[c][NF]);
+    if constexpr (C == 1) {
+      if (hw) hweno2d_faces<NG>(d, P_.gam, P_.eps, 0, NF, P[c]);
+    }
+  }
+  if constexpr (C == 4) {
+    if (hw) {
+      R hv[4][NF];
+      hw_faces_euler_vals<NG>(sm, ci, cj, P_.gam, P_.eps, P_.gas, hv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int p = 0; p < NF; ++p) P[c][p] = hv[c][p];
+    }
+  }
+
+  // adjoints of the point values, in place
+  constexpr double r15 = 0.38729833462074168852;  // sqrt(15)/10
+  constexpr double r3 = 0.28867513459481288225;   // sqrt(3)/6
+  const R gw[3] = {NG == 3 ? R(5.0 / 18.0) : R(0.5), NG == 3 ? R(4.0 / 9.0) : R(0.5), R(5.0 / 18.0)};
+  const R gx[3] = {NG == 3 ? R(-r15) : R(-r3), NG == 3 ? R(0) : R(r3), R(r15)};
+  const R hax = R(0.5) * ax, hay = R(0.5) * ay;
+  const int lx = ci + 1, ly = cj + 1;
+#define LAM(c, m, di, dj) sm.lam[c][m][ly + (dj)][lx + (di)]
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    const R wxk = gw[k] * P_.inv_dx, wyk = gw[k] * P_.inv_dy;
+    R lf[C], U[C], o[C];
+    // x_{i-1/2}: own left point k is u^+
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lf[c] = wxk * (LAM(c, 0, 0, 0) - R(0.5) * LAM(c, 1, 0, 0) + gx[k] * LAM(c, 2, 0, 0) -
+                     LAM(c, 0, -1, 0) - R(0.5) * LAM(c, 1, -1, 0) - gx[k] * LAM(c, 2, -1, 0));
+      U[c] = P[c][k];
+    }
+    flux_jt2<R, C>(P_.gas, U, 0, lf, o);
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c][k] = R(0.5) * o[c] - hax * lf[c];
+    // x_{i+1/2}: own right point NG+k is u^-
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lf[c] = wxk * (-LAM(c, 0, 0, 0) - R(0.5) * LAM(c, 1, 0, 0) - gx[k] * LAM(c, 2, 0, 0) +
+                     LAM(c, 0, 1, 0) - R(0.5) * LAM(c, 1, 1, 0) + gx[k] * LAM(c, 2, 1, 0));
+      U[c] = P[c][NG + k];
+    }
+    flux_jt2<R, C>(P_.gas, U, 0, lf, o);
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c][NG + k] = R(0.5) * o[c] + hax * lf[c];
+    // y_{j-1/2}: own bottom point 2NG+k is u^+
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lf[c] = wyk * (LAM(c, 0, 0, 0) + gx[k] * LAM(c, 1, 0, 0) - R(0.5) * LAM(c, 2, 0, 0) -
+                     LAM(c, 0, 0, -1) - gx[k] * LAM(c, 1, 0, -1) - R(0.5) * LAM(c, 2, 0, -1));
+      U[c] = P[c][2 * NG + k];
+    }
+    flux_jt2<R, C>(P_.gas, U, 1, lf, o);
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c][2 * NG + k] = R(0.5) * o[c] - hay * lf[c];
+    // y_{j+1/2}: own top point 3NG+k is u^-
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      lf[c] = wyk * (-LAM(c, 0, 0, 0) - gx[k] * LAM(c, 1, 0, 0) - R(0.5) * LAM(c, 2, 0, 0) +
+                     LAM(c, 0, 0, 1) + gx[k] * LAM(c, 1, 0, 1) - R(0.5) * LAM(c, 2, 0, 1));
+      U[c] = P[c][3 * NG + k];
+    }
+    flux_jt2<R, C>(P_.gas, U, 1, lf, o);
+#pragma unroll
+    for (int c = 0; c < C; ++c) P[c][3 * NG + k] = R(0.5) * o[c] + hay * lf[c];
+  }
+  // interior points: the volume integrals of Eq. (ode2)'s moment equations
+#pragma unroll
+  for (int l = 0; l < NG; ++l)
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int p = NF + l * NG + k;
+      const R wk = gw[k] * gw[l];
+      R U[C], l1[C], l2[C], o1[C], o2[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        U[c] = P[c][p];
+        l1[c] = wk * P_.inv_dx * LAM(c, 1, 0, 0);
+        l2[c] = wk * P_.inv_dy * LAM(c, 2, 0, 0);
+      }
+      flux_jt2<R, C>(P_.gas, U, 0, l1, o1);
+      flux_jt2<R, C>(P_.gas, U, 1, l2, o2);
+#pragma unroll
+      for (int c = 0; c < C; ++c) P[c][p] = o1[c] + o2[c];
+    }
+#undef LAM
+
+  // adjoints of the 19 data
+  R* __restrict__ G = static_cast<R*>(a.G);
+  const size_t s = (size_t)gj * nx + gi;
+  if (C == 1 || !hw) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      R g[19];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) g[k] = R(0);
+      if (!hw) {
+        p0_faces_T<NG>(P[c], g);
+      } else {
+        R d[19];
+        gather19a(sm, c, ci, cj, d);
+        hweno2d_faces_vjp<NG>(d, P_.gam, P_.eps, P[c], g);
+      }
+      p0_interior_T<NG>(&P[c][NF], g);
+#pragma unroll
+      for (int k = 0; k < 19; ++k) G[(size_t)(k * C + c) * plane + s] = g[k];
+    }
+  } else if constexpr (C == 4) {
+    R lamF[4][NF], Gl[4][19];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+      for (int p = 0; p < NF; ++p) lamF[c][p] = P[c][p];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) Gl[c][k] = R(0);
+    }
+    hw_faces_euler_vjp<NG>(sm, ci, cj, P_.gam, P_.eps, P_.gas, lamF, Gl);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      p0_interior_T<NG>(&P[c][NF], Gl[c]);
+#pragma unroll
+      for (int k = 0; k < 19; ++k) G[(size_t)(k * 4 + c) * plane + s] = Gl[c][k];
+    }
+  }
+}
+
+// ------------------------------------------------------------- kernel B
+
+template <typename R, int C>
+__global__ void __launch_bounds__(NT) adj2d_gather_kernel(Adj2DArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemB<R, C>& sm = *reinterpret_cast<SmemB<R, C>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int nx = a.nx, ny = a.ny;
+  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+  const size_t plane = (size_t)nx * ny;
+  const AdjParams<R> P_(a);
+  const R* __restrict__ lam = static_cast<const R*>(a.lam);
+  const R* __restrict__ G = static_cast<const R*>(a.G);
+  const R* acc_in = static_cast<const R*>(a.acc);
+  const R bco = stage_b<R>(a.stage);
+  const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
+
+  // mu on the tile and its 1-cell halo
+  int any = 0;
+  for (int k = tid; k < BX * BY; k += NT) {
+    const int lx = k % BX, ly = k / BX;
+    const int gi = bc_map(bx0 - 1 + lx, nx, 0), gj = bc_map(by0 - 1 + ly, ny, 0);
+    const size_t s = (size_t)gj * nx + gi;
+    const uint8_t f = a.flags[s] != 0;
+    sm.fl[ly][lx] = f;
+    any |= f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      R m0 = R(0), m1 = R(0), m2 = R(0);
+      if (a.stage > 0) {
+        m0 = bco * lam[(3 * c) * plane + s];
+        m1 = bco * lam[(3 * c + 1) * plane + s];
+        m2 = bco * lam[(3 * c + 2) * plane + s];
+      }
+      if (a.stage == 1) {
+        m0 += acc_in[(3 * c) * plane + s];
+        m1 += acc_in[(3 * c + 1) * plane + s];
+        m2 += acc_in[(3 * c + 2) * plane + s];
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const size_t s2 = (size_t)bc_map(gj - (q / 3 - 1), ny, 0) * nx + bc_map(gi - (q % 3 - 1), nx, 0);
+        m0 += G[(size_t)(q * C + c) * plane + s2];
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const size_t s2 = (size_t)bc_map(gj - my[q], ny, 0) * nx + bc_map(gi - mx[q], nx, 0);
+        m1 += G[(size_t)((9 + q) * C + c) * plane + s2];
+        m2 += G[(size_t)((14 + q) * C + c) * plane + s2];
+      }
+      sm.mu[c][0][ly][lx] = m0;
+      sm.mu[c][1][ly][lx] = m1;
+      sm.mu[c][2][ly][lx] = m2;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (any) {
+    const R* __restrict__ w = static_cast<const R*>(a.w);
+    for (int k = tid; k < AX * AY; k += NT) {
+      const int rx = k % AX, ry = k / AX;
+      const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 2 + rx, nx, 0);
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+    }
+    __syncthreads();
+    for (int k = tid; k < BX * BY; k += NT) {
+      const int lx = k % BX, ly = k / BX;
+      if (!sm.fl[ly][lx]) continue;
+      const int rx = lx + 1, ry = ly + 1;
+      if constexpr (C == 1) {
+        R g[5] = {R(0), R(0), R(0), R(0), R(0)};
+        limit_first_moment_vjp(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx], sm.u[0][0][ry][rx + 1],
+                               sm.u[0][1][ry][rx - 1], sm.u[0][1][ry][rx + 1], P_.gam, P_.eps,
+                               sm.mu[0][1][ly][lx], g);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sm.cx[0][q][ly][lx] = g[q];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) g[q] = R(0);
+        limit_first_moment_vjp(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx], sm.u[0][0][ry + 1][rx],
+                               sm.u[0][2][ry - 1][rx], sm.u[0][2][ry + 1][rx], P_.gam, P_.eps,
+                               sm.mu[0][2][ly][lx], g);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sm.cy[0][q][ly][lx] = g[q];
+      } else {
+        limit_euler2d_vjp(sm, lx, ly, P_.gam, P_.eps, P_.gas);
+      }
+    }
+    __syncthreads();
+  }
+
+  const int ci = tid % TX, cj = tid / TX;
+  const int gi = bx0 + ci, gj = by0 + cj;
+  if (gi >= nx || gj >= ny) return;
+  const int lx = ci + 1, ly = cj + 1;
+  const size_t s = (size_t)gj * nx + gi;
+  const bool t0 = sm.fl[ly][lx] != 0;
+  R* __restrict__ out = static_cast<R*>(a.lam_in);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    R g0 = sm.mu[c][0][ly][lx];
+    R g1 = t0 ? R(0) : sm.mu[c][1][ly][lx];
+    R g2 = t0 ? R(0) : sm.mu[c][2][ly][lx];
+    if (any) {
+      if (sm.fl[ly][lx - 1]) { g0 += sm.cx[c][2][ly][lx - 1]; g1 += sm.cx[c][4][ly][lx - 1]; }
+      if (sm.fl[ly][lx + 1]) { g0 += sm.cx[c][0][ly][lx + 1]; g1 += sm.cx[c][3][ly][lx + 1]; }
+      if (sm.fl[ly - 1][lx]) { g0 += sm.cy[c][2][ly - 1][lx]; g2 += sm.cy[c][4][ly - 1][lx]; }
+      if (sm.fl[ly + 1][lx]) { g0 += sm.cy[c][0][ly + 1][lx]; g2 += sm.cy[c][3][ly + 1][lx]; }
+      if (t0) g0 += sm.cx[c][1][ly][lx] + sm.cy[c][1][ly][lx];
+    }
+    out[(3 * c) * plane + s] = g0;
+    out[(3 * c + 1) * plane + s] = g1;
+    out[(3 * c + 2) * plane + s] = g2;
+    if (a.stage >= 2) {
+      R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const size_t e = (3 * c + m) * plane + s;
+        acc[e] = a.stage == 3 ? R(1.0 / 3.0) * lam[e] : acc[e] + R(0.75) * lam[e];
+      }
+    }
+  }
+}
+
+template <typename R, int C, int NG>
+cudaError_t launch_t(const Adj2DArgs& a, cudaStream_t s) {
+  const dim3 grid((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
+  adj2d_points_kernel<R, C, NG><<<grid, NT, sizeof(SmemA<R, C>), s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj2d_gather_kernel<R, C><<<grid, NT, sizeof(SmemB<R, C>), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int C, int NG>
+cudaError_t prepare_t() {
+  cudaError_t e = cudaFuncSetAttribute(adj2d_points_kernel<R, C, NG>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmemA<R, C>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(adj2d_gather_kernel<R, C>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(SmemB<R, C>));
+}
+
+}  // namespace
+
+void finish_adj2d_args(Adj2DArgs& a) {
+  for (int k = 0; k < 5; ++k) a.f32[k] = (float)a.gam[k];
+  a.f32[5] = (float)a.eps;
+  a.f32[6] = (float)a.gas;
+  a.f32[7] = (float)(1.0 / a.dx);
+  a.f32[8] = (float)(1.0 / a.dy);
+}
+
+cudaError_t prepare_adj2d(int system, int fp64, int ng) {
+  if (system == 0) {
+    if (fp64) return ng == 2 ? prepare_t<double, 1, 2>() : prepare_t<double, 1, 3>();
+    return ng == 2 ? prepare_t<float, 1, 2>() : prepare_t<float, 1, 3>();
+  }
+  if (fp64) return ng == 2 ? prepare_t<double, 4, 2>() : prepare_t<double, 4, 3>();
+  return ng == 2 ? prepare_t<float, 4, 2>() : prepare_t<float, 4, 3>();
+}
+
+cudaError_t launch_adj2d(const Adj2DArgs& a, cudaStream_t s) {
+  if (a.system == 0) {
+    if (a.fp64) return a.ng == 2 ? launch_t<double, 1, 2>(a, s) : launch_t<double, 1, 3>(a, s);
+    return a.ng == 2 ? launch_t<float, 1, 2>(a, s) : launch_t<float, 1, 3>(a, s);
+  }
+  if (a.fp64) return a.ng == 2 ? launch_t<double, 4, 2>(a, s) : launch_t<double, 4, 3>(a, s);
+  return a.ng == 2 ? launch_t<float, 4, 2>(a, s) : launch_t<float, 4, 3>(a, s);
+}
+
+}  // namespace hw

@@ -1,0 +1,214 @@
+// 2D pieces shared by the stage kernel and the adjoint kernels of the hybrid
+// HWENO scheme (Zhao & Qiu, arXiv:2002.08816, Sec. 2.2): the Euler flux and
+// its eigen-system, the wave speeds, and Step 5.1's nonlinear combination on
+// the generated straight-line maps of hweno2d_coef.cuh.
+#pragma once
+#include <math.h>
+
+#include "hweno1d_recon.cuh"
+#include "hweno2d_coef.cuh"
+
+namespace hw {
+
+// ------------------------------------------------------------ physics (2D)
+
+template <typename R>
+struct Euler2D {
+  static __device__ __forceinline__ void flux(R g, const R* U, int dir, R* F) {
+    const R rho = U[0], m = U[1], n = U[2], E = U[3];
+    const R ir = sizeof(R) == 4 ? R(__frcp_rn((float)rho)) : R(1) / rho;
+    const R mu = sizeof(R) == 4 ? m * ir : m / rho;
+    const R nu = sizeof(R) == 4 ? n * ir : n / rho;
+    const R p = (g - R(1)) * (E - R(0.5) * (m * mu + n * nu));
+    const R vn = dir == 0 ? mu : nu;
+    F[0] = dir == 0 ? m : n;
+    F[1] = m * vn + (dir == 0 ? p : R(0));
+    F[2] = n * vn + (dir == 1 ? p : R(0));
+    F[3] = vn * (E + p);
+  }
+  // Right (columns: v-c, v, v, v+c with v the normal velocity) and left
+  // eigenvectors of dF/dU (dir 0) or dG/dU (dir 1) at U.
+  static __device__ __forceinline__ void eigen(R g, const R* U, int dir, R Rm[4][4], R Lm[4][4]) {
+    const R rho = U[0], mu = U[1] / rho, nu = U[2] / rho;
+    const R q2 = mu * mu + nu * nu;
+    const R p = (g - R(1)) * (U[3] - R(0.5) * rho * q2);
+    const R c = sqrt(g * p / rho);
+    const R H = (U[3] + p) / rho;
+    const R ic = R(1) / c;
+    const R b1 = (g - R(1)) * ic * ic;
+    const R b2 = R(0.5) * b1 * q2;
+    const R vn = dir == 0 ? mu : nu;
+    // columns
+    Rm[0][0] = R(1); Rm[0][1] = R(1); Rm[0][3] = R(1);
+    Rm[3][0] = H - vn * c; Rm[3][1] = R(0.5) * q2; Rm[3][3] = H + vn * c;
+    if (dir == 0) {
+      Rm[1][0] = mu - c; Rm[1][1] = mu; Rm[1][3] = mu + c;
+      Rm[2][0] = nu;     Rm[2][1] = nu; Rm[2][3] = nu;
+      Rm[0][2] = R(0); Rm[1][2] = R(0); Rm[2][2] = R(1); Rm[3][2] = nu;
+    } else {
+      Rm[1][0] = mu;     Rm[1][1] = mu; Rm[1][3] = mu;
+      Rm[2][0] = nu - c; Rm[2][1] = nu; Rm[2][3] = nu + c;
+      Rm[0][2] = R(0); Rm[1][2] = R(1); Rm[2][2] = R(0); Rm[3][2] = mu;
+    }
+    // rows
+    const R ex = dir == 0 ? ic : R(0), ey = dir == 1 ? ic : R(0);
+    Lm[0][0] = R(0.5) * (b2 + vn * ic);
+    Lm[0][1] = R(-0.5) * (b1 * mu + ex);
+    Lm[0][2] = R(-0.5) * (b1 * nu + ey);
+    Lm[0][3] = R(0.5) * b1;
+    Lm[1][0] = R(1) - b2;
+    Lm[1][1] = b1 * mu;
+    Lm[1][2] = b1 * nu;
+    Lm[1][3] = -b1;
+    if (dir == 0) {
+      Lm[2][0] = -nu; Lm[2][1] = R(0); Lm[2][2] = R(1); Lm[2][3] = R(0);
+    } else {
+      Lm[2][0] = -mu; Lm[2][1] = R(1); Lm[2][2] = R(0); Lm[2][3] = R(0);
+    }
+    Lm[3][0] = R(0.5) * (b2 - vn * ic);
+    Lm[3][1] = R(-0.5) * (b1 * mu - ex);
+    Lm[3][2] = R(-0.5) * (b1 * nu - ey);
+    Lm[3][3] = R(0.5) * b1;
+  }
+};
+
+template <typename R, int C>
+__device__ __forceinline__ void phys_flux2(R gas, const R* U, int dir, R* F) {
+  if constexpr (C == 1) {
+    F[0] = R(0.5) * U[0] * U[0];
+  } else {
+    Euler2D<R>::flux(gas, U, dir, F);
+  }
+}
+
+// max |f'| (dir 0) and |g'| (dir 1) at a cell average; NaN when not physical
+template <typename R, int C>
+__device__ __forceinline__ void wave_speeds2(R gas, const R* U, R& sx, R& sy) {
+  if constexpr (C == 1) {
+    sx = sy = fabs(U[0]);
+  } else {
+    const R rho = U[0];
+    if (!(rho > R(0))) {
+      sx = sy = R(NAN);
+      return;
+    }
+    const R mu = U[1] / rho, nu = U[2] / rho;
+    const R p = (gas - R(1)) * (U[3] - R(0.5) * rho * (mu * mu + nu * nu));
+    if (!(p > R(0))) {
+      sx = sy = R(NAN);
+      return;
+    }
+    const R c = sqrt(gas * p / rho);
+    sx = fabs(mu) + c;
+    sy = fabs(nu) + c;
+  }
+}
+
+// ------------------------------------------------------ HWENO helpers (2D)
+
+template <int NG, typename R>
+__device__ __forceinline__ void p0_faces(const R* d, R* o) {
+  if constexpr (NG == 3) hw2::p0_faces_ng3(d, o); else hw2::p0_faces_ng2(d, o);
+}
+template <int NG, typename R>
+__device__ __forceinline__ void p0_interior(const R* d, R* o) {
+  if constexpr (NG == 3) hw2::p0_interior_ng3(d, o); else hw2::p0_interior_ng2(d, o);
+}
+template <int NG, typename R>
+__device__ __forceinline__ void q_faces(int n, const R* d, R* o) {
+  if constexpr (NG == 3) {
+    if (n == 1) hw2::q1_faces_ng3(d, o);
+    else if (n == 2) hw2::q2_faces_ng3(d, o);
+    else if (n == 3) hw2::q3_faces_ng3(d, o);
+    else hw2::q4_faces_ng3(d, o);
+  } else {
+    if (n == 1) hw2::q1_faces_ng2(d, o);
+    else if (n == 2) hw2::q2_faces_ng2(d, o);
+    else if (n == 3) hw2::q3_faces_ng2(d, o);
+    else hw2::q4_faces_ng2(d, o);
+  }
+}
+
+// HWENO values (Step 5.1) at the interface points [p_lo, p_hi) of one scalar
+// field from its 19 data: tau of Eq. (tao4), weights of Eq. (99), and the
+// combination omega_0 (p0/gamma_0 - sum gamma_n/gamma_0 p_n) + sum omega_n p_n
+// accumulated candidate by candidate (it is linear in the candidates).
+template <int NG, typename R>
+__device__ __forceinline__ void hweno2d_faces(const R* d, const R* gam, R eps, int p_lo,
+                                              int p_hi, R* out) {
+  constexpr int NF = 4 * NG;
+  R b[5];
+  b[0] = hw2::beta_p0(d);
+  b[1] = hw2::beta_q1(d);
+  b[2] = hw2::beta_q2(d);
+  b[3] = hw2::beta_q3(d);
+  b[4] = hw2::beta_q4(d);
+  const R s = R(0.25) * (fabs(b[0] - b[1]) + fabs(b[0] - b[2]) + fabs(b[0] - b[3]) + fabs(b[0] - b[4]));
+  const R tau = s * s;
+  R a[5], sum = R(0);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) {
+    a[n] = gam[n] * (R(1) + tau / (b[n] + eps));
+    sum += a[n];
+  }
+  const R inv = R(1) / sum;
+  const R c0 = a[0] * inv / gam[0];
+  R tmp[NF];
+  p0_faces<NG>(d, tmp);
+#pragma unroll
+  for (int p = 0; p < NF; ++p)
+    if (p >= p_lo && p < p_hi) out[p] = c0 * tmp[p];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const R cn = a[n + 1] * inv - c0 * gam[n + 1];
+    q_faces<NG>(n + 1, d, tmp);
+#pragma unroll
+    for (int p = 0; p < NF; ++p)
+      if (p >= p_lo && p < p_hi) out[p] += cn * tmp[p];
+  }
+}
+
+// Step 4 for a troubled Euler cell (lx, ly) of the flag grid: vbar from the
+// x-neighbours in the x characteristic fields, wbar from the y-neighbours in
+// the y fields, with the 1D Step 1 formula.  Rare: kept out of line so that
+// its registers do not weigh on the common path.
+template <typename S, typename R>
+__device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, const R* gam, R eps, R gas) {
+  const int rx = lx + 1, ry = ly + 1;
+  R U[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][ry][rx];
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    R Rm[4][4], Lm[4][4];
+    Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
+    const int sx = dir == 0 ? 1 : 0, sy = dir == 0 ? 0 : 1;
+    const int mom = dir == 0 ? 1 : 2;
+    R q[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      R wv[5];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        wv[s] = R(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) wv[s] += Lm[f][c] * sm.u[c][0][ry + (s - 1) * sy][rx + (s - 1) * sx];
+      }
+      wv[3] = R(0);
+      wv[4] = R(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        wv[3] += Lm[f][c] * sm.u[c][mom][ry - sy][rx - sx];
+        wv[4] += Lm[f][c] * sm.u[c][mom][ry + sy][rx + sx];
+      }
+      q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const R v = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2] + Rm[c][3] * q[3];
+      if (dir == 0) sm.vl[c][ly][lx] = v; else sm.wl[c][ly][lx] = v;
+    }
+  }
+}
+
+}  // namespace hw

@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "hweno.h"
 #include "hweno_internal.h"
@@ -44,6 +45,25 @@ struct hweno_ctx {
   int* d_tile_base = nullptr;
   hw::BatchInst* d_binst = nullptr;
   hw::BatchScalars* d_bsc = nullptr;
+  // adjoint: the tape of hweno_record and the scratch of hweno_backward
+  struct Tape {
+    int nsteps = 0, every = 0, nck = 0;
+    void* ck = nullptr;         // checkpoints: u^n for n % every == 0
+    uint8_t* flags = nullptr;   // troubled cells, one plane per stage
+    void* alpha = nullptr;      // (alpha_x, alpha_y) per stage, kernel precision
+    void* dt = nullptr;         // dt per step, kernel precision
+    std::vector<double> dt_host;
+    int seg_every = 0;          // capacity of seg, in steps
+    void* seg = nullptr;        // 3 every + 1 recomputed stage inputs
+    void* w0 = nullptr;         // limited u^n of the recomputed step
+    void* G = nullptr;          // 19 C planes
+    void* lam[2] = {nullptr, nullptr};
+    void* acc = nullptr;
+    double* slots = nullptr;    // 3 x 2 kAlphaSlots
+    hw::DevScalars* sc = nullptr;
+    void* aux = nullptr;        // (alpha_x, alpha_y) of hweno_rhs_vjp
+    bool prepared = false;
+  } tape;
 };
 
 namespace {
@@ -114,36 +134,75 @@ hw::Stage2DArgs base_args2d(const hweno_ctx* h) {
   return a;
 }
 
-cudaError_t enqueue_step2d(hweno_ctx* h, cudaStream_t s) {
+// The buffers of one 2D Runge-Kutta step: in -> s1 -> s2 -> out, the limited
+// u^n in w0, alpha carried through part[0..2]; optional recording of the
+// switches (flags: 3 planes; rec_alpha: 3 pairs; rec_dt) or replay of a
+// recorded dt (dt_in).
+struct Step2DIO {
+  const void* in;
+  void* s1;
+  void* s2;
+  void* out;
+  void* w0;
+  double* part[3];
+  hw::DevScalars* sc;
+  uint8_t* flags;
+  void* rec_alpha;
+  void* rec_dt;
+  const void* dt_in;
+};
+
+void* byte_off(const void* p, size_t bytes) {
+  return static_cast<char*>(const_cast<void*>(p)) + bytes;
+}
+
+cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) {
   hw::Stage2DArgs a = base_args2d(h);
-  a.sc = h->sc;
+  const size_t pair = 2 * h->esize;
+  a.sc = io.sc;
   a.nin = hw::kAlphaSlots;
   a.stage = 1;
-  a.w = h->U[0];
-  a.out = h->U[1];
-  a.lim_out = h->U0;
-  a.a_in = h->part[0];
-  a.a_out = h->part[1];
-  a.a_zero = h->part[2];
+  a.w = io.in;
+  a.out = io.s1;
+  a.lim_out = io.w0;
+  a.a_in = io.part[0];
+  a.a_out = io.part[1];
+  a.a_zero = io.part[2];
+  a.flags_out = io.flags;
+  a.rec_alpha = io.rec_alpha;
+  a.rec_dt = io.rec_dt;
+  a.dt_in = io.dt_in;
   cudaError_t e = hw::launch_stage2d(a, s);
   if (e != cudaSuccess) return e;
+  a.rec_dt = nullptr;
+  a.dt_in = nullptr;
   a.stage = 2;
-  a.w = h->U[1];
-  a.u0 = h->U0;
-  a.out = h->U[2];
+  a.w = io.s1;
+  a.u0 = io.w0;
+  a.out = io.s2;
   a.lim_out = nullptr;
-  a.a_in = h->part[1];
-  a.a_out = h->part[2];
-  a.a_zero = h->part[0];
+  a.a_in = io.part[1];
+  a.a_out = io.part[2];
+  a.a_zero = io.part[0];
+  if (io.flags) a.flags_out = io.flags + (size_t)h->n;
+  if (io.rec_alpha) a.rec_alpha = byte_off(io.rec_alpha, pair);
   e = hw::launch_stage2d(a, s);
   if (e != cudaSuccess) return e;
   a.stage = 3;
-  a.w = h->U[2];
-  a.out = h->U[0];
-  a.a_in = h->part[2];
-  a.a_out = h->part[0];
-  a.a_zero = h->part[1];
+  a.w = io.s2;
+  a.out = io.out;
+  a.a_in = io.part[2];
+  a.a_out = io.part[0];
+  a.a_zero = io.part[1];
+  if (io.flags) a.flags_out = io.flags + 2 * (size_t)h->n;
+  if (io.rec_alpha) a.rec_alpha = byte_off(io.rec_alpha, 2 * pair);
   return hw::launch_stage2d(a, s);
+}
+
+cudaError_t enqueue_step2d(hweno_ctx* h, cudaStream_t s) {
+  Step2DIO io = {h->U[0], h->U[1], h->U[2], h->U[0], h->U0,
+                 {h->part[0], h->part[1], h->part[2]}, h->sc, nullptr, nullptr, nullptr, nullptr};
+  return enqueue_step2d_io(h, io, s);
 }
 
 cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
@@ -246,6 +305,73 @@ hweno_status check_scalars(hweno_ctx* h, hw::DevScalars* dev, hw::DevScalars* ho
   if (host->status & hw::ST_NONFINITE) return fail(h, HWENO_ERR_NONPHYSICAL, "non-finite value");
   if (host->status & hw::ST_TIMEOUT) return fail(h, HWENO_ERR_TIMEOUT, "device wait timed out");
   return HWENO_OK;
+}
+
+void free_ptr(void** p) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+}
+
+// Frees the recorded run (and, with scratch, the buffers of the backward pass).
+void free_tape(hweno_ctx* h, bool scratch) {
+  hweno_ctx::Tape& t = h->tape;
+  free_ptr(&t.ck);
+  free_ptr(reinterpret_cast<void**>(&t.flags));
+  free_ptr(&t.alpha);
+  free_ptr(&t.dt);
+  t.dt_host.clear();
+  t.nsteps = t.every = t.nck = 0;
+  if (!scratch) return;
+  free_ptr(&t.seg);
+  free_ptr(&t.w0);
+  free_ptr(&t.G);
+  free_ptr(&t.lam[0]);
+  free_ptr(&t.lam[1]);
+  free_ptr(&t.acc);
+  free_ptr(reinterpret_cast<void**>(&t.slots));
+  free_ptr(reinterpret_cast<void**>(&t.sc));
+  free_ptr(&t.aux);
+  t.seg_every = 0;
+}
+
+hweno_status check_adjoint_config(hweno_ctx* h) {
+  if (h->dim != 2) return fail(h, HWENO_ERR_ARG, "the adjoint is for 2D handles");
+  if (h->n_batch > 0) return fail(h, HWENO_ERR_ARG, "the adjoint takes a single-instance handle");
+  if (h->cfg.bc != HWENO_BC_PERIODIC) return fail(h, HWENO_ERR_ARG, "the adjoint needs periodic boundaries");
+  return HWENO_OK;
+}
+
+// Scratch of the adjoint kernels (G, the alpha pair, the device scalars),
+// allocated on first use.
+hweno_status adjoint_scratch(hweno_ctx* h) {
+  hweno_ctx::Tape& t = h->tape;
+  if (!t.prepared) {
+    HW_CUDA(h, hw::prepare_adj2d(h->cfg.system, h->cfg.precision == HWENO_FP64, h->cfg.n_gauss));
+    t.prepared = true;
+  }
+  if (!t.G) HW_CUDA(h, cudaMalloc(&t.G, (size_t)19 * h->C * h->n * h->esize));
+  if (!t.aux) HW_CUDA(h, cudaMalloc(&t.aux, 2 * sizeof(double)));
+  if (!t.sc) HW_CUDA(h, cudaMalloc(&t.sc, sizeof(hw::DevScalars)));
+  return HWENO_OK;
+}
+
+hw::Adj2DArgs base_adj_args(const hweno_ctx* h) {
+  hw::Adj2DArgs a;
+  memset(&a, 0, sizeof(a));
+  const hweno_config& c = h->cfg;
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.system = c.system;
+  a.fp64 = c.precision == HWENO_FP64;
+  a.ng = c.n_gauss;
+  a.dx = (c.x1 - c.x0) / c.nx;
+  a.dy = (c.y1 - c.y0) / c.ny;
+  a.eps = c.eps;
+  a.gas = c.gas_gamma;
+  for (int k = 0; k < 5; ++k) a.gam[k] = c.lin_w[k];
+  a.G = h->tape.G;
+  hw::finish_adj2d_args(a);
+  return a;
 }
 
 }  // namespace
@@ -490,6 +616,7 @@ void hweno_destroy(hweno_handle h) {
   if (h->d_tile_base) cudaFree(h->d_tile_base);
   if (h->d_binst) cudaFree(h->d_binst);
   if (h->d_bsc) cudaFree(h->d_bsc);
+  free_tape(h, true);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }
@@ -577,6 +704,174 @@ hweno_status hweno_batch_times(hweno_handle h, double* t) {
   for (int k = 0; k < h->n_batch && e == cudaSuccess; ++k) t[k] = b[k].t;
   delete[] b;
   if (e != cudaSuccess) return fail(h, HWENO_ERR_CUDA, cudaGetErrorString(e));
+  return HWENO_OK;
+}
+
+hweno_status hweno_record(hweno_handle h, int nsteps, int checkpoint_every, double t_final,
+                          double* t_out) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  hweno_status st = check_adjoint_config(h);
+  if (st != HWENO_OK) return st;
+  if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_record before hweno_set_state");
+  if (nsteps < 1 || checkpoint_every < 1)
+    return fail(h, HWENO_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
+  free_tape(h, false);
+  hweno_ctx::Tape& t = h->tape;
+  const size_t sbytes = h->elems * h->esize;
+  const int nck = (nsteps + checkpoint_every - 1) / checkpoint_every;
+  HW_CUDA(h, cudaMalloc(&t.ck, sbytes * nck));
+  HW_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&t.flags), (size_t)3 * nsteps * h->n));
+  HW_CUDA(h, cudaMalloc(&t.alpha, (size_t)6 * nsteps * h->esize));
+  HW_CUDA(h, cudaMalloc(&t.dt, (size_t)nsteps * h->esize));
+  HW_CUDA(h, cudaMemsetAsync(t.dt, 0, (size_t)nsteps * h->esize, h->stream));
+  HW_CUDA(h, hw::launch_set_scalars(h->sc, 0, t_final, h->stream));
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % checkpoint_every == 0)
+      HW_CUDA(h, cudaMemcpyAsync(byte_off(t.ck, sbytes * (n / checkpoint_every)), h->U[0], sbytes,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    Step2DIO io = {h->U[0], h->U[1], h->U[2], h->U[0], h->U0,
+                   {h->part[0], h->part[1], h->part[2]}, h->sc,
+                   t.flags + (size_t)3 * n * h->n, byte_off(t.alpha, (size_t)6 * n * h->esize),
+                   byte_off(t.dt, (size_t)n * h->esize), nullptr};
+    HW_CUDA(h, enqueue_step2d_io(h, io, h->stream));
+  }
+  hw::DevScalars sc;
+  st = check_scalars(h, h->sc, &sc);
+  if (t_out) *t_out = sc.t;
+  if (st != HWENO_OK) return st;
+  t.dt_host.assign(nsteps, 0.0);
+  if (h->esize == 8) {
+    HW_CUDA(h, cudaMemcpy(t.dt_host.data(), t.dt, sizeof(double) * nsteps, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> f(nsteps);
+    HW_CUDA(h, cudaMemcpy(f.data(), t.dt, sizeof(float) * nsteps, cudaMemcpyDeviceToHost));
+    for (int n = 0; n < nsteps; ++n) t.dt_host[n] = f[n];
+  }
+  t.nsteps = nsteps;
+  t.every = checkpoint_every;
+  t.nck = nck;
+  return HWENO_OK;
+}
+
+hweno_status hweno_backward(hweno_handle h, const void* grad_out, void* grad_in, int dtype,
+                            int on_device) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  hweno_ctx::Tape& t = h->tape;
+  if (t.nsteps < 1) return fail(h, HWENO_ERR_STATE, "hweno_backward without a recorded run");
+  if (!grad_out || !grad_in) return fail(h, HWENO_ERR_ARG, "grad_out and grad_in are required");
+  if (dtype != HWENO_FP32 && dtype != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "unknown dtype");
+  hweno_status st = adjoint_scratch(h);
+  if (st != HWENO_OK) return st;
+  const size_t sbytes = h->elems * h->esize;
+  if (t.seg_every < t.every) {
+    free_ptr(&t.seg);
+    HW_CUDA(h, cudaMalloc(&t.seg, sbytes * (3 * (size_t)t.every + 1)));
+    t.seg_every = t.every;
+  }
+  if (!t.w0) HW_CUDA(h, cudaMalloc(&t.w0, sbytes));
+  for (int k = 0; k < 2; ++k)
+    if (!t.lam[k]) HW_CUDA(h, cudaMalloc(&t.lam[k], sbytes));
+  if (!t.acc) HW_CUDA(h, cudaMalloc(&t.acc, sbytes));
+  if (!t.slots) HW_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&t.slots), sizeof(double) * 6 * hw::kAlphaSlots));
+  const int src64 = dtype == HWENO_FP64, k64 = h->cfg.precision == HWENO_FP64;
+  // the adjoint of the final state, in the kernel precision
+  const void* src = grad_out;
+  if (!on_device) {
+    void* dst = src64 == k64 ? t.lam[0] : h->stage_buf;
+    HW_CUDA(h, cudaMemcpyAsync(dst, grad_out, h->elems * (src64 ? 8 : 4), cudaMemcpyHostToDevice,
+                               h->stream));
+    src = src64 == k64 ? nullptr : h->stage_buf;
+  }
+  if (src) HW_CUDA(h, hw::launch_convert(src, src64, t.lam[0], k64, h->elems, h->stream));
+  HW_CUDA(h, hw::launch_set_scalars(t.sc, 1, -1.0, h->stream));
+  void* cur = t.lam[0];
+  void* oth = t.lam[1];
+  const size_t pair = 2 * h->esize;
+  for (int seg = t.nck - 1; seg >= 0; --seg) {
+    const int n0 = seg * t.every, n1 = n0 + t.every < t.nsteps ? n0 + t.every : t.nsteps;
+    // recompute the segment's stage inputs from its checkpoint
+    HW_CUDA(h, cudaMemcpyAsync(t.seg, byte_off(t.ck, sbytes * seg), sbytes, cudaMemcpyDeviceToDevice,
+                               h->stream));
+    HW_CUDA(h, cudaMemsetAsync(t.slots, 0, sizeof(double) * 6 * hw::kAlphaSlots, h->stream));
+    double* sl[3] = {t.slots, t.slots + 2 * hw::kAlphaSlots, t.slots + 4 * hw::kAlphaSlots};
+    HW_CUDA(h, hw::launch_alpha2d(t.seg, sl[0], h->cfg.nx, h->cfg.ny, h->cfg.system, k64,
+                                  h->cfg.gas_gamma, t.sc, 1, h->stream));
+    for (int n = n0; n < n1; ++n) {
+      if (!(t.dt_host[n] > 0.0)) break;  // past t_final: the remaining steps did nothing
+      const size_t m = (size_t)(n - n0);
+      Step2DIO io = {byte_off(t.seg, sbytes * 3 * m), byte_off(t.seg, sbytes * (3 * m + 1)),
+                     byte_off(t.seg, sbytes * (3 * m + 2)), byte_off(t.seg, sbytes * (3 * m + 3)),
+                     t.w0, {sl[0], sl[1], sl[2]}, t.sc, nullptr, nullptr, nullptr,
+                     byte_off(t.dt, (size_t)n * h->esize)};
+      HW_CUDA(h, enqueue_step2d_io(h, io, h->stream));
+    }
+    // the adjoint stages, last step first
+    for (int n = n1 - 1; n >= n0; --n) {
+      if (!(t.dt_host[n] > 0.0)) continue;
+      const size_t m = (size_t)(n - n0);
+      hw::Adj2DArgs a = base_adj_args(h);
+      a.dt = byte_off(t.dt, (size_t)n * h->esize);
+      a.acc = t.acc;
+      for (int stage = 3; stage >= 1; --stage) {
+        const size_t ks = (size_t)3 * n + (stage - 1);
+        a.stage = stage;
+        a.w = byte_off(t.seg, sbytes * (3 * m + stage - 1));
+        a.flags = t.flags + ks * h->n;
+        a.alpha = byte_off(t.alpha, ks * pair);
+        a.lam = cur;
+        a.lam_in = oth;
+        HW_CUDA(h, hw::launch_adj2d(a, h->stream));
+        void* x = cur;
+        cur = oth;
+        oth = x;
+      }
+    }
+  }
+  hw::DevScalars sc;
+  st = check_scalars(h, t.sc, &sc);
+  if (st != HWENO_OK) return st;
+  const int d64 = dtype == HWENO_FP64;
+  if (on_device) {
+    HW_CUDA(h, hw::launch_convert(cur, k64, grad_in, d64, h->elems, h->stream));
+  } else {
+    const void* from = cur;
+    if (d64 != k64) {
+      HW_CUDA(h, hw::launch_convert(cur, k64, h->stage_buf, d64, h->elems, h->stream));
+      from = h->stage_buf;
+    }
+    HW_CUDA(h, cudaMemcpyAsync(grad_in, from, h->elems * (d64 ? 8 : 4), cudaMemcpyDeviceToHost,
+                               h->stream));
+  }
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags, double alpha_x,
+                           double alpha_y, const void* lam, void* grad) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  hweno_status st = check_adjoint_config(h);
+  if (st != HWENO_OK) return st;
+  if (!in || !flags || !lam || !grad) return fail(h, HWENO_ERR_ARG, "in, flags, lam and grad are required");
+  if (grad == in || grad == lam) return fail(h, HWENO_ERR_ARG, "grad must not overlap in or lam");
+  st = adjoint_scratch(h);
+  if (st != HWENO_OK) return st;
+  if (h->esize == 8) {
+    const double al[2] = {alpha_x, alpha_y};
+    HW_CUDA(h, cudaMemcpy(h->tape.aux, al, sizeof(al), cudaMemcpyHostToDevice));
+  } else {
+    const float al[2] = {(float)alpha_x, (float)alpha_y};
+    HW_CUDA(h, cudaMemcpy(h->tape.aux, al, sizeof(al), cudaMemcpyHostToDevice));
+  }
+  hw::Adj2DArgs a = base_adj_args(h);
+  a.stage = 0;
+  a.w = in;
+  a.flags = flags;
+  a.alpha = h->tape.aux;
+  a.dt = h->tape.aux;
+  a.lam = lam;
+  a.lam_in = grad;
+  HW_CUDA(h, hw::launch_adj2d(a, h->stream));
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
   return HWENO_OK;
 }
 

@@ -102,6 +102,9 @@ struct Stage2DArgs {
   void* a_zero;          // 2 * kAlphaSlots slots to zero (nullable)
   DevScalars* sc;
   uint8_t* flags_out;
+  void* rec_alpha;       // nullable: (alpha_x, alpha_y) of the stage, kernel precision
+  void* rec_dt;          // nullable: dt of the step (stage 1), kernel precision
+  const void* dt_in;     // nullable: stage 1 takes this dt (replay of a recorded step)
   int nx, ny, stage, bc, mode, system, fp64, ng;
   double dx, dy, cfl, eps, thr, gas;
   double gam[5];
@@ -121,6 +124,30 @@ cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s);
 // entries) or into 2 * kAlphaSlots zeroed slots (slots = 1).
 cudaError_t launch_alpha2d(const void* w, void* a_out, int nx, int ny, int system, int fp64,
                            double gas, DevScalars* sc, int slots, cudaStream_t s);
+
+// One backward stage of the 2D adjoint (device pointers).  For the stage
+// u_out = a W0 + b (W + dt L(W)), W = Step 4 applied to the raw input w with
+// the recorded troubled cells: lam_in = (dW/dw)^T [b lam + (dL/dW)^T (b dt
+// lam)] (+ acc at stage 1), and acc, the adjoint of W0 = W of stage 1, gets
+// a lam (stage 3 sets it, stage 2 adds).  Stage 0: lam_in = (d L(W(w))/dw)^T lam.
+struct Adj2DArgs {
+  const void* w;          // raw stage input [C][3][ny][nx]
+  const uint8_t* flags;   // troubled cells of the stage [ny][nx]
+  const void* alpha;      // (alpha_x, alpha_y) of the stage, kernel precision
+  const void* dt;         // dt of the step, kernel precision (stage 0: unused)
+  const void* lam;        // adjoint of the stage output
+  void* G;                // scratch [19][C][ny][nx]: adjoints of each cell's 19 data
+  void* acc;              // adjoint of W0
+  void* lam_in;           // out: adjoint of the stage input
+  int stage, nx, ny, system, fp64, ng;
+  double dx, dy, eps, gas;
+  double gam[5];
+  float f32[9];           // FP32 copies: gamma_0..4, eps, gas, 1/dx, 1/dy
+};
+void finish_adj2d_args(Adj2DArgs& a);
+cudaError_t prepare_adj2d(int system, int fp64, int ng);
+// The two kernels of one backward stage (periodic boundaries).
+cudaError_t launch_adj2d(const Adj2DArgs& a, cudaStream_t s);
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
 // Batched variants: one launch over all instances (a.tile_inst != nullptr);

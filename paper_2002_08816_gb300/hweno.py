@@ -78,6 +78,12 @@ def lib():
         L.hweno_create_batch.argtypes = [P, _I, ctypes.POINTER(_I), _VP, ctypes.POINTER(_VP)]
         L.hweno_batch_times.restype = _I
         L.hweno_batch_times.argtypes = [_VP, ctypes.POINTER(_D)]
+        L.hweno_record.restype = _I
+        L.hweno_record.argtypes = [_VP, _I, _I, _D, ctypes.POINTER(_D)]
+        L.hweno_backward.restype = _I
+        L.hweno_backward.argtypes = [_VP, _VP, _VP, _I, _I]
+        L.hweno_rhs_vjp.restype = _I
+        L.hweno_rhs_vjp.argtypes = [_VP, _VP, _VP, _D, _D, _VP, _VP]
         L.hweno_rhs1d_noalloc.restype = _I
         L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
         _lib = L
@@ -139,6 +145,23 @@ def hweno_rhs1d_noalloc(cfg, stream, in_ptr, out_ptr, flags_ptr=0, ulim_ptr=0):
     handle, so no error text)."""
     return lib().hweno_rhs1d_noalloc(ctypes.byref(cfg), _VP(stream or None), _VP(in_ptr),
                                      _VP(out_ptr), _VP(flags_ptr or None), _VP(ulim_ptr or None))
+
+
+def hweno_record(h, nsteps, checkpoint_every, t_final=-1.0):
+    """Runs nsteps steps recording the tape for hweno_backward; returns t."""
+    t = _D()
+    _check(lib().hweno_record(h, int(nsteps), int(checkpoint_every), float(t_final),
+                              ctypes.byref(t)), h)
+    return t.value
+
+
+def hweno_backward(h, grad_out_ptr, grad_in_ptr, dtype, on_device):
+    _check(lib().hweno_backward(h, _VP(grad_out_ptr), _VP(grad_in_ptr), dtype, int(on_device)), h)
+
+
+def hweno_rhs_vjp(h, in_ptr, flags_ptr, alpha_x, alpha_y, lam_ptr, grad_ptr):
+    _check(lib().hweno_rhs_vjp(h, _VP(in_ptr), _VP(flags_ptr), float(alpha_x), float(alpha_y),
+                               _VP(lam_ptr), _VP(grad_ptr)), h)
 
 
 def hweno_get_state(h, ptr, dtype, on_device):
