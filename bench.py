@@ -356,7 +356,7 @@ def bench_euler2d(args):
     torch.cuda.set_device(local)
     __graft_entry__.build()
     stream = torch.cuda.current_stream()
-    ng = args.n_gauss
+    ng = args.n_gauss or 2
     u0 = W.euler_vortex_modes_2d(NX2, NX2, seed=SEED_2D + rank, npts=2).astype(np.float32)
     cfg = H.make_config(2, H.HWENO_EULER, NX2, NX2, x0=0.0, x1=10.0, y0=0.0, y1=10.0,
                         bc=H.HWENO_BC_PERIODIC, cfl=CFL_2D, precision=H.HWENO_FP32, n_gauss=ng)
@@ -445,6 +445,108 @@ def bench_euler2d(args):
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- adjoint workload
+
+NX_ADJ = 1024
+STEPS_ADJ = 200
+EVERY_ADJ = 20
+SEED_ADJ = 4242
+
+
+def bench_adjoint2d(args):
+    """Gradient of sum(rho^2) after STEPS_ADJ steps with respect to the initial
+    moments: 2D Euler 1024 x 1024 periodic [0, 10]^2, vortex plus density
+    modes, FP32, forward with the tape (checkpoint every EVERY_ADJ steps), then
+    the checkpointed adjoint.  Reports forward, backward and their ratio."""
+    import torch
+
+    from paper_2002_08816_gb300 import hweno as H
+    from paper_2002_08816_gb300 import workloads as W
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    ng = args.n_gauss or 3
+    n = NX_ADJ
+    u0 = W.euler_vortex_modes_2d(n, n, seed=SEED_ADJ + rank).astype(np.float32)
+    cfg = H.make_config(2, H.HWENO_EULER, n, n, x0=0.0, x1=10.0, y0=0.0, y1=10.0,
+                        bc=H.HWENO_BC_PERIODIC, cfl=CFL_2D, precision=H.HWENO_FP32, n_gauss=ng)
+    h = H.hweno_create(cfg, stream.cuda_stream)
+    dev = torch.from_numpy(u0).to("cuda")
+    uN = torch.empty_like(dev)
+    grad = torch.empty_like(dev)
+    seed_grad = torch.zeros_like(dev)
+
+    def forward():
+        H.hweno_set_state(h, dev.data_ptr(), H.HWENO_FP32, True)
+        H.hweno_record(h, STEPS_ADJ, EVERY_ADJ)
+        H.hweno_get_state(h, uN.data_ptr(), H.HWENO_FP32, True)
+
+    def backward():
+        seed_grad[0, 0] = 2.0 * uN[0, 0]  # d sum(rho^2) / d u_N
+        H.hweno_backward(h, seed_grad.data_ptr(), grad.data_ptr(), H.HWENO_FP32, True)
+
+    for _ in range(args.warmup):
+        forward()
+        backward()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    tf, tb = [], []
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        forward()
+        e[1].record(stream)
+        backward()
+        e[2].record(stream)
+        e[2].synchronize()
+        tf.append(e[0].elapsed_time(e[1]) / 1e3)
+        tb.append(e[1].elapsed_time(e[2]) / 1e3)
+    # one adjoint stage (kernels A and B) on the final state, and one forward
+    # stage, timed alone
+    flags = torch.zeros(n * n, dtype=torch.uint8, device="cuda")
+    lam = torch.randn_like(dev)
+    out = torch.empty_like(dev)
+    reps = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    H.hweno_rhs(h, uN.data_ptr(), out.data_ptr(), flags.data_ptr(), 0)
+    a.record(stream)
+    for _ in range(reps):
+        H.hweno_rhs_vjp(h, uN.data_ptr(), flags.data_ptr(), 1.0, 1.0, lam.data_ptr(), out.data_ptr())
+    b.record(stream)
+    b.synchronize()
+    adj_stage_s = a.elapsed_time(b) / 1e3 / reps
+    sampler.__exit__(None, None, None)
+    H.hweno_destroy(h)
+    if rank != 0:
+        return
+    t_f, t_b = statistics.median(tf), statistics.median(tb)
+    cells = n * n * 3 * STEPS_ADJ
+    clocks = sampler.summary()
+    line = {
+        "metric": "cell-stages/s of forward + adjoint (gradient of sum rho^2)", "value": cells / (t_f + t_b),
+        "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * (t_f + t_b), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint: 2D Euler 1024x1024 periodic, vortex + 8 density modes, "
+                               "loss sum(rho^2) after %d RK3 steps, checkpoint every %d, "
+                               "%d Gauss points, FP32" % (STEPS_ADJ, EVERY_ADJ, ng),
+                   "seed": SEED_ADJ, "l2": "state 50 MB, tape and segment states > L2"},
+        "forward_ms": t_f * 1e3, "backward_ms": t_b * 1e3,
+        "adjoint_over_forward": t_b / t_f,
+        "adjoint_stage_ms": adj_stage_s * 1e3,
+        "forward_cell_stages_per_s": cells / t_f,
+        "clocks": clocks,
+        # forward and recomputed stages, two adjoint kernels per stage, one
+        # wave-speed launch per segment, and the state conversions and resets
+        "gpu_launches": args.steps * (3 * STEPS_ADJ * 2 + 6 * STEPS_ADJ + STEPS_ADJ // EVERY_ADJ + 6),
+    }
+    print(json.dumps(line))
 
 
 # ----------------------------------------------------------------------------- batched 1D workload
@@ -552,10 +654,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="euler1d", choices=["euler1d", "euler2d", "batch1d"],
+    ap.add_argument("--workload", default="euler1d",
+                    choices=["euler1d", "euler2d", "batch1d", "adjoint2d"],
                     help="euler1d: the headline 65536-cell 1D workload; euler2d: the "
-                         "4096 x 4096 2D Euler workload; batch1d: 512 uneven 1D instances")
-    ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
+                         "4096 x 4096 2D Euler workload; batch1d: 512 uneven 1D instances; "
+                         "adjoint2d: gradient through 200 steps of 2D Euler at 1024 x 1024")
+    ap.add_argument("--n-gauss", type=int, default=None, choices=[2, 3],
+                    help="Gauss points per direction (2D): default 2 for euler2d (its "
+                         "configuration), 3 for adjoint2d (the paper's)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
@@ -563,6 +669,8 @@ def main():
         bench_euler2d(args)
     elif args.workload == "batch1d":
         bench_batch1d(args)
+    elif args.workload == "adjoint2d":
+        bench_adjoint2d(args)
     else:
         bench_hweno(args)
 
