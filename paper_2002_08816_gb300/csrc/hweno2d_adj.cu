@@ -13,12 +13,16 @@
 //     i and of its four neighbours, times b dt), of its point values (through
 //     the flux Jacobians), and G_i = (dP_i/dD_i)^T lam_P, the adjoints of its
 //     19 data (transposed linear p0, or the reverse of Step 5.1's nonlinear
-//     combination where the stencil holds a troubled cell);
-//   kernel B, per cell j: mu_j = b lam_j + the entries of G_i that belong to
-//     j, over the cells i whose stencil holds j (+ the adjoint of W0 at stage
-//     1): the adjoint of W; then the reverse of Step 4, where mu passes
-//     through unmodified moments and each troubled cell sends the adjoint of
-//     its modified moments back to the five data Step 1 read.
+//     combination where the stencil holds a troubled cell).  The tile sums, in
+//     shared memory and in a fixed order, the entries of its cells' G_i for
+//     every cell of the tile and its 1-cell ring, and writes these partial
+//     sums (12 values per position) instead of the 76 per cell;
+//   kernel B, per cell j: mu_j = b lam_j + the partial sums that the tiles
+//     holding j's neighbours wrote for j (+ the adjoint of W0 at stage 1): the
+//     adjoint of W, which passes through the moments Step 4 did not modify;
+//   kernel C, only on tiles near a troubled cell: the reverse of Step 4, each
+//     troubled cell sending the adjoint of its modified moments back to the
+//     five data Step 1 read.
 // Reverse-mode arithmetic: hweno_adj.cuh; transposed maps and smoothness-
 // indicator gradients: the generated hweno2d_adj_coef.cuh.
 #include <cuda_runtime.h>
@@ -44,8 +48,34 @@ struct SmemA {
   R lam[C][3][BY][BX];  // b dt lam (the adjoint of L)
   R vl[C][BY][BX];      // Step 4 moments
   R wl[C][BY][BX];
+  R g[19][TY][TX];      // one component's stencil adjoints of the own cells
   uint8_t fl[BY][BX];
 };
+
+// Offsets of the 19 stencil data (Fig. 1): averages of cells 1..9, then the
+// x- and the y-moments of cells 2, 4, 5, 6, 8.
+__device__ __forceinline__ int data_dx(int k) {
+  return k < 9 ? k % 3 - 1 : ((k - 9) % 5 == 1 ? -1 : (k - 9) % 5 == 3 ? 1 : 0);
+}
+__device__ __forceinline__ int data_dy(int k) {
+  return k < 9 ? k / 3 - 1 : ((k - 9) % 5 == 0 ? -1 : (k - 9) % 5 == 4 ? 1 : 0);
+}
+
+// The (tile, position) pairs along one axis under which the partial sums of
+// kernel A hold cell j: position p of tile t is the cell t T + p - 1 (wrapped);
+// j gets contributions from the cells j - 1, j, j + 1 (d = 0, 1, 2), each in
+// its own tile; u[d] is false when an earlier d gave the same pair.
+__device__ __forceinline__ void part_pairs(int j, int n, int T, int* t, int* p, bool* u) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int i = bc_map(j + d - 1, n, 0);
+    t[d] = i / T;
+    p[d] = i - t[d] * T - (d - 1) + 1;
+    u[d] = true;
+#pragma unroll
+    for (int q = 0; q < d; ++q) u[d] = u[d] && !(t[q] == t[d] && p[q] == p[d]);
+  }
+}
 
 template <typename R, int C>
 struct SmemB {
@@ -273,6 +303,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
 #pragma unroll
       for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
   }
+  int ring_troubled = 0;
   for (int k = tid; k < BX * BY; k += NT) {
     const int lx = k % BX, ly = k / BX;
     const size_t s = (size_t)bc_map(by0 - 1 + ly, ny, 0) * nx + bc_map(bx0 - 1 + lx, nx, 0);
@@ -281,8 +312,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
 #pragma unroll
       for (int m = 0; m < 3; ++m) sm.lam[c][m][ly][lx] = scale * lam[(3 * c + m) * plane + s];
     sm.fl[ly][lx] = a.flags[s] != 0;
+    ring_troubled |= sm.fl[ly][lx];
   }
-  __syncthreads();
+  if (__syncthreads_or(ring_troubled) && tid == 0) {  // kernel C's work list
+    const int q = atomicAdd(a.tile_list, 1);
+    a.tile_list[1 + q] = blockIdx.y * gridDim.x + blockIdx.x;
+  }
 
   // Step 4 on the tile and its 1-cell halo (the forward values)
   for (int k = tid; k < BX * BY; k += NT) {
@@ -309,7 +344,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
 
   const int ci = tid % TX, cj = tid / TX;
   const int gi = bx0 + ci, gj = by0 + cj;
-  if (gi >= nx || gj >= ny) return;  // no barrier below
+  const bool own = gi < nx && gj < ny;
   bool hw = false;
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj)
@@ -413,177 +448,255 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
     }
 #undef LAM
 
-  // adjoints of the 19 data
-  R* __restrict__ G = static_cast<R*>(a.G);
-  const size_t s = (size_t)gj * nx + gi;
-  if (C == 1 || !hw) {
+  // adjoints of the 19 data, summed per target cell over the tile's own cells
+  R Gl[C == 4 ? 4 : 1][19];
+  if constexpr (C == 4) {
+    if (own && hw) {
+      R lamF[4][NF];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      R g[19];
+      for (int c = 0; c < 4; ++c) {
 #pragma unroll
-      for (int k = 0; k < 19; ++k) g[k] = R(0);
+        for (int p = 0; p < NF; ++p) lamF[c][p] = P[c][p];
+#pragma unroll
+        for (int k = 0; k < 19; ++k) Gl[c][k] = R(0);
+      }
+      hw_faces_euler_vjp<NG>(sm, ci, cj, P_.gam, P_.eps, P_.gas, lamF, Gl);
+    }
+  }
+  R* __restrict__ part = static_cast<R*>(a.G) + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (C * 3 * BX * BY);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    R g[19];
+#pragma unroll
+    for (int k = 0; k < 19; ++k) g[k] = R(0);
+    if (own) {
       if (!hw) {
         p0_faces_T<NG>(P[c], g);
-      } else {
+      } else if constexpr (C == 1) {
         R d[19];
         gather19a(sm, c, ci, cj, d);
         hweno2d_faces_vjp<NG>(d, P_.gam, P_.eps, P[c], g);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) g[k] = Gl[c][k];
       }
       p0_interior_T<NG>(&P[c][NF], g);
-#pragma unroll
-      for (int k = 0; k < 19; ++k) G[(size_t)(k * C + c) * plane + s] = g[k];
     }
-  } else if constexpr (C == 4) {
-    R lamF[4][NF], Gl[4][19];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int k = 0; k < 19; ++k) sm.g[k][cj][ci] = g[k];
+    __syncthreads();
+    for (int t = tid; t < BX * BY; t += NT) {
+      const int tx = t % BX - 1, ty = t / BX - 1;  // tile coordinates of the target
+      R m[3] = {R(0), R(0), R(0)};
 #pragma unroll
-      for (int p = 0; p < NF; ++p) lamF[c][p] = P[c][p];
+      for (int k = 0; k < 19; ++k) {
+        const int sx = tx - data_dx(k), sy = ty - data_dy(k);
+        if (sx >= 0 && sx < TX && sy >= 0 && sy < TY) m[k < 9 ? 0 : (k < 14 ? 1 : 2)] += sm.g[k][sy][sx];
+      }
 #pragma unroll
-      for (int k = 0; k < 19; ++k) Gl[c][k] = R(0);
+      for (int q = 0; q < 3; ++q) part[(c * 3 + q) * (BX * BY) + t] = m[q];
     }
-    hw_faces_euler_vjp<NG>(sm, ci, cj, P_.gam, P_.eps, P_.gas, lamF, Gl);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- kernels B, C
+
+// m[c][q] += the partial sums kernel A's tiles wrote for cell (gi, gj).
+template <typename R, int C>
+__device__ __forceinline__ void part_sums(const Adj2DArgs& a, int gi, int gj, R (*m)[3]) {
+  const R* __restrict__ part = static_cast<const R*>(a.G);
+  int tx[3], px[3], ty[3], py[3];
+  bool ux[3], uy[3];
+  part_pairs(gi, a.nx, TX, tx, px, ux);
+  part_pairs(gj, a.ny, TY, ty, py, uy);
+  const int ntx = (a.nx + TX - 1) / TX;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      p0_interior_T<NG>(&P[c][NF], Gl[c]);
+  for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int k = 0; k < 19; ++k) G[(size_t)(k * 4 + c) * plane + s] = Gl[c][k];
+    for (int q = 0; q < 3; ++q) {
+      if (!(uy[b] && ux[q])) continue;
+      const R* pt = part + (size_t)(ty[b] * ntx + tx[q]) * (C * 3 * BX * BY) + py[b] * BX + px[q];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) m[c][r] += pt[(c * 3 + r) * (BX * BY)];
+    }
+}
+
+// mu = b lam + (stage 1: the adjoint of W0) + the partial sums, one component.
+template <typename R, int C>
+__device__ __forceinline__ void mu_at(const Adj2DArgs& a, int gi, int gj, int c, R* mc) {
+  const size_t plane = (size_t)a.nx * a.ny, s = (size_t)gj * a.nx + gi;
+  const R* __restrict__ lam = static_cast<const R*>(a.lam);
+  const R bco = stage_b<R>(a.stage);
+  R m[C][3];
+#pragma unroll
+  for (int k = 0; k < C; ++k)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) m[k][q] = R(0);
+  part_sums<R, C>(a, gi, gj, m);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    mc[q] = (a.stage > 0 ? bco * lam[(3 * c + q) * plane + s] : R(0));
+    if (a.stage == 1) mc[q] += static_cast<const R*>(a.acc)[(3 * c + q) * plane + s];
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (k == c) mc[q] += m[k][q];
+  }
+}
+
+// Kernel B, one cell per thread: the adjoint of the stage input where Step 4
+// changed nothing (mu itself; zero for the first moments of a troubled cell),
+// and the adjoint of W0 (stage 3 sets it to lam / 3, stage 2 adds 3 lam / 4).
+template <typename R, int C>
+__global__ void __launch_bounds__(NT) adj2d_pass_kernel(Adj2DArgs a) {
+  const int gi = blockIdx.x * TX + threadIdx.x % TX, gj = blockIdx.y * TY + threadIdx.x / TX;
+  if (gi >= a.nx || gj >= a.ny) return;
+  const size_t plane = (size_t)a.nx * a.ny, s = (size_t)gj * a.nx + gi;
+  const bool t0 = a.flags[s] != 0;
+  R* __restrict__ out = static_cast<R*>(a.lam_in);
+  const R* __restrict__ lam = static_cast<const R*>(a.lam);
+  R* __restrict__ acc = static_cast<R*>(a.acc);
+  // every load first, then the stores
+  R lv[C][3], m[C][3], av[C][3];
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      lv[c][q] = lam[(3 * c + q) * plane + s];
+      av[c][q] = a.stage == 1 || a.stage == 2 ? acc[(3 * c + q) * plane + s] : R(0);
+    }
+  const R bco = stage_b<R>(a.stage);
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) m[c][q] = (a.stage > 0 ? bco * lv[c][q] : R(0)) + (a.stage == 1 ? av[c][q] : R(0));
+  part_sums<R, C>(a, gi, gj, m);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    out[(3 * c) * plane + s] = m[c][0];
+    out[(3 * c + 1) * plane + s] = t0 ? R(0) : m[c][1];
+    out[(3 * c + 2) * plane + s] = t0 ? R(0) : m[c][2];
+    if (a.stage >= 2) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        acc[(3 * c + q) * plane + s] =
+            a.stage == 3 ? R(1.0 / 3.0) * lv[c][q] : av[c][q] + R(0.75) * lv[c][q];
     }
   }
 }
 
-// ------------------------------------------------------------- kernel B
-
+// One tile of kernel C (a tile with a troubled cell in its 1-cell ring): adds
+// the reverse of Step 4 (each troubled cell's modified moments back to the
+// five data Step 1 read) to the adjoints kernel B wrote.
 template <typename R, int C>
-__global__ void __launch_bounds__(NT) adj2d_gather_kernel(Adj2DArgs a) {
+__device__ __noinline__ void fix_tile(const Adj2DArgs& a, int tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemB<R, C>& sm = *reinterpret_cast<SmemB<R, C>*>(smem_raw);
   const int tid = threadIdx.x;
   const int nx = a.nx, ny = a.ny;
-  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+  const int ntx = (nx + TX - 1) / TX;
+  const int bx0 = (tile % ntx) * TX, by0 = (tile / ntx) * TY;
   const size_t plane = (size_t)nx * ny;
-  const AdjParams<R> P_(a);
-  const R* __restrict__ lam = static_cast<const R*>(a.lam);
-  const R* __restrict__ G = static_cast<const R*>(a.G);
-  const R* acc_in = static_cast<const R*>(a.acc);
-  const R bco = stage_b<R>(a.stage);
-  const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
-
-  // mu on the tile and its 1-cell halo
-  int any = 0;
   for (int k = tid; k < BX * BY; k += NT) {
     const int lx = k % BX, ly = k / BX;
-    const int gi = bc_map(bx0 - 1 + lx, nx, 0), gj = bc_map(by0 - 1 + ly, ny, 0);
-    const size_t s = (size_t)gj * nx + gi;
-    const uint8_t f = a.flags[s] != 0;
-    sm.fl[ly][lx] = f;
-    any |= f;
+    const size_t s = (size_t)bc_map(by0 - 1 + ly, ny, 0) * nx + bc_map(bx0 - 1 + lx, nx, 0);
+    sm.fl[ly][lx] = a.flags[s] != 0;
+  }
+  const AdjParams<R> P_(a);
+  for (int k = tid; k < BX * BY * C; k += NT) {
+    const int cell = k % (BX * BY), c = k / (BX * BY);
+    const int lx = cell % BX, ly = cell / BX;
+    R m[3];
+    mu_at<R, C>(a, bc_map(bx0 - 1 + lx, nx, 0), bc_map(by0 - 1 + ly, ny, 0), c, m);
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      R m0 = R(0), m1 = R(0), m2 = R(0);
-      if (a.stage > 0) {
-        m0 = bco * lam[(3 * c) * plane + s];
-        m1 = bco * lam[(3 * c + 1) * plane + s];
-        m2 = bco * lam[(3 * c + 2) * plane + s];
-      }
-      if (a.stage == 1) {
-        m0 += acc_in[(3 * c) * plane + s];
-        m1 += acc_in[(3 * c + 1) * plane + s];
-        m2 += acc_in[(3 * c + 2) * plane + s];
-      }
+    for (int q = 0; q < 3; ++q) sm.mu[c][q][ly][lx] = m[q];
+  }
+  const R* __restrict__ w = static_cast<const R*>(a.w);
+  for (int k = tid; k < AX * AY; k += NT) {
+    const int rx = k % AX, ry = k / AX;
+    const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 2 + rx, nx, 0);
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const size_t s2 = (size_t)bc_map(gj - (q / 3 - 1), ny, 0) * nx + bc_map(gi - (q % 3 - 1), nx, 0);
-        m0 += G[(size_t)(q * C + c) * plane + s2];
-      }
+    for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const size_t s2 = (size_t)bc_map(gj - my[q], ny, 0) * nx + bc_map(gi - mx[q], nx, 0);
-        m1 += G[(size_t)((9 + q) * C + c) * plane + s2];
-        m2 += G[(size_t)((14 + q) * C + c) * plane + s2];
-      }
-      sm.mu[c][0][ly][lx] = m0;
-      sm.mu[c][1][ly][lx] = m1;
-      sm.mu[c][2][ly][lx] = m2;
+      for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+  }
+  __syncthreads();
+  for (int k = tid; k < BX * BY; k += NT) {
+    const int lx = k % BX, ly = k / BX;
+    if (!sm.fl[ly][lx]) continue;
+    const int rx = lx + 1, ry = ly + 1;
+    if constexpr (C == 1) {
+      R g[5] = {R(0), R(0), R(0), R(0), R(0)};
+      limit_first_moment_vjp(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx], sm.u[0][0][ry][rx + 1],
+                             sm.u[0][1][ry][rx - 1], sm.u[0][1][ry][rx + 1], P_.gam, P_.eps,
+                             sm.mu[0][1][ly][lx], g);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sm.cx[0][q][ly][lx] = g[q];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) g[q] = R(0);
+      limit_first_moment_vjp(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx], sm.u[0][0][ry + 1][rx],
+                             sm.u[0][2][ry - 1][rx], sm.u[0][2][ry + 1][rx], P_.gam, P_.eps,
+                             sm.mu[0][2][ly][lx], g);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sm.cy[0][q][ly][lx] = g[q];
+    } else {
+      limit_euler2d_vjp(sm, lx, ly, P_.gam, P_.eps, P_.gas);
     }
   }
-  any = __syncthreads_or(any);
-  if (any) {
-    const R* __restrict__ w = static_cast<const R*>(a.w);
-    for (int k = tid; k < AX * AY; k += NT) {
-      const int rx = k % AX, ry = k / AX;
-      const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 2 + rx, nx, 0);
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
-    }
-    __syncthreads();
-    for (int k = tid; k < BX * BY; k += NT) {
-      const int lx = k % BX, ly = k / BX;
-      if (!sm.fl[ly][lx]) continue;
-      const int rx = lx + 1, ry = ly + 1;
-      if constexpr (C == 1) {
-        R g[5] = {R(0), R(0), R(0), R(0), R(0)};
-        limit_first_moment_vjp(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx], sm.u[0][0][ry][rx + 1],
-                               sm.u[0][1][ry][rx - 1], sm.u[0][1][ry][rx + 1], P_.gam, P_.eps,
-                               sm.mu[0][1][ly][lx], g);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) sm.cx[0][q][ly][lx] = g[q];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) g[q] = R(0);
-        limit_first_moment_vjp(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx], sm.u[0][0][ry + 1][rx],
-                               sm.u[0][2][ry - 1][rx], sm.u[0][2][ry + 1][rx], P_.gam, P_.eps,
-                               sm.mu[0][2][ly][lx], g);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) sm.cy[0][q][ly][lx] = g[q];
-      } else {
-        limit_euler2d_vjp(sm, lx, ly, P_.gam, P_.eps, P_.gas);
-      }
-    }
-    __syncthreads();
-  }
-
+  __syncthreads();
   const int ci = tid % TX, cj = tid / TX;
   const int gi = bx0 + ci, gj = by0 + cj;
   if (gi >= nx || gj >= ny) return;
   const int lx = ci + 1, ly = cj + 1;
+  const bool fl = sm.fl[ly][lx - 1] || sm.fl[ly][lx + 1] || sm.fl[ly - 1][lx] || sm.fl[ly + 1][lx] ||
+                  sm.fl[ly][lx];
+  if (!fl) return;
   const size_t s = (size_t)gj * nx + gi;
-  const bool t0 = sm.fl[ly][lx] != 0;
   R* __restrict__ out = static_cast<R*>(a.lam_in);
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    R g0 = sm.mu[c][0][ly][lx];
-    R g1 = t0 ? R(0) : sm.mu[c][1][ly][lx];
-    R g2 = t0 ? R(0) : sm.mu[c][2][ly][lx];
-    if (any) {
-      if (sm.fl[ly][lx - 1]) { g0 += sm.cx[c][2][ly][lx - 1]; g1 += sm.cx[c][4][ly][lx - 1]; }
-      if (sm.fl[ly][lx + 1]) { g0 += sm.cx[c][0][ly][lx + 1]; g1 += sm.cx[c][3][ly][lx + 1]; }
-      if (sm.fl[ly - 1][lx]) { g0 += sm.cy[c][2][ly - 1][lx]; g2 += sm.cy[c][4][ly - 1][lx]; }
-      if (sm.fl[ly + 1][lx]) { g0 += sm.cy[c][0][ly + 1][lx]; g2 += sm.cy[c][3][ly + 1][lx]; }
-      if (t0) g0 += sm.cx[c][1][ly][lx] + sm.cy[c][1][ly][lx];
-    }
-    out[(3 * c) * plane + s] = g0;
-    out[(3 * c + 1) * plane + s] = g1;
-    out[(3 * c + 2) * plane + s] = g2;
-    if (a.stage >= 2) {
-      R* acc = static_cast<R*>(a.acc);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const size_t e = (3 * c + m) * plane + s;
-        acc[e] = a.stage == 3 ? R(1.0 / 3.0) * lam[e] : acc[e] + R(0.75) * lam[e];
-      }
-    }
+    R g0 = R(0), g1 = R(0), g2 = R(0);
+    if (sm.fl[ly][lx - 1]) { g0 += sm.cx[c][2][ly][lx - 1]; g1 += sm.cx[c][4][ly][lx - 1]; }
+    if (sm.fl[ly][lx + 1]) { g0 += sm.cx[c][0][ly][lx + 1]; g1 += sm.cx[c][3][ly][lx + 1]; }
+    if (sm.fl[ly - 1][lx]) { g0 += sm.cy[c][2][ly - 1][lx]; g2 += sm.cy[c][4][ly - 1][lx]; }
+    if (sm.fl[ly + 1][lx]) { g0 += sm.cy[c][0][ly + 1][lx]; g2 += sm.cy[c][3][ly + 1][lx]; }
+    if (sm.fl[ly][lx]) g0 += sm.cx[c][1][ly][lx] + sm.cy[c][1][ly][lx];
+    out[(3 * c) * plane + s] += g0;
+    out[(3 * c + 1) * plane + s] += g1;
+    out[(3 * c + 2) * plane + s] += g2;
+  }
+}
+
+// Kernel C: a grid-stride loop over the tiles kernel A listed (tiles without a
+// troubled cell in their ring have nothing to add).
+template <typename R, int C>
+__global__ void __launch_bounds__(NT) adj2d_fix_kernel(Adj2DArgs a) {
+  const int count = a.tile_list[0];
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    fix_tile<R, C>(a, a.tile_list[1 + i]);
+    __syncthreads();
   }
 }
 
 template <typename R, int C, int NG>
 cudaError_t launch_t(const Adj2DArgs& a, cudaStream_t s) {
   const dim3 grid((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
-  adj2d_points_kernel<R, C, NG><<<grid, NT, sizeof(SmemA<R, C>), s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(a.tile_list, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  adj2d_gather_kernel<R, C><<<grid, NT, sizeof(SmemB<R, C>), s>>>(a);
+  adj2d_points_kernel<R, C, NG><<<grid, NT, sizeof(SmemA<R, C>), s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj2d_pass_kernel<R, C><<<grid, NT, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const unsigned ntile = grid.x * grid.y, gc = 2u * (unsigned)nsm;
+  adj2d_fix_kernel<R, C><<<ntile < gc ? ntile : gc, NT, sizeof(SmemB<R, C>), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -593,7 +706,7 @@ cudaError_t prepare_t() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SmemA<R, C>));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(adj2d_gather_kernel<R, C>,
+  return cudaFuncSetAttribute(adj2d_fix_kernel<R, C>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmemB<R, C>));
 }

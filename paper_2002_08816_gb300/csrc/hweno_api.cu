@@ -56,7 +56,8 @@ struct hweno_ctx {
     int seg_every = 0;          // capacity of seg, in steps
     void* seg = nullptr;        // 3 every + 1 recomputed stage inputs
     void* w0 = nullptr;         // limited u^n of the recomputed step
-    void* G = nullptr;          // 19 C planes
+    void* G = nullptr;          // per-tile partial sums of the stencil adjoints
+    int* tile_list = nullptr;   // count + the tiles near a troubled cell
     void* lam[2] = {nullptr, nullptr};
     void* acc = nullptr;
     double* slots = nullptr;    // 3 x 2 kAlphaSlots
@@ -331,6 +332,7 @@ void free_tape(hweno_ctx* h, bool scratch) {
   free_ptr(reinterpret_cast<void**>(&t.slots));
   free_ptr(reinterpret_cast<void**>(&t.sc));
   free_ptr(&t.aux);
+  free_ptr(reinterpret_cast<void**>(&t.tile_list));
   t.seg_every = 0;
 }
 
@@ -349,8 +351,11 @@ hweno_status adjoint_scratch(hweno_ctx* h) {
     HW_CUDA(h, hw::prepare_adj2d(h->cfg.system, h->cfg.precision == HWENO_FP64, h->cfg.n_gauss));
     t.prepared = true;
   }
-  if (!t.G) HW_CUDA(h, cudaMalloc(&t.G, (size_t)19 * h->C * h->n * h->esize));
+  if (!t.G)
+    HW_CUDA(h, cudaMalloc(&t.G, (size_t)h->ntile * h->C * 3 * (hw::kTile2DX + 2) *
+                                    (hw::kTile2DY + 2) * h->esize));
   if (!t.aux) HW_CUDA(h, cudaMalloc(&t.aux, 2 * sizeof(double)));
+  if (!t.tile_list) HW_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&t.tile_list), sizeof(int) * (1 + (size_t)h->ntile)));
   if (!t.sc) HW_CUDA(h, cudaMalloc(&t.sc, sizeof(hw::DevScalars)));
   return HWENO_OK;
 }
@@ -370,6 +375,7 @@ hw::Adj2DArgs base_adj_args(const hweno_ctx* h) {
   a.gas = c.gas_gamma;
   for (int k = 0; k < 5; ++k) a.gam[k] = c.lin_w[k];
   a.G = h->tape.G;
+  a.tile_list = h->tape.tile_list;
   hw::finish_adj2d_args(a);
   return a;
 }

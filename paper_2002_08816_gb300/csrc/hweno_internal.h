@@ -136,9 +136,11 @@ struct Adj2DArgs {
   const void* alpha;      // (alpha_x, alpha_y) of the stage, kernel precision
   const void* dt;         // dt of the step, kernel precision (stage 0: unused)
   const void* lam;        // adjoint of the stage output
-  void* G;                // scratch [19][C][ny][nx]: adjoints of each cell's 19 data
+  void* G;                // scratch: per tile, C x 3 x (TY + 2) x (TX + 2) partial sums of
+                          // its cells' stencil adjoints (kernel A writes, kernel B reads)
   void* acc;              // adjoint of W0
   void* lam_in;           // out: adjoint of the stage input
+  int* tile_list;         // scratch, 1 + tiles ints: count, then the tiles kernel C visits
   int stage, nx, ny, system, fp64, ng;
   double dx, dy, eps, gas;
   double gam[5];

@@ -3,11 +3,15 @@
   python -m paper_2002_08816_gb300.profile_stage [--nx 65536] [--rk-steps 10]
                                                   [--precision fp32|fp64] [--system euler|burgers]
                                                   [--dim 1|2] [--n-gauss 2|3]
+                                                  [--adjoint EVERY]
 
 Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
 --dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
 requested number of Runge-Kutta steps through the C ABI (3 stage launches per
-step after one alpha launch) and checks the status word.
+step after one alpha launch) and checks the status word.  With --adjoint
+EVERY (2D) the steps are recorded with a checkpoint every EVERY steps and the
+gradient of sum(rho^2) is taken (hweno_backward: recomputed stages, then two
+adjoint kernels per stage).
 """
 
 import argparse
@@ -32,6 +36,7 @@ def main():
     ap.add_argument("--seed", type=int, default=20250)
     ap.add_argument("--dim", type=int, default=1, choices=[1, 2])
     ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--adjoint", type=int, default=0)
     args = ap.parse_args()
     B.build()
     prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
@@ -52,7 +57,17 @@ def main():
     h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
         H.hweno_set_state(h, dev.data_ptr(), prec, True)
-        t = H.hweno_step(h, args.rk_steps)
+        if args.adjoint > 0:
+            t = H.hweno_record(h, args.rk_steps, args.adjoint)
+            out = torch.empty_like(dev)
+            H.hweno_get_state(h, out.data_ptr(), prec, True)
+            seed = torch.zeros_like(dev)
+            seed[0, 0] = 2.0 * out[0, 0]
+            grad = torch.empty_like(dev)
+            H.hweno_backward(h, seed.data_ptr(), grad.data_ptr(), prec, True)
+            print("gradient norm %.6g" % float(grad.double().norm()))
+        else:
+            t = H.hweno_step(h, args.rk_steps)
         st = H.hweno_stats(h)
     finally:
         H.hweno_destroy(h)
