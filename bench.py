@@ -38,6 +38,12 @@ UNIT = "cell-stages/s"
 # stages 2 and 3 read u^n and u^(k) and write (3S); mean 8S/3 with
 # S = 3 components x 2 moments x sizeof(real)
 BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
+# DRAM bytes (read + write) per stage launch from ncu captures of the current
+# kernels (profiles/stage1d_euler65536_fp32.md: mean over the three stages at
+# the bench's 65536 cells; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled
+# by the cell count to 4096^2)
+TRAFFIC_1D_FP32 = (1.622528e6 + 2 * 3.195392e6) / 3
+TRAFFIC_2D_NG2 = 4 * (403.311616e6 + 178.976512e6)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -297,7 +303,7 @@ def bench_hweno(args):
                  "e2e": results["fp64"]["e2e"]},
         "troubled_frac": r["troubled_frac"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_1D_FP32,
                      "kernel": "stage1d_kernel<float,3>",
                      "note": "avg stage-launch time = timed region / 6000 launches; peak %s" % peak_kind},
         "cpu_baseline": cpu,
@@ -419,12 +425,14 @@ def bench_euler2d(args):
     t_hbm = byts / (hbm * 1e9)
     if t_alu >= t_hbm:
         roof = {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": t_alu / stage_s, "traffic": None,
+                "unit": "TFLOP/s", "frac": t_alu / stage_s,
+                "traffic": TRAFFIC_2D_NG2 if ng == 2 else None,
                 "note": "FP32 peak = 152 SMs x 128 lanes x 2 flops x sampled SM clock; "
                         "%d flops per smooth cell-stage" % flops_per_cell_stage_2d(ng)}
     else:
         roof = {"bound": "hbm", "achieved": byts / stage_s / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": t_hbm / stage_s, "traffic": None, "note": "peak %s" % peak_kind}
+                "frac": t_hbm / stage_s, "traffic": TRAFFIC_2D_NG2 if ng == 2 else None,
+                "note": "peak %s" % peak_kind}
     roof["kernel"] = "stage2d_kernel<float,4,%d>" % ng
     line = {
         "metric": METRIC, "value": ws * cells * args.steps / tot, "unit": UNIT, "n_gpus": ws,
