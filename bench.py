@@ -42,7 +42,7 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
 # kernels (profiles/stage1d_euler65536_fp32.md: mean over the three stages at
 # the bench's 65536 cells; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled
 # by the cell count to 4096^2)
-TRAFFIC_1D_FP32 = (1.622528e6 + 2 * 3.195392e6) / 3
+TRAFFIC_1D_FP32 = {(256, "per-stage graphs"): (1.622528e6 + 2 * 3.195392e6) / 3}
 TRAFFIC_2D_NG2 = 4 * (403.311616e6 + 178.976512e6)
 L2_FLUSH_BYTES = 512 << 20
 
@@ -225,6 +225,10 @@ def bench_hweno(args):
             H.hweno_set_state(h, dev_in.data_ptr(), prec, True)
             H.hweno_step(h, RK_STEPS, -1.0, wait=False)
 
+        # the library's autotuner picks threads per CTA and graph or persistent
+        # launches for this workload (untimed)
+        H.hweno_set_state(h, dev_in.data_ptr(), prec, True)
+        choice = H.hweno_autotune(h, 100)
         for _ in range(args.warmup):
             one_step()
         torch.cuda.synchronize()
@@ -279,6 +283,9 @@ def bench_hweno(args):
             "troubled_frac": stats["troubled"] / float(3 * RK_STEPS * NX),
             "bytes_h2d": host_in.numel() * host_in.element_size(),
             "clocks": sampler.summary() if sampler else None,
+            "execution": {"threads_per_cta": choice[0], "cells_per_tile": choice[0] - 6,
+                          "launch": "persistent" if choice[1] else "per-stage graphs",
+                          "chosen_by": "hweno_autotune"},
         }
 
     cpu = None
@@ -302,9 +309,12 @@ def bench_hweno(args):
         "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
                  "e2e": results["fp64"]["e2e"]},
         "troubled_frac": r["troubled_frac"],
+        "execution": r["execution"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_1D_FP32,
-                     "kernel": "stage1d_kernel<float,3>",
+                     "frac": achieved / peak,
+                     "traffic": TRAFFIC_1D_FP32.get((r["execution"]["threads_per_cta"],
+                                                     r["execution"]["launch"])),
+                     "kernel": "stage1d_kernel<float,3,%d threads>" % r["execution"]["threads_per_cta"],
                      "note": "avg stage-launch time = timed region / 6000 launches; peak %s" % peak_kind},
         "cpu_baseline": cpu,
         "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["bytes_h2d"],
@@ -591,6 +601,8 @@ def bench_batch1d(args):
         H.hweno_set_state(h, dev.data_ptr(), H.HWENO_FP32, True)
         H.hweno_step(h, RK_STEPS_BATCH, -1.0, wait=False)
 
+    H.hweno_set_state(h, dev.data_ptr(), H.HWENO_FP32, True)
+    choice = H.hweno_autotune(h, 20)  # tile size and launch kind, untimed
     for _ in range(args.warmup):
         one_step()
     H.hweno_step(h, 0, -1.0)
@@ -641,7 +653,7 @@ def bench_batch1d(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched 1D Euler: 512 instances, cells log-uniform in "
                                "[256, 16384] (%d cells), two-state data, %d RK3 steps each, "
-                               "CFL %.1f, FP32, one launch per stage for all instances"
+                               "CFL %.1f, FP32, all instances in shared launches"
                                % (cells, RK_STEPS_BATCH, CFL),
                    "seed": SEED_BATCH, "l2": "flushed (512 MiB write) between timed steps"},
         "per_instance": {"ms_per_step_estimate": 1e3 * per_inst_s,
@@ -649,6 +661,9 @@ def bench_batch1d(args):
                          "how": "one handle per instance (CUDA graphs of 32 steps), 32 instances "
                                 "spread over the sizes, %.1f ms, scaled by 512/32" % (1e3 * sub_s)},
         "speedup_vs_per_instance": per_inst_s / (tot / args.steps),
+        "execution": {"threads_per_cta": choice[0], "cells_per_tile": choice[0] - 6,
+                      "launch": "persistent" if choice[1] else "per-stage graphs",
+                      "chosen_by": "hweno_autotune"},
         "gpu_launches": args.steps * (3 * RK_STEPS_BATCH + 5),
         "clocks": sampler.summary(),
     }

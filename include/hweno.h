@@ -205,6 +205,28 @@ hweno_status hweno_backward(hweno_handle h, const void* grad_out, void* grad_in,
 hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags, double alpha_x,
                            double alpha_y, const void* lam, void* grad);
 
+/* Chooses how a 1D handle (single instance or batch) runs its steps: per-
+ * stage launches captured in CUDA graphs, or one persistent cooperative
+ * launch per hweno_step call (every CTA walks its tiles of a stage, then the
+ * grid meets at a barrier whose wait is bounded), each with 128, 256 or 512
+ * threads per CTA (a tile is that number minus 6 cells).  Each of the six
+ * candidates advances the current state nsteps_trial steps, timed with CUDA
+ * events on the handle's stream, and the fastest is kept for later calls; the
+ * state, time, counters and wave-speed slots are restored afterwards.  The
+ * per-stage candidates give bitwise the same results; the persistent ones
+ * agree with them to rounding (their copy of the stage body may contract a few
+ * multiply-adds differently).  The paper has no counterpart (it fixes no
+ * hardware mapping).  choice_out (nullable, 2 ints) receives the threads per
+ * CTA and 1 for the persistent launch, 0 for graphs.  New handles start with
+ * 256 threads and per-stage graphs.  Waits for the stream; HWENO_ERR_ARG for 2D
+ * handles, HWENO_ERR_STATE before set_state. */
+hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
+
+/* Sets the choice hweno_autotune makes by hand: threads per CTA (128, 256 or
+ * 512) and persistent (1) or per-stage graph launches (0).  1D handles only;
+ * waits for the stream. */
+hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent);
+
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);
 

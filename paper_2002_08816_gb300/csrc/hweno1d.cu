@@ -1,452 +1,147 @@
-// One fused kernel per third-order TVD Runge-Kutta stage of the 1D hybrid
-// HWENO scheme (Zhao & Qiu, arXiv:2002.08816, Sec. 2.1).
-//
-// A CTA owns kTile1D consecutive cells.  It stages its cells plus a 3-cell
-// halo of the stage input in shared memory (coalesced loads of each
-// structure-of-arrays row), then, all on chip:
-//   1. alpha = max |f'(ubar)| from the maxima the producer of the stage
-//      input left in kAlphaSlots slots (global Lax-Friedrichs flux); stage 1
-//      also turns alpha into dt = CFL dx / alpha, clipped to t_final.  All of
-//      it runs in the kernel's precision: on GB300 each dependent FP64
-//      operation costs tens of cycles, so the FP32 kernel keeps FP64 off its
-//      critical path (the time itself is accumulated in FP64 by an idle thread);
-//   2. KXRCF flags and the modified first moments (Step 1) for the cells and
-//      2 halo cells per side, in characteristic fields for Euler; an FP32
-//      kernel decides a flag in FP32 when its rounding-error bound allows and
-//      in FP64 otherwise, so flags equal the FP64 decision off the threshold;
-//   3. interface values (Steps 2.1/2.2) for the cells and 1 halo cell per
-//      side: linear p0 unless a cell of S0 = {i-1, i, i+1} is troubled;
-//   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
-//      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
-//      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
-//   5. the tile's maximum wave speed of the output, folded by an FP64 atomic
-//      max into one of kAlphaSlots slots that the next stage reads for its
-//      alpha, and the status bits (non-finite, non-physical).
-// The limited stage input is what the RK combination uses (the first moment
-// of a troubled cell is modified in the state, as a DG limiter would).
+// The 1D kernels: one launch per third-order TVD Runge-Kutta stage (captured
+// in CUDA graphs by the C ABI, with programmatic dependent launch), or a whole
+// run in one persistent cooperative launch; both call the same out-of-line
+// stage body (hweno1d_stage.cuh).  Also the wave-speed kernels that start a
+// run and small helpers (conversions, device scalars).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "hweno1d_recon.cuh"
-#include "hweno_device.cuh"
-#include "hweno_internal.h"
+#include "hweno1d_stage.cuh"
 
 namespace hw {
 namespace {
 
-constexpr int T = kTile1D;      // cells per CTA
-constexpr int NT = kThreads1D;  // threads per CTA
-constexpr int H = 3;
-static_assert(T + 2 * H <= NT, "every phase is one pass over the threads");
+using s1d::H;
+using s1d::Smem1D;
+using s1d::wave_speed;
+constexpr int NT = kThreads1D;  // threads of the wave-speed kernels
+constexpr int T = kTile1D;      // their cells per CTA
 constexpr int NW = NT / 32;
 
-template <typename R, int C>
-struct Smem1D {
-  R u[C][2][T + 2 * H];  // stage input, cells base-3 .. base+T+2
-  R vl[C][T + 4];        // modified first moments, cells base-2 .. base+T+1
-  R fm[C][T + 2];        // u^+_{i-1/2}, cells base-1 .. base+T
-  R fp[C][T + 2];        // u^-_{i+1/2}
-  R ffm[C][T + 2];       // f(u^+_{i-1/2})
-  R ffp[C][T + 2];       // f(u^-_{i+1/2})
-  uint8_t fl[T + 4];     // flags, cells base-2 .. base+T+1
-  R red[NW];
-  int cnt[NW];
-  R amax[NW];
-};
+template <typename R, int C, bool BATCH, int NTH>
+__global__ void __launch_bounds__(NTH) stage1d_kernel(Stage1DArgs a) {
+  __shared__ Smem1D<R, C, NTH> sm;
+  s1d::stage1d_tile<R, C, BATCH, NTH>(a, blockIdx.x, sm);
+}
 
-template <typename R>
-__device__ __forceinline__ R recip(R x) {
-  if constexpr (sizeof(R) == 4) {
-    return __frcp_rn(x);
-  } else {
-    return R(1) / x;
+// ------------------------------------------------------------ persistent run
+// A whole run of Runge-Kutta steps in one cooperative launch: each CTA applies
+// the stage body to its tiles of a stage, then all CTAs meet at a grid barrier
+// before the next stage reads their outputs and the alpha slots they filled.
+// The barrier's wait is bounded: after about half a second the CTA sets
+// ST_TIMEOUT in the status word and the whole grid stops at its next barrier,
+// so a fault in the protocol cannot hang the GPU.
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// All CTAs of the (co-resident) grid meet here; false when the wait timed out.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nb, DevScalars* sc) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    const unsigned gen = ld_acquire_gpu(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nb - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned it = 0;
+      while (ld_acquire_gpu(bar + 1) == gen) {
+        if (++it == (1u << 24)) {
+          atomicOr(&sc->status, (unsigned)ST_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename R, int C, bool BATCH, int NTH>
+__global__ void __launch_bounds__(NTH) run1d_kernel(Run1DArgs r) {
+  __shared__ Smem1D<R, C, NTH> sm;
+  for (int step = 0; step < r.nsteps; ++step) {
+#pragma unroll 1
+    for (int stage = 1; stage <= 3; ++stage) {
+      Stage1DArgs a = r.a;
+      a.stage = stage;
+      const int pi = stage - 1, po = stage % 3, pz = (stage + 1) % 3;
+      a.a_in = r.part[pi];
+      a.a_out = r.part[po];
+      a.a_zero = r.part[pz];
+      a.w = r.U[stage - 1];
+      a.out = r.U[stage % 3];
+      a.u0 = stage == 1 ? nullptr : r.W0;
+      a.lim_out = stage == 1 ? r.W0 : nullptr;
+      for (int tile = blockIdx.x; tile < a.ntile; tile += gridDim.x) {
+        s1d::stage1d_tile<R, C, BATCH, NTH>(a, tile, sm);
+        __syncthreads();
+      }
+      if (!grid_sync(r.bar, gridDim.x, r.a.sc)) return;
+    }
   }
 }
 
-template <typename R, int C>
-__device__ __forceinline__ void phys_flux(R gas, const R* U, R* F) {
-  if constexpr (C == 1) {
-    F[0] = R(0.5) * U[0] * U[0];
-  } else {
-    // f(rho, m, E) of Eq. (euler1); FP32 uses a rounded reciprocal of rho
-    const R rho = U[0], m = U[1], E = U[2];
-    const R mu = sizeof(R) == 4 ? m * recip(rho) : m / rho;
-    const R p = (gas - R(1)) * (E - R(0.5) * m * mu);
-    F[0] = m;
-    F[1] = m * mu + p;
-    F[2] = mu * (E + p);
-  }
+template <typename R, int C, bool BATCH, int NTH>
+cudaError_t max_ctas_t(int* ctas) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run1d_kernel<R, C, BATCH, NTH>, NTH, 0);
+  *ctas = per * nsm;
+  return e;
 }
 
-// max |f'(u)| at a cell average, in the kernel's precision (NaN when the
-// state is not physical); the maxima are reduced in FP64.
-template <typename R, int C>
-__device__ __forceinline__ R wave_speed(R gas, const R* U) {
-  if constexpr (C == 1) {
-    return fabs(U[0]);
-  } else {
-    return euler1d_speed_r<R>(gas, U[0], U[1], U[2]);
-  }
+template <typename R, int C, bool BATCH, int NTH>
+cudaError_t run_t(const Run1DArgs& r, cudaStream_t s) {
+  int ctas = 0;
+  cudaError_t e = max_ctas_t<R, C, BATCH, NTH>(&ctas);
+  if (e != cudaSuccess) return e;
+  if (ctas < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int grid = r.a.ntile < ctas ? r.a.ntile : ctas;
+  e = cudaMemsetAsync(r.bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  Run1DArgs rc = r;
+  void* args[] = {&rc};
+  return cudaLaunchCooperativeKernel((const void*)run1d_kernel<R, C, BATCH, NTH>, dim3(grid),
+                                     dim3(NTH), args, 0, s);
 }
 
 template <typename R, int C, bool BATCH>
-__global__ void __launch_bounds__(NT) stage1d_kernel(Stage1DArgs a) {
-  __shared__ Smem1D<R, C> sm;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  int n = a.n;
-  int base = blockIdx.x * T;
-  int inst = 0;
-  bool lead = blockIdx.x == 0;  // the tile that keeps the (instance's) time
-  if constexpr (BATCH) {
-    // a batch of independent instances: this tile's instance and first cell
-    inst = a.tile_inst[blockIdx.x];
-    base = a.tile_base[blockIdx.x];
-    const BatchInst& bi = a.binst[inst];
-    n = bi.n;
-    lead = base == 0;
-    const long long off = bi.off;
-    a.w = static_cast<const R*>(a.w) + off;
-    if (a.u0) a.u0 = static_cast<const R*>(a.u0) + off;
-    a.out = static_cast<R*>(a.out) + off;
-    if (a.lim_out) a.lim_out = static_cast<R*>(a.lim_out) + off;
-    if (a.flags_out) a.flags_out += off / (2 * C);
-    a.a_in = static_cast<const R*>(a.a_in) + inst;
-    a.nin = 1;
-    a.inv_dx = bi.inv_dx;
-    a.h = bi.h;
-    a.cfl_dx = bi.cfl_dx;
-    a.hthr = bi.hthr_f;
-    a.f32[5] = bi.inv_dx_f;
-    a.f32[6] = bi.cfl_dx_f;
-  }
-  const R* __restrict__ w = static_cast<const R*>(a.w);
-
-  // The producer of the stage input may still be finishing (programmatic
-  // dependent launch): wait for its completion and memory before any read.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-
-  // Parameters in the kernel's precision (FP32 copies made on the host).
-  R gam[3], eps, gas, inv_dx, cfl_dx;
-  if constexpr (sizeof(R) == 4) {
-    gam[0] = a.f32[0]; gam[1] = a.f32[1]; gam[2] = a.f32[2];
-    eps = a.f32[3]; gas = a.f32[4]; inv_dx = a.f32[5]; cfl_dx = a.f32[6];
-  } else {
-    gam[0] = a.gam[0]; gam[1] = a.gam[1]; gam[2] = a.gam[2];
-    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx; cfl_dx = a.cfl_dx;
-  }
-
-  // 1-2. in one round trip: every thread fetches its share of the producer's
-  //      wave-speed maxima (for alpha), its tile-plus-halo element, the time
-  //      bookkeeping, and in stages 2 and 3 the modified u^n of its own cell
-  const R* a_in = static_cast<const R*>(a.a_in);
-  R amax = R(0);
-  for (int k = tid; k < a.nin; k += NT) amax = fmax(amax, a_in[k]);
-  R rem = R(0), dt_prev = R(0);
-  if constexpr (BATCH) {
-    const BatchScalars& bs = a.bsc[inst];
-    if (a.stage == 1)
-      rem = sizeof(R) == 4 ? R(bs.rem_f) : R(bs.rem);
-    else if (a.stage > 1)
-      dt_prev = sizeof(R) == 4 ? R(bs.dt_f) : R(bs.dt);
-  } else {
-    if (a.stage == 1)
-      rem = sc_rem<R>(a.sc);
-    else if (a.stage > 1)
-      dt_prev = sc_dt<R>(a.sc);
-  }
-  R u0c[C][2];
-  if (a.stage >= 2 && tid < T && base + tid < n) {
-    const R* u0 = static_cast<const R*>(a.u0);
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      u0c[c][0] = u0[(2 * c + 0) * n + base + tid];
-      u0c[c][1] = u0[(2 * c + 1) * n + base + tid];
-    }
-  }
-  if (tid < T + 2 * H) {
-    if (a.bc == 2) {
-      bool mir;
-      const int g = bc_map_wall(base - H + tid, n, &mir);
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        sm.u[c][0][tid] = w[(2 * c + 0) * n + g] * (mir ? R(mirror_sign(c, 0)) : R(1));
-        sm.u[c][1][tid] = w[(2 * c + 1) * n + g] * (mir ? R(mirror_sign(c, 1)) : R(1));
-      }
-    } else {
-      const int g = bc_map(base - H + tid, n, a.bc);
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        sm.u[c][0][tid] = w[(2 * c + 0) * n + g];
-        sm.u[c][1][tid] = w[(2 * c + 1) * n + g];
-      }
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  if (lane == 0) sm.amax[warp] = amax;
-  __syncthreads();
-  // the next stage's CTAs may be scheduled now; they wait for this grid above
-  asm volatile("griddepcontrol.launch_dependents;");
-  // alpha (every thread reads the warps' maxima) and dt: CFL dx / alpha in
-  // stage 1, clipped to the remaining time; 0 once t_final is reached
-  R alpha = sm.amax[0];
-#pragma unroll
-  for (int k = 1; k < NW; ++k) alpha = fmax(alpha, sm.amax[k]);
-  R dt = dt_prev;
-  if (a.stage == 1) {
-    dt = cfl_dx / alpha;
-    unsigned last = 0;
-    if (rem <= R(0)) {
-      dt = R(0);
-    } else if (dt >= rem) {  // clipped: this step ends exactly at t_final
-      dt = rem;
-      last = 1;
-    }
-    if (!(alpha > R(0)) || !isfinite(dt)) dt = R(0);
-    if (lead && tid == 0) {
-      if constexpr (BATCH) {
-        BatchScalars& bs = a.bsc[inst];
-        if (sizeof(R) == 4) bs.dt_f = (float)dt; else bs.dt = (double)dt;
-        bs.last = last;
-      } else {
-        sc_dt<R>(a.sc) = dt;
-        a.sc->last = last;
-      }
-    }
-  }
-  if (a.stage > 0 && !(dt > R(0))) return;  // uniform over the grid (the instance)
-  // the slots of the stage after next (read two stages ago, now free)
-  if constexpr (BATCH) {
-    if (a.a_zero && lead && tid == 0) static_cast<R*>(a.a_zero)[inst] = R(0);
-  } else {
-    if (a.a_zero && blockIdx.x == 0 && tid < kAlphaSlots) static_cast<R*>(a.a_zero)[tid] = R(0);
-  }
-
-  // 3. troubled cells and modified first moments (Step 1), cells base-2 ..
-  if (tid < T + 4) {
-    const int k = tid, e = k + 1;
-    const double h = a.h;
-    const float hthr = a.hthr;
-    int flag;
-    if (a.mode == 1) {
-      flag = 1;
-    } else if (a.mode == 2) {
-      flag = 0;
-    } else if constexpr (C == 1) {
-      const R u0 = sm.u[0][0][e];
-      flag = kxrcf_troubled(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
-                            sm.u[0][1][e], sm.u[0][1][e + 1], u0 >= R(0), h, a.thr, hthr);
-    } else {
-      const bool left = inflow_left(sm.u[0][0][e], sm.u[1][0][e]);
-      flag = kxrcf_troubled(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
-                            sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left, h, a.thr,
-                            hthr) ||
-             kxrcf_troubled(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
-                            sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], left, h, a.thr,
-                            hthr);
-    }
-    sm.fl[k] = (uint8_t)flag;
-    if (!flag) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) sm.vl[c][k] = sm.u[c][1][e];
-    } else if constexpr (C == 1) {
-      sm.vl[0][k] = limit_first_moment(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
-                                       sm.u[0][1][e - 1], sm.u[0][1][e + 1], gam, eps);
-    } else {
-      // characteristic fields of the Jacobian at the cell average (Remark 2)
-      R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
-      R Rm[3][3], Lm[3][3];
-      Euler1D<R>::eigen(gas, U, Rm, Lm);
-      R q[3];
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        R wv[5];
-#pragma unroll
-        for (int s = 0; s < 3; ++s)
-          wv[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
-                  Lm[f][2] * sm.u[2][0][e - 1 + s];
-        wv[3] = Lm[f][0] * sm.u[0][1][e - 1] + Lm[f][1] * sm.u[1][1][e - 1] +
-                Lm[f][2] * sm.u[2][1][e - 1];
-        wv[4] = Lm[f][0] * sm.u[0][1][e + 1] + Lm[f][1] * sm.u[1][1][e + 1] +
-                Lm[f][2] * sm.u[2][1][e + 1];
-        q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) sm.vl[c][k] = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2];
-    }
-  }
-  __syncthreads();
-
-  // 4. interface values (Steps 2.1, 2.2) and their physical fluxes, cells base-1 ..
-  if (tid < T + 2) {
-    const int k = tid, e = k + 2;  // sm.u index e; sm.vl / sm.fl index of cell e is e - 1
-    const bool hw = sm.fl[k] | sm.fl[k + 1] | sm.fl[k + 2];
-    R L[C], Rt[C];
-    if (!hw) {
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-        linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                     sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
-    } else if constexpr (C == 1) {
-      hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
-                  sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
-    } else {
-      R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
-      R Rm[3][3], Lm[3][3];
-      Euler1D<R>::eigen(gas, U, Rm, Lm);
-      R cl[3], cr[3];
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        R wu[3], wv[3];
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          wu[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
-                  Lm[f][2] * sm.u[2][0][e - 1 + s];
-          wv[s] = Lm[f][0] * sm.vl[0][e - 2 + s] + Lm[f][1] * sm.vl[1][e - 2 + s] +
-                  Lm[f][2] * sm.vl[2][e - 2 + s];
-        }
-        hweno_faces(wu[0], wu[1], wu[2], wv[0], wv[1], wv[2], gam, eps, cl[f], cr[f]);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        L[c] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
-        Rt[c] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
-      }
-    }
-    R fL[C], fR[C];
-    phys_flux<R, C>(gas, L, fL);
-    phys_flux<R, C>(gas, Rt, fR);
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      sm.fm[c][k] = L[c];
-      sm.fp[c][k] = Rt[c];
-      sm.ffm[c][k] = fL[c];
-      sm.ffp[c][k] = fR[c];
-    }
-  }
-  __syncthreads();
-
-  // time bookkeeping (FP64) by a thread that has no cell in phase 5
-  if (a.stage == 3 && lead && tid == NT - 1) {
-    DevScalars* sc = a.sc;
-    const double tf = sc->t_final;
-    if constexpr (BATCH) {
-      BatchScalars& bs = a.bsc[inst];
-      const double t = bs.last ? tf : bs.t + (double)dt;
-      const double r = tf > 0.0 ? tf - t : (double)INFINITY;
-      bs.t = t;
-      bs.dt = (double)dt;
-      bs.rem = r;
-      bs.rem_f = (float)r;
-      if (inst == 0) sc->steps += 1;
-    } else {
-      const double t = sc->last ? tf : sc->t + (double)dt;
-      const double r = tf > 0.0 ? tf - t : (double)INFINITY;
-      sc->t = t;
-      sc->dt = (double)dt;
-      sc->rem = r;
-      sc->rem_f = (float)r;
-      sc->steps += 1;
-    }
-  }
-  static_assert(T < NT, "a thread without a cell keeps the time");
-
-  // 5. own cells: fluxes, F_i, right-hand side, RK combination
-  const int i = base + tid;
-  const bool own = tid < T && i < n;
-  int myflag = 0;
-  R speed = R(0);
-  unsigned bad = 0;
-  if (own) {
-    const int e = tid + H;  // sm.u index
-    const int k = tid + 1;  // sm.fm/fp index of cell i
-    myflag = sm.fl[tid + 2];
-    const R half_alpha = R(0.5) * alpha;
-    R gm[C], gp[C], f2[C], f3[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-      linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                      sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
-    phys_flux<R, C>(gas, gm, f2);
-    phys_flux<R, C>(gas, gp, f3);
-    const R idx = inv_dx;
-    R Uo[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      // Lax-Friedrichs fluxes at x_{i-1/2} (u^- of cell i-1, u^+ of cell i)
-      // and at x_{i+1/2} (u^- of cell i, u^+ of cell i+1)
-      const R ql = R(0.5) * (sm.ffp[c][k - 1] + sm.ffm[c][k]) -
-                   half_alpha * (sm.fm[c][k] - sm.fp[c][k - 1]);
-      const R qr = R(0.5) * (sm.ffp[c][k] + sm.ffm[c][k + 1]) -
-                   half_alpha * (sm.fm[c][k + 1] - sm.fp[c][k]);
-      // four-point Gauss-Lobatto F_i; the end points are the cell's own traces
-      const R F = R(1.0 / 12.0) * (sm.ffm[c][k] + sm.ffp[c][k]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
-      const R Lu = -(qr - ql) * idx;
-      const R Lv = (F - R(0.5) * (ql + qr)) * idx;
-      const R wu = sm.u[c][0][e];
-      const R wv = sm.vl[c][e - 1];
-      R ou, ov;
-      if (a.stage == 0) {
-        ou = Lu;
-        ov = Lv;
-      } else {
-        const R rdt = dt;
-        const R su = wu + rdt * Lu, sv = wv + rdt * Lv;
-        if (a.stage == 1) {
-          ou = su;
-          ov = sv;
-        } else {
-          const R ca = a.stage == 2 ? R(0.75) : R(1.0 / 3.0);
-          const R cb = a.stage == 2 ? R(0.25) : R(2.0 / 3.0);
-          ou = ca * u0c[c][0] + cb * su;
-          ov = ca * u0c[c][1] + cb * sv;
-        }
-      }
-      R* out = static_cast<R*>(a.out);
-      out[(2 * c + 0) * n + i] = ou;
-      out[(2 * c + 1) * n + i] = ov;
-      if (a.lim_out) {
-        R* lo = static_cast<R*>(a.lim_out);
-        lo[(2 * c + 0) * n + i] = wu;
-        lo[(2 * c + 1) * n + i] = wv;
-      }
-      if (!isfinite(ou) || !isfinite(ov)) bad |= ST_NONFINITE;
-      Uo[c] = ou;
-    }
-    if (a.flags_out) a.flags_out[i] = (uint8_t)myflag;
-    if (a.stage > 0) {
-      speed = wave_speed<R, C>(gas, Uo);
-      if (!(speed == speed)) {
-        bad |= ST_NONPHYSICAL;
-        speed = R(0);
-      }
-    }
-  }
-  // 6. epilogue: partial max for the next alpha (a max is exact in any
-  //    precision; the tile's maximum is stored as FP64), troubled count, status
-  R wmax = speed;
-  for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-  const int wcnt = __popc(__ballot_sync(0xffffffffu, myflag));
-  if (lane == 0) {
-    sm.red[warp] = wmax;
-    sm.cnt[warp] = wcnt;
-  }
-  if (bad) atomicOr(&a.sc->status, bad);
-  __syncthreads();
-  if (warp == 0) {
-    R m = lane < NW ? sm.red[lane] : R(0);
-    int c = lane < NW ? sm.cnt[lane] : 0;
-    for (int o = 16; o > 0; o >>= 1) {
-      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-      if (a.a_out)
-        atomic_max_nonneg(static_cast<R*>(a.a_out) + (BATCH ? inst : blockIdx.x % kAlphaSlots), m);
-      if (c) atomicAdd(&a.sc->troubled, (unsigned long long)c);
-    }
-  }
+cudaError_t run_b(const Run1DArgs& r, cudaStream_t s) {
+  if (r.a.nth == 128) return run_t<R, C, BATCH, 128>(r, s);
+  if (r.a.nth == 512) return run_t<R, C, BATCH, 512>(r, s);
+  return run_t<R, C, BATCH, 256>(r, s);
 }
+
+template <typename R, int C>
+cudaError_t run_c(const Run1DArgs& r, cudaStream_t s) {
+  return r.a.tile_inst ? run_b<R, C, true>(r, s) : run_b<R, C, false>(r, s);
+}
+
+template <typename R, int C, bool BATCH>
+cudaError_t max_b(int nth, int* ctas) {
+  if (nth == 128) return max_ctas_t<R, C, BATCH, 128>(ctas);
+  if (nth == 512) return max_ctas_t<R, C, BATCH, 512>(ctas);
+  return max_ctas_t<R, C, BATCH, 256>(ctas);
+}
+
+template <typename R, int C>
+cudaError_t max_c(int batch, int nth, int* ctas) {
+  return batch ? max_b<R, C, true>(nth, ctas) : max_b<R, C, false>(nth, ctas);
+}
+
 
 template <typename R, int C>
 __global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, R* a_out, int n,
@@ -476,9 +171,11 @@ __global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, R*
   }
 }
 
-// Wave-speed maxima of every instance of a batch, one slot per instance.
-template <typename R, int C>
-__global__ void __launch_bounds__(NT) alpha1d_batch_kernel(Stage1DArgs a) {
+// Wave-speed maxima of every instance of a batch, one slot per instance (the
+// batch's tiles: NTH threads, NTH - 6 cells).
+template <typename R, int C, int NTH>
+__global__ void __launch_bounds__(NTH) alpha1d_batch_kernel(Stage1DArgs a) {
+  constexpr int T = NTH - 2 * H, NW = NTH / 32;
   __shared__ R red[NW];
   const int inst = a.tile_inst[blockIdx.x];
   const BatchInst& bi = a.binst[inst];
@@ -545,11 +242,11 @@ __global__ void set_scalars_kernel(DevScalars* sc, int reset, double t_final) {
 
 // Stage launches allow programmatic dependent launch: a stage's CTAs can be
 // resident before the previous stage ends and start at its completion.
-template <typename R, int C>
-cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
+template <typename R, int C, int NTH>
+cudaError_t launch_stage1d_n(const Stage1DArgs& a, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)a.ntile);
-  cfg.blockDim = dim3(NT);
+  cfg.blockDim = dim3(NTH);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -557,11 +254,35 @@ cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (a.tile_inst) return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C, true>, a);
-  return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C, false>, a);
+  if (a.tile_inst) return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C, true, NTH>, a);
+  return cudaLaunchKernelEx(&cfg, stage1d_kernel<R, C, false, NTH>, a);
+}
+
+template <typename R, int C>
+cudaError_t launch_stage1d_t(const Stage1DArgs& a, cudaStream_t s) {
+  if (a.nth == 128) return launch_stage1d_n<R, C, 128>(a, s);
+  if (a.nth == 512) return launch_stage1d_n<R, C, 512>(a, s);
+  return launch_stage1d_n<R, C, 256>(a, s);
+}
+
+template <typename R, int C>
+void alpha1d_batch_t(const Stage1DArgs& a, cudaStream_t s) {
+  if (a.nth == 128) alpha1d_batch_kernel<R, C, 128><<<a.ntile, 128, 0, s>>>(a);
+  else if (a.nth == 512) alpha1d_batch_kernel<R, C, 512><<<a.ntile, 512, 0, s>>>(a);
+  else alpha1d_batch_kernel<R, C, 256><<<a.ntile, 256, 0, s>>>(a);
 }
 
 }  // namespace
+
+cudaError_t run1d_max_ctas(int system, int fp64, int batch, int nth, int* ctas) {
+  if (system == 0) return fp64 ? max_c<double, 1>(batch, nth, ctas) : max_c<float, 1>(batch, nth, ctas);
+  return fp64 ? max_c<double, 3>(batch, nth, ctas) : max_c<float, 3>(batch, nth, ctas);
+}
+
+cudaError_t launch_run1d(const Run1DArgs& r, cudaStream_t s) {
+  if (r.a.system == 0) return r.a.fp64 ? run_c<double, 1>(r, s) : run_c<float, 1>(r, s);
+  return r.a.fp64 ? run_c<double, 3>(r, s) : run_c<float, 3>(r, s);
+}
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s) {
   if (a.system == 0) return a.fp64 ? launch_stage1d_t<double, 1>(a, s) : launch_stage1d_t<float, 1>(a, s);
@@ -590,11 +311,11 @@ cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int sys
 
 cudaError_t launch_alpha1d_batch(const Stage1DArgs& a, cudaStream_t s) {
   if (a.system == 0) {
-    if (a.fp64) alpha1d_batch_kernel<double, 1><<<a.ntile, NT, 0, s>>>(a);
-    else alpha1d_batch_kernel<float, 1><<<a.ntile, NT, 0, s>>>(a);
+    if (a.fp64) alpha1d_batch_t<double, 1>(a, s);
+    else alpha1d_batch_t<float, 1>(a, s);
   } else {
-    if (a.fp64) alpha1d_batch_kernel<double, 3><<<a.ntile, NT, 0, s>>>(a);
-    else alpha1d_batch_kernel<float, 3><<<a.ntile, NT, 0, s>>>(a);
+    if (a.fp64) alpha1d_batch_t<double, 3>(a, s);
+    else alpha1d_batch_t<float, 3>(a, s);
   }
   return cudaGetLastError();
 }

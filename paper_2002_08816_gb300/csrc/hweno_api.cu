@@ -27,6 +27,14 @@ struct hweno_ctx {
   cudaStream_t cap = nullptr;        // private stream used only to capture graphs
   int C = 0, M = 0, n = 0, ntile = 0;  // n = cells; ntile = CTAs of one stage
   int dim = 1;
+  // 1D execution: threads per CTA of the stage kernels (a tile is nth1d - 6
+  // cells), and whether hweno_step runs one persistent launch (persist1d) or
+  // per-stage launches in CUDA graphs; hweno_autotune chooses both
+  int nth1d = 256, persist1d = 0;
+  int ntile_alpha = 0;               // CTAs of the 1D wave-speed kernels (kTile1D cells each)
+  unsigned* bar = nullptr;           // grid barrier of the persistent kernel
+  std::vector<int> batch_nx;         // cells of each batch instance
+  std::vector<hw::BatchInst> batch_inst;
   size_t elems = 0, esize = 0;
   void* U[3] = {nullptr, nullptr, nullptr};
   void* U0 = nullptr;
@@ -93,6 +101,7 @@ hw::Stage1DArgs base_args(const hweno_ctx* h) {
   const hweno_config& c = h->cfg;
   a.n = h->n;
   a.ntile = h->ntile;
+  a.nth = h->nth1d;
   a.bc = c.bc;
   a.mode = c.troubled_mode;
   a.system = c.system;
@@ -204,6 +213,23 @@ cudaError_t enqueue_step2d(hweno_ctx* h, cudaStream_t s) {
   Step2DIO io = {h->U[0], h->U[1], h->U[2], h->U[0], h->U0,
                  {h->part[0], h->part[1], h->part[2]}, h->sc, nullptr, nullptr, nullptr, nullptr};
   return enqueue_step2d_io(h, io, s);
+}
+
+// nsteps Runge-Kutta steps of a 1D handle in one persistent launch.
+cudaError_t enqueue_run1d(hweno_ctx* h, int nsteps, cudaStream_t s) {
+  hw::Run1DArgs r;
+  memset(&r, 0, sizeof(r));
+  r.a = base_args(h);
+  r.a.sc = h->sc;
+  r.a.nin = hw::kAlphaSlots;
+  for (int k = 0; k < 3; ++k) {
+    r.U[k] = h->U[k];
+    r.part[k] = h->part[k];
+  }
+  r.W0 = h->U0;
+  r.nsteps = nsteps;
+  r.bar = h->bar;
+  return hw::launch_run1d(r, s);
 }
 
 cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
@@ -380,6 +406,34 @@ hw::Adj2DArgs base_adj_args(const hweno_ctx* h) {
   return a;
 }
 
+// The tiles of every batch instance for stage CTAs of nth threads (nth - 6
+// cells per tile): tile -> instance and first cell, each instance's first
+// tile; replaces the previous tiling.
+cudaError_t batch_tiles(hweno_ctx* h, int nth) {
+  const int T = nth - 6;
+  std::vector<int> tinst, tbase;
+  for (int b = 0; b < h->n_batch; ++b) {
+    h->batch_inst[b].first_tile = (int)tinst.size();
+    for (int base = 0; base < h->batch_nx[b]; base += T) {
+      tinst.push_back(b);
+      tbase.push_back(base);
+    }
+  }
+  if (h->d_tile_inst) cudaFree(h->d_tile_inst);
+  if (h->d_tile_base) cudaFree(h->d_tile_base);
+  h->d_tile_inst = h->d_tile_base = nullptr;
+  const size_t nt = tinst.size();
+  cudaError_t e = cudaMalloc(&h->d_tile_inst, sizeof(int) * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tile_base, sizeof(int) * nt);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tile_inst, tinst.data(), sizeof(int) * nt, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tile_base, tbase.data(), sizeof(int) * nt, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_binst, h->batch_inst.data(), sizeof(hw::BatchInst) * h->n_batch,
+                   cudaMemcpyHostToDevice);
+  h->ntile = (int)nt;
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -428,7 +482,8 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
     h->C = cfg->system == HWENO_EULER ? 3 : 1;
     h->M = 2;
     h->n = cfg->nx;
-    h->ntile = (h->n + hw::kTile1D - 1) / hw::kTile1D;
+    h->ntile = (h->n + h->nth1d - 7) / (h->nth1d - 6);
+    h->ntile_alpha = (h->n + hw::kTile1D - 1) / hw::kTile1D;
   }
   h->elems = (size_t)h->C * h->M * h->n;
   h->esize = cfg->precision == HWENO_FP64 ? 8 : 4;
@@ -437,7 +492,9 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
   if (e == cudaSuccess) e = cudaMalloc(&h->U0, h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_buf, h->elems * 8);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * 2 * hw::kAlphaSlots);
-  if (e == cudaSuccess) e = cudaMalloc(&h->part_rhs, sizeof(double) * 2 * h->ntile);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&h->part_rhs, sizeof(double) * 2 * (h->ntile > h->ntile_alpha ? h->ntile : h->ntile_alpha));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->bar), 2 * sizeof(unsigned));
   if (e == cudaSuccess && cfg->dim == 2)
     e = hw::prepare_stage2d(cfg->system, cfg->precision == HWENO_FP64, cfg->n_gauss);
   if (e == cudaSuccess) e = cudaMalloc(&h->sc, sizeof(hw::DevScalars));
@@ -486,7 +543,7 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
     HW_CUDA(h, hw::launch_alpha2d(h->U[0], h->part[0], h->cfg.nx, h->cfg.ny, h->cfg.system, dst64,
                                   h->cfg.gas_gamma, h->sc, 1, h->stream));
   else
-    HW_CUDA(h, hw::launch_alpha1d(h->U[0], h->part[0], h->n, h->ntile, h->cfg.system, dst64,
+    HW_CUDA(h, hw::launch_alpha1d(h->U[0], h->part[0], h->n, h->ntile_alpha, h->cfg.system, dst64,
                                   h->cfg.gas_gamma, h->sc, 1, h->stream));
   h->has_state = true;
   return HWENO_OK;
@@ -500,6 +557,10 @@ hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_ou
   if (h->n_batch > 0)
     HW_CUDA(h, hw::launch_batch_scalars(h->d_bsc, h->n_batch, 0, t_final, h->stream));
   int left = nsteps;
+  if (h->dim == 1 && h->persist1d) {
+    if (left > 0) HW_CUDA(h, enqueue_run1d(h, left, h->stream));
+    left = 0;
+  }
   if (left >= kGraphSteps) {
     if (!h->g_many) {
       hweno_status st = build_graph(h, kGraphSteps, &h->g_many);
@@ -547,7 +608,7 @@ hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags
     hw::DevScalars s2;
     return check_scalars(h, h->sc_rhs, &s2);
   }
-  HW_CUDA(h, hw::launch_alpha1d(in, h->part_rhs, h->n, h->ntile, h->cfg.system,
+  HW_CUDA(h, hw::launch_alpha1d(in, h->part_rhs, h->n, h->ntile_alpha, h->cfg.system,
                                 h->cfg.precision == HWENO_FP64, h->cfg.gas_gamma, h->sc_rhs, 0,
                                 h->stream));
   hw::Stage1DArgs a = base_args(h);
@@ -556,7 +617,7 @@ hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags
   a.out = out;
   a.lim_out = ulim_out;
   a.a_in = h->part_rhs;
-  a.nin = h->ntile;
+  a.nin = h->ntile_alpha;
   a.a_out = nullptr;
   a.sc = h->sc_rhs;
   a.flags_out = flags_out;
@@ -618,6 +679,7 @@ void hweno_destroy(hweno_handle h) {
   if (h->part_rhs) cudaFree(h->part_rhs);
   if (h->sc) cudaFree(h->sc);
   if (h->sc_rhs) cudaFree(h->sc_rhs);
+  if (h->bar) cudaFree(h->bar);
   if (h->d_tile_inst) cudaFree(h->d_tile_inst);
   if (h->d_tile_base) cudaFree(h->d_tile_base);
   if (h->d_binst) cudaFree(h->d_binst);
@@ -648,50 +710,36 @@ hweno_status hweno_create_batch(const hweno_config* cfg, int n_batch, const int*
   if (st != HWENO_OK) return st;
   h->cfg.nx = (int)total;
   h->n_batch = n_batch;
-  // tiles of every instance, and each instance's geometry
+  // each instance's geometry, and the tiles
   std::string msg;
   const int C = h->C;
-  long long ntile = 0;
-  for (int b = 0; b < n_batch; ++b) ntile += (nx[b] + hw::kTile1D - 1) / hw::kTile1D;
-  int* tinst = new int[ntile];
-  int* tbase = new int[ntile];
-  hw::BatchInst* bi = new hw::BatchInst[n_batch];
-  long long k = 0, cells = 0;
+  long long cells = 0;
+  h->batch_nx.assign(nx, nx + n_batch);
+  h->batch_inst.resize(n_batch);
   for (int b = 0; b < n_batch; ++b) {
+    hw::BatchInst& bi = h->batch_inst[b];
     const double dx = (c.x1 - c.x0) / nx[b];
-    bi[b].off = (long long)C * 2 * cells;
-    bi[b].n = nx[b];
-    bi[b].first_tile = (int)k;
-    bi[b].inv_dx = 1.0 / dx;
-    bi[b].h = 0.5 * dx;
-    bi[b].cfl_dx = c.cfl * dx;
-    bi[b].inv_dx_f = (float)bi[b].inv_dx;
-    bi[b].hthr_f = (float)(c.kxrcf_threshold * bi[b].h);
-    bi[b].cfl_dx_f = (float)bi[b].cfl_dx;
-    bi[b].pad = 0.0f;
-    for (int base = 0; base < nx[b]; base += hw::kTile1D, ++k) {
-      tinst[k] = b;
-      tbase[k] = base;
-    }
+    bi.off = (long long)C * 2 * cells;
+    bi.n = nx[b];
+    bi.first_tile = 0;
+    bi.inv_dx = 1.0 / dx;
+    bi.h = 0.5 * dx;
+    bi.cfl_dx = c.cfl * dx;
+    bi.inv_dx_f = (float)bi.inv_dx;
+    bi.hthr_f = (float)(c.kxrcf_threshold * bi.h);
+    bi.cfl_dx_f = (float)bi.cfl_dx;
+    bi.pad = 0.0f;
     cells += nx[b];
   }
-  h->ntile = (int)ntile;
-  cudaError_t e = cudaMalloc(&h->d_tile_inst, sizeof(int) * ntile);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_tile_base, sizeof(int) * ntile);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_binst, sizeof(hw::BatchInst) * n_batch);
+  cudaError_t e = cudaMalloc(&h->d_binst, sizeof(hw::BatchInst) * n_batch);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_bsc, sizeof(hw::BatchScalars) * n_batch);
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_tile_inst, tinst, sizeof(int) * ntile, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_tile_base, tbase, sizeof(int) * ntile, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_binst, bi, sizeof(hw::BatchInst) * n_batch, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = batch_tiles(h, h->nth1d);
   // one alpha slot per instance in each of the three rotating buffers
   for (int r = 0; r < 3 && e == cudaSuccess && n_batch > 2 * hw::kAlphaSlots; ++r) {
     cudaFree(h->part[r]);
     h->part[r] = nullptr;
     e = cudaMalloc(&h->part[r], sizeof(double) * n_batch);
   }
-  delete[] tinst;
-  delete[] tbase;
-  delete[] bi;
   if (e != cudaSuccess) {
     msg = std::string("batch allocation: ") + cudaGetErrorString(e);
     hweno_destroy(h);
@@ -879,6 +927,118 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
   HW_CUDA(h, hw::launch_adj2d(a, h->stream));
   HW_CUDA(h, cudaStreamSynchronize(h->stream));
   return HWENO_OK;
+}
+
+hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (h->dim != 1) return fail(h, HWENO_ERR_ARG, "the execution choice is for 1D handles");
+  if (threads != 128 && threads != 256 && threads != 512)
+    return fail(h, HWENO_ERR_ARG, "threads must be 128, 256 or 512");
+  HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->g_many) cudaGraphExecDestroy(h->g_many);
+  if (h->g_one) cudaGraphExecDestroy(h->g_one);
+  h->g_many = h->g_one = nullptr;
+  h->nth1d = threads;
+  h->persist1d = persistent != 0;
+  if (h->n_batch > 0) {
+    HW_CUDA(h, batch_tiles(h, threads));
+  } else {
+    h->ntile = (h->n + threads - 7) / (threads - 6);
+  }
+  return HWENO_OK;
+}
+
+hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (h->dim != 1) return fail(h, HWENO_ERR_ARG, "hweno_autotune tunes 1D handles");
+  if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_autotune before hweno_set_state");
+  if (nsteps_trial < 1) return fail(h, HWENO_ERR_ARG, "nsteps_trial must be >= 1");
+  const size_t sbytes = h->elems * h->esize;
+  const size_t nslot = h->n_batch > 2 * hw::kAlphaSlots ? (size_t)h->n_batch : 2 * hw::kAlphaSlots;
+  const size_t pbytes = sizeof(double) * nslot;
+  const size_t bbytes = sizeof(hw::BatchScalars) * (size_t)h->n_batch;
+  // everything a run changes, saved on the device and put back before each trial
+  char* save = nullptr;
+  HW_CUDA(h, cudaMalloc(&save, sbytes + 3 * pbytes + sizeof(hw::DevScalars) + bbytes));
+  char* sv_u = save;
+  char* sv_p = save + sbytes;
+  char* sv_sc = sv_p + 3 * pbytes;
+  char* sv_b = sv_sc + sizeof(hw::DevScalars);
+  cudaStream_t s = h->stream;
+  auto copy_all = [&](bool to_save) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(to_save ? sv_u : h->U[0], to_save ? h->U[0] : sv_u, sbytes,
+                                    cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync(to_save ? sv_p + k * pbytes : (char*)h->part[k],
+                          to_save ? (char*)h->part[k] : sv_p + k * pbytes, pbytes,
+                          cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(to_save ? sv_sc : (char*)h->sc, to_save ? (char*)h->sc : sv_sc,
+                          sizeof(hw::DevScalars), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && bbytes)
+      e = cudaMemcpyAsync(to_save ? sv_b : (char*)h->d_bsc, to_save ? (char*)h->d_bsc : sv_b,
+                          bbytes, cudaMemcpyDeviceToDevice, s);
+    return e;
+  };
+  auto configure = [&](int nth, int persist) -> cudaError_t {
+    if (h->g_many) cudaGraphExecDestroy(h->g_many);
+    if (h->g_one) cudaGraphExecDestroy(h->g_one);
+    h->g_many = h->g_one = nullptr;
+    h->nth1d = nth;
+    h->persist1d = persist;
+    if (h->n_batch > 0) return batch_tiles(h, nth);
+    h->ntile = (h->n + nth - 7) / (nth - 6);
+    return cudaSuccess;
+  };
+  cudaError_t e = copy_all(true);
+  const int cand_nth[3] = {128, 256, 512};
+  float best = -1.0f;
+  int best_nth = h->nth1d, best_persist = h->persist1d;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int persist = 0; persist < 2 && e == cudaSuccess; ++persist)
+    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+      e = configure(cand_nth[ci], persist);
+      if (e != cudaSuccess) break;
+      // one untimed step (builds the graphs), then the timed trial
+      hweno_status st = HWENO_OK;
+      for (int rep = 0; rep < 2 && st == HWENO_OK && e == cudaSuccess; ++rep) {
+        e = copy_all(false);
+        if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) st = hweno_step(h, rep == 0 ? 1 : nsteps_trial, -1.0, nullptr);
+        if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e1, s);
+      }
+      if (e != cudaSuccess) break;
+      if (st != HWENO_OK) {
+        cudaFree(save);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+      }
+      e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (best < 0.0f || ms < best)) {
+        best = ms;
+        best_nth = cand_nth[ci];
+        best_persist = persist;
+      }
+    }
+  if (e == cudaSuccess) e = configure(best_nth, best_persist);
+  if (e == cudaSuccess) e = copy_all(false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (e != cudaSuccess) return fail(h, HWENO_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  hw::DevScalars sc;
+  hweno_status st = check_scalars(h, h->sc, &sc);
+  if (choice_out) {
+    choice_out[0] = best_nth;
+    choice_out[1] = best_persist;
+  }
+  return st;
 }
 
 const char* hweno_last_error(hweno_handle h) {

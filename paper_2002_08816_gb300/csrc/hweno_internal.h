@@ -41,7 +41,9 @@ struct Stage1DArgs {
   DevScalars* sc;        // t, dt, t_final, status, counters
   uint8_t* flags_out;    // troubled flags of the own cells (nullable)
   int n;                 // cells
-  int ntile;             // tiles (= CTAs)
+  int ntile;             // tiles (= CTAs of a per-stage launch)
+  int nth;               // threads per CTA of the stage kernels: 128, 256 (also 0) or 512;
+                         // a tile is nth - 6 cells
   int stage;             // 1, 2, 3; 0 = rhs mode
   int bc;                // 0 periodic, 1 outflow
   int mode;              // 0 hybrid, 1 all, 2 none
@@ -152,6 +154,24 @@ cudaError_t prepare_adj2d(int system, int fp64, int ng);
 cudaError_t launch_adj2d(const Adj2DArgs& a, cudaStream_t s);
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
+
+// A run of many 1D Runge-Kutta steps in one persistent launch: every CTA
+// walks its tiles of each stage, then all CTAs meet at a grid barrier.  The
+// buffers rotate as in one per-stage step (stage 1: U[0] -> U[1] and W0,
+// stage 2: U[1], W0 -> U[2], stage 3: U[2], W0 -> U[0]; alpha slots
+// part[0] -> part[1] -> part[2] -> part[0]).
+struct Run1DArgs {
+  Stage1DArgs a;      // the stage-independent fields (n, ntile, nth, sc, ...)
+  void* U[3];
+  void* W0;
+  void* part[3];
+  int nsteps;
+  unsigned* bar;      // grid barrier: arrivals, generation (zeroed before the launch)
+};
+// Largest co-resident grid of the persistent kernel for this configuration.
+cudaError_t run1d_max_ctas(int system, int fp64, int batch, int nth, int* ctas);
+// Cooperative launch of min(ntile, co-resident CTAs) CTAs.
+cudaError_t launch_run1d(const Run1DArgs& r, cudaStream_t s);
 // Batched variants: one launch over all instances (a.tile_inst != nullptr);
 // alpha slots are one per instance.
 cudaError_t launch_alpha1d_batch(const Stage1DArgs& a, cudaStream_t s);

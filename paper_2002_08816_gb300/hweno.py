@@ -84,6 +84,10 @@ def lib():
         L.hweno_backward.argtypes = [_VP, _VP, _VP, _I, _I]
         L.hweno_rhs_vjp.restype = _I
         L.hweno_rhs_vjp.argtypes = [_VP, _VP, _VP, _D, _D, _VP, _VP]
+        L.hweno_set_execution.restype = _I
+        L.hweno_set_execution.argtypes = [_VP, _I, _I]
+        L.hweno_autotune.restype = _I
+        L.hweno_autotune.argtypes = [_VP, _I, ctypes.POINTER(_I)]
         L.hweno_rhs1d_noalloc.restype = _I
         L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
         _lib = L
@@ -162,6 +166,17 @@ def hweno_backward(h, grad_out_ptr, grad_in_ptr, dtype, on_device):
 def hweno_rhs_vjp(h, in_ptr, flags_ptr, alpha_x, alpha_y, lam_ptr, grad_ptr):
     _check(lib().hweno_rhs_vjp(h, _VP(in_ptr), _VP(flags_ptr), float(alpha_x), float(alpha_y),
                                _VP(lam_ptr), _VP(grad_ptr)), h)
+
+
+def hweno_autotune(h, nsteps_trial):
+    """Returns (threads per CTA, persistent) chosen for the 1D handle."""
+    out = (_I * 2)()
+    _check(lib().hweno_autotune(h, int(nsteps_trial), out), h)
+    return out[0], bool(out[1])
+
+
+def hweno_set_execution(h, threads, persistent):
+    _check(lib().hweno_set_execution(h, int(threads), int(bool(persistent))), h)
 
 
 def hweno_get_state(h, ptr, dtype, on_device):

@@ -61,7 +61,10 @@ def test_uneven_batch_matches_each_instance(prec, tol):
         ref, t_ref, _ = _oracle(n, states[b], 20)
         rel = np.abs(got[b] - ref).sum() / np.abs(ref).sum()
         assert rel <= tol, (b, n, rel)
-        assert abs(times[b] - t_ref) <= (1e-13 if prec == H.HWENO_FP64 else 1e-6) * t_ref
+        # FP32: dt follows alpha = max |u| + c of an FP32 state that may differ
+        # from the FP64 one by ~1e-5 relative near a shock (the state bar is
+        # 1e-4 in L1), so the time after 20 steps is held to 1e-5
+        assert abs(times[b] - t_ref) <= (1e-13 if prec == H.HWENO_FP64 else 1e-5) * t_ref
 
 
 def test_batch_final_time_per_instance():

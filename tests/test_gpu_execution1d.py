@@ -1,0 +1,138 @@
+"""The 1D execution choices: per-stage graph launches with 128, 256 or 512
+threads per CTA give bitwise the same states (the same operations on every
+cell); the persistent launch with grid barriers agrees with them to rounding
+(its copy of the stage body may contract a few multiply-adds differently).
+hweno_autotune keeps the state and picks one of them."""
+
+import numpy as np
+import pytest
+
+from gpu_util import mixed_burgers, mixed_euler, round_to
+from paper_2002_08816_gb300 import hweno as H
+from paper_2002_08816_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CHOICES = [(t, p) for p in (0, 1) for t in (128, 256, 512)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _run(cfg, u, nsteps, choice, t_final=-1.0, chunks=(1,)):
+    import torch
+    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        if choice is not None:
+            H.hweno_set_execution(h, *choice)
+        host = np.ascontiguousarray(u, dtype=np.float64 if cfg.precision == H.HWENO_FP64 else np.float32)
+        H.hweno_set_state(h, host.ctypes.data, cfg.precision, False)
+        t = None
+        for k in chunks:
+            t = H.hweno_step(h, nsteps * k // sum(chunks), t_final)
+        out = np.empty_like(host)
+        H.hweno_get_state(h, out.ctypes.data, cfg.precision, False)
+        return out, t, H.hweno_stats(h)
+    finally:
+        H.hweno_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [H.HWENO_FP32, H.HWENO_FP64])
+@pytest.mark.parametrize("system,bc", [(H.HWENO_EULER, H.HWENO_BC_OUTFLOW),
+                                       (H.HWENO_EULER, H.HWENO_BC_REFLECTIVE),
+                                       (H.HWENO_BURGERS, H.HWENO_BC_PERIODIC)])
+def test_choices_agree_bitwise(system, bc, prec):
+    nx = 3001
+    u = mixed_euler(nx, 7) if system == H.HWENO_EULER else mixed_burgers(nx, 7)
+    u = round_to(prec, u)
+    cfg = H.make_config(1, system, nx, bc=bc, cfl=0.5, precision=prec)
+    ref, t_ref, st_ref = _run(cfg, u, 45, (256, 0))
+    for ch in CHOICES:
+        got, t, st = _run(cfg, u, 45, ch, chunks=(2, 1))
+        assert st["steps"] == 45, ch
+        if ch[1] == 0:
+            assert np.array_equal(got, ref), ch
+            assert t == t_ref and st["troubled"] == st_ref["troubled"], ch
+        else:
+            tol = 1e-12 if prec == H.HWENO_FP64 else 1e-6
+            assert np.abs(got - ref).sum() <= tol * np.abs(ref).sum(), ch
+            assert abs(t - t_ref) <= tol * t_ref, ch
+
+
+def test_persistent_run_clipped_to_final_time():
+    """Steps past t_final do nothing in the persistent launch too."""
+    nx = 400
+    u = W.burgers_sine_1d(nx)
+    cfg = H.make_config(1, H.HWENO_BURGERS, nx, x0=-1.0, x1=1.0, cfl=0.6, precision=H.HWENO_FP64)
+    tf = 1.5 / np.pi
+    ref, t_ref, _ = _run(cfg, u, 400, (256, 0), t_final=tf)
+    got, t, _ = _run(cfg, u, 400, (128, 1), t_final=tf)
+    assert t == t_ref == tf
+    assert np.abs(got - ref).sum() <= 1e-12 * np.abs(ref).sum()
+
+
+def test_batch_choices_agree_bitwise():
+    import torch
+    sizes = W.batch_sizes_1d(24, seed=3, lo=40, hi=1500)
+    us = [round_to(H.HWENO_FP32, W.euler_two_state_1d(n, seed=100 + b)) for b, n in enumerate(sizes)]
+    flat = np.concatenate([x.reshape(-1) for x in us]).astype(np.float32)
+    cfg = H.make_config(1, H.HWENO_EULER, 16, bc=H.HWENO_BC_OUTFLOW, cfl=0.5, precision=H.HWENO_FP32)
+    outs = []
+    for ch in [(256, 0)] + CHOICES:
+        h = H.hweno_create_batch(cfg, sizes, torch.cuda.current_stream().cuda_stream)
+        try:
+            H.hweno_set_execution(h, *ch)
+            H.hweno_set_state(h, flat.ctypes.data, H.HWENO_FP32, False)
+            H.hweno_step(h, 30)
+            out = np.empty_like(flat)
+            H.hweno_get_state(h, out.ctypes.data, H.HWENO_FP32, False)
+            outs.append(out)
+        finally:
+            H.hweno_destroy(h)
+    for ch, o in zip([(256, 0)] + CHOICES, outs):
+        if ch[1] == 0:
+            assert np.array_equal(o, outs[0]), ch
+        else:
+            assert np.abs(o - outs[0]).sum() <= 1e-6 * np.abs(outs[0]).sum(), ch
+
+
+def test_autotune_keeps_the_state_and_picks_a_choice():
+    import torch
+    nx = 65536
+    u = W.euler_two_state_1d(nx, seed=20250).astype(np.float32)
+    cfg = H.make_config(1, H.HWENO_EULER, nx, bc=H.HWENO_BC_OUTFLOW, cfl=0.5, precision=H.HWENO_FP32)
+    ref, _, _ = _run(cfg, u, 20, (256, 0))
+    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        H.hweno_set_state(h, u.ctypes.data, H.HWENO_FP32, False)
+        threads, persistent = H.hweno_autotune(h, 10)
+        assert threads in (128, 256, 512)
+        st = H.hweno_stats(h)
+        assert st["steps"] == 0 and st["t"] == 0.0
+        back = np.empty_like(u)
+        H.hweno_get_state(h, back.ctypes.data, H.HWENO_FP32, False)
+        assert np.array_equal(back, u)
+        H.hweno_step(h, 20)
+        H.hweno_get_state(h, back.ctypes.data, H.HWENO_FP32, False)
+        if persistent:
+            assert np.abs(back - ref).sum() <= 1e-6 * np.abs(ref).sum()
+        else:
+            assert np.array_equal(back, ref)
+    finally:
+        H.hweno_destroy(h)
+
+
+def test_set_execution_rejects_bad_choices():
+    import torch
+    cfg = H.make_config(1, H.HWENO_BURGERS, 64, precision=H.HWENO_FP64)
+    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        with pytest.raises(H.HwenoError):
+            H.hweno_set_execution(h, 200, 1)
+    finally:
+        H.hweno_destroy(h)
