@@ -44,6 +44,9 @@ typedef struct {
   double kxrcf_threshold; /* troubled iff indicator > threshold (1) */
   int troubled_mode;      /* HWO_TROUBLED_* */
   int limit_in_place;     /* 1: the RK combination uses the limited first moments */
+  int char_state;         /* 0: characteristic fields of the cell average (both
+                             interfaces); 1: of the mean of the two averages at
+                             each interface (the variant) */
 } hwo1d_cfg;
 
 typedef struct {
@@ -58,6 +61,7 @@ typedef struct {
   int troubled_mode;
   int limit_in_place;
   int n_gauss;            /* 3 (the paper) or 2 Gauss points per direction */
+  int char_state;         /* as in 1D: 1 = fields of each interface's mean state */
 } hwo2d_cfg;
 
 /* ---------------- 1D ---------------- */

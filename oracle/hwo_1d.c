@@ -317,6 +317,38 @@ int hwo1d_rhs(const hwo1d_cfg* cfg, const double* u, double alpha, double* rhs,
   return hwo1d_rhs_ex(cfg, u, alpha, rhs, ulim, flags, indicator, NULL);
 }
 
+/* Step 2.1 for the Euler cell at extended index e in the characteristic fields
+ * of the x-Jacobian at the state U: the interface values at x_{e-1/2} (pm) and
+ * x_{e+1/2} (pp). */
+static void char_faces1d(const hwo1d_cfg* cfg, const double* ub, const double* vl, int NE,
+                         int e, const double U[3], double pm[3], double pp[3]) {
+  double R[9], L[9];
+  hwo_euler1d_eigen(cfg->gas_gamma, U, R, L);
+  double Wu[3][3], Wv[3][3]; /* [field][cell] */
+  for (int k = 0; k < 3; ++k) {
+    double su[3], sv[3], wu[3], wv[3];
+    for (int c = 0; c < 3; ++c) {
+      su[c] = ub[c * NE + e - 1 + k];
+      sv[c] = vl[c * NE + e - 1 + k];
+    }
+    hwo_matvec(3, 3, L, su, wu);
+    hwo_matvec(3, 3, L, sv, wv);
+    for (int f = 0; f < 3; ++f) {
+      Wu[f][k] = wu[f];
+      Wv[f][k] = wv[f];
+    }
+  }
+  double cm[3], cp[3];
+  for (int f = 0; f < 3; ++f) {
+    double out[4];
+    hwo1d_recon_scalar(cfg->lin_w, cfg->eps, Wu[f], Wv[f], 1, out);
+    cm[f] = out[0];
+    cp[f] = out[1];
+  }
+  hwo_matvec(3, 3, R, cm, pm);
+  hwo_matvec(3, 3, R, cp, pp);
+}
+
 /* As hwo1d_rhs; faces (nullable, [C][2][nx]) receives u^+_{i-1/2}, u^-_{i+1/2}. */
 int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rhs,
                  double* ulim, unsigned char* flags, double* indicator,
@@ -423,35 +455,23 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
         gp[c * NE + e] = out[3];
       }
     } else {
-      /* Step 2.1 in characteristic fields for the interface values; Step 2.3
-       * component by component for the interior values. */
-      double R[9], L[9], U[3];
-      for (int c = 0; c < 3; ++c) U[c] = ub[c * NE + e];
-      hwo_euler1d_eigen(cfg->gas_gamma, U, R, L);
-      double Wu[3][3], Wv[3][3]; /* [field][cell] */
-      for (int k = 0; k < 3; ++k) {
-        double su[3], sv[3], wu[3], wv[3];
+      /* Step 2.1 in characteristic fields for the interface values (of the
+       * cell average, or with char_state of the mean state at each interface);
+       * Step 2.3 component by component for the interior values. */
+      double pm[3], pp[3], tmp[3];
+      if (!cfg->char_state) {
+        double U[3];
+        for (int c = 0; c < 3; ++c) U[c] = ub[c * NE + e];
+        char_faces1d(cfg, ub, vl, NE, e, U, pm, pp);
+      } else {
+        double Um[3], Up[3];
         for (int c = 0; c < 3; ++c) {
-          su[c] = ub[c * NE + e - 1 + k];
-          sv[c] = vl[c * NE + e - 1 + k];
+          Um[c] = 0.5 * (ub[c * NE + e - 1] + ub[c * NE + e]);
+          Up[c] = 0.5 * (ub[c * NE + e] + ub[c * NE + e + 1]);
         }
-        hwo_matvec(3, 3, L, su, wu);
-        hwo_matvec(3, 3, L, sv, wv);
-        for (int f = 0; f < 3; ++f) {
-          Wu[f][k] = wu[f];
-          Wv[f][k] = wv[f];
-        }
+        char_faces1d(cfg, ub, vl, NE, e, Um, pm, tmp);
+        char_faces1d(cfg, ub, vl, NE, e, Up, tmp, pp);
       }
-      double cm[3], cp[3];
-      for (int f = 0; f < 3; ++f) {
-        double out[4];
-        hwo1d_recon_scalar(cfg->lin_w, cfg->eps, Wu[f], Wv[f], 1, out);
-        cm[f] = out[0];
-        cp[f] = out[1];
-      }
-      double pm[3], pp[3];
-      hwo_matvec(3, 3, R, cm, pm);
-      hwo_matvec(3, 3, R, cp, pp);
       for (int c = 0; c < 3; ++c) {
         double u3[3] = {ub[c * NE + e - 1], ub[c * NE + e], ub[c * NE + e + 1]};
         double v3[3] = {vl[c * NE + e - 1], vl[c * NE + e], vl[c * NE + e + 1]};

@@ -584,10 +584,15 @@ int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
       }
       if (hw && euler) {
         /* Step 5.1 in characteristic fields: x-faces with the x-Jacobian,
-         * y-faces with the y-Jacobian, both at the cell average (Remark 4) */
-        for (int dir = 0; dir < 2; ++dir) {
+         * y-faces with the y-Jacobian, both at the cell average (Remark 4), or
+         * with char_state at the mean of the averages on the two sides of the
+         * face (one eigen-system per face) */
+        for (int dir = 0; dir < 2; ++dir)
+        for (int side = 0; side < 2; ++side) {
+          const int nb = dir == 0 ? (side == 0 ? 3 : 5) : (side == 0 ? 1 : 7);
           double R[16], L[16], U[4];
-          for (int c = 0; c < 4; ++c) U[c] = su[c][4];
+          for (int c = 0; c < 4; ++c)
+            U[c] = cfg->char_state ? 0.5 * (su[c][4] + su[c][nb]) : su[c][4];
           hwo_euler2d_eigen(cfg->gas_gamma, U, dir, R, L);
           double cu[4][9], cv[4][9], cw[4][9];
           for (int k = 0; k < 9; ++k) {
@@ -604,14 +609,14 @@ int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
             gather19(cu[f], cv[f], cw[f], d);
             candidates(d, ng, B4, B2, val, beta);
             tau_weights5(cfg->lin_w, cfg->eps, beta, om);
-            for (int p = 0; p < 2 * ng; ++p) {
+            for (int p = side * ng; p < (side + 1) * ng; ++p) {
               int pp = dir * 2 * ng + p;
               double v5[5];
               for (int n = 0; n < 5; ++n) v5[n] = val[n * np + pp];
               chv[f][p] = hwo_combine(5, cfg->lin_w, om, v5);
             }
           }
-          for (int p = 0; p < 2 * ng; ++p) {
+          for (int p = side * ng; p < (side + 1) * ng; ++p) {
             double wv[4], cv4[4];
             for (int f = 0; f < 4; ++f) wv[f] = chv[f][p];
             hwo_matvec(4, 4, R, wv, cv4);

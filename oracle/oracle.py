@@ -30,12 +30,13 @@ class Cfg1D(ctypes.Structure):
         ("system", _I), ("nx", _I), ("x0", _D), ("x1", _D), ("bc", _I),
         ("gas_gamma", _D), ("lin_w", _D * 3), ("eps", _D),
         ("kxrcf_threshold", _D), ("troubled_mode", _I), ("limit_in_place", _I),
+        ("char_state", _I),
     ]
 
     @classmethod
     def make(cls, system, nx, x0, x1, bc, lin_w=(0.98, 0.01, 0.01),
              gas_gamma=1.4, eps=1e-6, threshold=1.0,
-             troubled_mode=TROUBLED_HYBRID, limit_in_place=1):
+             troubled_mode=TROUBLED_HYBRID, limit_in_place=1, char_state=0):
         c = cls()
         c.system, c.nx, c.x0, c.x1, c.bc = system, nx, x0, x1, bc
         c.gas_gamma = gas_gamma
@@ -43,6 +44,7 @@ class Cfg1D(ctypes.Structure):
             c.lin_w[k] = lin_w[k]
         c.eps, c.kxrcf_threshold = eps, threshold
         c.troubled_mode, c.limit_in_place = troubled_mode, limit_in_place
+        c.char_state = char_state
         return c
 
     @property
@@ -55,14 +57,14 @@ class Cfg2D(ctypes.Structure):
         ("system", _I), ("nx", _I), ("ny", _I), ("x0", _D), ("x1", _D),
         ("y0", _D), ("y1", _D), ("bc", _I), ("gas_gamma", _D),
         ("lin_w", _D * 5), ("eps", _D), ("kxrcf_threshold", _D),
-        ("troubled_mode", _I), ("limit_in_place", _I), ("n_gauss", _I),
+        ("troubled_mode", _I), ("limit_in_place", _I), ("n_gauss", _I), ("char_state", _I),
     ]
 
     @classmethod
     def make(cls, system, nx, ny, x0, x1, y0, y1, bc,
              lin_w=(0.96, 0.01, 0.01, 0.01, 0.01), gas_gamma=1.4, eps=1e-6,
              threshold=1.0, troubled_mode=TROUBLED_HYBRID, limit_in_place=1,
-             n_gauss=3):
+             n_gauss=3, char_state=0):
         c = cls()
         c.system, c.nx, c.ny = system, nx, ny
         c.x0, c.x1, c.y0, c.y1, c.bc = x0, x1, y0, y1, bc
@@ -71,6 +73,7 @@ class Cfg2D(ctypes.Structure):
             c.lin_w[k] = lin_w[k]
         c.eps, c.kxrcf_threshold = eps, threshold
         c.troubled_mode, c.limit_in_place, c.n_gauss = troubled_mode, limit_in_place, n_gauss
+        c.char_state = char_state
         return c
 
     @property
