@@ -71,7 +71,16 @@ typedef struct {
   int troubled_mode;      /* HWENO_TROUBLED_HYBRID (the paper's scheme), _ALL, _NONE */
   int n_gauss;            /* 2D quadrature points per direction: 3 (paper) or 2 */
   int precision;          /* HWENO_FP32 or HWENO_FP64 bulk arithmetic */
+  int variant;            /* 0, or HWENO_VARIANT_* bits (readings the paper leaves open) */
 } hweno_config;
+
+/* Variants of two points the paper leaves open (0 = the readings used
+ * throughout: the modified first moments are stored in the state, and the
+ * characteristic fields are those of the cell average). */
+#define HWENO_VARIANT_RAW_COMBINE 1  /* the RK combination uses the unmodified first moments */
+#define HWENO_VARIANT_MEAN_EIGEN 2   /* Euler HWENO interface values in the characteristic
+                                        fields of the mean of the two averages at that
+                                        interface (one eigen-system per interface) */
 
 typedef struct hweno_ctx* hweno_handle;
 

@@ -31,6 +31,7 @@
 
 #include "hweno1d_recon.cuh"
 #include "hweno_device.cuh"
+#include "hweno.h"
 #include "hweno_internal.h"
 
 namespace hw {
@@ -92,6 +93,33 @@ __device__ __forceinline__ R wave_speed(R gas, const R* U) {
     return fabs(U[0]);
   } else {
     return euler1d_speed_r<R>(gas, U[0], U[1], U[2]);
+  }
+}
+
+// Step 2.1 for the Euler cell at sm.u index e in the characteristic fields of
+// the Jacobian at U: the interface values u^+_{i-1/2} (L) and u^-_{i+1/2} (Rt).
+template <typename S, typename R>
+__device__ __noinline__ void char_faces(const S& sm, int e, const R* U, const R* gam, R eps,
+                                        R gas, R* L, R* Rt) {
+  R Rm[3][3], Lm[3][3];
+  Euler1D<R>::eigen(gas, U, Rm, Lm);
+  R cl[3], cr[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    R wu[3], wv[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      wu[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
+              Lm[f][2] * sm.u[2][0][e - 1 + s];
+      wv[s] = Lm[f][0] * sm.vl[0][e - 2 + s] + Lm[f][1] * sm.vl[1][e - 2 + s] +
+              Lm[f][2] * sm.vl[2][e - 2 + s];
+    }
+    hweno_faces(wu[0], wu[1], wu[2], wv[0], wv[1], wv[2], gam, eps, cl[f], cr[f]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    L[c] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
+    Rt[c] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
   }
 }
 
@@ -300,28 +328,20 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
     } else if constexpr (C == 1) {
       hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
                   sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
-    } else {
+    } else if (!(a.variant & HWENO_VARIANT_MEAN_EIGEN)) {
+      // characteristic fields of the cell average, both interfaces (Remark 2)
       R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
-      R Rm[3][3], Lm[3][3];
-      Euler1D<R>::eigen(gas, U, Rm, Lm);
-      R cl[3], cr[3];
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        R wu[3], wv[3];
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          wu[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
-                  Lm[f][2] * sm.u[2][0][e - 1 + s];
-          wv[s] = Lm[f][0] * sm.vl[0][e - 2 + s] + Lm[f][1] * sm.vl[1][e - 2 + s] +
-                  Lm[f][2] * sm.vl[2][e - 2 + s];
-        }
-        hweno_faces(wu[0], wu[1], wu[2], wv[0], wv[1], wv[2], gam, eps, cl[f], cr[f]);
-      }
+      char_faces(sm, e, U, gam, eps, gas, L, Rt);
+    } else {
+      // variant: the fields of the mean of the two averages at each interface
+      R Um[3], Up[3], tmp[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        L[c] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
-        Rt[c] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
+        Um[c] = R(0.5) * (sm.u[c][0][e - 1] + sm.u[c][0][e]);
+        Up[c] = R(0.5) * (sm.u[c][0][e] + sm.u[c][0][e + 1]);
       }
+      char_faces(sm, e, Um, gam, eps, gas, L, tmp);
+      char_faces(sm, e, Up, gam, eps, gas, tmp, Rt);
     }
     R fL[C], fR[C];
     phys_flux<R, C>(gas, L, fL);
@@ -394,7 +414,10 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       const R Lu = -(qr - ql) * idx;
       const R Lv = (F - R(0.5) * (ql + qr)) * idx;
       const R wu = sm.u[c][0][e];
-      const R wv = sm.vl[c][e - 1];
+      // the stage input the combination uses: first moments as modified by
+      // Step 1 (stored, the default), or unmodified (variant)
+      const R wvm = sm.vl[c][e - 1];
+      const R wv = (a.variant & HWENO_VARIANT_RAW_COMBINE) ? sm.u[c][1][e] : wvm;
       R ou, ov;
       if (a.stage == 0) {
         ou = Lu;
@@ -418,7 +441,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       if (a.lim_out) {
         R* lo = static_cast<R*>(a.lim_out);
         lo[(2 * c + 0) * n + i] = wu;
-        lo[(2 * c + 1) * n + i] = wv;
+        lo[(2 * c + 1) * n + i] = a.stage == 0 ? wvm : wv;  // rhs mode: the modified moment
       }
       if (!isfinite(ou) || !isfinite(ov)) bad |= ST_NONFINITE;
       Uo[c] = ou;

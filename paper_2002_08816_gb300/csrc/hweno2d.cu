@@ -27,6 +27,7 @@
 #include "hweno1d_recon.cuh"
 #include "hweno2d_common.cuh"
 #include "hweno_device.cuh"
+#include "hweno.h"
 #include "hweno_internal.h"
 
 namespace hw {
@@ -127,16 +128,30 @@ __device__ __forceinline__ void store_point(S& sm, int c, int p, int ci, int cj,
 // characteristic fields of the cell average (Remark 4).  Rare: out of line.
 template <int NG, typename S, typename R>
 __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo, int p_hi,
-                                                 const R* gam, R eps, R gas) {
+                                                 const R* gam, R eps, R gas, bool mean_eigen) {
   constexpr int NF = 4 * NG;
-  R U[4];
+  R Uc[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][cj + 3][ci + 3];
+  for (int c = 0; c < 4; ++c) Uc[c] = sm.u[c][0][cj + 3][ci + 3];
+  // one eigen-system per direction (the cell average), or with mean_eigen one
+  // per face (the mean of the averages on its two sides): "parts" of the
+  // direction's 2 NG points
+  const int nparts = mean_eigen ? 2 : 1;
 #pragma unroll 1
-  for (int dir = 0; dir < 2; ++dir) {
-    const int lo = dir == 0 ? 0 : 2 * NG, hi = dir == 0 ? 2 * NG : 4 * NG;
+  for (int q = 0; q < 2 * nparts; ++q) {
+    const int dir = q / nparts, side = q % nparts;
+    const int lo = dir * 2 * NG + side * NG, hi = lo + 2 * NG / nparts;
     const int plo = p_lo > lo ? p_lo : lo, phi = p_hi < hi ? p_hi : hi;
     if (plo >= phi) continue;
+    R U[4];
+    if (!mean_eigen) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) U[c] = Uc[c];
+    } else {
+      const int dx = dir == 0 ? 2 * side - 1 : 0, dy = dir == 1 ? 2 * side - 1 : 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) U[c] = R(0.5) * (Uc[c] + sm.u[c][0][cj + 3 + dy][ci + 3 + dx]);
+    }
     R Rm[4][4], Lm[4][4];
     Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
     R acc[4][NF];
@@ -351,7 +366,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
           if (p >= p_lo && p < p_hi) store_point(sm, c, p, ci, cj, v[p]);
       }
     } else if constexpr (C == 4) {
-      hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam, eps, gas);
+      hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam, eps, gas,
+                              (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
     }
   }
   __syncthreads();
@@ -441,7 +457,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
       const R L0 = -sfx[c] * inv_dx - sgy[c] * inv_dy;
       const R L1 = -R(0.5) * sfs[c] * inv_dx + Fv[c] * inv_dx - sgyx[c] * inv_dy;
       const R L2 = -sfxe[c] * inv_dx - R(0.5) * sgs[c] * inv_dy + Gv[c] * inv_dy;
-      const R W[3] = {sm.u[c][0][cj + 3][ci + 3], sm.vl[c][cj + 2][ci + 2], sm.wl[c][cj + 2][ci + 2]};
+      // the stage input the combination uses: first moments as modified by
+      // Step 4 (stored, the default), or unmodified (variant)
+      const bool raw = (a.variant & HWENO_VARIANT_RAW_COMBINE) != 0;
+      const R W[3] = {sm.u[c][0][cj + 3][ci + 3],
+                      raw ? sm.u[c][1][cj + 3][ci + 3] : sm.vl[c][cj + 2][ci + 2],
+                      raw ? sm.u[c][2][cj + 3][ci + 3] : sm.wl[c][cj + 2][ci + 2]};
       const R Lm[3] = {L0, L1, L2};
       R o[3];
 #pragma unroll
@@ -464,10 +485,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
         const size_t s = (size_t)gj * nx + gi;
 #pragma unroll
         for (int m = 0; m < 3; ++m) out[(3 * c + m) * plane + s] = o[m];
-        if (a.lim_out) {
+        if (a.lim_out) {  // rhs mode: the modified moments; stage 1: what stages 2-3 combine
           R* lo = static_cast<R*>(a.lim_out);
+          const R M[3] = {W[0], sm.vl[c][cj + 2][ci + 2], sm.wl[c][cj + 2][ci + 2]};
 #pragma unroll
-          for (int m = 0; m < 3; ++m) lo[(3 * c + m) * plane + s] = W[m];
+          for (int m = 0; m < 3; ++m) lo[(3 * c + m) * plane + s] = a.stage == 0 ? M[m] : W[m];
         }
       }
       Uo[c] = o[0];

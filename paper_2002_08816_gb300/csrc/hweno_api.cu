@@ -106,6 +106,7 @@ hw::Stage1DArgs base_args(const hweno_ctx* h) {
   a.mode = c.troubled_mode;
   a.system = c.system;
   a.fp64 = c.precision == HWENO_FP64;
+  a.variant = c.variant;
   a.dx = (c.x1 - c.x0) / c.nx;
   a.cfl = c.cfl;
   a.eps = c.eps;
@@ -132,6 +133,7 @@ hw::Stage2DArgs base_args2d(const hweno_ctx* h) {
   a.mode = c.troubled_mode;
   a.system = c.system;
   a.fp64 = c.precision == HWENO_FP64;
+  a.variant = c.variant;
   a.ng = c.n_gauss;
   a.dx = (c.x1 - c.x0) / c.nx;
   a.dy = (c.y1 - c.y0) / c.ny;
@@ -321,6 +323,8 @@ hweno_status validate(const hweno_config* c) {
   if (c->troubled_mode < 0 || c->troubled_mode > 2) return fail(nullptr, HWENO_ERR_ARG, "unknown troubled_mode");
   if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64)
     return fail(nullptr, HWENO_ERR_ARG, "unknown precision");
+  if (c->variant & ~(HWENO_VARIANT_RAW_COMBINE | HWENO_VARIANT_MEAN_EIGEN))
+    return fail(nullptr, HWENO_ERR_ARG, "unknown variant bits");
   return HWENO_OK;
 }
 
@@ -366,6 +370,7 @@ hweno_status check_adjoint_config(hweno_ctx* h) {
   if (h->dim != 2) return fail(h, HWENO_ERR_ARG, "the adjoint is for 2D handles");
   if (h->n_batch > 0) return fail(h, HWENO_ERR_ARG, "the adjoint takes a single-instance handle");
   if (h->cfg.bc != HWENO_BC_PERIODIC) return fail(h, HWENO_ERR_ARG, "the adjoint needs periodic boundaries");
+  if (h->cfg.variant != 0) return fail(h, HWENO_ERR_ARG, "the adjoint is of the default variant");
   return HWENO_OK;
 }
 

@@ -49,6 +49,7 @@ struct Stage1DArgs {
   int mode;              // 0 hybrid, 1 all, 2 none
   int system;            // 0 Burgers, 1 Euler
   int fp64;              // 0 FP32, 1 FP64
+  int variant;           // HWENO_VARIANT_* bits
   double dx, cfl, eps, thr, gas;
   double gam[3];
   // derived on the host so that no thread spends FP64 work on them (on
@@ -108,6 +109,7 @@ struct Stage2DArgs {
   void* rec_dt;          // nullable: dt of the step (stage 1), kernel precision
   const void* dt_in;     // nullable: stage 1 takes this dt (replay of a recorded step)
   int nx, ny, stage, bc, mode, system, fp64, ng;
+  int variant;            // HWENO_VARIANT_* bits
   double dx, dy, cfl, eps, thr, gas;
   double gam[5];
   double inv_dx, inv_dy;  // derived

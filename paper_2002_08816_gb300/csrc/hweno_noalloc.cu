@@ -135,6 +135,7 @@ hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, con
     a.mode = cfg->troubled_mode;
     a.system = cfg->system;
     a.fp64 = fp64;
+    a.variant = cfg->variant;
     a.dx = (cfg->x1 - cfg->x0) / n;
     a.cfl = cfg->cfl;
     a.eps = cfg->eps;

@@ -18,6 +18,8 @@ HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL, HWENO_ERR_TIMEOU
 HWENO_NOALLOC_MAX_CELLS = 4194304
 HWENO_BURGERS, HWENO_EULER = 0, 1
 HWENO_BC_PERIODIC, HWENO_BC_OUTFLOW, HWENO_BC_REFLECTIVE = 0, 1, 2
+HWENO_VARIANT_RAW_COMBINE = 1  # the RK combination uses the unmodified first moments
+HWENO_VARIANT_MEAN_EIGEN = 2  # characteristic fields of each interface's mean state
 HWENO_TROUBLED_HYBRID, HWENO_TROUBLED_ALL, HWENO_TROUBLED_NONE = 0, 1, 2
 HWENO_FP32, HWENO_FP64 = 0, 1
 
@@ -35,6 +37,7 @@ class hweno_config(ctypes.Structure):
         ("x0", _D), ("x1", _D), ("y0", _D), ("y1", _D),
         ("bc", _I), ("gas_gamma", _D), ("lin_w", _D * 5), ("cfl", _D), ("eps", _D),
         ("kxrcf_threshold", _D), ("troubled_mode", _I), ("n_gauss", _I), ("precision", _I),
+        ("variant", _I),
     ]
 
 
@@ -202,12 +205,13 @@ def hweno_last_error(h=None):
 
 def make_config(dim, system, nx, ny=0, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=HWENO_BC_PERIODIC,
                 lin_w=None, cfl=0.6, precision=HWENO_FP32, troubled_mode=HWENO_TROUBLED_HYBRID,
-                gas_gamma=1.4, eps=1e-6, threshold=1.0, n_gauss=3):
+                gas_gamma=1.4, eps=1e-6, threshold=1.0, n_gauss=3, variant=0):
     cfg = hweno_default_config(dim, system)
     cfg.nx, cfg.ny = nx, ny
     cfg.x0, cfg.x1, cfg.y0, cfg.y1 = x0, x1, y0, y1
     cfg.bc, cfg.cfl, cfg.precision, cfg.troubled_mode = bc, cfl, precision, troubled_mode
     cfg.gas_gamma, cfg.eps, cfg.kxrcf_threshold, cfg.n_gauss = gas_gamma, eps, threshold, n_gauss
+    cfg.variant = variant
     if lin_w is not None:
         for k, v in enumerate(lin_w):
             cfg.lin_w[k] = v

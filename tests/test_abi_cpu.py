@@ -47,7 +47,7 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=3), dict(dim=3), dict(system=7), dict(bc=5), dict(cfl=0.0), dict(eps=-1.0),
-    dict(gas_gamma=1.0), dict(troubled_mode=9), dict(precision=4), dict(x1=0.0),
+    dict(gas_gamma=1.0), dict(troubled_mode=9), dict(precision=4), dict(x1=0.0), dict(variant=4),
 ])
 def test_invalid_configuration_is_rejected(lib, bad):
     h = ctypes.c_void_p()
