@@ -337,22 +337,23 @@ COEF_HDR = os.path.join(ROOT, "paper_2002_08816_gb300", "csrc", "hweno2d_coef.cu
 
 
 def flops_per_cell_stage_2d(ng, ncomp=4):
-    """FP32 operations of one smooth 2D Euler cell-stage, counted on the
-    operations the method needs (halo recomputation excluded): the linear p0
-    maps of the generated code (one FMA = 2 flops per nonzero coefficient) for
-    the 4 ng interface and ng^2 interior points of every component, the
-    Lax-Friedrichs flux of each of the cell's own 2 ng interface points (two
-    Euler fluxes of 15 flops and 16 for the combination), f and g at the
-    interior points (2 x 15 + 16), the right-hand-side sums (6 per quadrature
-    point and component plus 10) and the Runge-Kutta combination (4 per
-    moment)."""
+    """FP32 operations of one smooth 2D cell-stage, counted on the operations
+    the method needs (halo recomputation excluded): the linear p0 maps of the
+    generated code (one FMA = 2 flops per nonzero coefficient) for the 4 ng
+    interface and ng^2 interior points of every component, the Lax-Friedrichs
+    flux of each of the cell's own 2 ng interface points (Euler: two fluxes of
+    15 flops and 16 for the combination; Burgers: two u^2/2 and 4), f and g at
+    the interior points (Euler 2 x 15 + 16; Burgers 2 + 4), the right-hand-side
+    sums (6 per quadrature point and component plus 10) and the Runge-Kutta
+    combination (4 per moment)."""
     import re
     txt = open(COEF_HDR).read()
     nnz = 0
     for name in ("p0_faces_ng%d" % ng, "p0_interior_ng%d" % ng):
         body = re.search(r"void %s\(const R\* d, R\* o\) \{(.*?)\n\}" % name, txt, re.S).group(1)
         nnz += len(re.findall(r"\* d\[", body))
-    return (2 * ncomp * nnz + 2 * ng * 46 + ng * ng * 46 + ncomp * (6 * 3 * ng + 10)
+    pt = 46 if ncomp == 4 else 8
+    return (2 * ncomp * nnz + 2 * ng * pt + ng * ng * pt + ncomp * (6 * 3 * ng + 10)
             + 4 * 3 * ncomp)
 
 
@@ -373,9 +374,16 @@ def bench_euler2d(args):
     __graft_entry__.build()
     stream = torch.cuda.current_stream()
     ng = args.n_gauss or 2
-    u0 = W.euler_vortex_modes_2d(NX2, NX2, seed=SEED_2D + rank, npts=2).astype(np.float32)
-    cfg = H.make_config(2, H.HWENO_EULER, NX2, NX2, x0=0.0, x1=10.0, y0=0.0, y1=10.0,
-                        bc=H.HWENO_BC_PERIODIC, cfl=CFL_2D, precision=H.HWENO_FP32, n_gauss=ng)
+    burgers = args.workload == "burgers2d"
+    ncomp = 1 if burgers else 4
+    if burgers:  # Example 3.9's data (0.5 + sin(pi (x + y)/2) on [0, 4]^2), past the shock
+        u0 = W.burgers_sine_2d(NX2, NX2, npts=2).astype(np.float32)
+        cfg = H.make_config(2, H.HWENO_BURGERS, NX2, NX2, x0=0.0, x1=4.0, y0=0.0, y1=4.0,
+                            bc=H.HWENO_BC_PERIODIC, cfl=0.6, precision=H.HWENO_FP32, n_gauss=ng)
+    else:
+        u0 = W.euler_vortex_modes_2d(NX2, NX2, seed=SEED_2D + rank, npts=2).astype(np.float32)
+        cfg = H.make_config(2, H.HWENO_EULER, NX2, NX2, x0=0.0, x1=10.0, y0=0.0, y1=10.0,
+                            bc=H.HWENO_BC_PERIODIC, cfl=CFL_2D, precision=H.HWENO_FP32, n_gauss=ng)
     h = H.hweno_create(cfg, stream.cuda_stream)
     dev = torch.from_numpy(u0).to("cuda")
     host_in = torch.from_numpy(u0).pin_memory()
@@ -428,30 +436,34 @@ def bench_euler2d(args):
     clocks = sampler.summary()
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
-    flops = flops_per_cell_stage_2d(ng) * NX2 * NX2
-    byts = 128.0 * NX2 * NX2
+    flops = flops_per_cell_stage_2d(ng, ncomp) * NX2 * NX2
+    byts = (8 * 3 * 4 * ncomp / 3) * NX2 * NX2  # 8S/3, S = 3 moments x ncomp x 4 B
     hbm, peak_kind = peaks()
     t_alu = flops / (fp32_peak * 1e12)
     t_hbm = byts / (hbm * 1e9)
     if t_alu >= t_hbm:
         roof = {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": t_alu / stage_s,
-                "traffic": TRAFFIC_2D_NG2 if ng == 2 else None,
+                "traffic": TRAFFIC_2D_NG2 if (ng == 2 and not burgers) else None,
                 "note": "FP32 peak = 152 SMs x 128 lanes x 2 flops x sampled SM clock; "
-                        "%d flops per smooth cell-stage" % flops_per_cell_stage_2d(ng)}
+                        "%d flops per smooth cell-stage" % flops_per_cell_stage_2d(ng, ncomp)}
     else:
         roof = {"bound": "hbm", "achieved": byts / stage_s / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": t_hbm / stage_s, "traffic": TRAFFIC_2D_NG2 if ng == 2 else None,
+                "frac": t_hbm / stage_s,
+                "traffic": TRAFFIC_2D_NG2 if (ng == 2 and not burgers) else None,
                 "note": "peak %s" % peak_kind}
-    roof["kernel"] = "stage2d_kernel<float,4,%d>" % ng
+    roof["kernel"] = "stage2d_kernel<float,%d,%d>" % (ncomp, ng)
     line = {
         "metric": METRIC, "value": ws * cells * args.steps / tot, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "2D Euler 4096x4096 periodic, vortex + 8 density modes, %d RK3 "
-                               "steps, %d Gauss points, CFL %.1f, FP32" % (RK_STEPS_2D, ng, CFL_2D),
-                   "seed": SEED_2D, "l2": "state (805 MB) larger than L2"},
+        "config": {"workload": ("2D Burgers 4096x4096 periodic on [0,4]^2, 0.5 + sin(pi (x+y)/2) "
+                                "(Example 3.3/3.9 data), %d RK3 steps, %d Gauss points, CFL 0.6, "
+                                "FP32" % (RK_STEPS_2D, ng)) if burgers else
+                               ("2D Euler 4096x4096 periodic, vortex + 8 density modes, %d RK3 "
+                                "steps, %d Gauss points, CFL %.1f, FP32" % (RK_STEPS_2D, ng, CFL_2D)),
+                   "seed": SEED_2D, "l2": "state (%d MB) larger than L2" % (u0.nbytes // 10 ** 6)},
         "stage_ms": stage_s * 1e3,
         "troubled_frac": st["troubled"] / float(cells * (args.steps + args.warmup)),
         "roofline": roof,
@@ -678,9 +690,10 @@ def main():
     ap.add_argument("--impl", default="hweno", choices=["hweno", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="euler1d",
-                    choices=["euler1d", "euler2d", "batch1d", "adjoint2d"],
+                    choices=["euler1d", "euler2d", "burgers2d", "batch1d", "adjoint2d"],
                     help="euler1d: the headline 65536-cell 1D workload; euler2d: the "
-                         "4096 x 4096 2D Euler workload; batch1d: 512 uneven 1D instances; "
+                         "4096 x 4096 2D Euler workload; burgers2d: 2D Burgers (Example "
+                         "3.9's data) at 4096 x 4096; batch1d: 512 uneven 1D instances; "
                          "adjoint2d: gradient through 200 steps of 2D Euler at 1024 x 1024")
     ap.add_argument("--n-gauss", type=int, default=None, choices=[2, 3],
                     help="Gauss points per direction (2D): default 2 for euler2d (its "
@@ -688,7 +701,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
-    elif args.workload == "euler2d":
+    elif args.workload in ("euler2d", "burgers2d"):
         bench_euler2d(args)
     elif args.workload == "batch1d":
         bench_batch1d(args)

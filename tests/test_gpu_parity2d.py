@@ -105,6 +105,17 @@ def test_run2d_burgers_to_final_time(prec, tol):
                  W.burgers_sine_2d(n, n), dom, tol, cfl=0.5, t_final=0.5 / np.pi)
 
 
+@pytest.mark.parametrize("prec,tol", [(H.HWENO_FP64, 1e-11), (H.HWENO_FP32, 1e-4)])
+def test_run2d_burgers_shock_example_3_9(prec, tol):
+    """Example 3.9: Example 3.3's data through the shock to T = 1.5/pi with the
+    paper's CFL 0.6 (the oracle's run is pinned against the entropy solution)."""
+    n = 40
+    dom = (0.0, 4.0, 0.0, 4.0)
+    st, nt = _compare_run(H.HWENO_BURGERS, n, n, H.HWENO_BC_PERIODIC, prec, 200,
+                          W.burgers_sine_2d(n, n), dom, tol, cfl=0.6, t_final=1.5 / np.pi)
+    assert nt > 0 and st["troubled"] > 0
+
+
 def test_periodic_conservation_2d_fp64():
     n = 24
     dom = square_domain(n, n)

@@ -259,6 +259,41 @@ def test_table3_burgers2d():
     assert np.log(errs[20] / errs[40]) / np.log(2) > 3.5
 
 
+def test_example_3_9_shocked_burgers2d():
+    """Example 3.9: Example 3.3's data to T = 1.5/pi, past the shock.  The
+    solution is w((x + y)/2, T) with w the entropy solution of the 1D problem
+    v_t + v v_x = 0, v0 = 0.5 + sin(pi x) (Hopf-Lax, helpers.burgers_entropy_1d).
+    The paper shows figures only, so the pins are convergence to the entropy
+    solution: away from the shock line (more than 3 cells in x + y) the error
+    falls from 2.0e-4 to 6.4e-5 (N = 20 -> 40; measured), the troubled cells
+    sit on the shock line, and the overall L1 error is O(dx) from the shock."""
+    from helpers import burgers_entropy_1d
+    T = 1.5 / np.pi
+    sv = np.linspace(0.0, 2.0, 20001)
+    ws = burgers_entropy_1d(sv, T)
+    s_shock = sv[np.argmin(np.diff(ws))]
+    far_max = {}
+    for nx in (20, 40):
+        cfg = O.Cfg2D.make(O.BURGERS, nx, nx, 0, 4, 0, 4, O.BC_PERIODIC)
+        u, t, nt = O.run2d(cfg, W.burgers_sine_2d(nx, nx), t_final=T, cfl=0.6)
+        assert abs(t - T) < 1e-14 and nt > 0
+        h, K = 4.0 / nx, 24
+        off = (np.arange(K) + 0.5) / K * h
+        xc = np.arange(nx) * h
+        X = xc[None, :, None, None] + off[None, None, None, :]
+        Y = xc[:, None, None, None] + off[None, None, :, None]
+        ex = np.interp(np.mod((X + Y) / 2.0, 2.0), sv, ws).mean(axis=(2, 3))  # [j][i]
+        err = np.abs(u[0, 0] - ex)
+        sig = (xc[None, :] + xc[:, None] + h) / 2.0
+        dist = np.abs(((sig - s_shock + 1.0) % 2.0) - 1.0)
+        far = dist > 3 * h
+        far_max[nx] = err[far].max()
+        assert err.mean() < 1e-2
+        _, _, fl, _ = O.rhs2d(cfg, u)
+        assert fl.sum() > 0 and np.all(dist[fl.astype(bool)] < 4 * h)
+    assert far_max[20] < 4e-4 and far_max[40] < 1.3e-4 and far_max[40] < far_max[20] / 2.5, far_max
+
+
 def test_table4_euler2d():
     """Table 4 (Example 3.4), new hybrid HWENO at 30 x 30: L1 = 3.11E-07, with
     the time step small enough that the spatial error dominates."""
