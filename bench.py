@@ -273,6 +273,8 @@ def bench_hweno(args):
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
         e2e_s = max_over_ranks(sum(e2e_ms) / 1e3)
+        final = np.empty(u0.shape, dtype=np.float64)  # the state after RK_STEPS steps
+        H.hweno_get_state(h, final.ctypes.data, H.HWENO_FP64, False)
         H.hweno_destroy(h)
         cells = NX * 3 * RK_STEPS
         results[prec_name] = {
@@ -286,6 +288,7 @@ def bench_hweno(args):
             "execution": {"threads_per_cta": choice[0], "cells_per_tile": choice[0] - 6,
                           "launch": "persistent" if choice[1] else "per-stage graphs",
                           "chosen_by": "hweno_autotune"},
+            "final": final,
         }
 
     cpu = None
@@ -296,6 +299,16 @@ def bench_hweno(args):
         return
     r = results["fp32"]
     peak, peak_kind = peaks()
+    # per-field error of the FP32 path against the FP64 path after the 2000
+    # steps (the FP64 path matches the FP64 oracle to 1e-12 in the parity tests)
+    a32, a64 = results["fp32"].pop("final"), results["fp64"].pop("final")
+    field_err = {}
+    for c, name in enumerate(("rho", "m", "E")):
+        for m, mom in enumerate(("average", "first_moment")):
+            d = np.abs(a32[c, m] - a64[c, m])
+            field_err["%s_%s" % (name, mom)] = {
+                "L1": float(d.mean()), "Linf": float(d.max()),
+                "rel_L1": float(d.sum() / max(np.abs(a64[c, m]).sum(), 1e-300))}
     per_launch = BYTES_PER_CELL_STAGE["fp32"] * NX
     achieved = per_launch / (r["stage_us"] * 1e-6) / 1e9
     line = {
@@ -309,6 +322,7 @@ def bench_hweno(args):
         "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
                  "e2e": results["fp64"]["e2e"]},
         "troubled_frac": r["troubled_frac"],
+        "fp32_vs_fp64": field_err,
         "execution": r["execution"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,

@@ -236,6 +236,15 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
  * waits for the stream. */
 hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent);
 
+/* The conserved totals of the current state: totals[c] = the sum over cells
+ * of the average of component c times the cell size (dx, or dx dy in 2D),
+ * accumulated in FP64 on the device in a fixed order (so repeatable to the
+ * bit).  C values (Burgers 1, 1D Euler 3, 2D Euler 4); for a batch, n_batch
+ * x C values, instance after instance.  With periodic boundaries the scheme
+ * conserves them (Eq. (odeH), Eq. (ode2) are in flux form).  Waits for the
+ * stream. */
+hweno_status hweno_totals(hweno_handle h, double* totals);
+
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);
 

@@ -224,6 +224,37 @@ __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, s
     dst[k] = (D)src[k];
 }
 
+// Sums in FP64 of the cell averages of each component: n cells from base,
+// component c at base + c * comp_stride.  Pass 1: one FP64 partial per block and
+// component, in a fixed order; pass 2 (one block): the partials, in order.
+template <typename R>
+__global__ void __launch_bounds__(256) totals_kernel(const R* __restrict__ base, long long comp_stride,
+                                                     int C, long long n, double* partials) {
+  __shared__ double red[8];
+  for (int c = 0; c < C; ++c) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+      s += (double)base[c * comp_stride + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < 8; ++k) t += red[k];
+      partials[c * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void totals_finish_kernel(const double* partials, int nblocks, int C, double* out) {
+  if (threadIdx.x < C) {
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[threadIdx.x * nblocks + b];
+    out[threadIdx.x] = t;
+  }
+}
+
 __global__ void set_scalars_kernel(DevScalars* sc, int reset, double t_final) {
   if (reset) {
     sc->t = 0.0;
@@ -342,6 +373,18 @@ cudaError_t launch_convert(const void* src, int src_fp64, void* dst, int dst_fp6
     convert_kernel<<<(unsigned)blocks, threads, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), count);
   else
     convert_kernel<<<(unsigned)blocks, threads, 0, s>>>(static_cast<const float*>(src), static_cast<float*>(dst), count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const void* base, int fp64, long long comp_stride, int C, long long n,
+                          double* partials, int nblocks, double* out, cudaStream_t s) {
+  if (fp64)
+    totals_kernel<double><<<nblocks, 256, 0, s>>>(static_cast<const double*>(base), comp_stride, C, n, partials);
+  else
+    totals_kernel<float><<<nblocks, 256, 0, s>>>(static_cast<const float*>(base), comp_stride, C, n, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  totals_finish_kernel<<<1, 32, 0, s>>>(partials, nblocks, C, out);
   return cudaGetLastError();
 }
 

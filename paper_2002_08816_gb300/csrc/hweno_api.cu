@@ -35,6 +35,7 @@ struct hweno_ctx {
   unsigned* bar = nullptr;           // grid barrier of the persistent kernel
   std::vector<int> batch_nx;         // cells of each batch instance
   std::vector<hw::BatchInst> batch_inst;
+  double* tot_buf = nullptr;         // hweno_totals: partials, then the sums
   size_t elems = 0, esize = 0;
   void* U[3] = {nullptr, nullptr, nullptr};
   void* U0 = nullptr;
@@ -685,6 +686,7 @@ void hweno_destroy(hweno_handle h) {
   if (h->sc) cudaFree(h->sc);
   if (h->sc_rhs) cudaFree(h->sc_rhs);
   if (h->bar) cudaFree(h->bar);
+  if (h->tot_buf) cudaFree(h->tot_buf);
   if (h->d_tile_inst) cudaFree(h->d_tile_inst);
   if (h->d_tile_base) cudaFree(h->d_tile_base);
   if (h->d_binst) cudaFree(h->d_binst);
@@ -931,6 +933,43 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
   a.lam_in = grad;
   HW_CUDA(h, hw::launch_adj2d(a, h->stream));
   HW_CUDA(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_totals(hweno_handle h, double* totals) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (!totals) return fail(h, HWENO_ERR_ARG, "totals is NULL");
+  if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_totals before hweno_set_state");
+  constexpr int kBlocks = 304;  // 2 per SM
+  const int C = h->C;
+  if (!h->tot_buf)
+    HW_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->tot_buf), sizeof(double) * (kBlocks + 1) * 8));
+  double* part = h->tot_buf;
+  double* out = h->tot_buf + kBlocks * 8;
+  const int fp64 = h->cfg.precision == HWENO_FP64;
+  const int ninst = h->n_batch > 0 ? h->n_batch : 1;
+  for (int b = 0; b < ninst; ++b) {
+    long long n, off = 0;
+    double cell;
+    if (h->n_batch > 0) {
+      n = h->batch_nx[b];
+      off = h->batch_inst[b].off;
+      cell = (h->cfg.x1 - h->cfg.x0) / n;
+    } else if (h->dim == 2) {
+      n = h->n;
+      cell = (h->cfg.x1 - h->cfg.x0) / h->cfg.nx * ((h->cfg.y1 - h->cfg.y0) / h->cfg.ny);
+    } else {
+      n = h->n;
+      cell = (h->cfg.x1 - h->cfg.x0) / h->cfg.nx;
+    }
+    const long long stride = (long long)h->M * n;  // [c][m][cells]: component c's averages
+    HW_CUDA(h, hw::launch_totals(byte_off(h->U[0], (size_t)off * h->esize), fp64, stride, C, n, part,
+                                 kBlocks, out, h->stream));
+    double sums[8];
+    HW_CUDA(h, cudaMemcpyAsync(sums, out, sizeof(double) * C, cudaMemcpyDeviceToHost, h->stream));
+    HW_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < C; ++c) totals[(size_t)b * C + c] = sums[c] * cell;
+  }
   return HWENO_OK;
 }
 

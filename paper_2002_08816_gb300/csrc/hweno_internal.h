@@ -186,5 +186,9 @@ cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int sys
 cudaError_t launch_convert(const void* src, int src_fp64, void* dst, int dst_fp64, size_t count,
                            cudaStream_t s);
 cudaError_t launch_set_scalars(DevScalars* sc, int reset, double t_final, cudaStream_t s);
+// out[c] = sum over n cells of base[c * comp_stride + i] in FP64, c < C <= 8, with
+// nblocks partials per component in partials; a fixed summation order.
+cudaError_t launch_totals(const void* base, int fp64, long long comp_stride, int C, long long n,
+                          double* partials, int nblocks, double* out, cudaStream_t s);
 
 }  // namespace hw

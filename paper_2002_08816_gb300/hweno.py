@@ -87,6 +87,8 @@ def lib():
         L.hweno_backward.argtypes = [_VP, _VP, _VP, _I, _I]
         L.hweno_rhs_vjp.restype = _I
         L.hweno_rhs_vjp.argtypes = [_VP, _VP, _VP, _D, _D, _VP, _VP]
+        L.hweno_totals.restype = _I
+        L.hweno_totals.argtypes = [_VP, ctypes.POINTER(_D)]
         L.hweno_set_execution.restype = _I
         L.hweno_set_execution.argtypes = [_VP, _I, _I]
         L.hweno_autotune.restype = _I
@@ -176,6 +178,13 @@ def hweno_autotune(h, nsteps_trial):
     out = (_I * 2)()
     _check(lib().hweno_autotune(h, int(nsteps_trial), out), h)
     return out[0], bool(out[1])
+
+
+def hweno_totals(h, count):
+    """The count (= instances x components) conserved totals, FP64."""
+    out = (_D * count)()
+    _check(lib().hweno_totals(h, out), h)
+    return list(out)
 
 
 def hweno_set_execution(h, threads, persistent):
