@@ -42,7 +42,9 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
 # kernels (profiles/stage1d_euler65536_fp32.md: mean over the three stages at
 # the bench's 65536 cells; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled
 # by the cell count to 4096^2)
-TRAFFIC_1D_FP32 = {(256, "per-stage graphs"): (1.622528e6 + 2 * 3.195392e6) / 3}
+TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3203584 + 1626368 + 3198208) / 3,
+                   (256, "per-stage graphs"): (3203328 + 1625344 + 256 + 3198208 + 512) / 3,
+                   (512, "per-stage graphs"): (3203072 + 1625344 + 3198720) / 3}
 TRAFFIC_2D_NG2 = 4 * (403.311616e6 + 178.976512e6)
 L2_FLUSH_BYTES = 512 << 20
 

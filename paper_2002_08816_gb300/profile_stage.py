@@ -3,7 +3,7 @@
   python -m paper_2002_08816_gb300.profile_stage [--nx 65536] [--rk-steps 10]
                                                   [--precision fp32|fp64] [--system euler|burgers]
                                                   [--dim 1|2] [--n-gauss 2|3]
-                                                  [--adjoint EVERY]
+                                                  [--adjoint EVERY] [--threads 128|256|512]
 
 Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
 --dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
@@ -37,6 +37,8 @@ def main():
     ap.add_argument("--dim", type=int, default=1, choices=[1, 2])
     ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
     ap.add_argument("--adjoint", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0, choices=[0, 128, 256, 512],
+                    help="1D: threads per CTA of the per-stage kernels (0: the default)")
     args = ap.parse_args()
     B.build()
     prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
@@ -56,6 +58,8 @@ def main():
     dev = torch.from_numpy(u).to("cuda", dt).contiguous()
     h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
+        if args.threads and args.dim == 1:
+            H.hweno_set_execution(h, args.threads, False)
         H.hweno_set_state(h, dev.data_ptr(), prec, True)
         if args.adjoint > 0:
             t = H.hweno_record(h, args.rk_steps, args.adjoint)
