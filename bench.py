@@ -56,6 +56,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, device="cuda"):
+    """The slowest rank's time: an all-reduce MAX over the process group (one
+    independent replica per rank, so this is the only collective); x itself
+    when there is no group or one rank."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, units_per_rank, seconds):
+    """Whole-job throughput of weak-scaled replicas: every rank processes
+    units_per_rank units, the job takes the slowest rank's seconds."""
+    return world_size * units_per_rank / seconds
+
+
 def workload(rank):
     from paper_2002_08816_gb300 import workloads as W
     return W.euler_two_state_1d(NX, seed=SEED + rank)
@@ -206,13 +225,6 @@ def bench_hweno(args):
         if ws > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     results = {}
     for prec_name, prec in (("fp32", H.HWENO_FP32), ("fp64", H.HWENO_FP64)):
         cfg = H.make_config(1, H.HWENO_EULER, NX, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=CFL,
@@ -280,10 +292,10 @@ def bench_hweno(args):
         H.hweno_destroy(h)
         cells = NX * 3 * RK_STEPS
         results[prec_name] = {
-            "value": ws * cells * args.steps / tot_s,
+            "value": job_value(ws, cells * args.steps, tot_s),
             "ms_per_step": 1e3 * tot_s / args.steps,
             "stage_us": 1e6 * tot_s / (args.steps * 3 * RK_STEPS),
-            "e2e": ws * cells * len(e2e_ms) / e2e_s,
+            "e2e": job_value(ws, cells * len(e2e_ms), e2e_s),
             "troubled_frac": stats["troubled"] / float(3 * RK_STEPS * NX),
             "bytes_h2d": host_in.numel() * host_in.element_size(),
             "clocks": sampler.summary() if sampler else None,
@@ -428,11 +440,7 @@ def bench_euler2d(args):
     ms = [a.elapsed_time(b) for a, b in ev]
     H.hweno_step(h, 0, -1.0)
     st = H.hweno_stats(h)
-    tot = sum(ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = max_over_ranks(sum(ms) / 1e3)
     # end to end from pinned host buffers
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -470,7 +478,7 @@ def bench_euler2d(args):
                 "note": "peak %s" % peak_kind}
     roof["kernel"] = "stage2d_kernel<float,%d,%d>" % (ncomp, ng)
     line = {
-        "metric": METRIC, "value": ws * cells * args.steps / tot, "unit": UNIT, "n_gpus": ws,
+        "metric": METRIC, "value": job_value(ws, cells * args.steps, tot), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
