@@ -18,8 +18,14 @@ constexpr int NT = kThreads1D;  // threads of the wave-speed kernels
 constexpr int T = kTile1D;      // their cells per CTA
 constexpr int NW = NT / 32;
 
+// The 128-thread tiles are the high-occupancy choice: 12 CTAs per SM in FP32
+// (40 registers, a few spilled), 6 in FP64, which hides the stage's dependent
+// load and arithmetic chains on large states and batches; on small states,
+// which sit at the per-stage latency floor, the 256-thread tiles at the
+// register count the compiler picks are faster.  hweno_autotune chooses.
 template <typename R, int C, bool BATCH, int NTH>
-__global__ void __launch_bounds__(NTH) stage1d_kernel(Stage1DArgs a) {
+__global__ void __launch_bounds__(NTH, NTH == 128 ? (sizeof(R) == 4 ? 12 : 6) : 1)
+    stage1d_kernel(Stage1DArgs a) {
   __shared__ Smem1D<R, C, NTH> sm;
   s1d::stage1d_tile<R, C, BATCH, NTH>(a, blockIdx.x, sm);
 }
@@ -39,29 +45,27 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 }
 
 // All CTAs of the (co-resident) grid meet here; false when the wait timed out.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nb, DevScalars* sc) {
+// bar[0] counts the arrivals of the whole launch (zeroed by the host before
+// it), so the k-th meeting is over once it reaches target = k * gridDim.x:
+// each CTA publishes its writes (fence), adds its arrival without waiting for
+// a reply, and polls; nobody resets the counter or bumps a generation, which
+// would put two more round trips to L2 on the last arriver's path.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, DevScalars* sc) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int good = 1;
-    const unsigned gen = ld_acquire_gpu(bar + 1);
     __threadfence();
-    if (atomicAdd(bar, 1u) == nb - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned it = 0;
-      while (ld_acquire_gpu(bar + 1) == gen) {
-        if (++it == (1u << 24)) {
-          atomicOr(&sc->status, (unsigned)ST_TIMEOUT);
-          good = 0;
-          break;
-        }
-        __nanosleep(32);
+    atomicAdd(bar, 1u);
+    unsigned it = 0;
+    while (static_cast<int>(ld_acquire_gpu(bar) - target) < 0) {
+      if (++it == (1u << 24)) {
+        atomicOr(&sc->status, (unsigned)ST_TIMEOUT);
+        good = 0;
+        break;
       }
+      __nanosleep(32);
     }
-    __threadfence();
     ok = good;
   }
   __syncthreads();
@@ -71,6 +75,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nb, DevScalars
 template <typename R, int C, bool BATCH, int NTH>
 __global__ void __launch_bounds__(NTH) run1d_kernel(Run1DArgs r) {
   __shared__ Smem1D<R, C, NTH> sm;
+  unsigned meet = 0;  // arrivals that end the next meeting
   for (int step = 0; step < r.nsteps; ++step) {
 #pragma unroll 1
     for (int stage = 1; stage <= 3; ++stage) {
@@ -88,7 +93,8 @@ __global__ void __launch_bounds__(NTH) run1d_kernel(Run1DArgs r) {
         s1d::stage1d_tile<R, C, BATCH, NTH>(a, tile, sm);
         __syncthreads();
       }
-      if (!grid_sync(r.bar, gridDim.x, r.a.sc)) return;
+      meet += gridDim.x;
+      if (!grid_sync(r.bar, meet, r.a.sc)) return;
     }
   }
 }

@@ -11,6 +11,8 @@
 //   Step 2.2   p0 at x_{i-+1/2};   Step 2.3 p0 at x_{i-+sqrt5/10}.
 #pragma once
 
+#include "hweno_device.cuh"
+
 namespace hw {
 
 // Nonlinear combination shared by Step 1 and Step 2.1:
@@ -23,6 +25,20 @@ struct Weights3 {
   __device__ __forceinline__ Weights3(const R* gam, R eps, R b0, R b1, R b2) {
     R s = R(0.5) * (fabs(b0 - b1) + fabs(b0 - b2));
     R tau = s * s;
+    if constexpr (sizeof(R) == 4) {
+      // FP32: approximate reciprocals (the weights need a few ulp, not IEEE
+      // rounding), which shortens the dependent chain of a troubled cell
+      const R a0 = gam[0] * (R(1) + tau * fast_rcp(b0 + eps));
+      const R a1 = gam[1] * (R(1) + tau * fast_rcp(b1 + eps));
+      const R a2 = gam[2] * (R(1) + tau * fast_rcp(b2 + eps));
+      const R inv = fast_rcp(a0 + a1 + a2);
+      w0g = a0 * inv * fast_rcp(gam[0]);
+      w1 = a1 * inv;
+      w2 = a2 * inv;
+      g1 = gam[1];
+      g2 = gam[2];
+      return;
+    }
     R a0 = gam[0] * (R(1) + tau / (b0 + eps));
     R a1 = gam[1] * (R(1) + tau / (b1 + eps));
     R a2 = gam[2] * (R(1) + tau / (b2 + eps));
@@ -119,7 +135,7 @@ __device__ __forceinline__ void hweno_faces(R um, R u0, R up, R vm, R v0, R vp, 
 // The FP64 form is evaluated without contraction.
 __device__ __forceinline__ bool kxrcf_troubled(double um, double u0, double up, double vm,
                                                double v0, double vp, bool left, double h,
-                                               double thr, float /*hthr*/) {
+                                               double thr, float /*hthr*/, float /*hthr_lo*/) {
   double jump;
   if (left)
     jump = __dsub_rn(__dsub_rn(u0, __dmul_rn(6.0, v0)), __dadd_rn(um, __dmul_rn(6.0, vm)));
@@ -129,15 +145,35 @@ __device__ __forceinline__ bool kxrcf_troubled(double um, double u0, double up, 
   return fabs(jump) / __dmul_rn(h, nrm) > thr;
 }
 
-// FP32 inputs: decide in FP32 when the rounding-error bound allows, else fall
-// back to the FP64 form, so the decision equals the FP64 one away from the
-// threshold.  With S = |u0| + 6|v0| + |u_nb| + 6|v_nb|, the FP32 jump (four
-// roundings) is within 3 * 2^-24 * S of the exact one (bounded here by
-// 6e-7 S), and r = thr*h*max(|u0|,1e-12) (three roundings) within a relative
-// 4.8e-7; hthr = (float)(thr*h).
+// s + e = a + b exactly (Knuth's two-sum); the intrinsics keep the compiler
+// from contracting or reordering the steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// FP32 inputs: decide in FP32 when the rounding-error bound allows, else
+// evaluate the jump and the threshold as unevaluated float pairs (error-free
+// sums and products), so that the decision equals the FP64 one away from the
+// threshold without any FP64 arithmetic (a dependent FP64 division costs about
+// a thousand cycles on GB300, and the band is wide on fine grids: the jump is
+// a difference of O(|u|) numbers, the threshold O(h |u|)).
+//   Fast test: with S = |u0| + 6|v0| + |u_nb| + 6|v_nb|, the FP32 jump (four
+//   roundings) is within 3 * 2^-24 * S of the exact one (bounded here by
+//   6e-7 S), and r = thr*h*max(|u0|,1e-12) (three roundings) within a
+//   relative 4.8e-7; hthr = (float)(thr*h), hthr_lo = (float)(thr*h - hthr).
+//   Pair test: the four terms u0, -+6v0, -u_nb, -+6v_nb are exact as pairs
+//   (fma gives the rounding error of 6v); three two-sums leave the jump as
+//   jh + jl with jl rounded from five small terms, so within ~2^-46 S of the
+//   exact value, renormalised so that jh has the jump's sign; r = nrm * (hthr
+//   + hthr_lo) as rh + rl within ~2^-46 r.  The sign of (|jh| - rh) +
+//   (+-jl - rl) then equals the sign of |jump| - r
+//   unless they are within ~1e-13 S, i.e. well inside a 1e-6 relative band
+//   around the threshold for any grid with S / r below 1e7.
 __device__ __forceinline__ bool kxrcf_troubled(float um, float u0, float up, float vm, float v0,
-                                               float vp, bool left, double h, double thr,
-                                               float hthr) {
+                                               float vp, bool left, double /*h*/, double /*thr*/,
+                                               float hthr, float hthr_lo) {
   float a, b, s;
   if (left) {
     a = u0 - 6.0f * v0;
@@ -150,11 +186,30 @@ __device__ __forceinline__ bool kxrcf_troubled(float um, float u0, float up, flo
   }
   const float j = fabsf(a - b);
   const float e = 6.0e-7f * s;
-  const float r = hthr * fmaxf(fabsf(u0), 1e-12f);
+  const float nrm = fmaxf(fabsf(u0), 1e-12f);
+  const float r = hthr * nrm;
   if (j - e > r * (1.0f + 4.8e-7f)) return true;
   if (j + e < r * (1.0f - 4.8e-7f)) return false;
-  return kxrcf_troubled((double)um, (double)u0, (double)up, (double)vm, (double)v0, (double)vp,
-                        left, h, thr, hthr);
+  // jump = u0 + sv*6*v0 - unb + sv*6*vnb, sv = -1 on the left face, +1 on the right
+  const float sv = left ? -1.0f : 1.0f;
+  const float unb = left ? um : up, vnb = left ? vm : vp;
+  const float p0 = __fmul_rn(6.0f, v0), e0 = fmaf(6.0f, v0, -p0);
+  const float p1 = __fmul_rn(6.0f, vnb), e1 = fmaf(6.0f, vnb, -p1);
+  float s1, t1, s2, t2, s3, t3;
+  two_sum(u0, sv * p0, s1, t1);
+  two_sum(s1, -unb, s2, t2);
+  two_sum(s2, sv * p1, s3, t3);
+  // after cancellation the small terms may outweigh s3: renormalise, so that
+  // jh carries the sign of the jump and |jl| <= ulp(jh) / 2
+  float jh, jl;
+  two_sum(s3, __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), t3), sv * __fadd_rn(e0, e1)), jh, jl);
+  if (jh < 0.0f) {
+    jh = -jh;
+    jl = -jl;
+  }
+  const float rh = __fmul_rn(nrm, hthr);
+  const float rl = __fadd_rn(fmaf(nrm, hthr, -rh), __fmul_rn(nrm, hthr_lo));
+  return __fadd_rn(__fsub_rn(jh, rh), __fsub_rn(jl, rl)) > 0.0f;
 }
 
 // Side of the inflow face: left when the velocity m/rho is >= 0 (its sign

@@ -61,23 +61,15 @@ struct Smem1D {
   R amax[NW];
 };
 
-template <typename R>
-__device__ __forceinline__ R recip(R x) {
-  if constexpr (sizeof(R) == 4) {
-    return __frcp_rn(x);
-  } else {
-    return R(1) / x;
-  }
-}
 
 template <typename R, int C>
 __device__ __forceinline__ void phys_flux(R gas, const R* U, R* F) {
   if constexpr (C == 1) {
     F[0] = R(0.5) * U[0] * U[0];
   } else {
-    // f(rho, m, E) of Eq. (euler1); FP32 uses a rounded reciprocal of rho
+    // f(rho, m, E) of Eq. (euler1); FP32 uses an approximate reciprocal of rho
     const R rho = U[0], m = U[1], E = U[2];
-    const R mu = sizeof(R) == 4 ? m * recip(rho) : m / rho;
+    const R mu = sizeof(R) == 4 ? m * fast_rcp(rho) : m / rho;
     const R p = (gas - R(1)) * (E - R(0.5) * m * mu);
     F[0] = m;
     F[1] = m * mu + p;
@@ -96,31 +88,81 @@ __device__ __forceinline__ R wave_speed(R gas, const R* U) {
   }
 }
 
-// Step 2.1 for the Euler cell at sm.u index e in the characteristic fields of
-// the Jacobian at U: the interface values u^+_{i-1/2} (L) and u^-_{i+1/2} (Rt).
-template <typename S, typename R>
-__device__ __noinline__ void char_faces(const S& sm, int e, const R* U, const R* gam, R eps,
-                                        R gas, R* L, R* Rt) {
+// Euler troubled-cell work for one cell (Remark 2: the characteristic fields
+// of the Jacobian at a cell average).  Out of line, with scalar arguments and
+// results: compiled once per precision, so every tile size runs the same
+// instructions on a cell (the execution choice cannot change a result through
+// a multiply-add the optimiser contracts differently in another
+// instantiation), the kernel body keeps few registers, and no array of the
+// caller has its address taken.  The three fields are independent chains
+// that the one thread interleaves.
+template <typename R>
+struct ConsVec {
+  R v[3];
+};
+template <typename R>
+struct ConsFaces {
+  R L[3], Rt[3], fL[3], fR[3];
+};
+
+// Step 1 for cell i: the modified first moments, from the averages of cells
+// i-1, i, i+1 (am*, a0*, ap*) and the first moments of i-1, i+1 (vm*, vp*),
+// limited field by field and mapped back to the conserved variables.
+template <typename R>
+__device__ __noinline__ ConsVec<R> char_limit(R gas, R g0, R g1, R g2, R eps, R am0, R am1, R am2,
+                                              R a00, R a01, R a02, R ap0, R ap1, R ap2, R vm0,
+                                              R vm1, R vm2, R vp0, R vp1, R vp2) {
+  const R U[3] = {a00, a01, a02};
+  const R gam[3] = {g0, g1, g2};
+  R Rm[3][3], Lm[3][3];
+  Euler1D<R>::eigen(gas, U, Rm, Lm);
+  R q[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const R* l = Lm[f];
+    q[f] = limit_first_moment(l[0] * am0 + l[1] * am1 + l[2] * am2,
+                              l[0] * a00 + l[1] * a01 + l[2] * a02,
+                              l[0] * ap0 + l[1] * ap1 + l[2] * ap2,
+                              l[0] * vm0 + l[1] * vm1 + l[2] * vm2,
+                              l[0] * vp0 + l[1] * vp1 + l[2] * vp2, gam, eps);
+  }
+  ConsVec<R> o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) o.v[c] = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2];
+  return o;
+}
+
+// Step 2.1 for cell i: the HWENO values at x_{i-1/2} and x_{i+1/2} from the
+// averages of cells i-1, i, i+1 and their modified first moments (vm*, v0*,
+// vp*), in the characteristic fields of the state (b0, b1, b2), mapped back
+// to the conserved variables, with their physical fluxes.
+template <typename R>
+__device__ __noinline__ ConsFaces<R> char_faces(R gas, R g0, R g1, R g2, R eps, R b0, R b1, R b2,
+                                                R am0, R am1, R am2, R a00, R a01, R a02, R ap0,
+                                                R ap1, R ap2, R vm0, R vm1, R vm2, R v00, R v01,
+                                                R v02, R vp0, R vp1, R vp2) {
+  const R U[3] = {b0, b1, b2};
+  const R gam[3] = {g0, g1, g2};
   R Rm[3][3], Lm[3][3];
   Euler1D<R>::eigen(gas, U, Rm, Lm);
   R cl[3], cr[3];
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
-    R wu[3], wv[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      wu[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
-              Lm[f][2] * sm.u[2][0][e - 1 + s];
-      wv[s] = Lm[f][0] * sm.vl[0][e - 2 + s] + Lm[f][1] * sm.vl[1][e - 2 + s] +
-              Lm[f][2] * sm.vl[2][e - 2 + s];
-    }
-    hweno_faces(wu[0], wu[1], wu[2], wv[0], wv[1], wv[2], gam, eps, cl[f], cr[f]);
+    const R* l = Lm[f];
+    hweno_faces(l[0] * am0 + l[1] * am1 + l[2] * am2, l[0] * a00 + l[1] * a01 + l[2] * a02,
+                l[0] * ap0 + l[1] * ap1 + l[2] * ap2, l[0] * vm0 + l[1] * vm1 + l[2] * vm2,
+                l[0] * v00 + l[1] * v01 + l[2] * v02, l[0] * vp0 + l[1] * vp1 + l[2] * vp2, gam,
+                eps, cl[f], cr[f]);
   }
+  ConsFaces<R> o;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    L[c] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
-    Rt[c] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
+    o.L[c] = Rm[c][0] * cl[0] + Rm[c][1] * cl[1] + Rm[c][2] * cl[2];
+    o.Rt[c] = Rm[c][0] * cr[0] + Rm[c][1] * cr[1] + Rm[c][2] * cr[2];
   }
+  phys_flux<R, 3>(gas, o.L, o.fL);
+  phys_flux<R, 3>(gas, o.Rt, o.fR);
+  return o;
 }
 
 // One stage on one tile of T = NTH - 6 cells, by a CTA of NTH threads.  The
@@ -155,6 +197,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
     a.h = bi.h;
     a.cfl_dx = bi.cfl_dx;
     a.hthr = bi.hthr_f;
+    a.hthr_lo = bi.hthr_lo_f;
     a.f32[5] = bi.inv_dx_f;
     a.f32[6] = bi.cfl_dx_f;
   }
@@ -261,11 +304,13 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
   }
 
   // 3. troubled cells and modified first moments (Step 1), cells base-2 ..
+  //    base+T+1; Euler limits in the characteristic fields of the cell
+  //    average (Remark 2)
+  int flag = 0;
   if (tid < T + 4) {
     const int k = tid, e = k + 1;
     const double h = a.h;
-    const float hthr = a.hthr;
-    int flag;
+    const float hthr = a.hthr, hthr_lo = a.hthr_lo;
     if (a.mode == 1) {
       flag = 1;
     } else if (a.mode == 2) {
@@ -273,15 +318,15 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
     } else if constexpr (C == 1) {
       const R u0 = sm.u[0][0][e];
       flag = kxrcf_troubled(sm.u[0][0][e - 1], u0, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
-                            sm.u[0][1][e], sm.u[0][1][e + 1], u0 >= R(0), h, a.thr, hthr);
+                            sm.u[0][1][e], sm.u[0][1][e + 1], u0 >= R(0), h, a.thr, hthr, hthr_lo);
     } else {
       const bool left = inflow_left(sm.u[0][0][e], sm.u[1][0][e]);
       flag = kxrcf_troubled(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
                             sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left, h, a.thr,
-                            hthr) ||
+                            hthr, hthr_lo) ||
              kxrcf_troubled(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1],
                             sm.u[2][1][e - 1], sm.u[2][1][e], sm.u[2][1][e + 1], left, h, a.thr,
-                            hthr);
+                            hthr, hthr_lo);
     }
     sm.fl[k] = (uint8_t)flag;
     if (!flag) {
@@ -291,61 +336,66 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       sm.vl[0][k] = limit_first_moment(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1],
                                        sm.u[0][1][e - 1], sm.u[0][1][e + 1], gam, eps);
     } else {
-      // characteristic fields of the Jacobian at the cell average (Remark 2)
-      R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
-      R Rm[3][3], Lm[3][3];
-      Euler1D<R>::eigen(gas, U, Rm, Lm);
-      R q[3];
+      const ConsVec<R> o = char_limit<R>(
+          gas, gam[0], gam[1], gam[2], eps, sm.u[0][0][e - 1], sm.u[1][0][e - 1],
+          sm.u[2][0][e - 1], sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e], sm.u[0][0][e + 1],
+          sm.u[1][0][e + 1], sm.u[2][0][e + 1], sm.u[0][1][e - 1], sm.u[1][1][e - 1],
+          sm.u[2][1][e - 1], sm.u[0][1][e + 1], sm.u[1][1][e + 1], sm.u[2][1][e + 1]);
 #pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        R wv[5];
-#pragma unroll
-        for (int s = 0; s < 3; ++s)
-          wv[s] = Lm[f][0] * sm.u[0][0][e - 1 + s] + Lm[f][1] * sm.u[1][0][e - 1 + s] +
-                  Lm[f][2] * sm.u[2][0][e - 1 + s];
-        wv[3] = Lm[f][0] * sm.u[0][1][e - 1] + Lm[f][1] * sm.u[1][1][e - 1] +
-                Lm[f][2] * sm.u[2][1][e - 1];
-        wv[4] = Lm[f][0] * sm.u[0][1][e + 1] + Lm[f][1] * sm.u[1][1][e + 1] +
-                Lm[f][2] * sm.u[2][1][e + 1];
-        q[f] = limit_first_moment(wv[0], wv[1], wv[2], wv[3], wv[4], gam, eps);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) sm.vl[c][k] = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2];
+      for (int c = 0; c < 3; ++c) sm.vl[c][k] = o.v[c];
     }
   }
   __syncthreads();
 
   // 4. interface values (Steps 2.1, 2.2) and their physical fluxes, cells base-1 ..
+  //    base+T
   if (tid < T + 2) {
     const int k = tid, e = k + 2;  // sm.u index e; sm.vl / sm.fl index of cell e is e - 1
     const bool hw = sm.fl[k] | sm.fl[k + 1] | sm.fl[k + 2];
-    R L[C], Rt[C];
-    if (!hw) {
+    R L[C], Rt[C], fL[C], fR[C];
+    if (!hw || C == 1) {
+      if (!hw) {
 #pragma unroll
-      for (int c = 0; c < C; ++c)
-        linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                     sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
-    } else if constexpr (C == 1) {
-      hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
-                  sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
-    } else if (!(a.variant & HWENO_VARIANT_MEAN_EIGEN)) {
-      // characteristic fields of the cell average, both interfaces (Remark 2)
-      R U[3] = {sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e]};
-      char_faces(sm, e, U, gam, eps, gas, L, Rt);
-    } else {
-      // variant: the fields of the mean of the two averages at each interface
-      R Um[3], Up[3], tmp[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Um[c] = R(0.5) * (sm.u[c][0][e - 1] + sm.u[c][0][e]);
-        Up[c] = R(0.5) * (sm.u[c][0][e] + sm.u[c][0][e + 1]);
+        for (int c = 0; c < C; ++c)
+          linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                       sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
+      } else {
+        hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
+                    sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
       }
-      char_faces(sm, e, Um, gam, eps, gas, L, tmp);
-      char_faces(sm, e, Up, gam, eps, gas, tmp, Rt);
+      phys_flux<R, C>(gas, L, fL);
+      phys_flux<R, C>(gas, Rt, fR);
+    } else {
+      // Default: both faces in the fields of the cell average (Remark 2).
+      // Variant: u^+_{i-1/2} in the fields of the mean of the averages of
+      // cells i-1, i; u^-_{i+1/2} in those of cells i, i+1.
+      const bool mean = a.variant & HWENO_VARIANT_MEAN_EIGEN;
+      for (int side = 0; side < (mean ? 2 : 1); ++side) {
+        R B[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          B[c] = !mean ? sm.u[c][0][e]
+                 : side ? R(0.5) * (sm.u[c][0][e] + sm.u[c][0][e + 1])
+                        : R(0.5) * (sm.u[c][0][e - 1] + sm.u[c][0][e]);
+        const ConsFaces<R> o = char_faces<R>(
+            gas, gam[0], gam[1], gam[2], eps, B[0], B[1], B[2], sm.u[0][0][e - 1],
+            sm.u[1][0][e - 1], sm.u[2][0][e - 1], sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e],
+            sm.u[0][0][e + 1], sm.u[1][0][e + 1], sm.u[2][0][e + 1], sm.vl[0][e - 2],
+            sm.vl[1][e - 2], sm.vl[2][e - 2], sm.vl[0][e - 1], sm.vl[1][e - 1], sm.vl[2][e - 1],
+            sm.vl[0][e], sm.vl[1][e], sm.vl[2][e]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          if (!mean || side == 0) {
+            L[c] = o.L[c];
+            fL[c] = o.fL[c];
+          }
+          if (!mean || side == 1) {
+            Rt[c] = o.Rt[c];
+            fR[c] = o.fR[c];
+          }
+        }
+      }
     }
-    R fL[C], fR[C];
-    phys_flux<R, C>(gas, L, fL);
-    phys_flux<R, C>(gas, Rt, fR);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       sm.fm[c][k] = L[c];

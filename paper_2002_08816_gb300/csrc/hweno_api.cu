@@ -735,7 +735,7 @@ hweno_status hweno_create_batch(const hweno_config* cfg, int n_batch, const int*
     bi.inv_dx_f = (float)bi.inv_dx;
     bi.hthr_f = (float)(c.kxrcf_threshold * bi.h);
     bi.cfl_dx_f = (float)bi.cfl_dx;
-    bi.pad = 0.0f;
+    bi.hthr_lo_f = (float)(c.kxrcf_threshold * bi.h - (double)bi.hthr_f);
     cells += nx[b];
   }
   cudaError_t e = cudaMalloc(&h->d_binst, sizeof(hw::BatchInst) * n_batch);

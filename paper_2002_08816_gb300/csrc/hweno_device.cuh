@@ -8,6 +8,30 @@
 
 namespace hw {
 
+// FP32 reciprocal and square root by the approximate PTX instructions
+// (rcp.approx, sqrt.approx, flushing subnormals: within about 1 ulp, ~20
+// cycles of latency on GB300 against 45-65 for the correctly rounded forms);
+// FP64 keeps the correctly rounded forms.  Zero gives +inf, a negative
+// square root NaN, as the non-physical-state checks expect.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+template <typename R>
+__device__ __forceinline__ R fast_rcp(R x) {
+  if constexpr (sizeof(R) == 4) return rcp_approx(x); else return R(1) / x;
+}
+template <typename R>
+__device__ __forceinline__ R fast_sqrt(R x) {
+  if constexpr (sizeof(R) == 4) return sqrt_approx(x); else return sqrt(x);
+}
+
 // bits of the device status word
 enum : unsigned { ST_NONFINITE = 1u, ST_NONPHYSICAL = 2u, ST_TIMEOUT = 4u };
 
@@ -110,18 +134,34 @@ struct Euler1D {
     F[1] = m * mu + p;
     F[2] = mu * (E + p);
   }
-  // Right (columns: mu-c, mu, mu+c) and left eigenvectors of dF/dU at U.
-  static __device__ __forceinline__ void eigen(R g, const R* U, R Rm[3][3], R Lm[3][3]) {
-    const R rho = U[0], mu = U[1] / U[0];
-    const R p = (g - R(1)) * (U[2] - R(0.5) * rho * mu * mu);
-    const R c = sqrt(g * p / rho);
-    const R H = (U[2] + p) / rho;
-    const R ic = R(1) / c;
+  // Velocity, pressure, sound speed, enthalpy and 1/c at U; FP32 with one
+  // approximate reciprocal of rho and an approximate square root.
+  static __device__ __forceinline__ void primitive(R g, const R* U, R& mu, R& p, R& c, R& H,
+                                                   R& ic) {
+    const R rho = U[0];
+    if constexpr (sizeof(R) == 4) {
+      const R ir = fast_rcp(rho);
+      mu = U[1] * ir;
+      p = (g - R(1)) * (U[2] - R(0.5) * rho * mu * mu);
+      c = fast_sqrt(g * p * ir);
+      H = (U[2] + p) * ir;
+      ic = fast_rcp(c);
+    } else {
+      mu = U[1] / U[0];
+      p = (g - R(1)) * (U[2] - R(0.5) * rho * mu * mu);
+      c = sqrt(g * p / rho);
+      H = (U[2] + p) / rho;
+      ic = R(1) / c;
+    }
+  }
+  // Left eigenvectors (rows) of dF/dU at U, and the velocity mu, sound speed
+  // c and enthalpy H that fix the right ones.
+  static __device__ __forceinline__ void left(R g, const R* U, R Lm[3][3], R& mu_, R& c_, R& H_) {
+    R mu, p, c, H, ic;
+    primitive(g, U, mu, p, c, H, ic);
+    const R rho = U[0];
     const R b1 = (g - R(1)) * ic * ic;
     const R b2 = R(0.5) * b1 * mu * mu;
-    Rm[0][0] = R(1);        Rm[0][1] = R(1);              Rm[0][2] = R(1);
-    Rm[1][0] = mu - c;      Rm[1][1] = mu;                Rm[1][2] = mu + c;
-    Rm[2][0] = H - mu * c;  Rm[2][1] = R(0.5) * mu * mu;  Rm[2][2] = H + mu * c;
     Lm[0][0] = R(0.5) * (b2 + mu * ic);
     Lm[0][1] = R(-0.5) * (b1 * mu + ic);
     Lm[0][2] = R(0.5) * b1;
@@ -131,6 +171,21 @@ struct Euler1D {
     Lm[2][0] = R(0.5) * (b2 - mu * ic);
     Lm[2][1] = R(-0.5) * (b1 * mu - ic);
     Lm[2][2] = R(0.5) * b1;
+    mu_ = mu;
+    c_ = c;
+    H_ = H;
+  }
+  // Right eigenvectors (columns: mu-c, mu, mu+c) from mu, c and H.
+  static __device__ __forceinline__ void right(R mu, R c, R H, R Rm[3][3]) {
+    Rm[0][0] = R(1);        Rm[0][1] = R(1);              Rm[0][2] = R(1);
+    Rm[1][0] = mu - c;      Rm[1][1] = mu;                Rm[1][2] = mu + c;
+    Rm[2][0] = H - mu * c;  Rm[2][1] = R(0.5) * mu * mu;  Rm[2][2] = H + mu * c;
+  }
+  // Right and left eigenvectors of dF/dU at U.
+  static __device__ __forceinline__ void eigen(R g, const R* U, R Rm[3][3], R Lm[3][3]) {
+    R mu, c, H;
+    left(g, U, Lm, mu, c, H);
+    right(mu, c, H, Rm);
   }
 };
 
@@ -138,10 +193,18 @@ struct Euler1D {
 template <typename R>
 __device__ __forceinline__ R euler1d_speed_r(R g, R rho, R m, R E) {
   if (!(rho > R(0))) return R(NAN);
-  const R mu = m / rho;
-  const R p = (g - R(1)) * (E - R(0.5) * m * mu);
-  if (!(p > R(0))) return R(NAN);
-  return fabs(mu) + sqrt(g * p / rho);
+  if constexpr (sizeof(R) == 4) {
+    const R ir = fast_rcp(rho);
+    const R mu = m * ir;
+    const R p = (g - R(1)) * (E - R(0.5) * m * mu);
+    if (!(p > R(0))) return R(NAN);
+    return fabs(mu) + fast_sqrt(g * p * ir);
+  } else {
+    const R mu = m / rho;
+    const R p = (g - R(1)) * (E - R(0.5) * m * mu);
+    if (!(p > R(0))) return R(NAN);
+    return fabs(mu) + sqrt(g * p / rho);
+  }
 }
 
 }  // namespace hw

@@ -15,7 +15,7 @@ struct BatchInst {
   int n;                   // cells
   int first_tile;          // first tile of the instance
   double inv_dx, h, cfl_dx;
-  float inv_dx_f, hthr_f, cfl_dx_f, pad;
+  float inv_dx_f, hthr_f, cfl_dx_f, hthr_lo_f;
 };
 
 // Time bookkeeping of one instance.
@@ -58,6 +58,7 @@ struct Stage1DArgs {
   double h;              // dx / 2, the KXRCF cell size
   double cfl_dx;         // cfl * dx
   float hthr;            // (float)(thr * h)
+  float hthr_lo;         // (float)(thr * h - hthr): thr * h = hthr + hthr_lo to ~2^-48
   float f32[7];          // FP32 copies: gamma_0..2, eps, gas_gamma, 1/dx, cfl*dx
   // batches of independent instances (nullable): tile -> instance, first cell
   const int* tile_inst;
@@ -72,6 +73,7 @@ inline void finish_stage_args(Stage1DArgs& a) {
   a.h = 0.5 * a.dx;
   a.cfl_dx = a.cfl * a.dx;
   a.hthr = (float)(a.thr * a.h);
+  a.hthr_lo = (float)(a.thr * a.h - (double)a.hthr);
   a.f32[0] = (float)a.gam[0];
   a.f32[1] = (float)a.gam[1];
   a.f32[2] = (float)a.gam[2];

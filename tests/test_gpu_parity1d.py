@@ -49,6 +49,51 @@ def _compare_rhs(system, nx, bc, prec, mode, seed, u=None, x0=0.0, x1=1.0):
     return fl_o
 
 
+def _near_threshold_walk(nx, thr, h, seed):
+    """Cell averages built cell by cell so that the KXRCF indicator of every
+    cell (left inflow face: u >= 0) is thr (1 + delta), |delta| log-uniform in
+    [1e-5, 0.3] on either side: the zone where an FP32 evaluation alone cannot
+    decide the flag, yet outside the 1e-6 band where the flag may differ.  The
+    jump (u_i - 6 v_i) - (u_{i-1} + 6 v_{i-1}) = s k u_i, k = thr h (1 + delta),
+    fixes u_i from u_{i-1} and the moments."""
+    rng = np.random.default_rng(seed)
+    delta = rng.choice([-1.0, 1.0], nx) * 10.0 ** rng.uniform(-5.0, np.log10(0.3), nx)
+    sgn = rng.choice([-1.0, 1.0], nx)
+    v = rng.uniform(-0.05, 0.05, nx) * h
+    u = np.empty(nx)
+    u[0] = 1.0
+    for i in range(1, nx):
+        k = thr * h * (1.0 + delta[i])
+        u[i] = (u[i - 1] + 6.0 * (v[i - 1] + v[i])) / (1.0 - sgn[i] * k)
+    return u, v
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["burgers", "euler-rho", "euler-E"])
+def test_flags_near_threshold(prec, case):
+    """Most cells' indicators within 30 % of the threshold (the FP32 kernel
+    then decides with its error-free float-pair evaluation, the FP64 kernel
+    as the oracle does): flags bit-exact outside the 1e-6 band."""
+    nx = 4096
+    system = H.HWENO_BURGERS if case == "burgers" else H.HWENO_EULER
+    cfg, ocfg = make_pair(system, nx, 0.0, 1.0, H.HWENO_BC_OUTFLOW, prec)
+    thr, h = ocfg.kxrcf_threshold, 0.5 / nx
+    w, v = _near_threshold_walk(nx, thr, h, seed=len(case) + 7 * prec)
+    if system == H.HWENO_BURGERS:
+        u = np.stack([w, v])[None]
+    else:
+        flat, zero = np.full(nx, 2.5), np.zeros(nx)
+        rho, vr, E, vE = (w, v, flat, zero) if case == "euler-rho" else (flat, zero, w, v)
+        u = np.stack([np.stack([rho, vr]), np.stack([0.1 * rho, 0.1 * vr]), np.stack([E, vE])])
+    u = round_to(prec, u)
+    _, _, fl_o, ind = O.rhs1d(ocfg, u)
+    rel = np.abs(ind / thr - 1.0)
+    zone = (rel > 1e-6) & (rel < 0.3)
+    assert zone.sum() > 0.8 * nx, zone.sum()
+    assert 0.2 * nx < fl_o.sum() < 0.8 * nx
+    _compare_rhs(system, nx, H.HWENO_BC_OUTFLOW, prec, H.HWENO_TROUBLED_HYBRID, seed=0, u=u)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("bc", [H.HWENO_BC_PERIODIC, H.HWENO_BC_OUTFLOW])
 @pytest.mark.parametrize("nx", SIZES)
