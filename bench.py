@@ -38,13 +38,17 @@ UNIT = "cell-stages/s"
 # stages 2 and 3 read u^n and u^(k) and write (3S); mean 8S/3 with
 # S = 3 components x 2 moments x sizeof(real)
 BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
-# DRAM bytes (read + write) per stage launch from ncu captures of the current
-# kernels (profiles/stage1d_euler65536_fp32.md: mean over the three stages at
-# the bench's 65536 cells; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled
-# by the cell count to 4096^2)
-TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3203584 + 1626368 + 3198208) / 3,
-                   (256, "per-stage graphs"): (3203328 + 1625344 + 256 + 3198208 + 512) / 3,
-                   (512, "per-stage graphs"): (3203072 + 1625344 + 3198720) / 3}
+# DRAM bytes (read + write) per stage from ncu captures of the current kernels
+# (profiles/stage1d_euler65536_fp32.md: per-stage launches, mean over the three
+# stages at the bench's 65536 cells, cold L2; the persistent launch, its bytes
+# over its 6000 stages; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled by
+# the cell count to 4096^2)
+TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3187968 + 256 + 1609472 + 3183616 + 512) / 3,
+                   (256, "per-stage graphs"): (3180800 + 1607936 + 3181056) / 3,
+                   (512, "per-stage graphs"): (3180800 + 1607936 + 3181056) / 3,
+                   # one persistent launch of 2000 steps: the state stays in L2
+                   (256, "persistent"): (2261248 + 202752) / 6000,
+                   (128, "persistent"): (2078208 + 192256) / 6000}
 TRAFFIC_2D_NG2 = 4 * (403.311616e6 + 178.976512e6)
 L2_FLUSH_BYTES = 512 << 20
 
@@ -323,6 +327,7 @@ def bench_hweno(args):
             field_err["%s_%s" % (name, mom)] = {
                 "L1": float(d.mean()), "Linf": float(d.max()),
                 "rel_L1": float(d.sum() / max(np.abs(a64[c, m]).sum(), 1e-300))}
+    persistent = r["execution"]["launch"] == "persistent"
     per_launch = BYTES_PER_CELL_STAGE["fp32"] * NX
     achieved = per_launch / (r["stage_us"] * 1e-6) / 1e9
     line = {
@@ -342,12 +347,19 @@ def bench_hweno(args):
                      "frac": achieved / peak,
                      "traffic": TRAFFIC_1D_FP32.get((r["execution"]["threads_per_cta"],
                                                      r["execution"]["launch"])),
-                     "kernel": "stage1d_kernel<float,3,%d threads>" % r["execution"]["threads_per_cta"],
-                     "note": "avg stage-launch time = timed region / 6000 launches; peak %s" % peak_kind},
+                     "kernel": "%s<float,3,%d threads>" % (
+                         "run1d_kernel" if persistent else "stage1d_kernel",
+                         r["execution"]["threads_per_cta"]),
+                     "note": ("avg stage time = timed region / 6000 stages (one persistent launch "
+                              "per step, traffic per stage) " if persistent else
+                              "avg stage-launch time = timed region / 6000 launches ")
+                             + "; peak %s" % peak_kind},
         "cpu_baseline": cpu,
         "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["bytes_h2d"],
                 "d2h_bytes_per_step": r["bytes_h2d"]},
-        "gpu_launches": args.steps * (3 * RK_STEPS + 4),
+        # per step: alpha, convert and two scalar resets, plus the stage
+        # launches or the one persistent launch
+        "gpu_launches": args.steps * ((1 if persistent else 3 * RK_STEPS) + 4),
         "clocks": r["clocks"],
     }
     print(json.dumps(line))

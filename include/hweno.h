@@ -219,8 +219,9 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
  * launch per hweno_step call (every CTA walks its tiles of a stage, then the
  * grid meets at a barrier whose wait is bounded), each with 128, 256 or 512
  * threads per CTA (a tile is that number minus 6 cells).  Each of the six
- * candidates advances the current state nsteps_trial steps, timed with CUDA
- * events on the handle's stream, and the fastest is kept for later calls; the
+ * candidates advances the current state nsteps_trial steps once untimed (which
+ * builds its graphs) and then twice timed with CUDA events on the handle's
+ * stream; the one with the fastest trial is kept for later calls; the
  * state, time, counters and wave-speed slots are restored afterwards.  The
  * per-stage candidates give bitwise the same results; the persistent ones
  * agree with them to rounding (their copy of the stage body may contract a few

@@ -38,7 +38,9 @@ def main():
     ap.add_argument("--n-gauss", type=int, default=2, choices=[2, 3])
     ap.add_argument("--adjoint", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, choices=[0, 128, 256, 512],
-                    help="1D: threads per CTA of the per-stage kernels (0: the default)")
+                    help="1D: threads per CTA (0: the default)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="1D: one persistent launch with grid barriers instead of per-stage graphs")
     args = ap.parse_args()
     B.build()
     prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
@@ -58,8 +60,8 @@ def main():
     dev = torch.from_numpy(u).to("cuda", dt).contiguous()
     h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
-        if args.threads and args.dim == 1:
-            H.hweno_set_execution(h, args.threads, False)
+        if (args.threads or args.persistent) and args.dim == 1:
+            H.hweno_set_execution(h, args.threads or 256, args.persistent)
         H.hweno_set_state(h, dev.data_ptr(), prec, True)
         if args.adjoint > 0:
             t = H.hweno_record(h, args.rk_steps, args.adjoint)
