@@ -65,14 +65,17 @@ __device__ __forceinline__ double jump64(double u0, double v0, double unb, doubl
 
 // u0/v0/w0 the cell, (uxn, vxn) its inflow x-neighbour, (uyn, wyn) its inflow
 // y-neighbour; lowx / lowy: the inflow faces are the left / bottom ones.
+// Every argument by value: a reference to the launch's parameter block would
+// make each thread copy that block to local memory.
 __device__ __noinline__ bool kxrcf2_troubled64(double u0, double v0, double w0, double uxn,
                                                double vxn, double uyn, double wyn, bool lowx,
-                                               bool lowy, const Kx2& k) {
+                                               bool lowy, double dx, double dy, double den_h,
+                                               double thr) {
   const double jx = jump64(u0, v0, uxn, vxn, lowx);
   const double jy = jump64(u0, w0, uyn, wyn, lowy);
-  const double num = __dadd_rn(__dmul_rn(k.dy, jx), __dmul_rn(k.dx, jy));
+  const double num = __dadd_rn(__dmul_rn(dy, jx), __dmul_rn(dx, jy));
   const double nrm = fmax(fabs(u0), 1e-12);
-  return fabs(num) / __dmul_rn(k.den_h, nrm) > k.thr;
+  return fabs(num) / __dmul_rn(den_h, nrm) > thr;
 }
 
 __device__ __forceinline__ bool kxrcf2_troubled(float u0, float v0, float w0, float uxn, float vxn,
@@ -89,13 +92,14 @@ __device__ __forceinline__ bool kxrcf2_troubled(float u0, float v0, float w0, fl
   if (num - e > r * (1.0f + 4.8e-7f)) return true;
   if (num + e < r * (1.0f - 4.8e-7f)) return false;
   return kxrcf2_troubled64((double)u0, (double)v0, (double)w0, (double)uxn, (double)vxn,
-                           (double)uyn, (double)wyn, lowx, lowy, k);
+                           (double)uyn, (double)wyn, lowx, lowy, k.dx, k.dy, k.den_h, k.thr);
 }
 
 __device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0, double uxn,
                                                 double vxn, double uyn, double wyn, bool lowx,
                                                 bool lowy, const Kx2& k) {
-  return kxrcf2_troubled64(u0, v0, w0, uxn, vxn, uyn, wyn, lowx, lowy, k);
+  return kxrcf2_troubled64(u0, v0, w0, uxn, vxn, uyn, wyn, lowx, lowy, k.dx, k.dy, k.den_h,
+                           k.thr);
 }
 
 // The 19 data of component c of the cell at own-tile coordinates (ci, cj):
@@ -127,9 +131,11 @@ __device__ __forceinline__ void store_point(S& sm, int c, int p, int ci, int cj,
 // interface points [p_lo, p_hi) by HWENO in the x (x-faces) and y (y-faces)
 // characteristic fields of the cell average (Remark 4).  Rare: out of line.
 template <int NG, typename S, typename R>
-__device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo, int p_hi,
-                                                 const R* gam, R eps, R gas, bool mean_eigen) {
+__device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo, int p_hi, R g0,
+                                                 R g1, R g2, R g3, R g4, R eps, R gas,
+                                                 bool mean_eigen) {
   constexpr int NF = 4 * NG;
+  const R gam[5] = {g0, g1, g2, g3, g4};  // by value: no caller array on the stack
   R Uc[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) Uc[c] = sm.u[c][0][cj + 3][ci + 3];
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
                                             sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
                                             sm.u[0][2][ry + 1][rx], gam, eps);
     } else {
-      limit_euler2d(sm, lx, ly, gam, eps, gas);
+      limit_euler2d(sm, lx, ly, gam[0], gam[1], gam[2], gam[3], gam[4], eps, gas);
     }
   }
   __syncthreads();
@@ -366,8 +372,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
           if (p >= p_lo && p < p_hi) store_point(sm, c, p, ci, cj, v[p]);
       }
     } else if constexpr (C == 4) {
-      hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam, eps, gas,
-                              (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
+      hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam[0], gam[1], gam[2], gam[3], gam[4],
+                              eps, gas, (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
     }
   }
   __syncthreads();

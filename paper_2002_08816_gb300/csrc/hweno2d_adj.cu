@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
                                             sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
                                             sm.u[0][2][ry + 1][rx], P_.gam, P_.eps);
     } else {
-      limit_euler2d(sm, lx, ly, P_.gam, P_.eps, P_.gas);
+      limit_euler2d(sm, lx, ly, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4], P_.eps,
+                    P_.gas);
     }
   }
   __syncthreads();

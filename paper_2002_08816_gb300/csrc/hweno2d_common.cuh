@@ -16,7 +16,7 @@ template <typename R>
 struct Euler2D {
   static __device__ __forceinline__ void flux(R g, const R* U, int dir, R* F) {
     const R rho = U[0], m = U[1], n = U[2], E = U[3];
-    const R ir = sizeof(R) == 4 ? R(__frcp_rn((float)rho)) : R(1) / rho;
+    const R ir = fast_rcp(rho);  // FP32: approximate; FP64: 1 / rho
     const R mu = sizeof(R) == 4 ? m * ir : m / rho;
     const R nu = sizeof(R) == 4 ? n * ir : n / rho;
     const R p = (g - R(1)) * (E - R(0.5) * (m * mu + n * nu));
@@ -29,12 +29,17 @@ struct Euler2D {
   // Right (columns: v-c, v, v, v+c with v the normal velocity) and left
   // eigenvectors of dF/dU (dir 0) or dG/dU (dir 1) at U.
   static __device__ __forceinline__ void eigen(R g, const R* U, int dir, R Rm[4][4], R Lm[4][4]) {
-    const R rho = U[0], mu = U[1] / rho, nu = U[2] / rho;
+    // FP32 with one approximate reciprocal of rho and an approximate square
+    // root; FP64 correctly rounded
+    const R rho = U[0];
+    const R ir = sizeof(R) == 4 ? fast_rcp(rho) : R(1);
+    const R mu = sizeof(R) == 4 ? U[1] * ir : U[1] / rho;
+    const R nu = sizeof(R) == 4 ? U[2] * ir : U[2] / rho;
     const R q2 = mu * mu + nu * nu;
     const R p = (g - R(1)) * (U[3] - R(0.5) * rho * q2);
-    const R c = sqrt(g * p / rho);
-    const R H = (U[3] + p) / rho;
-    const R ic = R(1) / c;
+    const R c = sizeof(R) == 4 ? fast_sqrt(g * p * ir) : sqrt(g * p / rho);
+    const R H = sizeof(R) == 4 ? (U[3] + p) * ir : (U[3] + p) / rho;
+    const R ic = fast_rcp(c);
     const R b1 = (g - R(1)) * ic * ic;
     const R b2 = R(0.5) * b1 * q2;
     const R vn = dir == 0 ? mu : nu;
@@ -92,13 +97,15 @@ __device__ __forceinline__ void wave_speeds2(R gas, const R* U, R& sx, R& sy) {
       sx = sy = R(NAN);
       return;
     }
-    const R mu = U[1] / rho, nu = U[2] / rho;
+    const R ir = sizeof(R) == 4 ? fast_rcp(rho) : R(1);
+    const R mu = sizeof(R) == 4 ? U[1] * ir : U[1] / rho;
+    const R nu = sizeof(R) == 4 ? U[2] * ir : U[2] / rho;
     const R p = (gas - R(1)) * (U[3] - R(0.5) * rho * (mu * mu + nu * nu));
     if (!(p > R(0))) {
       sx = sy = R(NAN);
       return;
     }
-    const R c = sqrt(gas * p / rho);
+    const R c = sizeof(R) == 4 ? fast_sqrt(gas * p * ir) : sqrt(gas * p / rho);
     sx = fabs(mu) + c;
     sy = fabs(nu) + c;
   }
@@ -145,14 +152,16 @@ __device__ __forceinline__ void hweno2d_faces(const R* d, const R* gam, R eps, i
   b[4] = hw2::beta_q4(d);
   const R s = R(0.25) * (fabs(b[0] - b[1]) + fabs(b[0] - b[2]) + fabs(b[0] - b[3]) + fabs(b[0] - b[4]));
   const R tau = s * s;
+  // FP32: approximate reciprocals (the weights need a few ulp, not IEEE
+  // rounding); FP64: correctly rounded quotients
   R a[5], sum = R(0);
 #pragma unroll
   for (int n = 0; n < 5; ++n) {
-    a[n] = gam[n] * (R(1) + tau / (b[n] + eps));
+    a[n] = gam[n] * (R(1) + (sizeof(R) == 4 ? tau * fast_rcp(b[n] + eps) : tau / (b[n] + eps)));
     sum += a[n];
   }
-  const R inv = R(1) / sum;
-  const R c0 = a[0] * inv / gam[0];
+  const R inv = fast_rcp(sum);
+  const R c0 = sizeof(R) == 4 ? a[0] * inv * fast_rcp(gam[0]) : a[0] * inv / gam[0];
   R tmp[NF];
   p0_faces<NG>(d, tmp);
 #pragma unroll
@@ -173,7 +182,9 @@ __device__ __forceinline__ void hweno2d_faces(const R* d, const R* gam, R eps, i
 // the y fields, with the 1D Step 1 formula.  Rare: kept out of line so that
 // its registers do not weigh on the common path.
 template <typename S, typename R>
-__device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, const R* gam, R eps, R gas) {
+__device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, R g0, R g1, R g2, R g3, R g4,
+                                           R eps, R gas) {
+  const R gam[5] = {g0, g1, g2, g3, g4};  // by value: no caller array on the stack
   const int rx = lx + 1, ry = ly + 1;
   R U[4];
 #pragma unroll
