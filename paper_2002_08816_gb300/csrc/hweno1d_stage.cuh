@@ -20,9 +20,9 @@
 //   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
 //      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
 //      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
-//   5. the tile's maximum wave speed of the output, folded by an atomic max
-//      into one of kAlphaSlots slots that the next stage reads for its alpha,
-//      and the status bits (non-finite, non-physical).
+//   5. each warp's maximum wave speed of the output, folded by an atomic max
+//      into the tile's one of kAlphaSlots slots that the next stage reads for
+//      its alpha, and the status bits (non-finite, non-physical).
 // The limited stage input is what the RK combination uses (the first moment
 // of a troubled cell is modified in the state, as a DG limiter would).
 #pragma once
@@ -38,6 +38,8 @@ namespace hw {
 namespace s1d {
 
 constexpr int H = 3;  // halo cells per side
+// grids of at most this many tiles fold the wave-speed maxima warp by warp
+constexpr int kWarpAtomicTiles = 2048;
 
 // A load of data another CTA may have written earlier in the same launch
 // (the persistent kernel): through L2, never from a stale L1 line.
@@ -236,6 +238,23 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
     else if (a.stage > 1)
       dt_prev = sizeof(R) == 4 ? R(ldx(&a.sc->dt_f)) : R(ldx(&a.sc->dt));
   }
+  // the time bookkeeping's inputs (stage 3, the last thread of the lead
+  // tile), fetched with the rest: its FP64 update then costs no round trip
+  const bool keeper = a.stage == 3 && lead && tid == NT - 1;
+  double bk_tf = 0.0, bk_t = 0.0;
+  unsigned bk_last = 0u;
+  unsigned long long bk_steps = 0ull;
+  if (keeper) {
+    bk_tf = ldx(&a.sc->t_final);
+    bk_steps = ldx(&a.sc->steps);
+    if constexpr (BATCH) {
+      bk_last = ldx(&a.bsc[inst].last);
+      bk_t = ldx(&a.bsc[inst].t);
+    } else {
+      bk_last = ldx(&a.sc->last);
+      bk_t = ldx(&a.sc->t);
+    }
+  }
   R u0c[C][2];
   if (a.stage >= 2 && tid < T && base + tid < n) {
     const R* u0 = static_cast<const R*>(a.u0);
@@ -407,26 +426,24 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
   __syncthreads();
 
   // time bookkeeping (FP64) by a thread that has no cell in phase 5
-  if (a.stage == 3 && lead && tid == NT - 1) {
+  if (keeper) {
     DevScalars* sc = a.sc;
-    const double tf = ldx(&sc->t_final);
+    const double tf = bk_tf;
+    const double t = bk_last ? tf : bk_t + (double)dt;
+    const double r = tf > 0.0 ? tf - t : (double)INFINITY;
     if constexpr (BATCH) {
       BatchScalars& bs = a.bsc[inst];
-      const double t = ldx(&bs.last) ? tf : ldx(&bs.t) + (double)dt;
-      const double r = tf > 0.0 ? tf - t : (double)INFINITY;
       bs.t = t;
       bs.dt = (double)dt;
       bs.rem = r;
       bs.rem_f = (float)r;
-      if (inst == 0) sc->steps += 1;
+      if (inst == 0) sc->steps = bk_steps + 1ull;
     } else {
-      const double t = ldx(&sc->last) ? tf : ldx(&sc->t) + (double)dt;
-      const double r = tf > 0.0 ? tf - t : (double)INFINITY;
       sc->t = t;
       sc->dt = (double)dt;
       sc->rem = r;
       sc->rem_f = (float)r;
-      sc->steps += 1;
+      sc->steps = bk_steps + 1ull;
     }
   }
   static_assert(T < NT, "a thread without a cell keeps the time");
@@ -505,16 +522,28 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       }
     }
   }
-  // 6. epilogue: partial max for the next alpha (a max is exact in any
-  //    precision; the tile's maximum is stored as FP64), troubled count, status
+  // 6. epilogue: the maximum wave speed of the output into the tile's slot
+  //    for the next alpha (a maximum does not depend on the order of the
+  //    atomics), the troubled count, the status bits.  Batches and grids of up
+  //    to kWarpAtomicTiles tiles fold each warp's values directly (no CTA
+  //    barrier on the latency-bound path); larger grids reduce over the CTA
+  //    first, so that the slots' atomic queues stay short.
   R wmax = speed;
   for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
   const int wcnt = __popc(__ballot_sync(0xffffffffu, myflag));
+  if (bad) atomicOr(&a.sc->status, bad);
+  R* const slot = static_cast<R*>(a.a_out) + (BATCH ? inst : tile % kAlphaSlots);
+  if (BATCH || a.ntile <= kWarpAtomicTiles) {
+    if (lane == 0) {
+      if (a.a_out) atomic_max_nonneg(slot, wmax);
+      if (wcnt) atomicAdd(&a.sc->troubled, (unsigned long long)wcnt);
+    }
+    return;
+  }
   if (lane == 0) {
     sm.red[warp] = wmax;
     sm.cnt[warp] = wcnt;
   }
-  if (bad) atomicOr(&a.sc->status, bad);
   __syncthreads();
   if (warp == 0) {
     R m = lane < NW ? sm.red[lane] : R(0);
@@ -524,8 +553,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-      if (a.a_out)
-        atomic_max_nonneg(static_cast<R*>(a.a_out) + (BATCH ? inst : tile % kAlphaSlots), m);
+      if (a.a_out) atomic_max_nonneg(slot, m);
       if (c) atomicAdd(&a.sc->troubled, (unsigned long long)c);
     }
   }
