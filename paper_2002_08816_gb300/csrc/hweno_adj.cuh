@@ -26,14 +26,15 @@ struct NLWeights {
     for (int n = 1; n < N; ++n) t += fabs(b[0] - b[n]);
     s = sfac * t;
     tau = s * s;
+    // FP32: approximate reciprocals, as the forward kernels' weights
     R sum = R(0);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
-      a[n] = gam[n] * (R(1) + tau / (b[n] + eps));
+      a[n] = gam[n] * (R(1) + (sizeof(R) == 4 ? tau * fast_rcp(b[n] + eps) : tau / (b[n] + eps)));
       sum += a[n];
     }
-    inv = R(1) / sum;
-    c[0] = a[0] * inv / gam[0];
+    inv = fast_rcp(sum);
+    c[0] = sizeof(R) == 4 ? a[0] * inv * fast_rcp(gam[0]) : a[0] * inv / gam[0];
 #pragma unroll
     for (int n = 1; n < N; ++n) c[n] = a[n] * inv - c[0] * gam[n];
   }
@@ -47,14 +48,15 @@ struct NLWeights {
       linv += lc[n] * a[n];
       lc0 -= lc[n] * gam[n];
     }
-    la[0] = lc0 * inv / gam[0];
-    linv += lc0 * a[0] / gam[0];
+    const R ig0 = fast_rcp(gam[0]);
+    la[0] = sizeof(R) == 4 ? lc0 * inv * ig0 : lc0 * inv / gam[0];
+    linv += sizeof(R) == 4 ? lc0 * a[0] * ig0 : lc0 * a[0] / gam[0];
     const R lsum = -linv * inv * inv;
     R ltau = R(0);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
       la[n] += lsum;
-      const R ib = R(1) / (b[n] + eps);
+      const R ib = fast_rcp(b[n] + eps);
       ltau += la[n] * gam[n] * ib;
       lb[n] -= la[n] * gam[n] * tau * ib * ib;
     }
@@ -181,7 +183,7 @@ __device__ __forceinline__ void flux_jt2(R gas, const R* U, int dir, const R* l,
   if constexpr (C == 1) {
     o[0] = U[0] * l[0];
   } else {
-    const R ir = R(1) / U[0];
+    const R ir = fast_rcp(U[0]);  // FP32: approximate, as the forward flux
     const R u = U[1] * ir, v = U[2] * ir;
     const R g1 = gas - R(1);
     const R kq = g1 * R(0.5) * (u * u + v * v);
