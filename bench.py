@@ -339,7 +339,8 @@ def bench_hweno(args):
                    "seed": SEED, "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": "one independent instance per GPU"},
         "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
-                 "e2e": results["fp64"]["e2e"]},
+                 "e2e": results["fp64"]["e2e"], "execution": results["fp64"]["execution"],
+                 "bound": "FP64 pipe (profiles/stage1d_euler65536_fp64.md)"},
         "troubled_frac": r["troubled_frac"],
         "fp32_vs_fp64": field_err,
         "execution": r["execution"],

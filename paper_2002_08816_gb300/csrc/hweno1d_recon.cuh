@@ -132,7 +132,8 @@ __device__ __forceinline__ void hweno_faces(R um, R u0, R up, R vm, R v0, R vp, 
 // al. with the degree-1 cell polynomial ubar + 12 vbar (x - x_i)/dx, h = dx/2,
 // the inflow face chosen by the sign of the velocity, normalised by
 // max(|ubar_i|, 1e-12)): troubled iff |jump| / (h max(|u0|, 1e-12)) > thr.
-// The FP64 form is evaluated without contraction.
+// The FP64 form is evaluated without contraction, as the product form
+// |jump| > thr h max(|u0|, 1e-12).
 __device__ __forceinline__ bool kxrcf_troubled(double um, double u0, double up, double vm,
                                                double v0, double vp, bool left, double h,
                                                double thr, float /*hthr*/, float /*hthr_lo*/) {
@@ -141,8 +142,11 @@ __device__ __forceinline__ bool kxrcf_troubled(double um, double u0, double up, 
     jump = __dsub_rn(__dsub_rn(u0, __dmul_rn(6.0, v0)), __dadd_rn(um, __dmul_rn(6.0, vm)));
   else
     jump = __dsub_rn(__dadd_rn(u0, __dmul_rn(6.0, v0)), __dsub_rn(up, __dmul_rn(6.0, vp)));
+  // |jump| / (h nrm) > thr without the divide (FP64 divides occupy the FP64
+  // pipe for many cycles): the decision differs from the quotient form only
+  // within a few ulp of the threshold
   const double nrm = fmax(fabs(u0), 1e-12);
-  return fabs(jump) / __dmul_rn(h, nrm) > thr;
+  return fabs(jump) > __dmul_rn(thr, __dmul_rn(h, nrm));
 }
 
 // s + e = a + b exactly (Knuth's two-sum); the intrinsics keep the compiler

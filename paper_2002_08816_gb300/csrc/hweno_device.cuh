@@ -200,10 +200,11 @@ __device__ __forceinline__ R euler1d_speed_r(R g, R rho, R m, R E) {
     if (!(p > R(0))) return R(NAN);
     return fabs(mu) + fast_sqrt(g * p * ir);
   } else {
-    const R mu = m / rho;
+    const R ir = R(1) / rho;  // one divide for both quotients
+    const R mu = m * ir;
     const R p = (g - R(1)) * (E - R(0.5) * m * mu);
     if (!(p > R(0))) return R(NAN);
-    return fabs(mu) + sqrt(g * p / rho);
+    return fabs(mu) + sqrt(g * p * ir);
   }
 }
 
