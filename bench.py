@@ -43,12 +43,12 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
 # stages at the bench's 65536 cells, cold L2; the persistent launch, its bytes
 # over its 6000 stages; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled by
 # the cell count to 4096^2)
-TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3187968 + 256 + 1609472 + 3183616 + 512) / 3,
-                   (256, "per-stage graphs"): (3180800 + 1607936 + 3181056) / 3,
-                   (512, "per-stage graphs"): (3180800 + 1607936 + 3181056) / 3,
+TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3188992 + 256 + 1611008 + 3184640 + 1024) / 3,
+                   (256, "per-stage graphs"): (3181568 + 1608448 + 3181312) / 3,
+                   (512, "per-stage graphs"): (3181568 + 1608448 + 3181312) / 3,
                    # one persistent launch of 2000 steps: the state stays in L2
-                   (256, "persistent"): (2261248 + 202752) / 6000,
-                   (128, "persistent"): (2078208 + 192256) / 6000}
+                   (256, "persistent"): (2301696 + 280064) / 6000,
+                   (128, "persistent"): (2735360 + 475904) / 6000}
 TRAFFIC_2D_NG2 = 4 * (403589632 + 178616832 + 403410432 + 179490304) / 2
 L2_FLUSH_BYTES = 512 << 20
 
