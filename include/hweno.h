@@ -232,6 +232,21 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
  * handles, HWENO_ERR_STATE before set_state. */
 hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
 
+/* Failure-detection self-test of the grid barrier the persistent launch uses
+ * between stages (no counterpart in the paper).  ctas co-resident CTAs of 128
+ * threads (a cooperative launch) meet `meetings` times; each meeting waits for
+ * ctas + missing arrivals, polling a counter in device memory at most `polls`
+ * times.  With missing = 0 every meeting completes and the result is HWENO_OK;
+ * with missing > 0 nothing ever supplies the extra arrivals, so every wait runs
+ * out, each CTA records the timeout in a status word and returns, and the result
+ * is HWENO_ERR_TIMEOUT: the context stays usable (the persistent launch ends
+ * the same way, within about a second, when an arrival is lost).  The library
+ * allocates and frees its own device memory and stream; waits for completion.
+ * HWENO_ERR_ARG unless 1 <= ctas <= 1024, 1 <= meetings <= 1e6,
+ * 0 <= missing <= 1024 and polls >= 1 (checked before any CUDA call), or when
+ * ctas CTAs cannot all be resident.  The error text is hweno_last_error(NULL). */
+hweno_status hweno_check_barrier(int ctas, int meetings, int missing, unsigned polls);
+
 /* Sets the choice hweno_autotune makes by hand: threads per CTA (128, 256 or
  * 512) and persistent (1) or per-stage graph launches (0).  1D handles only;
  * waits for the stream. */

@@ -50,7 +50,11 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 // each CTA publishes its writes (fence), adds its arrival without waiting for
 // a reply, and polls; nobody resets the counter or bumps a generation, which
 // would put two more round trips to L2 on the last arriver's path.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, DevScalars* sc) {
+// At most `limit` polls: the persistent kernel passes kBarrierPolls (about a
+// second of polling); a CTA whose wait runs out sets ST_TIMEOUT and returns,
+// so that a lost arrival ends the launch with a status the host reads.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, DevScalars* sc,
+                                          unsigned limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -59,7 +63,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, DevSca
     atomicAdd(bar, 1u);
     unsigned it = 0;
     while (static_cast<int>(ld_acquire_gpu(bar) - target) < 0) {
-      if (++it == (1u << 24)) {
+      if (++it >= limit) {
         atomicOr(&sc->status, (unsigned)ST_TIMEOUT);
         good = 0;
         break;
@@ -70,6 +74,21 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned target, DevSca
   }
   __syncthreads();
   return ok != 0;
+}
+
+constexpr unsigned kBarrierPolls = 1u << 21;  // ~0.5-1 us a poll: about a second
+
+// Self-test of grid_sync: `meetings` meetings of the grid, each waiting for
+// gridDim.x + missing arrivals (missing > 0: arrivals that never come, so every
+// wait runs out after `limit` polls).
+__global__ void __launch_bounds__(128) barrier_check_kernel(unsigned* bar, int meetings,
+                                                            unsigned missing, unsigned limit,
+                                                            DevScalars* sc) {
+  unsigned meet = 0;
+  for (int m = 0; m < meetings; ++m) {
+    meet += gridDim.x + missing;
+    if (!grid_sync(bar, meet, sc, limit)) return;
+  }
 }
 
 template <typename R, int C, bool BATCH, int NTH>
@@ -94,7 +113,7 @@ __global__ void __launch_bounds__(NTH) run1d_kernel(Run1DArgs r) {
         __syncthreads();
       }
       meet += gridDim.x;
-      if (!grid_sync(r.bar, meet, r.a.sc)) return;
+      if (!grid_sync(r.bar, meet, r.a.sc, kBarrierPolls)) return;
     }
   }
 }
@@ -319,6 +338,24 @@ cudaError_t run1d_max_ctas(int system, int fp64, int batch, int nth, int* ctas) 
 cudaError_t launch_run1d(const Run1DArgs& r, cudaStream_t s) {
   if (r.a.system == 0) return r.a.fp64 ? run_c<double, 1>(r, s) : run_c<float, 1>(r, s);
   return r.a.fp64 ? run_c<double, 3>(r, s) : run_c<float, 3>(r, s);
+}
+
+cudaError_t launch_barrier_check(int ctas, int meetings, int missing, unsigned polls,
+                                 unsigned* bar, DevScalars* sc, cudaStream_t s, bool* too_many) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, barrier_check_kernel, 128, 0);
+  if (e != cudaSuccess) return e;
+  *too_many = ctas > per * nsm;
+  if (*too_many) return cudaSuccess;
+  e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  unsigned um = (unsigned)missing;
+  void* args[] = {&bar, &meetings, &um, &polls, &sc};
+  return cudaLaunchCooperativeKernel((const void*)barrier_check_kernel, dim3(ctas), dim3(128),
+                                     args, 0, s);
 }
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s) {

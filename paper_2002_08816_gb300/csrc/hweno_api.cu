@@ -1091,6 +1091,38 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
   return st;
 }
 
+hweno_status hweno_check_barrier(int ctas, int meetings, int missing, unsigned polls) {
+  if (ctas < 1 || ctas > 1024 || meetings < 1 || meetings > 1000000 || missing < 0 ||
+      missing > 1024 || polls < 1u)
+    return fail(nullptr, HWENO_ERR_ARG,
+                "hweno_check_barrier: need 1 <= ctas <= 1024, 1 <= meetings <= 1e6, "
+                "0 <= missing <= 1024, polls >= 1");
+  unsigned* bar = nullptr;
+  hw::DevScalars* sc = nullptr;
+  cudaStream_t s = nullptr;
+  bool too_many = false;
+  hw::DevScalars host;
+  memset(&host, 0, sizeof(host));
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&bar), 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sc), sizeof(hw::DevScalars));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc, 0, sizeof(hw::DevScalars), s);
+  if (e == cudaSuccess)
+    e = hw::launch_barrier_check(ctas, meetings, missing, polls, bar, sc, s, &too_many);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, sc, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (s) cudaStreamDestroy(s);
+  if (sc) cudaFree(sc);
+  if (bar) cudaFree(bar);
+  if (e != cudaSuccess)
+    return fail(nullptr, HWENO_ERR_CUDA, std::string("hweno_check_barrier: ") + cudaGetErrorString(e));
+  if (too_many)
+    return fail(nullptr, HWENO_ERR_ARG, "hweno_check_barrier: more CTAs than can be resident");
+  if (host.status & hw::ST_TIMEOUT)
+    return fail(nullptr, HWENO_ERR_TIMEOUT, "hweno_check_barrier: a bounded barrier wait ran out");
+  return HWENO_OK;
+}
+
 const char* hweno_last_error(hweno_handle h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }

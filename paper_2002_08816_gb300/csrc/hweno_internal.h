@@ -176,6 +176,9 @@ struct Run1DArgs {
 cudaError_t run1d_max_ctas(int system, int fp64, int batch, int nth, int* ctas);
 // Cooperative launch of min(ntile, co-resident CTAs) CTAs.
 cudaError_t launch_run1d(const Run1DArgs& r, cudaStream_t s);
+// hweno_check_barrier's launch; *too_many when ctas cannot all be resident
+cudaError_t launch_barrier_check(int ctas, int meetings, int missing, unsigned polls,
+                                 unsigned* bar, DevScalars* sc, cudaStream_t s, bool* too_many);
 // Batched variants: one launch over all instances (a.tile_inst != nullptr);
 // alpha slots are one per instance.
 cudaError_t launch_alpha1d_batch(const Stage1DArgs& a, cudaStream_t s);

@@ -28,7 +28,7 @@ _D, _I, _VP = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
 EXPORTED = ["hweno_default_config", "hweno_create", "hweno_set_state", "hweno_step",
             "hweno_rhs", "hweno_get_state", "hweno_stats", "hweno_destroy",
             "hweno_last_error", "hweno_rhs1d_noalloc", "hweno_create_batch",
-            "hweno_batch_times"]
+            "hweno_batch_times", "hweno_check_barrier"]
 
 
 class hweno_config(ctypes.Structure):
@@ -93,6 +93,8 @@ def lib():
         L.hweno_set_execution.argtypes = [_VP, _I, _I]
         L.hweno_autotune.restype = _I
         L.hweno_autotune.argtypes = [_VP, _I, ctypes.POINTER(_I)]
+        L.hweno_check_barrier.restype = _I
+        L.hweno_check_barrier.argtypes = [_I, _I, _I, ctypes.c_uint]
         L.hweno_rhs1d_noalloc.restype = _I
         L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
         _lib = L
@@ -185,6 +187,16 @@ def hweno_totals(h, count):
     out = (_D * count)()
     _check(lib().hweno_totals(h, out), h)
     return list(out)
+
+
+def hweno_check_barrier(ctas, meetings, missing, polls):
+    """Self-test of the persistent launch's bounded grid barrier; returns the
+    status code (HWENO_OK, or HWENO_ERR_TIMEOUT when a wait ran out) and raises
+    HwenoError on other failures."""
+    st = lib().hweno_check_barrier(int(ctas), int(meetings), int(missing), int(polls))
+    if st not in (HWENO_OK, HWENO_ERR_TIMEOUT):
+        raise HwenoError(st, lib().hweno_last_error(None).decode())
+    return st
 
 
 def hweno_set_execution(h, threads, persistent):

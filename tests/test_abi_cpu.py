@@ -57,6 +57,13 @@ def test_invalid_configuration_is_rejected(lib, bad):
     assert len(H.hweno_last_error(None)) > 0
 
 
+@pytest.mark.parametrize("args", [(0, 1, 0, 10), (2000, 1, 0, 10), (4, 0, 0, 10), (4, 1, -1, 10),
+                                  (4, 1, 2000, 10), (4, 1, 0, 0)])
+def test_barrier_self_test_rejects_bad_arguments_before_cuda(lib, args):
+    assert lib.hweno_check_barrier(*args) == H.HWENO_ERR_ARG
+    assert b"hweno_check_barrier" in lib.hweno_last_error(None)
+
+
 def test_linear_weights_must_be_positive_and_sum_to_one(lib):
     for w in ((0.5, 0.5, 0.0), (0.98, 0.01, 0.02), (1.2, -0.1, -0.1)):
         c = _cfg()
