@@ -43,7 +43,7 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
 # stages at the bench's 65536 cells, cold L2; the persistent launch, its bytes
 # over its 6000 stages; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled by
 # the cell count to 4096^2)
-TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3188992 + 256 + 1611008 + 3184640 + 1024) / 3,
+TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3188224 + 2304 + 1741568 + 768 + 3183104 + 768) / 3,
                    (256, "per-stage graphs"): (3181568 + 1608448 + 3181312) / 3,
                    (512, "per-stage graphs"): (3181568 + 1608448 + 3181312) / 3,
                    # one persistent launch of 2000 steps: the state stays in L2

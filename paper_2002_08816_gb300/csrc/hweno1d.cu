@@ -18,13 +18,13 @@ constexpr int NT = kThreads1D;  // threads of the wave-speed kernels
 constexpr int T = kTile1D;      // their cells per CTA
 constexpr int NW = NT / 32;
 
-// The 128-thread tiles are the high-occupancy choice: 12 CTAs per SM in FP32
-// (40 registers, a few spilled), 6 in FP64, which hides the stage's dependent
+// The 128-thread tiles are the high-occupancy choice: 10 CTAs per SM in FP32
+// (48 registers, a few spilled), 6 in FP64, which hides the stage's dependent
 // load and arithmetic chains on large states and batches; on small states,
 // which sit at the per-stage latency floor, the 256-thread tiles at the
 // register count the compiler picks are faster.  hweno_autotune chooses.
 template <typename R, int C, bool BATCH, int NTH>
-__global__ void __launch_bounds__(NTH, NTH == 128 ? (sizeof(R) == 4 ? 12 : 6) : 1)
+__global__ void __launch_bounds__(NTH, NTH == 128 ? (sizeof(R) == 4 ? 10 : 6) : 1)
     stage1d_kernel(Stage1DArgs a) {
   __shared__ Smem1D<R, C, NTH> sm;
   s1d::stage1d_tile<R, C, BATCH, NTH>(a, blockIdx.x, sm);
