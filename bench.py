@@ -49,6 +49,10 @@ TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3188224 + 2304 + 1741568 + 768 + 
                    # one persistent launch of 2000 steps: the state stays in L2
                    (256, "persistent"): (2301696 + 280064) / 6000,
                    (128, "persistent"): (2735360 + 475904) / 6000}
+# the batched workload (profiles/batch1d_euler512_fp32.md): DRAM bytes per
+# stage launch, mean over the three stages, cold L2
+TRAFFIC_BATCH_FP32 = {(128, False): (97092096 + 26866432 + 49318144 + 46779904 + 97016064 + 24710400) / 3,
+                      (256, False): (95641344 + 19350528 + 47903488 + 36089600 + 95667712 + 17846784) / 3}
 TRAFFIC_2D_NG2 = 4 * (403589632 + 178616832 + 403410432 + 179490304) / 2
 L2_FLUSH_BYTES = 512 << 20
 
@@ -726,6 +730,9 @@ def bench_batch1d(args):
         H.hweno_destroy(hb)
     per_inst_s = sub_s * N_BATCH / len(pick)
     value = cells * 3 * RK_STEPS_BATCH * args.steps / tot
+    hbm, peak_kind = peaks()
+    stage_s = tot / (args.steps * 3 * RK_STEPS_BATCH)
+    achieved = BYTES_PER_CELL_STAGE["fp32"] * cells / stage_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
@@ -743,6 +750,14 @@ def bench_batch1d(args):
         "execution": {"threads_per_cta": choice[0], "cells_per_tile": choice[0] - 6,
                       "launch": "persistent" if choice[1] else "per-stage graphs",
                       "chosen_by": "hweno_autotune"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm,
+                     "traffic": TRAFFIC_BATCH_FP32.get((choice[0], bool(choice[1]))),
+                     "kernel": "%s<float,3,batch,%d threads>" % (
+                         "run1d_kernel" if choice[1] else "stage1d_kernel", choice[0]),
+                     "note": "avg stage time = timed region (set_state included) / %d stages; "
+                             "the %d MB state fits in L2; peak %s"
+                             % (3 * RK_STEPS_BATCH, cells * 24 // 10 ** 6, peak_kind)},
         "gpu_launches": args.steps * (3 * RK_STEPS_BATCH + 5),
         "clocks": sampler.summary(),
     }

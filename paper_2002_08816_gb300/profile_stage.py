@@ -4,6 +4,7 @@
                                                   [--precision fp32|fp64] [--system euler|burgers]
                                                   [--dim 1|2] [--n-gauss 2|3]
                                                   [--adjoint EVERY] [--threads 128|256|512]
+                                                  [--persistent] [--batch N]
 
 Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
 --dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
@@ -11,7 +12,8 @@ requested number of Runge-Kutta steps through the C ABI (3 stage launches per
 step after one alpha launch) and checks the status word.  With --adjoint
 EVERY (2D) the steps are recorded with a checkpoint every EVERY steps and the
 gradient of sum(rho^2) is taken (hweno_backward: recomputed stages, then two
-adjoint kernels per stage).
+adjoint kernels per stage).  With --batch N it runs N independent 1D Euler
+instances in shared launches (hweno_create_batch).
 """
 
 import argparse
@@ -22,6 +24,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 
 def main():
+    import numpy as np
     import torch
 
     from paper_2002_08816_gb300 import build as B
@@ -41,6 +44,9 @@ def main():
                     help="1D: threads per CTA (0: the default)")
     ap.add_argument("--persistent", action="store_true",
                     help="1D: one persistent launch with grid barriers instead of per-stage graphs")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="1D Euler: this many instances, cells log-uniform in [256, 16384], "
+                         "two-state data (the batched workload's recipe, seed 77)")
     args = ap.parse_args()
     B.build()
     prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
@@ -49,6 +55,12 @@ def main():
         u = W.euler_vortex_modes_2d(args.nx, args.nx, seed=args.seed, npts=2)
         cfg = H.make_config(2, H.HWENO_EULER, args.nx, args.nx, x0=0.0, x1=10.0, y0=0.0,
                             y1=10.0, cfl=0.5, precision=prec, n_gauss=args.n_gauss)
+    elif args.batch > 0:
+        sizes = [int(v) for v in W.batch_sizes_1d(args.batch, seed=77)]
+        u = np.concatenate([W.euler_two_state_1d(n, seed=77 + b).reshape(-1)
+                            for b, n in enumerate(sizes)])
+        cfg = H.make_config(1, H.HWENO_EULER, 4, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
+                            precision=prec)
     elif args.system == "euler":
         u = W.euler_two_state_1d(args.nx, args.seed)
         cfg = H.make_config(1, H.HWENO_EULER, args.nx, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
@@ -58,7 +70,10 @@ def main():
         cfg = H.make_config(1, H.HWENO_BURGERS, args.nx, x0=-1.0, x1=1.0, cfl=0.5, precision=prec)
     dt = torch.float32 if prec == H.HWENO_FP32 else torch.float64
     dev = torch.from_numpy(u).to("cuda", dt).contiguous()
-    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    if args.batch > 0:
+        h = H.hweno_create_batch(cfg, sizes, torch.cuda.current_stream().cuda_stream)
+    else:
+        h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
         if (args.threads or args.persistent) and args.dim == 1:
             H.hweno_set_execution(h, args.threads or 256, args.persistent)
