@@ -136,3 +136,19 @@ def test_set_execution_rejects_bad_choices():
             H.hweno_set_execution(h, 200, 1)
     finally:
         H.hweno_destroy(h)
+
+
+def test_large_grid_epilogue_agrees_with_the_warp_level_one():
+    """300,000 cells: 128-thread tiles (2459 tiles) fold the wave-speed maxima
+    after a CTA reduction, 256-thread tiles (1200 tiles) warp by warp; a
+    maximum and an integer count do not depend on the order, so the runs are
+    bitwise equal."""
+    nx = 300000
+    u = round_to(H.HWENO_FP32, mixed_euler(nx, 11))
+    cfg = H.make_config(1, H.HWENO_EULER, nx, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
+                        precision=H.HWENO_FP32)
+    a, ta, sa = _run(cfg, u, 6, (128, 0))
+    b, tb, sb = _run(cfg, u, 6, (256, 0))
+    assert sa["troubled"] > 0 and sa["steps"] == 6
+    assert np.array_equal(a, b)
+    assert ta == tb and sa["troubled"] == sb["troubled"]
