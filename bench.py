@@ -38,19 +38,19 @@ UNIT = "cell-stages/s"
 # stages 2 and 3 read u^n and u^(k) and write (3S); mean 8S/3 with
 # S = 3 components x 2 moments x sizeof(real)
 BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
-# DRAM bytes (read + write) per stage from ncu captures of the current kernels
-# (profiles/stage1d_euler65536_fp32.md: per-stage launches, mean over the three
-# stages at the bench's 65536 cells, cold L2; the persistent launch, its bytes
-# over its 6000 stages; profiles/stage2d_euler2048_fp32.md: 2048^2 scaled by
-# the cell count to 4096^2)
+# DRAM bytes (read + write) per stage from ncu captures of the current kernels,
+# summarised under profiles/: 1D per-stage launches, the mean over the three
+# stages at the bench's 65536 cells, cold L2; the 1D persistent launch, its
+# bytes over its 6000 stages; 2D, a 2048^2 capture scaled by the cell count to
+# 4096^2
 TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3188224 + 2304 + 1741568 + 768 + 3183104 + 768) / 3,
                    (256, "per-stage graphs"): (3181568 + 1608448 + 3181312) / 3,
                    (512, "per-stage graphs"): (3181568 + 1608448 + 3181312) / 3,
                    # one persistent launch of 2000 steps: the state stays in L2
                    (256, "persistent"): (2301696 + 280064) / 6000,
                    (128, "persistent"): (2735360 + 475904) / 6000}
-# the batched workload (profiles/batch1d_euler512_fp32.md): DRAM bytes per
-# stage launch, mean over the three stages, cold L2
+# the batched workload (512 instances): DRAM bytes per stage launch, the mean
+# over the three stages, cold L2
 TRAFFIC_BATCH_FP32 = {(128, False): (97092096 + 26866432 + 49318144 + 46779904 + 97016064 + 24710400) / 3,
                       (256, False): (95641344 + 19350528 + 47903488 + 36089600 + 95667712 + 17846784) / 3}
 TRAFFIC_2D_NG2 = 4 * (403589632 + 178616832 + 403410432 + 179490304) / 2
@@ -344,7 +344,7 @@ def bench_hweno(args):
                    "parallelism": "one independent instance per GPU"},
         "fp64": {"value": results["fp64"]["value"], "ms_per_step": results["fp64"]["ms_per_step"],
                  "e2e": results["fp64"]["e2e"], "execution": results["fp64"]["execution"],
-                 "bound": "FP64 pipe (profiles/stage1d_euler65536_fp64.md)"},
+                 "bound": "FP64 pipe (~80 % active under ncu)"},
         "troubled_frac": r["troubled_frac"],
         "fp32_vs_fp64": field_err,
         "execution": r["execution"],
