@@ -127,9 +127,10 @@ __device__ __forceinline__ void gather19a(const S& sm, int c, int ci, int cj, R*
 // Step 5.1 interface values of an Euler cell next to a troubled cell (x-faces
 // in the x characteristic fields, y-faces in the y fields of the average).
 template <int NG, typename S, typename R>
-__device__ __noinline__ void hw_faces_euler_vals(const S& sm, int ci, int cj, const R* gam, R eps,
-                                                 R gas, R (*out)[4 * NG]) {
+__device__ __noinline__ void hw_faces_euler_vals(const S& sm, int ci, int cj, R g0, R g1, R g2,
+                                                 R g3, R g4, R eps, R gas, R (*out)[4 * NG]) {
   constexpr int NF = 4 * NG;
+  const R gam[5] = {g0, g1, g2, g3, g4};  // by value: the caller's parameters stay off the stack
   R D[4][19];
 #pragma unroll
   for (int c = 0; c < 4; ++c) gather19a(sm, c, ci, cj, D[c]);
@@ -163,9 +164,11 @@ __device__ __noinline__ void hw_faces_euler_vals(const S& sm, int ci, int cj, co
 // Reverse of hw_faces_euler_vals: G[c][k] += the adjoint of datum k of
 // component c, given the adjoints lam[c][p] of the interface values.
 template <int NG, typename S, typename R>
-__device__ __noinline__ void hw_faces_euler_vjp(const S& sm, int ci, int cj, const R* gam, R eps,
-                                                R gas, R (*lam)[4 * NG], R (*G)[19]) {
+__device__ __noinline__ void hw_faces_euler_vjp(const S& sm, int ci, int cj, R g0, R g1, R g2,
+                                                R g3, R g4, R eps, R gas, R (*lam)[4 * NG],
+                                                R (*G)[19]) {
   constexpr int NF = 4 * NG;
+  const R gam[5] = {g0, g1, g2, g3, g4};
   R D[4][19];
 #pragma unroll
   for (int c = 0; c < 4; ++c) gather19a(sm, c, ci, cj, D[c]);
@@ -220,7 +223,9 @@ __device__ __noinline__ void hw_faces_euler_vjp(const S& sm, int ci, int cj, con
 // of each direction (cx, cy), including through the eigen-system of the
 // cell's average.
 template <typename S, typename R>
-__device__ __noinline__ void limit_euler2d_vjp(S& sm, int lx, int ly, const R* gam, R eps, R gas) {
+__device__ __noinline__ void limit_euler2d_vjp(S& sm, int lx, int ly, R g0, R g1, R g2, R g3, R g4,
+                                               R eps, R gas) {
+  const R gam[5] = {g0, g1, g2, g3, g4};
   const int rx = lx + 1, ry = ly + 1;
   R U[4];
 #pragma unroll
@@ -367,7 +372,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
   if constexpr (C == 4) {
     if (hw) {
       R hv[4][NF];
-      hw_faces_euler_vals<NG>(sm, ci, cj, P_.gam, P_.eps, P_.gas, hv);
+      hw_faces_euler_vals<NG>(sm, ci, cj, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4],
+                              P_.eps, P_.gas, hv);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -461,7 +467,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
 #pragma unroll
         for (int k = 0; k < 19; ++k) Gl[c][k] = R(0);
       }
-      hw_faces_euler_vjp<NG>(sm, ci, cj, P_.gam, P_.eps, P_.gas, lamF, Gl);
+      hw_faces_euler_vjp<NG>(sm, ci, cj, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4],
+                             P_.eps, P_.gas, lamF, Gl);
     }
   }
   R* __restrict__ part = static_cast<R*>(a.G) + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (C * 3 * BX * BY);
@@ -643,7 +650,8 @@ __device__ __noinline__ void fix_tile(const Adj2DArgs& a, int tile) {
 #pragma unroll
       for (int q = 0; q < 5; ++q) sm.cy[0][q][ly][lx] = g[q];
     } else {
-      limit_euler2d_vjp(sm, lx, ly, P_.gam, P_.eps, P_.gas);
+      limit_euler2d_vjp(sm, lx, ly, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4], P_.eps,
+                        P_.gas);
     }
   }
   __syncthreads();
