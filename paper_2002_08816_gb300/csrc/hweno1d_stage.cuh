@@ -12,17 +12,19 @@
 //      operation costs tens of cycles, so the FP32 kernel keeps FP64 off its
 //      critical path (the time itself is accumulated in FP64 by an idle thread);
 //   2. KXRCF flags and the modified first moments (Step 1) for the cells and
-//      2 halo cells per side, in characteristic fields for Euler; an FP32
-//      kernel decides a flag in FP32 when its rounding-error bound allows and
-//      in FP64 otherwise, so flags equal the FP64 decision off the threshold;
+//      2 halo cells per side, in characteristic fields for Euler (out-of-line
+//      work of the troubled lanes); an FP32 kernel decides a flag in FP32 when
+//      its rounding-error bound allows and by an error-free float-pair
+//      evaluation otherwise, so flags equal the FP64 decision off the threshold;
 //   3. interface values (Steps 2.1/2.2) for the cells and 1 halo cell per
 //      side: linear p0 unless a cell of S0 = {i-1, i, i+1} is troubled;
 //   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
 //      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
 //      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
-//   5. each warp's maximum wave speed of the output, folded by an atomic max
-//      into the tile's one of kAlphaSlots slots that the next stage reads for
-//      its alpha, and the status bits (non-finite, non-physical).
+//   5. the maximum wave speed of the output, folded by atomic max into the
+//      tile's one of kAlphaSlots slots that the next stage reads for its alpha
+//      (warp by warp, or after a CTA reduction on large grids), the troubled
+//      count and the status bits (non-finite, non-physical).
 // The limited stage input is what the RK combination uses (the first moment
 // of a troubled cell is modified in the state, as a DG limiter would).
 #pragma once
@@ -62,7 +64,6 @@ struct Smem1D {
   int cnt[NW];
   R amax[NW];
 };
-
 
 template <typename R, int C>
 __device__ __forceinline__ void phys_flux(R gas, const R* U, R* F) {
