@@ -1,7 +1,7 @@
 // The 1D kernels: one launch per third-order TVD Runge-Kutta stage (captured
 // in CUDA graphs by the C ABI, with programmatic dependent launch), or a whole
-// run in one persistent cooperative launch; both call the same out-of-line
-// stage body (hweno1d_stage.cuh).  Also the wave-speed kernels that start a
+// run in one persistent cooperative launch; both inline the same stage body
+// (hweno1d_stage.cuh).  Also the wave-speed kernels that start a
 // run and small helpers (conversions, device scalars).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,9 +34,10 @@ __global__ void __launch_bounds__(NTH, NTH == 128 ? (sizeof(R) == 4 ? 10 : 6) : 
 // A whole run of Runge-Kutta steps in one cooperative launch: each CTA applies
 // the stage body to its tiles of a stage, then all CTAs meet at a grid barrier
 // before the next stage reads their outputs and the alpha slots they filled.
-// The barrier's wait is bounded: after about half a second the CTA sets
-// ST_TIMEOUT in the status word and the whole grid stops at its next barrier,
-// so a fault in the protocol cannot hang the GPU.
+// The barrier's wait is bounded: after kBarrierPolls polls (about a second)
+// the CTA sets ST_TIMEOUT in the status word and returns, and the others give
+// up at their own bounded waits, so a lost arrival cannot hang the GPU
+// (hweno_check_barrier exercises exactly that).
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
