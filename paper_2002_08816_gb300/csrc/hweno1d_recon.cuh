@@ -157,6 +157,25 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// The KXRCF jump (u0 -+ 6 v0) - (u_nb +- 6 v_nb) of FP32 data as an unevaluated
+// float pair jh + jl, with jh carrying its sign and |jl| <= ulp(jh) / 2, within
+// ~2^-46 S of the exact value (S = |u0| + 6|v0| + |u_nb| + 6|v_nb|): the four
+// terms u0, s 6 v0, -u_nb, s 6 v_nb (s = -1 on the low face, +1 on the high
+// one) are exact as pairs (fma gives the rounding error of 6v), three two-sums
+// add them, the five small terms are rounded into jl, and a last two-sum
+// renormalises (after cancellation the small terms may outweigh the sum).
+__device__ __forceinline__ void jump_pair(float u0, float v0, float unb, float vnb, bool low,
+                                          float& jh, float& jl) {
+  const float sv = low ? -1.0f : 1.0f;
+  const float p0 = __fmul_rn(6.0f, v0), e0 = fmaf(6.0f, v0, -p0);
+  const float p1 = __fmul_rn(6.0f, vnb), e1 = fmaf(6.0f, vnb, -p1);
+  float s1, t1, s2, t2, s3, t3;
+  two_sum(u0, sv * p0, s1, t1);
+  two_sum(s1, -unb, s2, t2);
+  two_sum(s2, sv * p1, s3, t3);
+  two_sum(s3, __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), t3), sv * __fadd_rn(e0, e1)), jh, jl);
+}
+
 // FP32 inputs: decide in FP32 when the rounding-error bound allows, else
 // evaluate the jump and the threshold as unevaluated float pairs (error-free
 // sums and products), so that the decision equals the FP64 one away from the
@@ -194,19 +213,8 @@ __device__ __forceinline__ bool kxrcf_troubled(float um, float u0, float up, flo
   const float r = hthr * nrm;
   if (j - e > r * (1.0f + 4.8e-7f)) return true;
   if (j + e < r * (1.0f - 4.8e-7f)) return false;
-  // jump = u0 + sv*6*v0 - unb + sv*6*vnb, sv = -1 on the left face, +1 on the right
-  const float sv = left ? -1.0f : 1.0f;
-  const float unb = left ? um : up, vnb = left ? vm : vp;
-  const float p0 = __fmul_rn(6.0f, v0), e0 = fmaf(6.0f, v0, -p0);
-  const float p1 = __fmul_rn(6.0f, vnb), e1 = fmaf(6.0f, vnb, -p1);
-  float s1, t1, s2, t2, s3, t3;
-  two_sum(u0, sv * p0, s1, t1);
-  two_sum(s1, -unb, s2, t2);
-  two_sum(s2, sv * p1, s3, t3);
-  // after cancellation the small terms may outweigh s3: renormalise, so that
-  // jh carries the sign of the jump and |jl| <= ulp(jh) / 2
   float jh, jl;
-  two_sum(s3, __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), t3), sv * __fadd_rn(e0, e1)), jh, jl);
+  jump_pair(u0, v0, left ? um : up, left ? vm : vp, left, jh, jl);
   if (jh < 0.0f) {
     jh = -jh;
     jl = -jl;

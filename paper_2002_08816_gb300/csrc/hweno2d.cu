@@ -65,19 +65,13 @@ __device__ __forceinline__ double jump64(double u0, double v0, double unb, doubl
 
 // u0/v0/w0 the cell, (uxn, vxn) its inflow x-neighbour, (uyn, wyn) its inflow
 // y-neighbour; lowx / lowy: the inflow faces are the left / bottom ones.
-// Every argument by value: a reference to the launch's parameter block would
-// make each thread copy that block to local memory.
-__device__ __noinline__ bool kxrcf2_troubled64(double u0, double v0, double w0, double uxn,
-                                               double vxn, double uyn, double wyn, bool lowx,
-                                               bool lowy, double dx, double dy, double den_h,
-                                               double thr) {
-  const double jx = jump64(u0, v0, uxn, vxn, lowx);
-  const double jy = jump64(u0, w0, uyn, wyn, lowy);
-  const double num = __dadd_rn(__dmul_rn(dy, jx), __dmul_rn(dx, jy));
-  const double nrm = fmax(fabs(u0), 1e-12);
-  return fabs(num) / __dmul_rn(den_h, nrm) > thr;
-}
-
+// FP32 data: decide in FP32 when the rounding-error bound allows, else with
+// float pairs (no FP64 on the FP32 kernel's path): the two jumps as exact-to-
+// ~2^-46 pairs (jump_pair), num = dy jx + dx jy from pair products (fma gives
+// each product's rounding error; dx and dy carry their own low parts), and the
+// threshold thr den_h max(|u0|, 1e-12) as a pair; the sign of |num| - r is then
+// that of the exact values unless they agree to ~1e-13 of dy S_x + dx S_y,
+// far inside the 1e-6 band around the threshold.
 __device__ __forceinline__ bool kxrcf2_troubled(float u0, float v0, float w0, float uxn, float vxn,
                                                 float uyn, float wyn, bool lowx, bool lowy,
                                                 const Kx2& k) {
@@ -88,18 +82,42 @@ __device__ __forceinline__ bool kxrcf2_troubled(float u0, float v0, float w0, fl
   const float num = fabsf(k.fdy * jx + k.fdx * jy);
   // |num - exact| <= 2^-24 (3 dy sx + 3 dx sy + 3 |num|) to first order
   const float e = 1.0e-6f * (k.fdy * sx + k.fdx * sy);
-  const float r = k.fthr_den * fmaxf(fabsf(u0), 1e-12f);
+  const float nrm = fmaxf(fabsf(u0), 1e-12f);
+  const float r = k.fthr_den * nrm;
   if (num - e > r * (1.0f + 4.8e-7f)) return true;
   if (num + e < r * (1.0f - 4.8e-7f)) return false;
-  return kxrcf2_troubled64((double)u0, (double)v0, (double)w0, (double)uxn, (double)vxn,
-                           (double)uyn, (double)wyn, lowx, lowy, k.dx, k.dy, k.den_h, k.thr);
+  float jxh, jxl, jyh, jyl;
+  jump_pair(u0, v0, uxn, vxn, lowx, jxh, jxl);
+  jump_pair(u0, w0, uyn, wyn, lowy, jyh, jyl);
+  const float p1h = __fmul_rn(k.fdy, jxh);
+  const float p1l = __fadd_rn(fmaf(k.fdy, jxh, -p1h),
+                              __fadd_rn(__fmul_rn(k.fdy, jxl), __fmul_rn(k.fdy_lo, jxh)));
+  const float p2h = __fmul_rn(k.fdx, jyh);
+  const float p2l = __fadd_rn(fmaf(k.fdx, jyh, -p2h),
+                              __fadd_rn(__fmul_rn(k.fdx, jyl), __fmul_rn(k.fdx_lo, jyh)));
+  float nh, nl, t;
+  two_sum(p1h, p2h, nh, t);
+  two_sum(nh, __fadd_rn(t, __fadd_rn(p1l, p2l)), nh, nl);
+  if (nh < 0.0f) {
+    nh = -nh;
+    nl = -nl;
+  }
+  const float rh = __fmul_rn(nrm, k.fthr_den);
+  const float rl = __fadd_rn(fmaf(nrm, k.fthr_den, -rh), __fmul_rn(nrm, k.fthr_den_lo));
+  return __fadd_rn(__fsub_rn(nh, rh), __fsub_rn(nl, rl)) > 0.0f;
 }
 
+// FP64 data: the decision of the reading, |dy jx + dx jy| / (den_h nrm) >
+// thr, in its divide-free product form (it differs from the quotient form only
+// within a few ulp of the threshold).
 __device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0, double uxn,
                                                 double vxn, double uyn, double wyn, bool lowx,
                                                 bool lowy, const Kx2& k) {
-  return kxrcf2_troubled64(u0, v0, w0, uxn, vxn, uyn, wyn, lowx, lowy, k.dx, k.dy, k.den_h,
-                           k.thr);
+  const double jx = jump64(u0, v0, uxn, vxn, lowx);
+  const double jy = jump64(u0, w0, uyn, wyn, lowy);
+  const double num = __dadd_rn(__dmul_rn(k.dy, jx), __dmul_rn(k.dx, jy));
+  const double nrm = fmax(fabs(u0), 1e-12);
+  return fabs(num) > __dmul_rn(k.thr, __dmul_rn(k.den_h, nrm));
 }
 
 // The 19 data of component c of the cell at own-tile coordinates (ci, cj):
@@ -641,6 +659,9 @@ void finish_stage2d_args(Stage2DArgs& a) {
   a.kx.fdx = (float)a.dx;
   a.kx.fdy = (float)a.dy;
   a.kx.fthr_den = (float)(a.thr * a.kx.den_h);
+  a.kx.fdx_lo = (float)(a.dx - (double)a.kx.fdx);
+  a.kx.fdy_lo = (float)(a.dy - (double)a.kx.fdy);
+  a.kx.fthr_den_lo = (float)(a.thr * a.kx.den_h - (double)a.kx.fthr_den);
   for (int k = 0; k < 5; ++k) a.f32[k] = (float)a.gam[k];
   a.f32[5] = (float)a.eps;
   a.f32[6] = (float)a.gas;

@@ -92,6 +92,7 @@ struct Kx2 {
   double dx, dy, den_h;      // den_h = h (dx + dy), h = sqrt(dx^2 + dy^2) / 2
   double thr;
   float fdx, fdy, fthr_den;  // FP32 copies: dx, dy, thr * den_h
+  float fdx_lo, fdy_lo, fthr_den_lo;  // their rounding errors: dx = fdx + fdx_lo to ~2^-48
 };
 
 // Everything one 2D stage launch needs.  Pointers are device pointers.

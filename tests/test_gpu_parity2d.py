@@ -47,6 +47,51 @@ def _compare_rhs(system, nx, ny, bc, prec, mode, ng, seed, u=None, dom=None):
     return fo
 
 
+def _near_threshold_state2d(system, nx, ny, thr, seed):
+    """Data constant in y (the y-jumps vanish) whose x-walk puts every cell's
+    KXRCF indicator at thr (1 + delta), |delta| log-uniform in [1e-5, 0.3] on
+    either side, for square cells of side 1/nx: with the left inflow face,
+    jx = (u_i - 6 v_i) - (u_{i-1} + 6 v_{i-1}) = s k u_i and
+    k = thr (1 + delta) h (dx + dy) / dy, h = sqrt(dx^2 + dy^2) / 2."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / nx
+    k0 = thr * np.sqrt(2.0) * dx  # thr h (dx + dy) / dy with dy = dx
+    delta = rng.choice([-1.0, 1.0], nx) * 10.0 ** rng.uniform(-5.0, np.log10(0.3), nx)
+    sgn = rng.choice([-1.0, 1.0], nx)
+    v = rng.uniform(-0.05, 0.05, nx) * dx
+    w = np.empty(nx)
+    w[0] = 1.0
+    for i in range(1, nx):
+        w[i] = (w[i - 1] + 6.0 * (v[i - 1] + v[i])) / (1.0 - sgn[i] * k0 * (1.0 + delta[i]))
+    ones = np.ones((ny, 1))
+    avg, mom, zero = ones * w, ones * v, np.zeros((ny, nx))
+    if system == H.HWENO_BURGERS:
+        return np.stack([np.stack([avg, mom, zero])])
+    flat = np.full((ny, nx), 2.5)
+    return np.stack([np.stack([avg, mom, zero]), np.stack([0.1 * avg, 0.1 * mom, zero]),
+                     np.stack([zero, zero, zero]), np.stack([flat, zero, zero])])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("system", [H.HWENO_BURGERS, H.HWENO_EULER])
+def test_flags2d_near_threshold(system, prec):
+    """Most cells' indicators within 30 % of the threshold (the FP32 kernel then
+    decides many with its float-pair evaluation): flags bit-exact outside the
+    1e-6 band."""
+    nx, ny = 512, 8
+    dom = square_domain(nx, ny)
+    cfg, ocfg = make_pair2d(system, nx, ny, dom, H.HWENO_BC_PERIODIC, prec,
+                            H.HWENO_TROUBLED_HYBRID, 2)
+    u = round_to(prec, _near_threshold_state2d(system, nx, ny, ocfg.kxrcf_threshold,
+                                               seed=3 + system))
+    _, _, fo, ind = O.rhs2d(ocfg, u)
+    rel = np.abs(ind / ocfg.kxrcf_threshold - 1.0)
+    assert ((rel > 1e-6) & (rel < 0.3)).sum() > 0.8 * rel.size
+    assert 0.2 < fo.mean() < 0.8
+    _compare_rhs(system, nx, ny, H.HWENO_BC_PERIODIC, prec, H.HWENO_TROUBLED_HYBRID, 2, seed=0,
+                 u=u, dom=dom)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("bc", [H.HWENO_BC_PERIODIC, H.HWENO_BC_OUTFLOW])
 @pytest.mark.parametrize("size", SIZES)
