@@ -53,7 +53,7 @@ TRAFFIC_1D_FP32 = {(128, "per-stage graphs"): (3188224 + 2304 + 1741568 + 768 + 
 # over the three stages, cold L2
 TRAFFIC_BATCH_FP32 = {(128, False): (97092096 + 26866432 + 49318144 + 46779904 + 97016064 + 24710400) / 3,
                       (256, False): (95641344 + 19350528 + 47903488 + 36089600 + 95667712 + 17846784) / 3}
-TRAFFIC_2D_NG2 = 4 * (403589632 + 178616832 + 403410432 + 179490304) / 2
+TRAFFIC_2D_NG2 = 4 * (403427584 + 178328320 + 403399680 + 179353600) / 2
 L2_FLUSH_BYTES = 512 << 20
 
 
