@@ -357,6 +357,7 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   const double dx = (cfg->x1 - cfg->x0) / N;
   const int euler = cfg->system == HWO_EULER;
   if (N < 3) return -1;
+  if (cfg->bc == HWO_BC_REFLECTIVE && !euler) return -1;
   init_fits();
   if (alpha < 0.0) alpha = hwo1d_alpha(cfg, u);
   if (!(alpha == alpha)) return -2;
@@ -373,7 +374,6 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   double* fh = (double*)malloc(sizeof(double) * C * NE); /* flux at e+1/2 */
   int status = 0;
 
-  if (cfg->bc == HWO_BC_REFLECTIVE && !euler) return -1;
   for (int e = 0; e < NE; ++e) {
     int mir;
     int s = ghost_src(cfg, e - G1, &mir);

@@ -483,3 +483,148 @@ def test_shock_suite_troubled_fraction(name):
     rho = u[0, 0]
     p = 0.4 * (u[2, 0] - 0.5 * u[1, 0] ** 2 / rho)
     assert np.all(rho > 0) and np.all(p > 0)
+
+
+# ----------------------------------------------------------------------------- brute force
+
+def _brute_cases():
+    """(name, system, u [C][2][6], dx, mode) on a 6-cell periodic grid: smooth
+    data (no flag), data with a jump (flags, limiter, HWENO), every cell
+    troubled (the new HWENO scheme, random weights)."""
+    nx, x0, x1 = 6, 0.0, 1.5
+    xs = 0.75
+    out = []
+    ub = W.cell_moments_1d(lambda x: 0.5 + 0.25 * np.sin(2 * np.pi * x / 1.5), nx, x0, x1)
+    out.append(("burgers-smooth", O.BURGERS, ub, "hybrid", (0.98, 0.01, 0.01)))
+    ub = W.cell_moments_1d(lambda x: np.where(x < xs + 0.1, 1.0 + 0.3 * x, -0.4 + 0.2 * x),
+                           nx, x0, x1)
+    out.append(("burgers-jump", O.BURGERS, ub, "hybrid", (0.98, 0.01, 0.01)))
+    out.append(("burgers-all", O.BURGERS, ub, "all", (0.5, 0.3, 0.2)))
+    ue = W.euler_riemann_1d(nx, (1.0, 0.3, 1.0), (0.5, 0.3, 0.4), x0, x1, 0.8)
+    out.append(("euler-jump", O.EULER, ue, "hybrid", (0.98, 0.01, 0.01)))
+    ue2 = W.cell_moments_1d(
+        lambda x: W.euler_conserved_1d(1.0 + 0.2 * np.sin(2 * np.pi * x / 1.5), 0.5 + 0 * x,
+                                       1.0 + 0 * x), nx, x0, x1)
+    out.append(("euler-smooth", O.EULER, ue2, "hybrid", (0.98, 0.01, 0.01)))
+    out.append(("euler-all", O.EULER, ue, "all", (0.2, 0.5, 0.3)))
+    return out, (x1 - x0) / nx
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_brute_force_operator(case):
+    """Sec. 2.1, Steps 1-2 and Eq. (odeH) on a 6-cell periodic grid: the
+    oracle's L, troubled flags, indicators and modified first moments equal a
+    40-digit evaluation written from the definitions (tests/brute1d.py:
+    polynomial fits solved afresh in physical coordinates, Eq. (GHYZ)
+    integrated exactly, the KXRCF reading, Lax-Friedrichs, Gauss-Lobatto)."""
+    import brute1d as B
+    cases, dx = _brute_cases()
+    name, system, u, mode, gam = cases[case]
+    nx = u.shape[2]
+    tm = {"hybrid": O.TROUBLED_HYBRID, "all": O.TROUBLED_ALL}[mode]
+    cfg = O.Cfg1D.make(system, nx, 0.0, 1.5, O.BC_PERIODIC, lin_w=gam, troubled_mode=tm)
+    alpha = O.alpha1d(cfg, u) * 1.05
+    rhs, ulim, flags, ind = O.rhs1d(cfg, u, alpha)
+    L, fb, ib, vl = B.rhs(u.tolist(), 0 if system == O.BURGERS else 1, dx, alpha, gam,
+                          mode=mode)
+    Lb = np.array([[[float(x) for x in row] for row in comp] for comp in L])
+    np.testing.assert_array_equal(flags, np.array(fb, dtype=np.uint8), err_msg=name)
+    ibf = np.array([float(x) for x in ib])
+    np.testing.assert_allclose(ind, ibf, rtol=1e-13, atol=1e-13 * ibf.max(), err_msg=name)
+    # the indicators stay clear of the threshold, so the flag comparison is sharp
+    assert all(abs(float(x) - 1.0) > 1e-3 for x in ib)
+    if mode == "hybrid" and name.endswith("jump"):
+        assert 0 < flags.sum() < nx
+    if name.endswith("smooth"):
+        assert flags.sum() == 0
+    vlb = np.array([[float(x) for x in comp] for comp in vl])
+    np.testing.assert_allclose(ulim[:, 1], vlb, rtol=1e-12, atol=1e-14, err_msg=name)
+    scale = np.max(np.abs(Lb))
+    np.testing.assert_allclose(rhs, Lb, rtol=0, atol=1e-12 * scale, err_msg=name)
+
+
+# ----------------------------------------------------------------------------- KXRCF
+
+def _kxrcf_exact(ub, vb, i, vel, dx):
+    """The reading of the KXRCF indicator in exact rationals: the degree-1 cell
+    polynomial P_j(x) = ubar_j + 12 vbar_j (x - x_j)/dx, the trace jump at the
+    inflow face (left when the velocity is >= 0), over h = dx/2 times
+    max(|ubar_i|, 1e-12) (the inflow boundary of a 1D cell has measure 1)."""
+    from fractions import Fraction as Fr
+    n = len(ub)
+
+    def P(j, s):
+        return Fr(ub[j % n]) + 12 * Fr(vb[j % n]) * s / Fr(dx)
+    half = Fr(dx) / 2
+    if vel >= 0:
+        jump = P(i, -half) - P(i - 1, half)
+    else:
+        jump = P(i, half) - P(i + 1, -half)
+    return abs(jump) / (half * max(abs(Fr(ub[i % n])), Fr(1e-12)))
+
+
+def test_kxrcf_indicator_hand_computed_1d():
+    """Sec. 2.1 Step 1 / Remark 1 (KXRCF, reading of the deferred reference):
+    the oracle's indicator equals the exact value on small periodic grids, for
+    Burgers with both velocity signs and for Euler through rho and through E
+    (the larger of the two), with the inflow face chosen by the sign of m/rho."""
+    rng = np.random.default_rng(11)
+    for trial in range(6):
+        nx, dx = 5, 0.2
+        u = np.zeros((1, 2, nx))
+        u[0, 0] = rng.uniform(-1, 1, nx)
+        u[0, 1] = rng.uniform(-0.1, 0.1, nx)
+        cfg = O.Cfg1D.make(O.BURGERS, nx, 0.0, nx * dx, O.BC_PERIODIC)
+        _, _, flags, ind = O.rhs1d(cfg, u, 2.0)
+        signs = set()
+        for i in range(nx):
+            want = _kxrcf_exact(u[0, 0], u[0, 1], i, u[0, 0, i], dx)
+            assert abs(ind[i] - float(want)) <= 1e-14 * float(want), (trial, i)
+            assert flags[i] == (want > 1)
+            signs.add(u[0, 0, i] >= 0)
+        assert signs == {True, False} or trial > 0
+    # Euler: rho and E indicators, velocity m/rho of the cell itself
+    nx, dx = 5, 0.3
+    rho = rng.uniform(0.5, 1.5, nx)
+    mu = np.array([0.4, -0.3, 0.2, -0.5, 0.1])
+    p = rng.uniform(0.5, 1.5, nx)
+    u = np.zeros((3, 2, nx))
+    u[:, 0] = W.euler_conserved_1d(rho, mu, p)
+    u[:, 1] = rng.uniform(-0.02, 0.02, (3, nx))
+    cfg = O.Cfg1D.make(O.EULER, nx, 0.0, nx * dx, O.BC_PERIODIC)
+    _, _, flags, ind = O.rhs1d(cfg, u, 3.0)
+    for i in range(nx):
+        vel = u[1, 0, i] / u[0, 0, i]
+        want = max(_kxrcf_exact(u[0, 0], u[0, 1], i, vel, dx),
+                   _kxrcf_exact(u[2, 0], u[2, 1], i, vel, dx))
+        assert abs(ind[i] - float(want)) <= 1e-14 * float(want), i
+        assert flags[i] == (want > 1)
+
+
+def test_kxrcf_scaling_laws_1d():
+    """What the KXRCF normalisation by h (k = 1) does: on smooth data the two
+    degree-1 traces at a face both miss u by dx^2 u''/12 (the L2 projection's
+    error at a cell end), so their jump is O(dx^3) and the indicator falls
+    like dx^2 (order 2 under refinement); across a discontinuity the jump stays
+    O(1) and the indicator grows like 1/dx.  A normalisation by h^2 or without
+    h shifts both orders by one; dx in place of dx/2 halves the step value."""
+    def ind_of(func, nx):
+        u = W.cell_moments_1d(func, nx, 0.0, 1.0)
+        cfg = O.Cfg1D.make(O.BURGERS, nx, 0.0, 1.0, O.BC_PERIODIC)
+        _, _, _, ind = O.rhs1d(cfg, u, 3.0)
+        return ind
+    smooth = lambda x: 1.5 + 0.5 * np.sin(2 * np.pi * x)
+    a, b = ind_of(smooth, 64).max(), ind_of(smooth, 128).max()
+    order = np.log2(a / b)
+    assert 1.8 < order < 2.2, order
+    assert a < 0.05
+    # a step between 0.5 and 1 on cell faces: the cell right of the rising face
+    # (velocity 1 > 0, inflow from the left) has I = 0.5 / (dx/2 * 1) = 1/dx,
+    # the cell right of the falling face I = 0.5 / (dx/2 * 0.5) = 2/dx
+    step = lambda x: np.where((x > 0.25) & (x < 0.75), 1.0, 0.5)
+    for nx in (64, 128):
+        ind = ind_of(step, nx)
+        np.testing.assert_allclose(ind[nx // 4], nx, rtol=1e-12)
+        np.testing.assert_allclose(ind[3 * nx // 4], 2 * nx, rtol=1e-12)
+        others = np.delete(ind, [nx // 4, 3 * nx // 4])
+        assert others.max() < 1e-9

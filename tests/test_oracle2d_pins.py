@@ -344,3 +344,118 @@ def test_hybrid_switch_and_nonlinear_weights_2d():
                               + np.sum(om[1:, None] * val[1:, face], axis=0))
             np.testing.assert_allclose(pts[0, :, j, i], want, rtol=1e-12, atol=1e-12)
     assert nhw > fl.sum()
+
+
+# ----------------------------------------------------------------------------- KXRCF
+
+def _kxrcf2d_exact(u, c, i, j, velx, vely, dx, dy):
+    """The reading of the 2D KXRCF indicator in exact rationals (h by a 40-digit
+    square root): the degree-1 cell polynomial P(x, y) = ubar + 12 vbar (x -
+    x_i)/dx + 12 wbar (y - y_j)/dy, the trace differences P_cell - P_nb
+    integrated exactly along the inflow x-face (left when velx >= 0) and the
+    inflow y-face (bottom when vely >= 0), the absolute value of their sum over
+    h |dI^-| max(|ubar|, 1e-12), h = sqrt(dx^2 + dy^2)/2 (half the diagonal),
+    |dI^-| = dy + dx (the inflow boundary's length)."""
+    from fractions import Fraction as Fr
+    import mpmath as mp
+    ny, nx = u.shape[2], u.shape[3]
+    dxf, dyf = Fr(dx), Fr(dy)
+
+    def coef(ci, cj):
+        ci, cj = ci % nx, cj % ny
+        return Fr(u[c, 0, cj, ci]), Fr(u[c, 1, cj, ci]), Fr(u[c, 2, cj, ci])
+
+    def P(ci, cj, sx, sy):  # sx = x - x_ci, sy = y - y_cj
+        a, v, w = coef(ci, cj)
+        return a + 12 * v * sx / dxf + 12 * w * sy / dyf
+
+    def line_int(f, t0, t1):
+        # f linear in t: the trapezoid rule is exact
+        return (f(t0) + f(t1)) / 2 * (t1 - t0)
+
+    hx, hy = dxf / 2, dyf / 2
+    if velx >= 0:   # face x = x_{i-1/2}: the cell at sx = -hx, the left neighbour at +hx
+        ix = line_int(lambda t: P(i, j, -hx, t) - P(i - 1, j, hx, t), -hy, hy)
+    else:
+        ix = line_int(lambda t: P(i, j, hx, t) - P(i + 1, j, -hx, t), -hy, hy)
+    if vely >= 0:
+        iy = line_int(lambda t: P(i, j, t, -hy) - P(i, j - 1, t, hy), -hx, hx)
+    else:
+        iy = line_int(lambda t: P(i, j, t, hy) - P(i, j + 1, t, -hy), -hx, hx)
+    nrm = max(abs(Fr(u[c, 0, j % ny, i % nx])), Fr(1e-12))
+    q = abs(ix + iy) / ((dxf + dyf) * nrm)
+    mp.mp.dps = 40
+    h = mp.sqrt(mp.mpf(dx) ** 2 + mp.mpf(dy) ** 2) / 2
+    return float(mp.mpf(q.numerator) / mp.mpf(q.denominator) / h)
+
+
+def test_kxrcf_indicator_hand_computed_2d():
+    """Sec. 2.2 Step 4 / Remark 3 (KXRCF, reading of the deferred reference):
+    the oracle's indicator equals the exact value on small periodic grids with
+    dx != dy, for Burgers (velocity (u, u): both signs occur) and for Euler
+    through rho and E with the velocity (m/rho, n/rho) of the cell (all four
+    sign pairs occur), so both face pairs and both sides of each are used."""
+    rng = np.random.default_rng(5)
+    nx, ny, dx, dy = 4, 3, 0.25, 0.4
+    u = np.zeros((1, 3, ny, nx))
+    u[0, 0] = rng.uniform(-1, 1, (ny, nx))
+    u[0, 1:] = rng.uniform(-0.1, 0.1, (2, ny, nx))
+    cfg = O.Cfg2D.make(O.BURGERS, nx, ny, 0.0, nx * dx, 0.0, ny * dy, O.BC_PERIODIC)
+    _, _, flags, ind = O.rhs2d(cfg, u, 2.0, 2.0)
+    signs = set()
+    for j in range(ny):
+        for i in range(nx):
+            v = u[0, 0, j, i]
+            want = _kxrcf2d_exact(u, 0, i, j, v, v, dx, dy)
+            assert abs(ind[j, i] - want) <= 1e-13 * want, (i, j, ind[j, i], want)
+            assert flags[j, i] == (want > 1.0)
+            signs.add(v >= 0)
+    assert signs == {True, False}
+    # Euler
+    rho = rng.uniform(0.5, 1.5, (ny, nx))
+    mu = rng.choice([-1, 1], (ny, nx)) * rng.uniform(0.1, 0.5, (ny, nx))
+    nu = rng.choice([-1, 1], (ny, nx)) * rng.uniform(0.1, 0.5, (ny, nx))
+    mu[0, :2], nu[0, :2] = [0.3, -0.3], [0.2, 0.2]
+    mu[1, :2], nu[1, :2] = [0.3, -0.3], [-0.2, -0.2]
+    p = rng.uniform(0.5, 1.5, (ny, nx))
+    u = np.zeros((4, 3, ny, nx))
+    u[:, 0] = W.euler_conserved_2d(rho, mu, nu, p)
+    u[:, 1:] = rng.uniform(-0.03, 0.03, (4, 2, ny, nx))
+    cfg = O.Cfg2D.make(O.EULER, nx, ny, 0.0, nx * dx, 0.0, ny * dy, O.BC_PERIODIC)
+    _, _, flags, ind = O.rhs2d(cfg, u, 3.0, 3.0)
+    pairs = set()
+    for j in range(ny):
+        for i in range(nx):
+            vx = u[1, 0, j, i] / u[0, 0, j, i]
+            vy = u[2, 0, j, i] / u[0, 0, j, i]
+            want = max(_kxrcf2d_exact(u, 0, i, j, vx, vy, dx, dy),
+                       _kxrcf2d_exact(u, 3, i, j, vx, vy, dx, dy))
+            assert abs(ind[j, i] - want) <= 1e-13 * want, (i, j)
+            assert flags[j, i] == (want > 1.0)
+            pairs.add((vx >= 0, vy >= 0))
+    assert len(pairs) == 4
+
+
+def test_kxrcf_scaling_laws_2d():
+    """The 2D normalisation h |dI^-| (h the half diagonal): on smooth data the
+    face-integrated jump is O(dx^4) (O(dx^3) per unit length by the same
+    projection symmetry as in 1D, times the face length), the denominator
+    O(dx^2), so the indicator falls like dx^2; across a discontinuity aligned
+    with the x-faces it grows like 1/dx, with the value fixed by the
+    normalisation: I = |jump| dy / (sqrt(2) dx/2 * 2 dx * |u|) on square cells."""
+    def ind_of(func, n):
+        u = W.cell_moments_2d(func, n, n, 0.0, 1.0, 0.0, 1.0, 3)
+        cfg = O.Cfg2D.make(O.BURGERS, n, n, 0.0, 1.0, 0.0, 1.0, O.BC_PERIODIC)
+        _, _, _, ind = O.rhs2d(cfg, u, 3.0, 3.0)
+        return ind
+    smooth = lambda x, y: 1.5 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    a, b = ind_of(smooth, 16).max(), ind_of(smooth, 32).max()
+    order = np.log2(a / b)
+    assert 1.7 < order < 2.3, order
+    step = lambda x, y: np.where((x > 0.25) & (x < 0.75), 1.0, 0.5) + 0 * y
+    for n in (16, 32):
+        ind = ind_of(step, n)
+        dx = 1.0 / n
+        want = 0.5 * dx / (np.sqrt(2) * dx / 2 * 2 * dx * 1.0)  # rising face, u = 1
+        np.testing.assert_allclose(ind[:, n // 4], want, rtol=1e-12)
+        np.testing.assert_allclose(ind[:, 3 * n // 4], 2 * want, rtol=1e-12)
