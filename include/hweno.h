@@ -144,21 +144,25 @@ hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* st
  * fail when the pool has reserved the memory), a process whose device memory
  * is budgeted allocation by allocation, or a latency-bound loop that cannot
  * afford the device synchronisation an allocation or a free may cause.
- * It needs no handle: cfg (dim must be 1) is validated as hweno_create would
- * and cuda_stream is the stream to run on (NULL: legacy default stream).
+ * It needs no handle: cfg (dim must be 1) passes the checks of hweno_create
+ * (every boundary condition, variant and precision hweno_create accepts for
+ * 1D) and cuda_stream is the stream to run on (NULL: legacy default stream).
  * in, out, flags_out and ulim_out mean exactly what they mean for hweno_rhs
  * (caller-owned device buffers in cfg->precision; flags_out and ulim_out
  * nullable; no overlap), and the result is the same L(in).
  * Scratch: a file-scope __device__ array inside the library, which every GPU
  * that loads the library holds until the process exits.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and caches it; make that first call before any stream
- * capture.  Every call shares the one array and each call resets the part
- * that must start at zero, so calls that overlap on the GPU (other streams,
- * other host threads) race and must be serialised by the caller.
+ * device current) and caches it for the life of the process; make that first
+ * call before any stream capture begins, and do not use the library across a
+ * cudaDeviceReset (the cached address would be stale).  Every call shares the
+ * one array and each call resets the part that must start at zero, so calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.
  * Returns HWENO_ERR_TOO_LARGE when cfg->nx > HWENO_NOALLOC_MAX_CELLS,
  * HWENO_ERR_ARG for any other invalid argument, HWENO_ERR_NONPHYSICAL for a
- * non-finite or non-physical result; waits for the stream before returning. */
+ * non-finite or non-physical result; copies the status word to the host and
+ * waits for the stream before returning. */
 hweno_status hweno_rhs1d_noalloc(const hweno_config* cfg, void* cuda_stream, const void* in,
                                  void* out, uint8_t* flags_out, void* ulim_out);
 

@@ -442,6 +442,11 @@ cudaError_t batch_tiles(hweno_ctx* h, int nth) {
 
 }  // namespace
 
+namespace hw {
+// The configuration checks of hweno_create, for entry points without a handle.
+hweno_status validate_config(const hweno_config* c) { return validate(c); }
+}  // namespace hw
+
 extern "C" {
 
 void hweno_default_config(hweno_config* cfg, int dim, int system) {

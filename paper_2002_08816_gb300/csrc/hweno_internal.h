@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hweno.h"
 #include "hweno_device.cuh"
 
 namespace hw {
@@ -159,6 +160,10 @@ cudaError_t prepare_adj2d(int system, int fp64, int ng);
 cudaError_t launch_adj2d(const Adj2DArgs& a, cudaStream_t s);
 
 cudaError_t launch_stage1d(const Stage1DArgs& a, cudaStream_t s);
+
+// hweno_create's configuration checks (HWENO_OK or HWENO_ERR_ARG; the reason
+// goes to hweno_last_error(NULL)).
+hweno_status validate_config(const hweno_config* c);
 
 // A run of many 1D Runge-Kutta steps in one persistent launch: every CTA
 // walks its tiles of each stage, then all CTAs meet at a grid barrier.  The

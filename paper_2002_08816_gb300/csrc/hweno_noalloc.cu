@@ -50,7 +50,9 @@ std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the life of the process:
+// after cudaDeviceReset the cached address is stale, so the library must not
+// be used across a device reset.
 hweno_status scratch_on_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -67,30 +69,13 @@ hweno_status scratch_on_current_device(double** out) {
   return HWENO_OK;
 }
 
+// hweno_create's checks, plus the two this entry point adds: one dimension,
+// and no more cells than the scratch holds.
 hweno_status check_config(const hweno_config* c) {
   if (!c) return HWENO_ERR_ARG;
   if (c->dim != 1) return HWENO_ERR_ARG;
-  if (c->system != HWENO_BURGERS && c->system != HWENO_EULER)
-    return HWENO_ERR_ARG;
-  if (c->nx < 4) return HWENO_ERR_ARG;
   if (c->nx > HWENO_NOALLOC_MAX_CELLS) return HWENO_ERR_TOO_LARGE;
-  if (!(c->x1 > c->x0)) return HWENO_ERR_ARG;
-  if (c->bc != HWENO_BC_PERIODIC && c->bc != HWENO_BC_OUTFLOW)
-    return HWENO_ERR_ARG;
-  if (c->system == HWENO_EULER && !(c->gas_gamma > 1.0))
-    return HWENO_ERR_ARG;
-  double s = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    if (!(c->lin_w[k] > 0.0)) return HWENO_ERR_ARG;
-    s += c->lin_w[k];
-  }
-  if (fabs(s - 1.0) > 1e-12) return HWENO_ERR_ARG;
-  if (!(c->eps > 0.0)) return HWENO_ERR_ARG;
-  if (!(c->kxrcf_threshold >= 0.0)) return HWENO_ERR_ARG;
-  if (c->troubled_mode < 0 || c->troubled_mode > 2) return HWENO_ERR_ARG;
-  if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64)
-    return HWENO_ERR_ARG;
-  return HWENO_OK;
+  return hw::validate_config(c);
 }
 
 }  // namespace
