@@ -18,13 +18,14 @@ constexpr int NT = kThreads1D;  // threads of the wave-speed kernels
 constexpr int T = kTile1D;      // their cells per CTA
 constexpr int NW = NT / 32;
 
-// The 128-thread tiles are the high-occupancy choice: 10 CTAs per SM in FP32
-// (48 registers, a few spilled), 6 in FP64, which hides the stage's dependent
+// Every CTA has NTH cell threads and one scalar warp (hweno1d_stage.cuh).
+// The 128-thread tiles are the high-occupancy choice: 8 CTAs per SM in FP32
+// (at most 51 registers), 6 in FP64, which hides the stage's dependent
 // load and arithmetic chains on large states and batches; on small states,
 // which sit at the per-stage latency floor, the 256-thread tiles at the
 // register count the compiler picks are faster.  hweno_autotune chooses.
 template <typename R, int C, bool BATCH, int NTH>
-__global__ void __launch_bounds__(NTH, NTH == 128 ? (sizeof(R) == 4 ? 10 : 6) : 1)
+__global__ void __launch_bounds__(NTH + 32, NTH == 128 ? (sizeof(R) == 4 ? 8 : 6) : 1)
     stage1d_kernel(Stage1DArgs a) {
   __shared__ Smem1D<R, C, NTH> sm;
   s1d::stage1d_tile<R, C, BATCH, NTH>(a, blockIdx.x, sm);
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(128) barrier_check_kernel(unsigned* bar, int m
 }
 
 template <typename R, int C, bool BATCH, int NTH>
-__global__ void __launch_bounds__(NTH) run1d_kernel(Run1DArgs r) {
+__global__ void __launch_bounds__(NTH + 32) run1d_kernel(Run1DArgs r) {
   __shared__ Smem1D<R, C, NTH> sm;
   unsigned meet = 0;  // arrivals that end the next meeting
   for (int step = 0; step < r.nsteps; ++step) {
@@ -124,7 +125,7 @@ cudaError_t max_ctas_t(int* ctas) {
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run1d_kernel<R, C, BATCH, NTH>, NTH, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run1d_kernel<R, C, BATCH, NTH>, NTH + 32, 0);
   *ctas = per * nsm;
   return e;
 }
@@ -141,7 +142,7 @@ cudaError_t run_t(const Run1DArgs& r, cudaStream_t s) {
   Run1DArgs rc = r;
   void* args[] = {&rc};
   return cudaLaunchCooperativeKernel((const void*)run1d_kernel<R, C, BATCH, NTH>, dim3(grid),
-                                     dim3(NTH), args, 0, s);
+                                     dim3(NTH + 32), args, 0, s);
 }
 
 template <typename R, int C, bool BATCH>
@@ -169,9 +170,11 @@ cudaError_t max_c(int batch, int nth, int* ctas) {
 }
 
 
+// Wave-speed maxima in FP64 slots (the per-cell speeds in the kernel's
+// precision, as the stage kernels compute them).
 template <typename R, int C>
-__global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, R* a_out, int n,
-                                                    double gas, DevScalars* sc, int slots) {
+__global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, double* a_out,
+                                                    int n, double gas, DevScalars* sc, int slots) {
   __shared__ R red[NW];
   const int i = blockIdx.x * T + threadIdx.x;
   R s = R(0);
@@ -191,9 +194,9 @@ __global__ void __launch_bounds__(NT) alpha1d_kernel(const R* __restrict__ w, R*
   if (threadIdx.x == 0) {
     for (int k = 0; k < NW; ++k) s = fmax(s, red[k]);
     if (slots)
-      atomic_max_nonneg(a_out + blockIdx.x % kAlphaSlots, s);
+      atomic_max_nonneg(a_out + blockIdx.x % kAlphaSlots, (double)s);
     else
-      a_out[blockIdx.x] = s;
+      a_out[blockIdx.x] = (double)s;
   }
 }
 
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(NTH) alpha1d_batch_kernel(Stage1DArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < NW; ++k) s = fmax(s, red[k]);
-    atomic_max_nonneg(static_cast<R*>(a.a_out) + inst, s);
+    atomic_max_nonneg(static_cast<double*>(a.a_out) + inst, (double)s);
   }
 }
 
@@ -303,7 +306,7 @@ template <typename R, int C, int NTH>
 cudaError_t launch_stage1d_n(const Stage1DArgs& a, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)a.ntile);
-  cfg.blockDim = dim3(NTH);
+  cfg.blockDim = dim3(NTH + 32);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -369,17 +372,16 @@ cudaError_t launch_alpha1d(const void* w, void* a_out, int n, int ntile, int sys
   const double* wd = static_cast<const double*>(w);
   const float* wf = static_cast<const float*>(w);
   double* od = static_cast<double*>(a_out);
-  float* of = static_cast<float*>(a_out);
   if (system == 0) {
     if (fp64)
       alpha1d_kernel<double, 1><<<ntile, NT, 0, s>>>(wd, od, n, gas, sc, slots);
     else
-      alpha1d_kernel<float, 1><<<ntile, NT, 0, s>>>(wf, of, n, gas, sc, slots);
+      alpha1d_kernel<float, 1><<<ntile, NT, 0, s>>>(wf, od, n, gas, sc, slots);
   } else {
     if (fp64)
       alpha1d_kernel<double, 3><<<ntile, NT, 0, s>>>(wd, od, n, gas, sc, slots);
     else
-      alpha1d_kernel<float, 3><<<ntile, NT, 0, s>>>(wf, of, n, gas, sc, slots);
+      alpha1d_kernel<float, 3><<<ntile, NT, 0, s>>>(wf, od, n, gas, sc, slots);
   }
   return cudaGetLastError();
 }

@@ -2,15 +2,19 @@
 // scheme (Zhao & Qiu, arXiv:2002.08816, Sec. 2.1) on one tile, shared by the
 // per-stage kernel and the persistent kernel (hweno1d.cu).
 //
-// A CTA of NTH threads owns T = NTH - 6 consecutive cells.  It stages its cells
-// plus a 3-cell halo of the stage input in shared memory (coalesced loads of
-// each structure-of-arrays row), then, all on chip:
-//   1. alpha = max |f'(ubar)| from the maxima the producer of the stage
-//      input left in kAlphaSlots slots (global Lax-Friedrichs flux); stage 1
-//      also turns alpha into dt = CFL dx / alpha, clipped to t_final.  All of
-//      it runs in the kernel's precision: on GB300 each dependent FP64
-//      operation costs tens of cycles, so the FP32 kernel keeps FP64 off its
-//      critical path (the time itself is accumulated in FP64 by an idle thread);
+// A CTA of NTH + 32 threads owns T = NTH - 6 consecutive cells: NTH cell
+// threads and one scalar warp.  The cell threads stage the cells plus a
+// 3-cell halo of the stage input in shared memory (coalesced loads of each
+// structure-of-arrays row), then, all on chip:
+//   1. (scalar warp, concurrently with steps 2-3 of the cell threads, all in
+//      FP64) alpha = max |f'(ubar)| over the maxima the producer of the stage
+//      input left in kAlphaSlots FP64 slots (global Lax-Friedrichs flux);
+//      stage 1 also turns alpha into dt = CFL dx / alpha, clipped to t_final;
+//      the lead tile records dt and, in stage 3, the time.  The per-cell
+//      wave speeds are bulk arithmetic in the kernel's precision; their
+//      maximum, dt, the clipping and the time are FP64, off the cell
+//      threads' critical path (a dependent FP64 operation costs tens of
+//      cycles on GB300, a division hundreds);
 //   2. KXRCF flags and the modified first moments (Step 1) for the cells and
 //      2 halo cells per side, in characteristic fields for Euler (out-of-line
 //      work of the troubled lanes); an FP32 kernel decides a flag in FP32 when
@@ -21,8 +25,8 @@
 //   4. for the own cells: interior Gauss-Lobatto values (Step 2.3), the
 //      Lax-Friedrichs fluxes at x_{i-+1/2}, F_i, the right-hand sides of
 //      Eq. (odeH) and the Runge-Kutta combination of Eq. (RK);
-//   5. the maximum wave speed of the output, folded by atomic max into the
-//      tile's one of kAlphaSlots slots that the next stage reads for its alpha
+//   5. the maximum wave speed of the output, folded by FP64 atomic max into
+//      the tile's one of kAlphaSlots slots that the next stage reads for its alpha
 //      (warp by warp, or after a CTA reduction on large grids), the troubled
 //      count and the status bits (non-finite, non-physical).
 // The limited stage input is what the RK combination uses (the first moment
@@ -43,6 +47,16 @@ constexpr int H = 3;  // halo cells per side
 // grids of at most this many tiles fold the wave-speed maxima warp by warp
 constexpr int kWarpAtomicTiles = 2048;
 
+// Named barriers: kBarCells among the NTH cell threads only; kBarAll for the
+// cell threads and the scalar warp (which only arrives) before step 4.
+constexpr int kBarCells = 1, kBarAll = 2;
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // A load of data another CTA may have written earlier in the same launch
 // (the persistent kernel): through L2, never from a stale L1 line.
 template <typename T>
@@ -62,7 +76,7 @@ struct Smem1D {
   uint8_t fl[T + 4];     // flags, cells base-2 .. base+T+1
   R red[NW];
   int cnt[NW];
-  R amax[NW];
+  R alpha, dt;           // from the scalar warp, in the kernel's precision
 };
 
 template <typename R, int C>
@@ -168,7 +182,7 @@ __device__ __noinline__ ConsFaces<R> char_faces(R gas, R g0, R g1, R g2, R eps, 
   return o;
 }
 
-// One stage on one tile of T = NTH - 6 cells, by a CTA of NTH threads.  The
+// One stage on one tile of T = NTH - 6 cells, by a CTA of NTH + 32 threads.  The
 // per-stage kernel calls it once; the persistent kernel calls it for each of
 // its tiles of each stage, between grid barriers, so every load of data
 // produced in the same launch goes through L2 (ldx).
@@ -194,7 +208,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
     a.out = static_cast<R*>(a.out) + off;
     if (a.lim_out) a.lim_out = static_cast<R*>(a.lim_out) + off;
     if (a.flags_out) a.flags_out += off / (2 * C);
-    a.a_in = static_cast<const R*>(a.a_in) + inst;
+    a.a_in = static_cast<const double*>(a.a_in) + inst;
     a.nin = 1;
     a.inv_dx = bi.inv_dx;
     a.h = bi.h;
@@ -211,51 +225,117 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
   // Parameters in the kernel's precision (FP32 copies made on the host).
-  R gam[3], eps, gas, inv_dx, cfl_dx;
+  R gam[3], eps, gas, inv_dx;
   if constexpr (sizeof(R) == 4) {
     gam[0] = a.f32[0]; gam[1] = a.f32[1]; gam[2] = a.f32[2];
-    eps = a.f32[3]; gas = a.f32[4]; inv_dx = a.f32[5]; cfl_dx = a.f32[6];
+    eps = a.f32[3]; gas = a.f32[4]; inv_dx = a.f32[5];
   } else {
     gam[0] = a.gam[0]; gam[1] = a.gam[1]; gam[2] = a.gam[2];
-    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx; cfl_dx = a.cfl_dx;
+    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx;
   }
 
-  // 1-2. in one round trip: every thread fetches its share of the producer's
-  //      wave-speed maxima (for alpha), its tile-plus-halo element, the time
-  //      bookkeeping, and in stages 2 and 3 the modified u^n of its own cell
-  const R* a_in = static_cast<const R*>(a.a_in);
-  R amax = R(0);
-  for (int k = tid; k < a.nin; k += NT) amax = fmax(amax, ldx(a_in + k));
-  R rem = R(0), dt_prev = R(0);
-  if constexpr (BATCH) {
-    const BatchScalars& bs = a.bsc[inst];
-    if (a.stage == 1)
-      rem = sizeof(R) == 4 ? R(ldx(&bs.rem_f)) : R(ldx(&bs.rem));
-    else if (a.stage > 1)
-      dt_prev = sizeof(R) == 4 ? R(ldx(&bs.dt_f)) : R(ldx(&bs.dt));
-  } else {
-    if (a.stage == 1)
-      rem = sizeof(R) == 4 ? R(ldx(&a.sc->rem_f)) : R(ldx(&a.sc->rem));
-    else if (a.stage > 1)
-      dt_prev = sizeof(R) == 4 ? R(ldx(&a.sc->dt_f)) : R(ldx(&a.sc->dt));
-  }
-  // the time bookkeeping's inputs (stage 3, the last thread of the lead
-  // tile), fetched with the rest: its FP64 update then costs no round trip
-  const bool keeper = a.stage == 3 && lead && tid == NT - 1;
-  double bk_tf = 0.0, bk_t = 0.0;
-  unsigned bk_last = 0u;
-  unsigned long long bk_steps = 0ull;
-  if (keeper) {
-    bk_tf = ldx(&a.sc->t_final);
-    bk_steps = ldx(&a.sc->steps);
-    if constexpr (BATCH) {
-      bk_last = ldx(&a.bsc[inst].last);
-      bk_t = ldx(&a.bsc[inst].t);
-    } else {
-      bk_last = ldx(&a.sc->last);
-      bk_t = ldx(&a.sc->t);
+  if (tid >= NT) {
+    // ---- the scalar warp: alpha, dt and the time, in FP64 ----------------
+    // its own loads go out first, concurrently with the cell threads' tile
+    const unsigned long long* a_in = static_cast<const unsigned long long*>(a.a_in);
+    unsigned long long am = 0ull;  // bit patterns of non-negative doubles: the
+                                   // integer order is the numeric order
+    for (int k = lane; k < a.nin; k += 32) {
+      const unsigned long long v = ldx(a_in + k);
+      am = v > am ? v : am;
     }
+    double rem = 0.0, dt = 0.0, tf = 0.0, t = 0.0;
+    unsigned last = 0u;
+    unsigned long long steps = 0ull;
+    const bool keep = a.stage == 3 && lead && lane == 0;  // the time keeper
+    if constexpr (BATCH) {
+      const BatchScalars& bs = a.bsc[inst];
+      if (a.stage == 1) rem = ldx(&bs.rem);
+      else if (a.stage > 1) dt = ldx(&bs.dt);
+      if (keep) {
+        last = ldx(&bs.last);
+        t = ldx(&bs.t);
+      }
+    } else {
+      if (a.stage == 1) rem = ldx(&a.sc->rem);
+      else if (a.stage > 1) dt = ldx(&a.sc->dt);
+      if (keep) {
+        last = ldx(&a.sc->last);
+        t = ldx(&a.sc->t);
+      }
+    }
+    if (keep) {
+      tf = ldx(&a.sc->t_final);
+      steps = ldx(&a.sc->steps);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, am, o);
+      am = v > am ? v : am;
+    }
+    asm volatile("griddepcontrol.launch_dependents;");
+    const double alpha = __longlong_as_double((long long)am);
+    if (a.stage == 1) {
+      // dt = CFL dx / alpha(u^n), clipped to the remaining time (the clipped
+      // step is the last one and ends exactly at t_final); 0 once t_final
+      // has been reached
+      dt = a.cfl_dx / alpha;
+      last = 0u;
+      if (rem <= 0.0) {
+        dt = 0.0;
+      } else if (dt >= rem) {
+        dt = rem;
+        last = 1u;
+      }
+      if (!(alpha > 0.0) || !isfinite(dt)) dt = 0.0;
+      if (lead && lane == 0) {
+        if constexpr (BATCH) {
+          BatchScalars& bs = a.bsc[inst];
+          bs.dt = dt;
+          bs.dt_f = (float)dt;
+          bs.last = last;
+        } else {
+          a.sc->dt = dt;
+          a.sc->dt_f = (float)dt;
+          a.sc->last = last;
+        }
+      }
+    }
+    if (lane == 0) {
+      sm.alpha = R(alpha);
+      sm.dt = R(dt);
+    }
+    if (a.stage > 0 && dt > 0.0) {
+      // the slots of the stage after next (read two stages ago, now free)
+      if constexpr (BATCH) {
+        if (a.a_zero && lead && lane == 0) static_cast<double*>(a.a_zero)[inst] = 0.0;
+      } else {
+        if (a.a_zero && tile == 0)
+          for (int k = lane; k < kAlphaSlots; k += 32) static_cast<double*>(a.a_zero)[k] = 0.0;
+      }
+      if (keep) {  // stage 3 of the lead tile: the step is complete
+        const double tn = last ? tf : t + dt;
+        const double r = tf > 0.0 ? tf - tn : (double)INFINITY;
+        if constexpr (BATCH) {
+          BatchScalars& bs = a.bsc[inst];
+          bs.t = tn;
+          bs.rem = r;
+          bs.rem_f = (float)r;
+          if (inst == 0) a.sc->steps = steps + 1ull;
+        } else {
+          a.sc->t = tn;
+          a.sc->rem = r;
+          a.sc->rem_f = (float)r;
+          a.sc->steps = steps + 1ull;
+        }
+      }
+    }
+    bar_arrive(kBarAll, NT + 32);
+    return;
   }
+
+  // ---- the cell threads --------------------------------------------------
+  // 2. in one round trip: the tile-plus-halo element of each thread and, in
+  //    stages 2 and 3, the modified u^n of its own cell
   R u0c[C][2];
   if (a.stage >= 2 && tid < T && base + tid < n) {
     const R* u0 = static_cast<const R*>(a.u0);
@@ -283,45 +363,9 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  if (lane == 0) sm.amax[warp] = amax;
-  __syncthreads();
+  bar_sync(kBarCells, NT);
   // the next stage's CTAs may be scheduled now; they wait for this grid above
   asm volatile("griddepcontrol.launch_dependents;");
-  // alpha (every thread reads the warps' maxima) and dt: CFL dx / alpha in
-  // stage 1, clipped to the remaining time; 0 once t_final is reached
-  R alpha = sm.amax[0];
-#pragma unroll
-  for (int k = 1; k < NW; ++k) alpha = fmax(alpha, sm.amax[k]);
-  R dt = dt_prev;
-  if (a.stage == 1) {
-    dt = cfl_dx / alpha;
-    unsigned last = 0;
-    if (rem <= R(0)) {
-      dt = R(0);
-    } else if (dt >= rem) {  // clipped: this step ends exactly at t_final
-      dt = rem;
-      last = 1;
-    }
-    if (!(alpha > R(0)) || !isfinite(dt)) dt = R(0);
-    if (lead && tid == 0) {
-      if constexpr (BATCH) {
-        BatchScalars& bs = a.bsc[inst];
-        if (sizeof(R) == 4) bs.dt_f = (float)dt; else bs.dt = (double)dt;
-        bs.last = last;
-      } else {
-        sc_dt<R>(a.sc) = dt;
-        a.sc->last = last;
-      }
-    }
-  }
-  if (a.stage > 0 && !(dt > R(0))) return;  // uniform over the grid (the instance)
-  // the slots of the stage after next (read two stages ago, now free)
-  if constexpr (BATCH) {
-    if (a.a_zero && lead && tid == 0) static_cast<R*>(a.a_zero)[inst] = R(0);
-  } else {
-    if (a.a_zero && tile == 0 && tid < kAlphaSlots) static_cast<R*>(a.a_zero)[tid] = R(0);
-  }
 
   // 3. troubled cells and modified first moments (Step 1), cells base-2 ..
   //    base+T+1; Euler limits in the characteristic fields of the cell
@@ -365,7 +409,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       for (int c = 0; c < 3; ++c) sm.vl[c][k] = o.v[c];
     }
   }
-  __syncthreads();
+  bar_sync(kBarCells, NT);
 
   // 4. interface values (Steps 2.1, 2.2) and their physical fluxes, cells base-1 ..
   //    base+T
@@ -424,30 +468,11 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       sm.ffp[c][k] = fR[c];
     }
   }
-  __syncthreads();
-
-  // time bookkeeping (FP64) by a thread that has no cell in phase 5
-  if (keeper) {
-    DevScalars* sc = a.sc;
-    const double tf = bk_tf;
-    const double t = bk_last ? tf : bk_t + (double)dt;
-    const double r = tf > 0.0 ? tf - t : (double)INFINITY;
-    if constexpr (BATCH) {
-      BatchScalars& bs = a.bsc[inst];
-      bs.t = t;
-      bs.dt = (double)dt;
-      bs.rem = r;
-      bs.rem_f = (float)r;
-      if (inst == 0) sc->steps = bk_steps + 1ull;
-    } else {
-      sc->t = t;
-      sc->dt = (double)dt;
-      sc->rem = r;
-      sc->rem_f = (float)r;
-      sc->steps = bk_steps + 1ull;
-    }
-  }
-  static_assert(T < NT, "a thread without a cell keeps the time");
+  // alpha and dt from the scalar warp; a zero dt (t_final reached) is
+  // uniform over the grid (the instance), and the stage then writes nothing
+  bar_sync(kBarAll, NT + 32);
+  const R alpha = sm.alpha, dt = sm.dt;
+  if (a.stage > 0 && !(dt > R(0))) return;
 
   // 5. own cells: fluxes, F_i, right-hand side, RK combination
   const int i = base + tid;
@@ -533,10 +558,10 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
   for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
   const int wcnt = __popc(__ballot_sync(0xffffffffu, myflag));
   if (bad) atomicOr(&a.sc->status, bad);
-  R* const slot = static_cast<R*>(a.a_out) + (BATCH ? inst : tile % kAlphaSlots);
+  double* const slot = static_cast<double*>(a.a_out) + (BATCH ? inst : tile % kAlphaSlots);
   if (BATCH || a.ntile <= kWarpAtomicTiles) {
     if (lane == 0) {
-      if (a.a_out) atomic_max_nonneg(slot, wmax);
+      if (a.a_out) atomic_max_nonneg(slot, (double)wmax);
       if (wcnt) atomicAdd(&a.sc->troubled, (unsigned long long)wcnt);
     }
     return;
@@ -545,7 +570,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
     sm.red[warp] = wmax;
     sm.cnt[warp] = wcnt;
   }
-  __syncthreads();
+  bar_sync(kBarCells, NT);
   if (warp == 0) {
     R m = lane < NW ? sm.red[lane] : R(0);
     int c = lane < NW ? sm.cnt[lane] : 0;
@@ -554,7 +579,7 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
       c += __shfl_xor_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-      if (a.a_out) atomic_max_nonneg(slot, m);
+      if (a.a_out) atomic_max_nonneg(slot, (double)m);
       if (c) atomicAdd(&a.sc->troubled, (unsigned long long)c);
     }
   }

@@ -259,3 +259,24 @@ def test_run_blast_waves_between_walls(prec, tol):
     stats, nt = _compare_run(H.HWENO_EULER, nx, H.HWENO_BC_REFLECTIVE, prec, 40, u, 0.0, 1.0, tol,
                              cfl=0.6)
     assert nt > 0
+
+
+@pytest.mark.parametrize("system", [H.HWENO_BURGERS, H.HWENO_EULER])
+def test_fp32_time_step_is_fp64(system):
+    """The FP32 path's global CFL reduction and dt are FP64 (Sec. 2.1, alpha =
+    max |f'(u)|; Sec. 3, CFL): after one step t equals the recorded dt, which
+    is the correctly rounded FP64 quotient CFL dx / alpha of an alpha that is
+    the FP64 maximum of FP32 wave speeds (so alpha is a float).  It agrees with
+    the oracle's dt on the same input to the FP32 wave speeds' few ulp."""
+    nx, cfl = 3001, 0.5
+    u = round_to(H.HWENO_FP32, mixed_euler(nx, 9) if system == H.HWENO_EULER
+                 else mixed_burgers(nx, 9))
+    cfg, ocfg = make_pair(system, nx, 0.0, 1.0, H.HWENO_BC_OUTFLOW, H.HWENO_FP32, cfl=cfl)
+    _, t, stats = gpu_run1d(cfg, u, 1)
+    dt = stats["dt"]
+    assert t == dt
+    cdx = cfl * (1.0 / nx)
+    alpha = np.float32(cdx / dt)
+    assert cdx / np.float64(alpha) == dt
+    dt_o = O.dt1d(ocfg, u, cfl)
+    assert abs(dt - dt_o) <= 1e-6 * dt_o
