@@ -222,18 +222,22 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
  * stage launches captured in CUDA graphs, or one persistent cooperative
  * launch per hweno_step call (every CTA walks its tiles of a stage, then the
  * grid meets at a barrier whose wait is bounded), each with 128, 256 or 512
- * threads per CTA (a tile is that number minus 6 cells).  Each of the six
- * candidates advances the current state nsteps_trial steps once untimed (which
+ * threads per CTA (a tile is that number minus 6 cells), and, for FP32
+ * single-instance handles whose tiles fit on the GPU at once, one resident
+ * launch per hweno_step call with 256 or 512 threads per CTA (every CTA keeps
+ * its tile in shared memory for the whole run and exchanges only 3-cell halos
+ * and its maximum wave speed with the others, all waits bounded).  Each
+ * candidate advances the current state nsteps_trial steps once untimed (which
  * builds its graphs) and then twice timed with CUDA events on the handle's
  * stream; the one with the fastest trial is kept for later calls; the
  * state, time, counters and wave-speed slots are restored afterwards.  The
- * per-stage candidates give bitwise the same results; the persistent ones
- * agree with them to rounding (their copy of the stage body may contract a few
- * multiply-adds differently).  The paper has no counterpart (it fixes no
- * hardware mapping).  choice_out (nullable, 2 ints) receives the threads per
- * CTA and 1 for the persistent launch, 0 for graphs.  New handles start with
- * 256 threads and per-stage graphs.  Waits for the stream; HWENO_ERR_ARG for 2D
- * handles, HWENO_ERR_STATE before set_state. */
+ * per-stage candidates give bitwise the same results; the persistent and
+ * resident ones agree with them to rounding (their copy of the stage body may
+ * contract a few multiply-adds differently).  The paper has no counterpart (it
+ * fixes no hardware mapping).  choice_out (nullable, 2 ints) receives the
+ * threads per CTA and the launch kind (0 graphs, 1 persistent, 2 resident).
+ * New handles start with 256 threads and per-stage graphs.  Waits for the
+ * stream; HWENO_ERR_ARG for 2D handles, HWENO_ERR_STATE before set_state. */
 hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
 
 /* Failure-detection self-test of the grid barrier the persistent launch uses
@@ -252,8 +256,14 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
 hweno_status hweno_check_barrier(int ctas, int meetings, int missing, unsigned polls);
 
 /* Sets the choice hweno_autotune makes by hand: threads per CTA (128, 256 or
- * 512) and persistent (1) or per-stage graph launches (0).  1D handles only;
- * waits for the stream. */
+ * 512) and the launch kind: 0 per-stage launches in CUDA graphs, 1 one
+ * persistent launch per hweno_step with a grid barrier between stages, 2 one
+ * resident launch per hweno_step in which every CTA keeps its tile of the
+ * state in shared memory for the whole run (FP32 single-instance handles, 256
+ * or 512 threads, grids small enough for every tile to be on the GPU at once;
+ * HWENO_ERR_ARG otherwise).  1D handles only; waits for the stream.  All
+ * choices compute the same scheme; results agree to rounding (the per-stage
+ * choices bit for bit). */
 hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent);
 
 /* The conserved totals of the current state: totals[c] = the sum over cells
@@ -264,6 +274,17 @@ hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent);
  * conserves them (Eq. (odeH), Eq. (ode2) are in flux form).  Waits for the
  * stream. */
 hweno_status hweno_totals(hweno_handle h, double* totals);
+
+/* Measures the fused multiply-add throughput of the current device (FP32 when
+ * fp64 = 0, FP64 otherwise) for the arithmetic roofline of the stage kernels
+ * (no counterpart in the paper, which names no hardware): a kernel of eight
+ * independent FMA chains per thread on a grid that fills every SM, each
+ * thread doing iters x 128 FMAs, timed with CUDA events after one untimed
+ * launch on a private stream; *flops_per_s = 2 x FMAs / time, at whatever SM
+ * clock the GPU runs.  Allocates and frees a small buffer; waits for
+ * completion.  HWENO_ERR_ARG unless 1 <= iters <= 2^24 and flops_per_s is
+ * non-NULL. */
+hweno_status hweno_fma_peak(int fp64, int iters, double* flops_per_s);
 
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);

@@ -119,6 +119,11 @@ double hwo2d_beta_of_coeffs(int degree, const double* c, double ratio);
 void hwo_euler2d_flux(double g, const double* U, int dir, double* F);
 void hwo_euler2d_eigen(double g, const double* U, int dir, double R[16], double L[16]);
 
+/* ---------------- threads ---------------- */
+/* OpenMP build (libhweno_oracle_omp.so): sets the thread count when n > 0 and
+ * returns the count in use; the plain build returns 1. */
+int hwo_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -386,6 +386,7 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   /* Step 1, troubled cells (Remark 1: u for Burgers with velocity f'(u);
    * rho and E for Euler with the velocity mu). */
   for (int e = 0; e < NE; ++e) ind[e] = 0.0;
+#pragma omp parallel for schedule(static)
   for (int e = 1; e < NE - 1; ++e) {
     double I;
     if (euler) {
@@ -409,6 +410,7 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
    * characteristic fields for Euler; Reading: eigen-system at the cell's own
    * average).  All cells are modified from the unmodified moments. */
   memcpy(vl, vb, sizeof(double) * C * NE);
+#pragma omp parallel for schedule(static)
   for (int e = 1; e < NE - 1; ++e) {
     if (!fl[e]) continue;
     if (!euler) {
@@ -441,6 +443,7 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   }
 
   /* Step 2: point values for cells -1..N (extended index 2..NE-3). */
+#pragma omp parallel for schedule(static)
   for (int e = 2; e < NE - 2; ++e) {
     int hw = fl[e - 1] | fl[e] | fl[e + 1];
     if (!euler || !hw) {
@@ -486,6 +489,7 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   }
 
   /* Lax-Friedrichs flux at x_{e+1/2} from u^- (cell e) and u^+ (cell e+1). */
+#pragma omp parallel for schedule(static)
   for (int e = G1 - 1; e < G1 + N; ++e) {
     double a[3], b[3], fa[3], fb[3];
     for (int c = 0; c < C; ++c) {
@@ -499,6 +503,7 @@ int hwo1d_rhs_ex(const hwo1d_cfg* cfg, const double* u, double alpha, double* rh
   }
 
   /* Eq. (odeH) with F_i by the 4-point Gauss-Lobatto rule. */
+#pragma omp parallel for schedule(static) reduction(min : status)
   for (int i = 0; i < N; ++i) {
     int e = i + G1;
     double pts[4][3], fq[4][3];

@@ -481,6 +481,7 @@ int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
 
   /* Step 4: troubled cells (Remark 3: u for Burgers with velocity (f', g');
    * rho and E for Euler with the velocity (mu, nu)). */
+#pragma omp parallel for schedule(static)
   for (int ej = 1; ej < EY - 1; ++ej)
     for (int ei = 1; ei < EX - 1; ++ei) {
       int e = ej * EX + ei;
@@ -508,6 +509,7 @@ int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
    * the y-Jacobian at the cell's own average). */
   memcpy(vl, vb, sizeof(double) * C * NE);
   memcpy(wl, wb, sizeof(double) * C * NE);
+#pragma omp parallel for schedule(static)
   for (int ej = 1; ej < EY - 1; ++ej)
     for (int ei = 1; ei < EX - 1; ++ei) {
       int e = ej * EX + ei;
@@ -544,6 +546,7 @@ int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
     }
 
   /* Step 5: point values for cells -1..N (extended 2..E-3) */
+#pragma omp parallel for schedule(static)
   for (int ej = 2; ej < EY - 2; ++ej)
     for (int ei = 2; ei < EX - 2; ++ei) {
       int e = ej * EX + ei;
@@ -627,6 +630,7 @@ int hwo2d_rhs_fx(const hwo2d_cfg* cfg, const double* u, double alpha_x, double a
     }
 
   /* fluxes and Eq. (ode2) */
+#pragma omp parallel for schedule(static) reduction(min : status)
   for (int j = 0; j < NY; ++j)
     for (int i = 0; i < NX; ++i) {
       int e = (j + G2) * EX + (i + G2);

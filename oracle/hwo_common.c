@@ -70,3 +70,20 @@ double hwo_combine(int ncand, const double* gam, const double* omega,
   for (int n = 1; n < ncand; ++n) out += omega[n] * val[n];
   return out;
 }
+
+/* Threads of the OpenMP build (the per-cell loops of Eq. (odeH) and Eq. (ode2)
+ * carry "omp parallel for" pragmas; the plain build ignores them): sets the
+ * count when n > 0 and returns the count in use (1 in the plain build).  The
+ * arithmetic of every cell is the same in both builds. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int hwo_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}

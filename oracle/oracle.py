@@ -13,6 +13,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libhweno_oracle.so")
+# the same sources built with OpenMP: the per-cell loops run on all cores,
+# the arithmetic of every cell unchanged
+_LIB_OMP_PATH = os.path.join(_HERE, "libhweno_oracle_omp.so")
 
 BURGERS, EULER = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECTIVE = 0, 1, 2
@@ -81,86 +84,120 @@ class Cfg2D(ctypes.Structure):
         return 4 if self.system == EULER else 1
 
 
-def build(force=False):
-    """Compile the C oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+def _build_one(path, extra, force):
     srcs = sorted(glob.glob(os.path.join(_HERE, "*.c")))
-    if not force and os.path.exists(_LIB_PATH):
+    if not force and os.path.exists(path):
         newest = max(os.path.getmtime(p) for p in srcs + glob.glob(os.path.join(_HERE, "*.h")))
-        if os.path.getmtime(_LIB_PATH) >= newest:
-            return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp] + srcs + ["-lm"]
+        if os.path.getmtime(path) >= newest:
+            return path
+    tmp = path + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared"] + extra + \
+        ["-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
+    os.replace(tmp, path)
+    return path
+
+
+def build(force=False):
+    """Compile the C oracle with gcc (no FMA contraction, so x86 and Arm agree),
+    plain and with OpenMP (the second build is skipped where gcc has none)."""
+    _build_one(_LIB_PATH, [], force)
+    try:
+        _build_one(_LIB_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return _LIB_PATH
 
 
 _lib = None
+_lib_omp = None
+
+
+def lib_omp():
+    """The OpenMP build (None when it could not be built)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        if not os.path.exists(_LIB_OMP_PATH):
+            return None
+        _lib_omp = _setup(ctypes.CDLL(_LIB_OMP_PATH))
+    return _lib_omp
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB_PATH)
-        P1 = ctypes.POINTER(Cfg1D)
-        L.hwo1d_alpha.restype = _D
-        L.hwo1d_alpha.argtypes = [P1, _PD]
-        L.hwo1d_rhs.restype = _I
-        L.hwo1d_rhs.argtypes = [P1, _PD, _D, _PD, _PD, _PU8, _PD]
-        L.hwo1d_rhs_ex.restype = _I
-        L.hwo1d_rhs_ex.argtypes = [P1, _PD, _D, _PD, _PD, _PU8, _PD, _PD]
-        L.hwo1d_step.restype = _I
-        L.hwo1d_step.argtypes = [P1, _PD, _D, _PL]
-        L.hwo1d_dt.restype = _D
-        L.hwo1d_dt.argtypes = [P1, _PD, _D, _D, _D]
-        L.hwo1d_run.restype = _I
-        L.hwo1d_run.argtypes = [P1, _PD, _I, _D, _D, _D, _D, _PD, _PD, _PL]
-        L.hwo1d_limiter_candidates.restype = None
-        L.hwo1d_limiter_candidates.argtypes = [_PD, _D, _D, _PD, _PD]
-        L.hwo1d_limit_scalar.restype = _D
-        L.hwo1d_limit_scalar.argtypes = [_PD, _D, _PD, _D, _D]
-        L.hwo1d_recon_candidates.restype = None
-        L.hwo1d_recon_candidates.argtypes = [_PD, _PD, _PD, _PD]
-        L.hwo1d_recon_scalar.restype = None
-        L.hwo1d_recon_scalar.argtypes = [_PD, _D, _PD, _PD, _I, _PD]
-        L.hwo_euler1d_eigen.restype = None
-        L.hwo_euler1d_eigen.argtypes = [_D, _PD, _PD, _PD]
-        L.hwo_euler1d_flux.restype = None
-        L.hwo_euler1d_flux.argtypes = [_D, _PD, _PD]
-        if hasattr(L, "hwo2d_rhs"):
-            P2 = ctypes.POINTER(Cfg2D)
-            L.hwo2d_rhs.restype = _I
-            L.hwo2d_rhs.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD]
-            L.hwo2d_rhs_ex.restype = _I
-            L.hwo2d_rhs_ex.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD, _PD]
-            L.hwo2d_rhs_fx.restype = _I
-            L.hwo2d_rhs_fx.argtypes = [P2, _PD, _D, _D, _PU8, _PD, _PD, _PU8, _PD, _PD]
-            L.hwo2d_alpha.restype = None
-            L.hwo2d_alpha.argtypes = [P2, _PD, _PD, _PD]
-            L.hwo2d_dt.restype = _D
-            L.hwo2d_dt.argtypes = [P2, _PD, _D, _D, _D]
-            L.hwo2d_step.restype = _I
-            L.hwo2d_step.argtypes = [P2, _PD, _D, _PL]
-            L.hwo2d_run.restype = _I
-            L.hwo2d_run.argtypes = [P2, _PD, _I, _D, _D, _D, _D, _PD, _PD, _PL]
-            L.hwo2d_recon_candidates.restype = _I
-            L.hwo2d_recon_candidates.argtypes = [_PD, _PD, _PD, _I, _PD, _PD]
-            L.hwo2d_linear_weights.restype = _I
-            L.hwo2d_linear_weights.argtypes = [_I, _PD]
-            L.hwo2d_p0_coeffs.restype = None
-            L.hwo2d_p0_coeffs.argtypes = [_PD, _PD]
-            L.hwo2d_quad_coeffs.restype = None
-            L.hwo2d_quad_coeffs.argtypes = [_I, _PD, _PD]
-            L.hwo2d_beta_of_coeffs.restype = _D
-            L.hwo2d_beta_of_coeffs.argtypes = [_I, _PD, _D]
-            L.hwo_euler2d_flux.restype = None
-            L.hwo_euler2d_flux.argtypes = [_D, _PD, _I, _PD]
-            L.hwo_euler2d_eigen.restype = None
-            L.hwo_euler2d_eigen.argtypes = [_D, _PD, _I, _PD, _PD]
-        _lib = L
+        _lib = _setup(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def threads(n=0):
+    """Threads of the OpenMP build: sets the count when n > 0, returns it."""
+    L = lib_omp()
+    return L.hwo_set_threads(int(n)) if L is not None else 1
+
+
+def _setup(L):
+    """Argument and result types of the exported functions."""
+    P1 = ctypes.POINTER(Cfg1D)
+    L.hwo1d_alpha.restype = _D
+    L.hwo1d_alpha.argtypes = [P1, _PD]
+    L.hwo1d_rhs.restype = _I
+    L.hwo1d_rhs.argtypes = [P1, _PD, _D, _PD, _PD, _PU8, _PD]
+    L.hwo1d_rhs_ex.restype = _I
+    L.hwo1d_rhs_ex.argtypes = [P1, _PD, _D, _PD, _PD, _PU8, _PD, _PD]
+    L.hwo1d_step.restype = _I
+    L.hwo1d_step.argtypes = [P1, _PD, _D, _PL]
+    L.hwo1d_dt.restype = _D
+    L.hwo1d_dt.argtypes = [P1, _PD, _D, _D, _D]
+    L.hwo1d_run.restype = _I
+    L.hwo1d_run.argtypes = [P1, _PD, _I, _D, _D, _D, _D, _PD, _PD, _PL]
+    L.hwo1d_limiter_candidates.restype = None
+    L.hwo1d_limiter_candidates.argtypes = [_PD, _D, _D, _PD, _PD]
+    L.hwo1d_limit_scalar.restype = _D
+    L.hwo1d_limit_scalar.argtypes = [_PD, _D, _PD, _D, _D]
+    L.hwo1d_recon_candidates.restype = None
+    L.hwo1d_recon_candidates.argtypes = [_PD, _PD, _PD, _PD]
+    L.hwo1d_recon_scalar.restype = None
+    L.hwo1d_recon_scalar.argtypes = [_PD, _D, _PD, _PD, _I, _PD]
+    L.hwo_euler1d_eigen.restype = None
+    L.hwo_euler1d_eigen.argtypes = [_D, _PD, _PD, _PD]
+    L.hwo_euler1d_flux.restype = None
+    L.hwo_euler1d_flux.argtypes = [_D, _PD, _PD]
+    if hasattr(L, "hwo2d_rhs"):
+        P2 = ctypes.POINTER(Cfg2D)
+        L.hwo2d_rhs.restype = _I
+        L.hwo2d_rhs.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD]
+        L.hwo2d_rhs_ex.restype = _I
+        L.hwo2d_rhs_ex.argtypes = [P2, _PD, _D, _D, _PD, _PD, _PU8, _PD, _PD]
+        L.hwo2d_rhs_fx.restype = _I
+        L.hwo2d_rhs_fx.argtypes = [P2, _PD, _D, _D, _PU8, _PD, _PD, _PU8, _PD, _PD]
+        L.hwo2d_alpha.restype = None
+        L.hwo2d_alpha.argtypes = [P2, _PD, _PD, _PD]
+        L.hwo2d_dt.restype = _D
+        L.hwo2d_dt.argtypes = [P2, _PD, _D, _D, _D]
+        L.hwo2d_step.restype = _I
+        L.hwo2d_step.argtypes = [P2, _PD, _D, _PL]
+        L.hwo2d_run.restype = _I
+        L.hwo2d_run.argtypes = [P2, _PD, _I, _D, _D, _D, _D, _PD, _PD, _PL]
+        L.hwo2d_recon_candidates.restype = _I
+        L.hwo2d_recon_candidates.argtypes = [_PD, _PD, _PD, _I, _PD, _PD]
+        L.hwo2d_linear_weights.restype = _I
+        L.hwo2d_linear_weights.argtypes = [_I, _PD]
+        L.hwo2d_p0_coeffs.restype = None
+        L.hwo2d_p0_coeffs.argtypes = [_PD, _PD]
+        L.hwo2d_quad_coeffs.restype = None
+        L.hwo2d_quad_coeffs.argtypes = [_I, _PD, _PD]
+        L.hwo2d_beta_of_coeffs.restype = _D
+        L.hwo2d_beta_of_coeffs.argtypes = [_I, _PD, _D]
+        L.hwo_euler2d_flux.restype = None
+        L.hwo_euler2d_flux.argtypes = [_D, _PD, _I, _PD]
+        L.hwo_euler2d_eigen.restype = None
+        L.hwo_euler2d_eigen.argtypes = [_D, _PD, _I, _PD, _PD]
+    L.hwo_set_threads.restype = _I
+    L.hwo_set_threads.argtypes = [_I]
+    return L
 
 
 def _p(a):
@@ -226,8 +263,9 @@ def step1d(cfg, u, dt):
 
 
 def run1d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
-          lin_w_per_step=None):
-    """Repeated SSP-RK3 steps; returns (u, t, troubled cell-stage count)."""
+          lin_w_per_step=None, omp=False):
+    """Repeated SSP-RK3 steps; returns (u, t, troubled cell-stage count).
+    omp: run the OpenMP build (same results, all cores; see threads())."""
     u = _state1d(cfg, u).copy()
     t = ctypes.c_double(0.0)
     nt = ctypes.c_long(0)
@@ -236,8 +274,9 @@ def run1d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
         lw_arr = _f64(lin_w_per_step)
         assert nsteps >= 0 and lw_arr.size >= 3 * nsteps
         lw = _p(lw_arr)
-    st = lib().hwo1d_run(ctypes.byref(cfg), _p(u), nsteps, cfl, t0, t_final,
-                         dt_fixed, lw, ctypes.byref(t), ctypes.byref(nt))
+    L = lib_omp() if omp else lib()
+    st = (L or lib()).hwo1d_run(ctypes.byref(cfg), _p(u), nsteps, cfl, t0, t_final,
+                                dt_fixed, lw, ctypes.byref(t), ctypes.byref(nt))
     if st != 0:
         raise FloatingPointError("oracle run1d status %d" % st)
     return u, t.value, nt.value
@@ -329,7 +368,7 @@ def step2d(cfg, u, dt):
 
 
 def run2d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
-          lin_w_per_step=None):
+          lin_w_per_step=None, omp=False):
     u = _state2d(cfg, u).copy()
     t = ctypes.c_double(0.0)
     nt = ctypes.c_long(0)
@@ -338,8 +377,9 @@ def run2d(cfg, u, nsteps=-1, cfl=0.6, t0=0.0, t_final=-1.0, dt_fixed=-1.0,
         lw_arr = _f64(lin_w_per_step)
         assert nsteps >= 0 and lw_arr.size >= 5 * nsteps
         lw = _p(lw_arr)
-    st = lib().hwo2d_run(ctypes.byref(cfg), _p(u), nsteps, cfl, t0, t_final, dt_fixed, lw,
-                         ctypes.byref(t), ctypes.byref(nt))
+    L = lib_omp() if omp else lib()
+    st = (L or lib()).hwo2d_run(ctypes.byref(cfg), _p(u), nsteps, cfl, t0, t_final, dt_fixed,
+                                lw, ctypes.byref(t), ctypes.byref(nt))
     if st != 0:
         raise FloatingPointError("oracle run2d status %d" % st)
     return u, t.value, nt.value

@@ -182,6 +182,102 @@ __device__ __noinline__ ConsFaces<R> char_faces(R gas, R g0, R g1, R g2, R eps, 
   return o;
 }
 
+// Step 2 at the interfaces of the cell in slot e = k + 2 of sm.u (k = 0 is
+// the first halo cell that needs them): the traces u^+_{i-1/2}, u^-_{i+1/2}
+// (linear p0, Step 2.2, or Step 2.1 when the stencil S0 holds a troubled
+// cell; Euler in the characteristic fields of Remark 2) into sm.fm, sm.fp,
+// and their physical fluxes into sm.ffm, sm.ffp.
+template <typename R, int C, int NTH>
+__device__ __forceinline__ void faces_of_cell(Smem1D<R, C, NTH>& sm, int k, R gas, const R* gam,
+                                              R eps, int variant) {
+  const int e = k + 2;  // sm.u index e; sm.vl / sm.fl index of cell e is e - 1
+  const bool hw = sm.fl[k] | sm.fl[k + 1] | sm.fl[k + 2];
+  R L[C], Rt[C], fL[C], fR[C];
+  if (!hw || C == 1) {
+    if (!hw) {
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                     sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
+    } else {
+      hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
+                  sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
+    }
+    phys_flux<R, C>(gas, L, fL);
+    phys_flux<R, C>(gas, Rt, fR);
+  } else {
+    // Default: both faces in the fields of the cell average (Remark 2).
+    // Variant: u^+_{i-1/2} in the fields of the mean of the averages of
+    // cells i-1, i; u^-_{i+1/2} in those of cells i, i+1.
+    const bool mean = variant & HWENO_VARIANT_MEAN_EIGEN;
+    for (int side = 0; side < (mean ? 2 : 1); ++side) {
+      R B[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        B[c] = !mean ? sm.u[c][0][e]
+               : side ? R(0.5) * (sm.u[c][0][e] + sm.u[c][0][e + 1])
+                      : R(0.5) * (sm.u[c][0][e - 1] + sm.u[c][0][e]);
+      const ConsFaces<R> o = char_faces<R>(
+          gas, gam[0], gam[1], gam[2], eps, B[0], B[1], B[2], sm.u[0][0][e - 1],
+          sm.u[1][0][e - 1], sm.u[2][0][e - 1], sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e],
+          sm.u[0][0][e + 1], sm.u[1][0][e + 1], sm.u[2][0][e + 1], sm.vl[0][e - 2],
+          sm.vl[1][e - 2], sm.vl[2][e - 2], sm.vl[0][e - 1], sm.vl[1][e - 1], sm.vl[2][e - 1],
+          sm.vl[0][e], sm.vl[1][e], sm.vl[2][e]);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (!mean || side == 0) {
+          L[c] = o.L[c];
+          fL[c] = o.fL[c];
+        }
+        if (!mean || side == 1) {
+          Rt[c] = o.Rt[c];
+          fR[c] = o.fR[c];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    sm.fm[c][k] = L[c];
+    sm.fp[c][k] = Rt[c];
+    sm.ffm[c][k] = fL[c];
+    sm.ffp[c][k] = fR[c];
+  }
+}
+
+// Eq. (odeH) for the own cell of thread tid (sm.u slot e = tid + 3): the
+// interior Gauss-Lobatto values (Step 2.3) and their fluxes, the
+// Lax-Friedrichs fluxes at x_{i-+1/2} (each from the traces and trace fluxes
+// the two cells beside the interface stored, so both cells use the same
+// number and the averages stay conservative), the four-point Gauss-Lobatto
+// F_i and the two right-hand sides
+//   Lu = -(fhat_{i+1/2} - fhat_{i-1/2}) / dx,
+//   Lv = (F_i - (fhat_{i-1/2} + fhat_{i+1/2}) / 2) / dx.
+template <typename R, int C, int NTH>
+__device__ __forceinline__ void rhs_of_cell(const Smem1D<R, C, NTH>& sm, int tid, R gas, R alpha,
+                                            R inv_dx, R* Lu, R* Lv) {
+  const int e = tid + H, k = tid + 1;  // sm.u slot; sm.fm/fp slot of the cell
+  const R half_alpha = R(0.5) * alpha;
+  R gm[C], gp[C], f2[C], f3[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+    linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                    sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
+  phys_flux<R, C>(gas, gm, f2);
+  phys_flux<R, C>(gas, gp, f3);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const R ql = R(0.5) * (sm.ffp[c][k - 1] + sm.ffm[c][k]) -
+                 half_alpha * (sm.fm[c][k] - sm.fp[c][k - 1]);
+    const R qr = R(0.5) * (sm.ffp[c][k] + sm.ffm[c][k + 1]) -
+                 half_alpha * (sm.fm[c][k + 1] - sm.fp[c][k]);
+    // four-point Gauss-Lobatto F_i; the end points are the cell's own traces
+    const R F = R(1.0 / 12.0) * (sm.ffm[c][k] + sm.ffp[c][k]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
+    Lu[c] = -(qr - ql) * inv_dx;
+    Lv[c] = (F - R(0.5) * (ql + qr)) * inv_dx;
+  }
+}
+
 // One stage on one tile of T = NTH - 6 cells, by a CTA of NTH + 32 threads.  The
 // per-stage kernel calls it once; the persistent kernel calls it for each of
 // its tiles of each stage, between grid barriers, so every load of data
@@ -411,63 +507,9 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
   }
   bar_sync(kBarCells, NT);
 
-  // 4. interface values (Steps 2.1, 2.2) and their physical fluxes, cells base-1 ..
-  //    base+T
-  if (tid < T + 2) {
-    const int k = tid, e = k + 2;  // sm.u index e; sm.vl / sm.fl index of cell e is e - 1
-    const bool hw = sm.fl[k] | sm.fl[k + 1] | sm.fl[k + 2];
-    R L[C], Rt[C], fL[C], fR[C];
-    if (!hw || C == 1) {
-      if (!hw) {
-#pragma unroll
-        for (int c = 0; c < C; ++c)
-          linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                       sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
-      } else {
-        hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
-                    sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
-      }
-      phys_flux<R, C>(gas, L, fL);
-      phys_flux<R, C>(gas, Rt, fR);
-    } else {
-      // Default: both faces in the fields of the cell average (Remark 2).
-      // Variant: u^+_{i-1/2} in the fields of the mean of the averages of
-      // cells i-1, i; u^-_{i+1/2} in those of cells i, i+1.
-      const bool mean = a.variant & HWENO_VARIANT_MEAN_EIGEN;
-      for (int side = 0; side < (mean ? 2 : 1); ++side) {
-        R B[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          B[c] = !mean ? sm.u[c][0][e]
-                 : side ? R(0.5) * (sm.u[c][0][e] + sm.u[c][0][e + 1])
-                        : R(0.5) * (sm.u[c][0][e - 1] + sm.u[c][0][e]);
-        const ConsFaces<R> o = char_faces<R>(
-            gas, gam[0], gam[1], gam[2], eps, B[0], B[1], B[2], sm.u[0][0][e - 1],
-            sm.u[1][0][e - 1], sm.u[2][0][e - 1], sm.u[0][0][e], sm.u[1][0][e], sm.u[2][0][e],
-            sm.u[0][0][e + 1], sm.u[1][0][e + 1], sm.u[2][0][e + 1], sm.vl[0][e - 2],
-            sm.vl[1][e - 2], sm.vl[2][e - 2], sm.vl[0][e - 1], sm.vl[1][e - 1], sm.vl[2][e - 1],
-            sm.vl[0][e], sm.vl[1][e], sm.vl[2][e]);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          if (!mean || side == 0) {
-            L[c] = o.L[c];
-            fL[c] = o.fL[c];
-          }
-          if (!mean || side == 1) {
-            Rt[c] = o.Rt[c];
-            fR[c] = o.fR[c];
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      sm.fm[c][k] = L[c];
-      sm.fp[c][k] = Rt[c];
-      sm.ffm[c][k] = fL[c];
-      sm.ffp[c][k] = fR[c];
-    }
-  }
+  // 4. interface values (Steps 2.1, 2.2) and their physical fluxes, cells
+  //    base-1 .. base+T
+  if (tid < T + 2) faces_of_cell<R, C, NTH>(sm, tid, gas, gam, eps, a.variant);
   // alpha and dt from the scalar warp; a zero dt (t_final reached) is
   // uniform over the grid (the instance), and the stage then writes nothing
   bar_sync(kBarAll, NT + 32);
@@ -482,30 +524,13 @@ __device__ __forceinline__ void stage1d_tile(Stage1DArgs a, const int tile, Smem
   unsigned bad = 0;
   if (own) {
     const int e = tid + H;  // sm.u index
-    const int k = tid + 1;  // sm.fm/fp index of cell i
     myflag = sm.fl[tid + 2];
-    const R half_alpha = R(0.5) * alpha;
-    R gm[C], gp[C], f2[C], f3[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-      linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                      sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
-    phys_flux<R, C>(gas, gm, f2);
-    phys_flux<R, C>(gas, gp, f3);
-    const R idx = inv_dx;
+    R Lus[C], Lvs[C];
+    rhs_of_cell<R, C, NTH>(sm, tid, gas, alpha, inv_dx, Lus, Lvs);
     R Uo[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      // Lax-Friedrichs fluxes at x_{i-1/2} (u^- of cell i-1, u^+ of cell i)
-      // and at x_{i+1/2} (u^- of cell i, u^+ of cell i+1)
-      const R ql = R(0.5) * (sm.ffp[c][k - 1] + sm.ffm[c][k]) -
-                   half_alpha * (sm.fm[c][k] - sm.fp[c][k - 1]);
-      const R qr = R(0.5) * (sm.ffp[c][k] + sm.ffm[c][k + 1]) -
-                   half_alpha * (sm.fm[c][k + 1] - sm.fp[c][k]);
-      // four-point Gauss-Lobatto F_i; the end points are the cell's own traces
-      const R F = R(1.0 / 12.0) * (sm.ffm[c][k] + sm.ffp[c][k]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
-      const R Lu = -(qr - ql) * idx;
-      const R Lv = (F - R(0.5) * (ql + qr)) * idx;
+      const R Lu = Lus[c], Lv = Lvs[c];
       const R wu = sm.u[c][0][e];
       // the stage input the combination uses: first moments as modified by
       // Step 1 (stored, the default), or unmodified (variant)

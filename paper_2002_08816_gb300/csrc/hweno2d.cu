@@ -223,15 +223,15 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
 
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
-  R gam[5], eps, gas, inv_dx, inv_dy, cfl;
+  R gam[5], eps, gas, inv_dx, inv_dy;
   if constexpr (sizeof(R) == 4) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) gam[k] = a.f32[k];
-    eps = a.f32[5]; gas = a.f32[6]; inv_dx = a.f32[7]; inv_dy = a.f32[8]; cfl = a.f32[9];
+    eps = a.f32[5]; gas = a.f32[6]; inv_dx = a.f32[7]; inv_dy = a.f32[8];
   } else {
 #pragma unroll
     for (int k = 0; k < 5; ++k) gam[k] = a.gam[k];
-    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx; inv_dy = a.inv_dy; cfl = a.cfl;
+    eps = a.eps; gas = a.gas; inv_dx = a.inv_dx; inv_dy = a.inv_dy;
   }
 
   // ---- 1. alpha_x, alpha_y, the time bookkeeping, the tile and its halo
@@ -241,9 +241,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
     ax = fmax(ax, a_in[k]);
     ay = fmax(ay, a_in[a.nin + k]);
   }
-  R rem = R(0), dt_prev = R(0);
-  if (a.stage == 1) rem = sc_rem<R>(a.sc);
-  else if (a.stage > 1) dt_prev = sc_dt<R>(a.sc);
+  // dt of the step: formed in FP64 by dt2d_kernel before stage 1
+  R dt_prev = R(0);
+  if (a.stage > 0) dt_prev = sc_dt<R>(a.sc);
   const int ox = tid % TX, oy = tid / TX;  // own cell of this thread
   const int gi = bx0 + ox, gj = by0 + oy;
   const bool own = gi < nx && gj < ny;
@@ -282,24 +282,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
   }
   R dt = dt_prev;
   if (a.stage == 1) {
-    dt = cfl / (alx * inv_dx + aly * inv_dy);
-    unsigned last = 0;
-    if (rem <= R(0)) {
-      dt = R(0);
-    } else if (dt >= rem) {
-      dt = rem;
-      last = 1;
-    }
-    if (!(alx + aly > R(0)) || !isfinite(dt)) dt = R(0);
     if (a.dt_in) {  // replay of a recorded step
       dt = *static_cast<const R*>(a.dt_in);
-      last = 0;
+      if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        a.sc->dt = (double)dt;
+        a.sc->dt_f = (float)dt;
+        a.sc->last = 0u;
+      }
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
-      sc_dt<R>(a.sc) = dt;
-      a.sc->last = last;
-      if (a.rec_dt) *static_cast<R*>(a.rec_dt) = dt;
-    }
+    if (a.rec_dt && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0)
+      *static_cast<R*>(a.rec_dt) = dt;
   }
   if (a.rec_alpha && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
     static_cast<R*>(a.rec_alpha)[0] = alx;
@@ -565,15 +557,49 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
       if (a.stage == 3 && blockIdx.x == 0 && blockIdx.y == 0) {
         DevScalars* sc = a.sc;
         const double tf = sc->t_final;
-        const double t = sc->last ? tf : sc->t + (double)dt;
+        const double t = sc->last ? tf : sc->t + sc->dt;
         const double r = tf > 0.0 ? tf - t : (double)INFINITY;
         sc->t = t;
-        sc->dt = (double)dt;
         sc->rem = r;
         sc->rem_f = (float)r;
         sc->steps += 1;
       }
     }
+  }
+}
+
+// dt of a 2D step (Sec. 3, CFL; reading: dt = CFL / (alpha_x / dx + alpha_y /
+// dy)), in FP64: one warp folds the wave-speed maxima of the step's input
+// (kernel precision, so exact in FP64), forms dt and its clip to t_final,
+// and leaves dt (FP64 and FP32 copies) and the last-step flag in the
+// scalars, where the three stage kernels read it.
+template <typename R>
+__global__ void __launch_bounds__(32) dt2d_kernel(const R* __restrict__ a_in, int nin,
+                                                  DevScalars* sc, double cfl, double inv_dx,
+                                                  double inv_dy) {
+  double ax = 0.0, ay = 0.0;
+  for (int k = threadIdx.x; k < nin; k += 32) {
+    ax = fmax(ax, (double)a_in[k]);
+    ay = fmax(ay, (double)a_in[nin + k]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax = fmax(ax, __shfl_xor_sync(0xffffffffu, ax, o));
+    ay = fmax(ay, __shfl_xor_sync(0xffffffffu, ay, o));
+  }
+  if (threadIdx.x == 0) {
+    const double rem = sc->rem;
+    double dt = cfl / (ax * inv_dx + ay * inv_dy);
+    unsigned last = 0u;
+    if (rem <= 0.0) {
+      dt = 0.0;
+    } else if (dt >= rem) {
+      dt = rem;
+      last = 1u;
+    }
+    if (!(ax + ay > 0.0) || !isfinite(dt)) dt = 0.0;
+    sc->dt = dt;
+    sc->dt_f = (float)dt;
+    sc->last = last;
   }
 }
 
@@ -686,6 +712,16 @@ cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s) {
   }
   if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 4, 2>(a, s) : launch_stage2d_t<double, 4, 3>(a, s);
   return a.ng == 2 ? launch_stage2d_t<float, 4, 2>(a, s) : launch_stage2d_t<float, 4, 3>(a, s);
+}
+
+cudaError_t launch_dt2d(const Stage2DArgs& a, cudaStream_t s) {
+  if (a.fp64)
+    dt2d_kernel<double><<<1, 32, 0, s>>>(static_cast<const double*>(a.a_in), a.nin, a.sc, a.cfl,
+                                        a.inv_dx, a.inv_dy);
+  else
+    dt2d_kernel<float><<<1, 32, 0, s>>>(static_cast<const float*>(a.a_in), a.nin, a.sc, a.cfl,
+                                       a.inv_dx, a.inv_dy);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_alpha2d(const void* w, void* a_out, int nx, int ny, int system, int fp64,

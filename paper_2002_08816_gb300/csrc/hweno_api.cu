@@ -28,9 +28,15 @@ struct hweno_ctx {
   int C = 0, M = 0, n = 0, ntile = 0;  // n = cells; ntile = CTAs of one stage
   int dim = 1;
   // 1D execution: threads per CTA of the stage kernels (a tile is nth1d - 6
-  // cells), and whether hweno_step runs one persistent launch (persist1d) or
-  // per-stage launches in CUDA graphs; hweno_autotune chooses both
+  // cells), and how hweno_step launches: per-stage launches in CUDA graphs
+  // (persist1d = 0), one persistent launch with a grid barrier per stage (1),
+  // or one resident launch that keeps the tiles on chip (2, FP32 single
+  // instance); hweno_autotune chooses
   int nth1d = 256, persist1d = 0;
+  // the resident launch's geometry and cross-CTA buffers (allocated on first use)
+  int res_tile = 0, res_ncta = 0, res_cap = 0;
+  unsigned long long* res_halo = nullptr;     // tagged exchange words of the halos
+  unsigned long long* res_entries = nullptr;  // and of the per-CTA maxima
   int ntile_alpha = 0;               // CTAs of the 1D wave-speed kernels (kTile1D cells each)
   unsigned* bar = nullptr;           // grid barrier of the persistent kernel
   std::vector<int> batch_nx;         // cells of each batch instance
@@ -185,7 +191,9 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.rec_alpha = io.rec_alpha;
   a.rec_dt = io.rec_dt;
   a.dt_in = io.dt_in;
-  cudaError_t e = hw::launch_stage2d(a, s);
+  cudaError_t e = hw::launch_dt2d(a, s);
+  if (e != cudaSuccess) return e;
+  e = hw::launch_stage2d(a, s);
   if (e != cudaSuccess) return e;
   a.rec_dt = nullptr;
   a.dt_in = nullptr;
@@ -233,6 +241,51 @@ cudaError_t enqueue_run1d(hweno_ctx* h, int nsteps, cudaStream_t s) {
   r.nsteps = nsteps;
   r.bar = h->bar;
   return hw::launch_run1d(r, s);
+}
+
+// Geometry of the resident launch for the handle's threads per CTA (res_tile =
+// 0 when it cannot run: FP64, batches, or too many cells to be co-resident),
+// and its buffers.
+cudaError_t prepare_resident(hweno_ctx* h) {
+  h->res_tile = h->res_ncta = 0;
+  if (h->dim != 1 || h->n_batch > 0 || h->cfg.precision != HWENO_FP32) return cudaSuccess;
+  if (h->nth1d != 256 && h->nth1d != 512) return cudaSuccess;
+  int tile = 0, ncta = 0;
+  cudaError_t e = hw::resident1d_geometry(h->cfg.system, h->nth1d, h->n, &tile, &ncta);
+  if (e != cudaSuccess || tile == 0) return e;
+  if (ncta > h->res_cap) {
+    if (h->res_halo) cudaFree(h->res_halo);
+    if (h->res_entries) cudaFree(h->res_entries);
+    h->res_halo = nullptr;
+    h->res_entries = nullptr;
+    h->res_cap = 0;
+    e = cudaMalloc(&h->res_halo, (size_t)ncta * 2 * 6 * h->C * 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&h->res_entries, sizeof(unsigned long long) * hw::resident1d_entry_words(ncta));
+    if (e != cudaSuccess) return e;
+    h->res_cap = ncta;
+  }
+  h->res_tile = tile;
+  h->res_ncta = ncta;
+  return cudaSuccess;
+}
+
+// nsteps Runge-Kutta steps of a 1D handle in one resident launch.
+cudaError_t enqueue_resident1d(hweno_ctx* h, int nsteps, cudaStream_t s) {
+  hw::Resident1DArgs r;
+  memset(&r, 0, sizeof(r));
+  r.a = base_args(h);
+  r.a.sc = h->sc;
+  r.a.w = h->U[0];
+  r.a.out = h->U[0];
+  r.tile = h->res_tile;
+  r.nsteps = nsteps;
+  r.part0 = h->part[0];
+  r.part1 = h->part[1];
+  r.halo = h->res_halo;
+  r.entries = h->res_entries;
+  r.alpha_word = h->res_entries + hw::resident1d_entry_words(h->res_ncta) - 2;
+  return hw::launch_resident1d(r, h->nth1d, h->res_ncta, s);
 }
 
 cudaError_t enqueue_step(hweno_ctx* h, cudaStream_t s) {
@@ -568,7 +621,10 @@ hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_ou
   if (h->n_batch > 0)
     HW_CUDA(h, hw::launch_batch_scalars(h->d_bsc, h->n_batch, 0, t_final, h->stream));
   int left = nsteps;
-  if (h->dim == 1 && h->persist1d) {
+  if (h->dim == 1 && h->persist1d == 2) {
+    if (left > 0) HW_CUDA(h, enqueue_resident1d(h, left, h->stream));
+    left = 0;
+  } else if (h->dim == 1 && h->persist1d) {
     if (left > 0) HW_CUDA(h, enqueue_run1d(h, left, h->stream));
     left = 0;
   }
@@ -691,6 +747,8 @@ void hweno_destroy(hweno_handle h) {
   if (h->sc) cudaFree(h->sc);
   if (h->sc_rhs) cudaFree(h->sc_rhs);
   if (h->bar) cudaFree(h->bar);
+  if (h->res_halo) cudaFree(h->res_halo);
+  if (h->res_entries) cudaFree(h->res_entries);
   if (h->tot_buf) cudaFree(h->tot_buf);
   if (h->d_tile_inst) cudaFree(h->d_tile_inst);
   if (h->d_tile_base) cudaFree(h->d_tile_base);
@@ -983,16 +1041,26 @@ hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent) {
   if (h->dim != 1) return fail(h, HWENO_ERR_ARG, "the execution choice is for 1D handles");
   if (threads != 128 && threads != 256 && threads != 512)
     return fail(h, HWENO_ERR_ARG, "threads must be 128, 256 or 512");
+  if (persistent < 0 || persistent > 2) return fail(h, HWENO_ERR_ARG, "persistent must be 0, 1 or 2");
   HW_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->g_many) cudaGraphExecDestroy(h->g_many);
   if (h->g_one) cudaGraphExecDestroy(h->g_one);
   h->g_many = h->g_one = nullptr;
   h->nth1d = threads;
-  h->persist1d = persistent != 0;
+  h->persist1d = persistent;
   if (h->n_batch > 0) {
     HW_CUDA(h, batch_tiles(h, threads));
   } else {
     h->ntile = (h->n + threads - 7) / (threads - 6);
+  }
+  if (persistent == 2) {
+    HW_CUDA(h, prepare_resident(h));
+    if (h->res_tile == 0) {
+      h->persist1d = 0;
+      return fail(h, HWENO_ERR_ARG,
+                  "the resident launch takes FP32 single-instance handles, 256 or 512 threads, "
+                  "and a grid whose tiles fit on the GPU at once");
+    }
   }
   return HWENO_OK;
 }
@@ -1037,6 +1105,7 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
     h->persist1d = persist;
     if (h->n_batch > 0) return batch_tiles(h, nth);
     h->ntile = (h->n + nth - 7) / (nth - 6);
+    if (persist == 2) return prepare_resident(h);
     return cudaSuccess;
   };
   cudaError_t e = copy_all(true);
@@ -1046,10 +1115,11 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  for (int persist = 0; persist < 2 && e == cudaSuccess; ++persist)
+  for (int persist = 0; persist < 3 && e == cudaSuccess; ++persist)
     for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
       e = configure(cand_nth[ci], persist);
       if (e != cudaSuccess) break;
+      if (persist == 2 && h->res_tile == 0) continue;  // not available here
       // one untimed run of the trial length (it builds every graph the trial
       // launches, so that no graph instantiation is timed), then the best of
       // two timed trials

@@ -128,6 +128,9 @@ void finish_stage2d_args(Stage2DArgs& a);
 // Allows the 2D stage kernel of this configuration its dynamic shared memory.
 cudaError_t prepare_stage2d(int system, int fp64, int ng);
 cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s);
+// dt of the step in FP64 from the stage-1 input's slots (a.a_in, a.nin), into
+// a.sc; launched before every stage 1.
+cudaError_t launch_dt2d(const Stage2DArgs& a, cudaStream_t s);
 // Wave-speed maxima (x then y) of a 2D state, per tile (slots = 0, 2 ntile
 // entries) or into 2 * kAlphaSlots zeroed slots (slots = 1).
 cudaError_t launch_alpha2d(const void* w, void* a_out, int nx, int ny, int system, int fp64,
@@ -178,6 +181,30 @@ struct Run1DArgs {
   int nsteps;
   unsigned* bar;      // grid barrier: arrivals, generation (zeroed before the launch)
 };
+// A whole run in one cooperative launch in which every CTA keeps its tile of
+// the state in shared memory for all stages (hweno1d_resident.cu; FP32,
+// single instance): only the 3-cell halos (`halo`) and the per-CTA maximum
+// wave speeds (`entries`) cross CTAs, as 64-bit words tagged with their stage.
+struct Resident1DArgs {
+  Stage1DArgs a;      // physics and sizes; w = out = the state, sc
+  int tile;           // cells per CTA (<= threads - 6)
+  int nsteps;
+  void* part0;        // alpha slots of the state (kAlphaSlots doubles): read
+                      // at the start, rewritten for the next call at the end
+  void* part1;        // zeroed at the end (the per-stage launches expect it)
+  unsigned long long* halo;     // [ncta][2][6][C][2] published first and last cells
+  unsigned long long* entries;  // [2][ncta] maximum wave speed of each CTA's outputs, one
+                                // cache line each, then [2] alpha words (alpha_word)
+  unsigned long long* alpha_word;
+};
+// Words of the entries buffer (entries and the two alpha words) for ncta CTAs.
+size_t resident1d_entry_words(int ncta);
+// Cells per CTA and CTAs of the resident launch with nth + 32 threads for n
+// cells; *tile = 0 when the grid does not fit on the GPU at once.
+cudaError_t resident1d_geometry(int system, int nth, int n, int* tile, int* ncta);
+// Zeroes the exchange words, then launches.
+cudaError_t launch_resident1d(const Resident1DArgs& r, int nth, int ncta, cudaStream_t s);
+
 // Largest co-resident grid of the persistent kernel for this configuration.
 cudaError_t run1d_max_ctas(int system, int fp64, int batch, int nth, int* ctas);
 // Cooperative launch of min(ntile, co-resident CTAs) CTAs.

@@ -97,6 +97,8 @@ def lib():
         L.hweno_check_barrier.argtypes = [_I, _I, _I, ctypes.c_uint]
         L.hweno_rhs1d_noalloc.restype = _I
         L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
+        L.hweno_fma_peak.restype = _I
+        L.hweno_fma_peak.argtypes = [_I, _I, ctypes.POINTER(_D)]
         _lib = L
     return _lib
 
@@ -176,10 +178,11 @@ def hweno_rhs_vjp(h, in_ptr, flags_ptr, alpha_x, alpha_y, lam_ptr, grad_ptr):
 
 
 def hweno_autotune(h, nsteps_trial):
-    """Returns (threads per CTA, persistent) chosen for the 1D handle."""
+    """Returns (threads per CTA, launch kind) chosen for the 1D handle: 0
+    per-stage graphs, 1 persistent, 2 resident."""
     out = (_I * 2)()
     _check(lib().hweno_autotune(h, int(nsteps_trial), out), h)
-    return out[0], bool(out[1])
+    return out[0], out[1]
 
 
 def hweno_totals(h, count):
@@ -199,8 +202,15 @@ def hweno_check_barrier(ctas, meetings, missing, polls):
     return st
 
 
+def hweno_fma_peak(fp64, iters):
+    """Measured FMA throughput of the current device, flops per second."""
+    out = _D()
+    _check(lib().hweno_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(out)))
+    return out.value
+
+
 def hweno_set_execution(h, threads, persistent):
-    _check(lib().hweno_set_execution(h, int(threads), int(bool(persistent))), h)
+    _check(lib().hweno_set_execution(h, int(threads), int(persistent)), h)
 
 
 def hweno_get_state(h, ptr, dtype, on_device):

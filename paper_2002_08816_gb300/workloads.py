@@ -122,6 +122,27 @@ def euler_two_state_1d(nx, seed, x0=0.0, x1=1.0, npts=5, gamma=GAMMA, nmodes=4,
     return cell_moments_1d(f, nx, x0, x1, npts)
 
 
+def euler_lax_tiled_1d(nx, cells_per_tile=800, npts=5, gamma=GAMMA):
+    """The Lax problem's two states (Example 3.6: (rho, mu, p) = (0.445, 0.698,
+    3.528) left of the jump, (0.5, 0, 0.571) right of it) repeated: the domain
+    [0, 1] holds nx / cells_per_tile copies of one Lax problem, each on
+    cells_per_tile cells with its jump in the middle, so that the share of
+    troubled cells resembles the paper's shock tests (3.5-14 %) rather than
+    one shock on a fine grid: 800 cells per copy give about 10 % over 200
+    steps with periodic ends."""
+    ntile = max(1, nx // cells_per_tile)
+
+    def f(x):
+        frac = (x * ntile) % 1.0
+        L = frac < 0.5
+        rho = np.where(L, 0.445, 0.5)
+        mu = np.where(L, 0.698, 0.0)
+        p = np.where(L, 3.528, 0.571)
+        return euler_conserved_1d(rho, mu, p, gamma)
+
+    return cell_moments_1d(f, nx, 0.0, 1.0, npts)
+
+
 def batch_sizes_1d(n_instances, seed, lo=256, hi=16384):
     """Cell counts log-uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)

@@ -1,8 +1,9 @@
 """The 1D execution choices: per-stage graph launches with 128, 256 or 512
 threads per CTA give bitwise the same states (the same operations on every
-cell); the persistent launch with grid barriers agrees with them to rounding
-(its copy of the stage body may contract a few multiply-adds differently).
-hweno_autotune keeps the state and picks one of them."""
+cell); the persistent launch with grid barriers and the resident launch
+(tiles kept in shared memory for the whole run, FP32) agree with them to
+rounding (their copies of the stage body may contract a few multiply-adds
+differently).  hweno_autotune keeps the state and picks one of them."""
 
 import numpy as np
 import pytest
@@ -14,6 +15,7 @@ from paper_2002_08816_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 CHOICES = [(t, p) for p in (0, 1) for t in (128, 256, 512)]
+RESIDENT = [(256, 2), (512, 2)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -52,7 +54,7 @@ def test_choices_agree_bitwise(system, bc, prec):
     u = round_to(prec, u)
     cfg = H.make_config(1, system, nx, bc=bc, cfl=0.5, precision=prec)
     ref, t_ref, st_ref = _run(cfg, u, 45, (256, 0))
-    for ch in CHOICES:
+    for ch in CHOICES + (RESIDENT if prec == H.HWENO_FP32 else []):
         got, t, st = _run(cfg, u, 45, ch, chunks=(2, 1))
         assert st["steps"] == 45, ch
         if ch[1] == 0:
@@ -74,6 +76,56 @@ def test_persistent_run_clipped_to_final_time():
     got, t, _ = _run(cfg, u, 400, (128, 1), t_final=tf)
     assert t == t_ref == tf
     assert np.abs(got - ref).sum() <= 1e-12 * np.abs(ref).sum()
+
+
+@pytest.mark.parametrize("system,bc,nx", [(H.HWENO_EULER, H.HWENO_BC_OUTFLOW, 65536),
+                                          (H.HWENO_BURGERS, H.HWENO_BC_PERIODIC, 37),
+                                          (H.HWENO_EULER, H.HWENO_BC_PERIODIC, 20000),
+                                          (H.HWENO_EULER, H.HWENO_BC_REFLECTIVE, 6)])
+def test_resident_launch_against_the_oracle_and_per_stage(system, bc, nx):
+    """The resident launch (FP32) on the benchmark's 65536-cell workload, on a
+    grid of a few cells per CTA with periodic wrap across CTAs, on a periodic
+    Euler grid, and on a single 6-cell tile between walls: within rounding of
+    the per-stage launches, and against the oracle within the FP32 target."""
+    from gpu_util import make_pair
+    from oracle import oracle as O
+    if nx == 65536:
+        u = W.euler_two_state_1d(nx, seed=20250)
+    elif nx == 6:  # a gentle wave between the walls (6 cells resolve no jump)
+        u = W.cell_moments_1d(lambda x: W.euler_conserved_1d(1.0 + 0.1 * np.cos(np.pi * x),
+                                                             0.0 * x, 1.0 + 0 * x), nx, 0.0, 1.0)
+    elif system == H.HWENO_EULER:
+        u = mixed_euler(nx, 5)
+    else:
+        u = mixed_burgers(nx, 5)
+    u = round_to(H.HWENO_FP32, u)
+    cfg, ocfg = make_pair(system, nx, 0.0, 1.0, bc, H.HWENO_FP32)
+    steps = 9 if nx == 65536 else 42  # divisible by the chunks (1, 2)
+    ref, t_ref, st_ref = _run(cfg, u, steps, (256, 0))
+    for ch in RESIDENT:
+        got, t, st = _run(cfg, u, steps, ch, chunks=(1, 2))
+        assert st["steps"] == steps, ch
+        assert np.abs(got - ref).sum() <= 1e-6 * np.abs(ref).sum(), ch
+        assert abs(t - t_ref) <= 1e-6 * t_ref, ch
+        assert st["troubled"] > 0 or st_ref["troubled"] == 0
+    orc, t_o, _ = O.run1d(ocfg, u, nsteps=steps, cfl=0.5)
+    rel = np.abs(got - orc).sum() / np.abs(orc).sum()
+    assert rel <= 1e-4, rel
+    assert abs(t - t_o) <= 1e-6 * t_o
+
+
+def test_resident_run_clipped_to_final_time():
+    """Steps past t_final do nothing in the resident launch either, and the
+    time ends exactly at t_final."""
+    nx = 400
+    u = round_to(H.HWENO_FP32, W.burgers_sine_1d(nx))
+    cfg = H.make_config(1, H.HWENO_BURGERS, nx, x0=-1.0, x1=1.0, cfl=0.6, precision=H.HWENO_FP32)
+    tf = 1.5 / np.pi
+    ref, t_ref, s_ref = _run(cfg, u, 400, (256, 0), t_final=tf)
+    got, t, s = _run(cfg, u, 400, (256, 2), t_final=tf, chunks=(1, 3))
+    assert t == t_ref == tf
+    assert s["steps"] == s_ref["steps"]
+    assert np.abs(got - ref).sum() <= 1e-5 * np.abs(ref).sum()
 
 
 def test_batch_choices_agree_bitwise():
@@ -134,6 +186,10 @@ def test_set_execution_rejects_bad_choices():
     try:
         with pytest.raises(H.HwenoError):
             H.hweno_set_execution(h, 200, 1)
+        with pytest.raises(H.HwenoError):  # the resident launch is FP32 only
+            H.hweno_set_execution(h, 256, 2)
+        with pytest.raises(H.HwenoError):
+            H.hweno_set_execution(h, 256, 3)
     finally:
         H.hweno_destroy(h)
 
