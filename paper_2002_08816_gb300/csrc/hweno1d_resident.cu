@@ -104,6 +104,19 @@ __device__ __forceinline__ bool gather_max(const u64* ent, int ncta, unsigned ta
   return ok;
 }
 
+// One word polled by one thread until it carries `tag`; false after kPolls
+// polls.
+__device__ __forceinline__ bool poll_word(const u64* p, unsigned tag, u64* out) {
+  for (unsigned it = 0; it < kPolls; ++it) {
+    const u64 w = ld_relaxed(p);
+    if (tag_of(w) == tag) {
+      *out = w;
+      return true;
+    }
+  }
+  return false;
+}
+
 template <typename R, int C, int NTH>
 struct SmemRes {
   Smem1D<R, C, NTH> w;  // the stage's working arrays (as the per-stage kernel)
@@ -195,12 +208,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
           if (got && lane == 0) st_relaxed(r.alpha_word + ((s - 1) & 1), tagged((unsigned)s, m));
         } else {
           u64 w = 0ull;
-          if (lane == 0) {
-            for (unsigned it = 0; it < kPolls; ++it) {
-              w = ld_relaxed(r.alpha_word + ((s - 1) & 1));
-              if (tag_of(w) == (unsigned)s) break;
-            }
-          }
+          if (lane == 0) poll_word(r.alpha_word + ((s - 1) & 1), (unsigned)s, &w);
           w = __shfl_sync(0xffffffffu, w, 0);
           got = tag_of(w) == (unsigned)s;
           m = value_of(w);
@@ -410,25 +418,30 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
 
     // Step 2: interface values and their physical fluxes, cells base-1 .. base+Tq
     if (tid < Tq + 2) s1d::faces_of_cell<R, C, NTH>(sm, tid, gas, gam, eps, a.variant);
+    bar_sync(kBarCells, NT);
+
+    // own cells: Eq. (odeH) up to its alpha-linear part, before alpha is known
+    int myflag = 0;
+    R speed = R(0);
+    R L0u[C], Du[C], L0v[C], Dv[C];
+    if (own) {
+      myflag = sm.fl[tid + 2];
+      s1d::rhs_parts_of_cell<R, C, NTH>(sm, tid, gas, inv_dx, L0u, Du, L0v, Dv);
+    }
     // alpha and dt from the scalar warp
     bar_sync(kBarAll, NT + 32);
     if (S.abort) break;
     const R alpha = sm.alpha, dt = sm.dt;
     if (!(dt > R(0))) break;  // t_final reached: uniform over the grid
 
-    // own cells: fluxes, F_i, Eq. (odeH), Eq. (RK); the output stays in
-    // registers, the first and last three are published for the neighbours
-    int myflag = 0;
-    R speed = R(0);
+    // the Runge-Kutta combination; the output stays in registers, the first
+    // and last three are published for the neighbours
     if (own) {
       const int e = tid + H;
-      myflag = sm.fl[tid + 2];
-      R Lus[C], Lvs[C];
-      s1d::rhs_of_cell<R, C, NTH>(sm, tid, gas, alpha, inv_dx, Lus, Lvs);
       R Uo[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const R Lu = Lus[c], Lv = Lvs[c];
+        const R Lu = L0u[c] - alpha * Du[c], Lv = L0v[c] - alpha * Dv[c];
         const R wu = sm.u[c][0][e];
         const R wv = (a.variant & HWENO_VARIANT_RAW_COMBINE) ? sm.u[c][1][e] : sm.vl[c][e - 1];
         const R su = wu + dt * Lu, sv = wv + dt * Lv;

@@ -278,6 +278,36 @@ __device__ __forceinline__ void rhs_of_cell(const Smem1D<R, C, NTH>& sm, int tid
   }
 }
 
+// Eq. (odeH) as above, split by its dependence on alpha: the Lax-Friedrichs
+// fluxes are linear in alpha, so Lu = L0u - alpha Du and Lv = L0v - alpha Dv
+// with L0 from the traces' fluxes and F_i and D from the trace jumps.  A
+// caller that learns alpha late computes the four parts first.
+template <typename R, int C, int NTH>
+__device__ __forceinline__ void rhs_parts_of_cell(const Smem1D<R, C, NTH>& sm, int tid, R gas,
+                                                  R inv_dx, R* L0u, R* Du, R* L0v, R* Dv) {
+  const int e = tid + H, k = tid + 1;  // sm.u slot; sm.fm/fp slot of the cell
+  R gm[C], gp[C], f2[C], f3[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+    linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                    sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
+  phys_flux<R, C>(gas, gm, f2);
+  phys_flux<R, C>(gas, gp, f3);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    // central parts and jumps of the fluxes at x_{i-1/2} and x_{i+1/2}
+    const R cl = R(0.5) * (sm.ffp[c][k - 1] + sm.ffm[c][k]);
+    const R cr = R(0.5) * (sm.ffp[c][k] + sm.ffm[c][k + 1]);
+    const R jl = sm.fm[c][k] - sm.fp[c][k - 1];
+    const R jr = sm.fm[c][k + 1] - sm.fp[c][k];
+    const R F = R(1.0 / 12.0) * (sm.ffm[c][k] + sm.ffp[c][k]) + R(5.0 / 12.0) * (f2[c] + f3[c]);
+    L0u[c] = -(cr - cl) * inv_dx;
+    Du[c] = R(-0.5) * (jr - jl) * inv_dx;
+    L0v[c] = (F - R(0.5) * (cl + cr)) * inv_dx;
+    Dv[c] = R(-0.25) * (jl + jr) * inv_dx;
+  }
+}
+
 // One stage on one tile of T = NTH - 6 cells, by a CTA of NTH + 32 threads.  The
 // per-stage kernel calls it once; the persistent kernel calls it for each of
 // its tiles of each stage, between grid barriers, so every load of data

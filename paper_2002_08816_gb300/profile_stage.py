@@ -4,7 +4,7 @@
                                                   [--precision fp32|fp64] [--system euler|burgers]
                                                   [--dim 1|2] [--n-gauss 2|3]
                                                   [--adjoint EVERY] [--threads 128|256|512]
-                                                  [--persistent] [--batch N]
+                                                  [--persistent | --resident] [--batch N]
 
 Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
 --dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
@@ -13,7 +13,8 @@ step after one alpha launch) and checks the status word.  With --adjoint
 EVERY (2D) the steps are recorded with a checkpoint every EVERY steps and the
 gradient of sum(rho^2) is taken (hweno_backward: recomputed stages, then two
 adjoint kernels per stage).  With --batch N it runs N independent 1D Euler
-instances in shared launches (hweno_create_batch).
+instances in shared launches (hweno_create_batch).  --persistent and
+--resident select the 1D launch kinds with one launch per run.
 """
 
 import argparse
@@ -44,6 +45,8 @@ def main():
                     help="1D: threads per CTA (0: the default)")
     ap.add_argument("--persistent", action="store_true",
                     help="1D: one persistent launch with grid barriers instead of per-stage graphs")
+    ap.add_argument("--resident", action="store_true",
+                    help="1D FP32: one resident launch (tiles kept on chip) per run")
     ap.add_argument("--batch", type=int, default=0,
                     help="1D Euler: this many instances, cells log-uniform in [256, 16384], "
                          "two-state data (the batched workload's recipe, seed 77)")
@@ -75,8 +78,9 @@ def main():
     else:
         h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
-        if (args.threads or args.persistent) and args.dim == 1:
-            H.hweno_set_execution(h, args.threads or 256, args.persistent)
+        if (args.threads or args.persistent or args.resident) and args.dim == 1:
+            H.hweno_set_execution(h, args.threads or 256,
+                                  2 if args.resident else (1 if args.persistent else 0))
         H.hweno_set_state(h, dev.data_ptr(), prec, True)
         if args.adjoint > 0:
             t = H.hweno_record(h, args.rk_steps, args.adjoint)
