@@ -51,8 +51,14 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
 # summarised under profiles/ (None where no capture of the current build exists):
 # the resident launch reads the state once per launch (2000 steps = 6000 stages)
 TRAFFIC_1D_FP32 = {(256, "resident"): (2340608 + 57856) / 6000}
-TRAFFIC_BATCH_FP32 = {}
-TRAFFIC_2D_NG2 = 4 * (403427584 + 178328320 + 403399680 + 179353600) / 2
+# the batched workload, 128-thread per-stage launches: the mean of the three
+# stages of one step, cold L2
+TRAFFIC_BATCH_FP32 = {(128, "per-stage graphs"): (48920064 + 43554304 + 96720384 + 22503424
+                                                  + 96724480 + 21628160) / 3}
+# 2D, 2 Gauss points: a 2048^2 capture (the three stages of one step) scaled
+# by the cell count to 4096^2 (the bytes per cell do not depend on the grid)
+TRAFFIC_2D_NG2 = 4 * (213615872 + 353926144 + 403311616 + 174973952 + 403310592
+                      + 175929856) / 3
 L2_FLUSH_BYTES = 512 << 20
 # hweno_autotune's launch kinds and the kernel each one times
 LAUNCH_KIND = {0: "per-stage graphs", 1: "persistent", 2: "resident"}

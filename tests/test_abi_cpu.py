@@ -80,3 +80,10 @@ def test_default_config_matches_the_paper(lib):
     assert c.cfl == 0.6 and c.eps == 1e-6 and c.gas_gamma == 1.4
     c2 = H.hweno_default_config(2, H.HWENO_EULER)
     assert list(c2.lin_w) == [0.96, 0.01, 0.01, 0.01, 0.01]
+
+
+def test_fma_peak_rejects_bad_arguments_before_any_cuda_call(lib):
+    out = ctypes.c_double(0.0)
+    assert lib.hweno_fma_peak(0, 0, ctypes.byref(out)) == H.HWENO_ERR_ARG
+    assert lib.hweno_fma_peak(1, (1 << 24) + 1, ctypes.byref(out)) == H.HWENO_ERR_ARG
+    assert lib.hweno_fma_peak(0, 10, None) == H.HWENO_ERR_ARG
