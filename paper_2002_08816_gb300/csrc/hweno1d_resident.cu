@@ -121,8 +121,9 @@ template <typename R, int C, int NTH>
 struct SmemRes {
   Smem1D<R, C, NTH> w;  // the stage's working arrays (as the per-stage kernel)
   int abort;            // a wait ran out: every thread leaves
-  int cnt[NTH / 32];
-  float amax[NTH / 32];
+  unsigned red_max[2];  // the CTA's maximum wave speed (bits), per stage parity
+  unsigned arrived[2];  // warps that have folded theirs in
+  unsigned trb;         // troubled cell-stages of the run
 };
 
 // Source of halo slot j (0..2 left, 3..5 right) of the tile of Tq cells from
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
   __shared__ SmemRes<R, C, NTH> S;
   Smem1D<R, C, NTH>& sm = S.w;
   const Stage1DArgs& a = r.a;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   constexpr int NT = NTH, NW = NTH / 32;
   const int T = r.tile, n = a.n, ncta = gridDim.x, q = blockIdx.x;
   const int base = q * T;
@@ -165,7 +166,12 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
   u64* const hal = r.halo;                 // [cta][parity][6 slots][C][2]
   constexpr int HS = 6 * C * 2;            // values of one CTA's published cells
 
-  if (tid == 0) S.abort = 0;
+  if (tid == 0) {
+    S.abort = 0;
+    S.red_max[0] = S.red_max[1] = 0u;
+    S.arrived[0] = S.arrived[1] = 0u;
+    S.trb = 0u;
+  }
   __syncthreads();
 
   if (tid >= NT) {
@@ -318,7 +324,6 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
   const int hj = tid < 3 ? tid : (tid >= Tq + 3 && tid < Tq + 6 ? tid - Tq : -1);
   HaloSrc hs = {0, 0, false};
   if (hj >= 0) hs = halo_source(hj, base, Tq, T, n, a.bc, ncta);
-  unsigned troubled = 0u;
   unsigned bad = 0u;
   int done = 0;  // stages completed
 
@@ -478,25 +483,23 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         }
       }
     }
-    // the CTA's maximum wave speed and troubled count
-    float wm = (float)speed;
-    for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    // the CTA's maximum wave speed (non-negative floats order as their bit
+    // patterns: one warp reduction instruction) and troubled count; the last
+    // warp to fold its own in publishes the CTA's (no CTA barrier: the next
+    // stage's first barrier orders the shared memory)
+    const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint((float)speed));
     const int wc = __popc(__ballot_sync(0xffffffffu, myflag));
     if (lane == 0) {
-      S.amax[warp] = wm;
-      S.cnt[warp] = wc;
-    }
-    bar_sync(kBarCells, NT);
-    if (tid == 0) {
-      float m = 0.0f;
-      int cn = 0;
-      for (int k = 0; k < NW; ++k) {
-        m = fmaxf(m, S.amax[k]);
-        cn += S.cnt[k];
+      const int g = s & 1;
+      atomicMax(&S.red_max[g], wm);
+      if (wc) atomicAdd(&S.trb, (unsigned)wc);
+      __threadfence_block();
+      if (atomicAdd(&S.arrived[g], 1u) == (unsigned)(NW - 1)) {
+        const unsigned m = atomicExch(&S.red_max[g], 0u);  // read, and reset for stage s + 2
+        S.arrived[g] = 0u;
+        st_relaxed(r.entries + ((size_t)g * ncta + q) * kEntStride,
+                   tagged((unsigned)(s + 1), __uint_as_float(m)));
       }
-      troubled += (unsigned)cn;
-      st_relaxed(r.entries + ((size_t)(s & 1) * ncta + q) * kEntStride,
-                 tagged((unsigned)(s + 1), (float)m));
     }
     ++done;
   }
@@ -511,7 +514,8 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
     }
   }
   if (bad) atomicOr(&a.sc->status, bad);
-  if (tid == 0 && troubled) atomicAdd(&a.sc->troubled, (unsigned long long)troubled);
+  bar_sync(kBarCells, NT);  // every warp's troubled count is in
+  if (tid == 0 && S.trb) atomicAdd(&a.sc->troubled, (unsigned long long)S.trb);
 }
 
 template <typename R, int C, int NTH>
