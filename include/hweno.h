@@ -255,6 +255,20 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
  * ctas CTAs cannot all be resident.  The error text is hweno_last_error(NULL). */
 hweno_status hweno_check_barrier(int ctas, int meetings, int missing, unsigned polls);
 
+/* Failure-detection self-test of the resident launch (no counterpart in the
+ * paper).  On a handle set to the resident launch (hweno_set_execution(h, 256
+ * or 512, 2)) with a state, runs nsteps Runge-Kutta steps in one resident
+ * launch in which CTA silent_cta (0 <= silent_cta < the launch's CTAs; -1:
+ * none) never publishes the maximum wave speed of its outputs, and every wait
+ * of the launch gives up after `polls` polls.  With a silent CTA no CTA can
+ * form alpha: the waits run out, each CTA records the timeout in the status
+ * word and leaves, the state is not written, and the result is
+ * HWENO_ERR_TIMEOUT; the context stays usable (hweno_set_state resets the
+ * status).  With silent_cta = -1 it is an ordinary run (HWENO_OK).  Waits for
+ * the stream.  HWENO_ERR_ARG for another launch kind or invalid arguments,
+ * HWENO_ERR_STATE before hweno_set_state. */
+hweno_status hweno_check_resident(hweno_handle h, int nsteps, int silent_cta, unsigned polls);
+
 /* Sets the choice hweno_autotune makes by hand: threads per CTA (128, 256 or
  * 512) and the launch kind: 0 per-stage launches in CUDA graphs, 1 one
  * persistent launch per hweno_step with a grid barrier between stages, 2 one

@@ -28,9 +28,10 @@
 //     threads compute the troubled flags, the limiter and the interface
 //     values, which do not need alpha.
 // Both buffers are zeroed before each launch (tags start at 1).
-// Every wait is bounded (kPolls polls, about a second): a CTA whose wait runs
-// out sets ST_TIMEOUT and leaves, so the others run out too and the launch
-// ends with a status the host reads.  The arithmetic of a cell is that of the
+// Every wait is bounded (r.polls polls; the library passes 2^21, about a
+// second): a CTA whose wait runs out sets ST_TIMEOUT and leaves, so the others
+// run out too and the launch ends with a status the host reads.  A self-test
+// (hweno_check_resident) names a CTA that never publishes its maximum.  The arithmetic of a cell is that of the
 // per-stage kernel (hweno1d_stage.cuh): the same helpers in the same order.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,7 +50,6 @@ using s1d::kBarCells;
 using s1d::ldx;
 using s1d::Smem1D;
 
-constexpr unsigned kPolls = 1u << 21;  // ~0.5-1 us a poll: about a second
 
 constexpr int kMaxEnt = 10;            // entries a scalar-warp lane polls (ncta <= 320)
 constexpr int kEntStride = 16;         // words between two CTAs' entries: one cache line each
@@ -71,14 +71,14 @@ __device__ __forceinline__ float value_of(u64 w) { return __uint_as_float((unsig
 
 // The maximum of the ncta entries (kEntStride words apart) once all carry
 // `tag` (the warp's lanes poll up to kMaxEnt entries each, every round's loads
-// in flight together); false after kPolls rounds.
+// in flight together); false after `polls` rounds.
 __device__ __forceinline__ bool gather_max(const u64* ent, int ncta, unsigned tag, int lane,
-                                           float* out) {
+                                           float* out, unsigned polls) {
   u64 w[kMaxEnt];
 #pragma unroll
   for (int j = 0; j < kMaxEnt; ++j) w[j] = 0ull;
   bool ok = false;
-  for (unsigned it = 0; it < kPolls; ++it) {
+  for (unsigned it = 0; it < polls; ++it) {
     bool mine = true;
 #pragma unroll
     for (int j = 0; j < kMaxEnt; ++j) {
@@ -104,10 +104,10 @@ __device__ __forceinline__ bool gather_max(const u64* ent, int ncta, unsigned ta
   return ok;
 }
 
-// One word polled by one thread until it carries `tag`; false after kPolls
+// One word polled by one thread until it carries `tag`; false after `polls`
 // polls.
-__device__ __forceinline__ bool poll_word(const u64* p, unsigned tag, u64* out) {
-  for (unsigned it = 0; it < kPolls; ++it) {
+__device__ __forceinline__ bool poll_word(const u64* p, unsigned tag, u64* out, unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it) {
     const u64 w = ld_relaxed(p);
     if (tag_of(w) == tag) {
       *out = w;
@@ -210,11 +210,11 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         bool got;
         if (q == 0) {
           got = gather_max(ent + (size_t)((s - 1) & 1) * ncta * kEntStride, ncta, (unsigned)s,
-                           lane, &m);
+                           lane, &m, r.polls);
           if (got && lane == 0) st_relaxed(r.alpha_word + ((s - 1) & 1), tagged((unsigned)s, m));
         } else {
           u64 w = 0ull;
-          if (lane == 0) poll_word(r.alpha_word + ((s - 1) & 1), (unsigned)s, &w);
+          if (lane == 0) poll_word(r.alpha_word + ((s - 1) & 1), (unsigned)s, &w, r.polls);
           w = __shfl_sync(0xffffffffu, w, 0);
           got = tag_of(w) == (unsigned)s;
           m = value_of(w);
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
     if (q == 0 && ok && s_end > 0) {
       float m = 0.0f;
       if (gather_max(ent + (size_t)((s_end - 1) & 1) * ncta * kEntStride, ncta, (unsigned)s_end,
-                     lane, &m)) {
+                     lane, &m, r.polls)) {
         const double am = (double)m;
         double* p0 = static_cast<double*>(r.part0);
         double* p1 = static_cast<double*>(r.part1);
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
 #pragma unroll
         for (int j = 0; j < C * 2; ++j) w[j] = 0ull;
         bool got = false;
-        for (unsigned it = 0; it < kPolls && !got; ++it) {
+        for (unsigned it = 0; it < r.polls && !got; ++it) {
           got = true;
 #pragma unroll
           for (int j = 0; j < C * 2; ++j)
@@ -497,8 +497,9 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
       if (atomicAdd(&S.arrived[g], 1u) == (unsigned)(NW - 1)) {
         const unsigned m = atomicExch(&S.red_max[g], 0u);  // read, and reset for stage s + 2
         S.arrived[g] = 0u;
-        st_relaxed(r.entries + ((size_t)g * ncta + q) * kEntStride,
-                   tagged((unsigned)(s + 1), __uint_as_float(m)));
+        if (q != r.silent_cta)
+          st_relaxed(r.entries + ((size_t)g * ncta + q) * kEntStride,
+                     tagged((unsigned)(s + 1), __uint_as_float(m)));
       }
     }
     ++done;

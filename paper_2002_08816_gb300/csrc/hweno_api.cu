@@ -270,8 +270,10 @@ cudaError_t prepare_resident(hweno_ctx* h) {
   return cudaSuccess;
 }
 
-// nsteps Runge-Kutta steps of a 1D handle in one resident launch.
-cudaError_t enqueue_resident1d(hweno_ctx* h, int nsteps, cudaStream_t s) {
+// nsteps Runge-Kutta steps of a 1D handle in one resident launch (silent_cta,
+// polls: the failure-detection self-test; -1 and 2^21 otherwise).
+cudaError_t enqueue_resident1d(hweno_ctx* h, int nsteps, cudaStream_t s, int silent_cta = -1,
+                               unsigned polls = 1u << 21) {
   hw::Resident1DArgs r;
   memset(&r, 0, sizeof(r));
   r.a = base_args(h);
@@ -285,6 +287,8 @@ cudaError_t enqueue_resident1d(hweno_ctx* h, int nsteps, cudaStream_t s) {
   r.halo = h->res_halo;
   r.entries = h->res_entries;
   r.alpha_word = h->res_entries + hw::resident1d_entry_words(h->res_ncta) - 2;
+  r.polls = polls;
+  r.silent_cta = silent_cta;
   return hw::launch_resident1d(r, h->nth1d, h->res_ncta, s);
 }
 
@@ -1196,6 +1200,20 @@ hweno_status hweno_check_barrier(int ctas, int meetings, int missing, unsigned p
   if (host.status & hw::ST_TIMEOUT)
     return fail(nullptr, HWENO_ERR_TIMEOUT, "hweno_check_barrier: a bounded barrier wait ran out");
   return HWENO_OK;
+}
+
+hweno_status hweno_check_resident(hweno_handle h, int nsteps, int silent_cta, unsigned polls) {
+  if (!h) return fail(nullptr, HWENO_ERR_ARG, "handle is NULL");
+  if (h->dim != 1 || h->persist1d != 2 || h->res_tile == 0)
+    return fail(h, HWENO_ERR_ARG, "hweno_check_resident: set the resident launch first");
+  if (!h->has_state) return fail(h, HWENO_ERR_STATE, "hweno_check_resident before hweno_set_state");
+  if (nsteps < 1 || silent_cta < -1 || silent_cta >= h->res_ncta || polls < 1u)
+    return fail(h, HWENO_ERR_ARG,
+                "hweno_check_resident: need nsteps >= 1, -1 <= silent_cta < CTAs, polls >= 1");
+  HW_CUDA(h, hw::launch_set_scalars(h->sc, 0, -1.0, h->stream));
+  HW_CUDA(h, enqueue_resident1d(h, nsteps, h->stream, silent_cta, polls));
+  hw::DevScalars host;
+  return check_scalars(h, h->sc, &host);  // HWENO_ERR_TIMEOUT when a wait ran out
 }
 
 const char* hweno_last_error(hweno_handle h) {

@@ -196,6 +196,8 @@ struct Resident1DArgs {
   unsigned long long* entries;  // [2][ncta] maximum wave speed of each CTA's outputs, one
                                 // cache line each, then [2] alpha words (alpha_word)
   unsigned long long* alpha_word;
+  unsigned polls;     // bound of every wait (2^21 polls: about a second)
+  int silent_cta;     // self-test: this CTA never publishes its maximum (-1: none)
 };
 // Words of the entries buffer (entries and the two alpha words) for ncta CTAs.
 size_t resident1d_entry_words(int ncta);

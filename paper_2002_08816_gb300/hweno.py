@@ -99,6 +99,8 @@ def lib():
         L.hweno_rhs1d_noalloc.argtypes = [P, _VP, _VP, _VP, _VP, _VP]
         L.hweno_fma_peak.restype = _I
         L.hweno_fma_peak.argtypes = [_I, _I, ctypes.POINTER(_D)]
+        L.hweno_check_resident.restype = _I
+        L.hweno_check_resident.argtypes = [_VP, _I, _I, ctypes.c_uint]
         _lib = L
     return _lib
 
@@ -207,6 +209,16 @@ def hweno_fma_peak(fp64, iters):
     out = _D()
     _check(lib().hweno_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(out)))
     return out.value
+
+
+def hweno_check_resident(h, nsteps, silent_cta, polls):
+    """Self-test of the resident launch's bounded waits; returns the status
+    code (HWENO_OK, or HWENO_ERR_TIMEOUT when a wait ran out) and raises
+    HwenoError on other failures."""
+    st = lib().hweno_check_resident(h, int(nsteps), int(silent_cta), int(polls))
+    if st not in (HWENO_OK, HWENO_ERR_TIMEOUT):
+        raise HwenoError(st, lib().hweno_last_error(h).decode())
+    return st
 
 
 def hweno_set_execution(h, threads, persistent):

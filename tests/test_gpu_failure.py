@@ -52,3 +52,43 @@ def test_lost_arrival_times_out_and_the_context_stays_usable():
     assert np.all(np.isfinite(out[1]))
     assert np.abs(out[0] - out[1]).sum() <= 1e-6 * np.abs(out[0]).sum()
     assert H.hweno_check_barrier(8, 10, 0, 1 << 20) == H.HWENO_OK
+
+
+def test_resident_launch_gives_up_when_a_cta_never_publishes():
+    """The resident launch's waits are bounded: with one CTA that never
+    publishes its maximum no CTA can form alpha, every wait runs out (2^14
+    polls here), the host reads HWENO_ERR_TIMEOUT, the state is left as it was,
+    and the handle then runs ordinary resident steps that agree with the
+    per-stage launches."""
+    import torch
+    nx = 65536
+    u = mixed_euler(nx, 4).astype(np.float32)
+    cfg = H.make_config(1, H.HWENO_EULER, nx, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
+                        precision=H.HWENO_FP32)
+    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        H.hweno_set_execution(h, 256, 2)
+        H.hweno_set_state(h, u.ctypes.data, H.HWENO_FP32, False)
+        assert H.hweno_check_resident(h, 3, -1, 1 << 21) == H.HWENO_OK  # no silent CTA
+        H.hweno_set_state(h, u.ctypes.data, H.HWENO_FP32, False)
+        t0 = time.time()
+        assert H.hweno_check_resident(h, 3, 17, 1 << 14) == H.HWENO_ERR_TIMEOUT
+        assert time.time() - t0 < 30.0
+        back = np.empty_like(u)
+        H.hweno_get_state(h, back.ctypes.data, H.HWENO_FP32, False)
+        assert np.array_equal(back, u)  # an aborted run writes nothing
+        H.hweno_set_state(h, u.ctypes.data, H.HWENO_FP32, False)  # resets the status
+        H.hweno_step(h, 10)
+        got = np.empty_like(u)
+        H.hweno_get_state(h, got.ctypes.data, H.HWENO_FP32, False)
+    finally:
+        H.hweno_destroy(h)
+    h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        H.hweno_set_state(h, u.ctypes.data, H.HWENO_FP32, False)
+        H.hweno_step(h, 10)
+        ref = np.empty_like(u)
+        H.hweno_get_state(h, ref.ctypes.data, H.HWENO_FP32, False)
+    finally:
+        H.hweno_destroy(h)
+    assert np.abs(got - ref).sum() <= 1e-6 * np.abs(ref).sum()
