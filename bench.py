@@ -917,7 +917,7 @@ def main():
                     help="skip the other workloads' sub-records of the default run")
     ap.add_argument("--workload", default="euler1d",
                     choices=["euler1d", "euler2d", "burgers2d", "batch1d", "adjoint2d",
-                             "troubled1d"],
+                             "adjoint2d_quadrants", "troubled1d"],
                     help="euler1d: the headline 65536-cell 1D workload (with every other "
                          "workload as a sub-record at one GPU); the others alone")
     ap.add_argument("--n-gauss", type=int, default=None, choices=[2, 3],
@@ -958,6 +958,8 @@ def main():
         line = bench_batch1d(args)
     elif args.workload == "adjoint2d":
         line = bench_adjoint2d(args)
+    elif args.workload == "adjoint2d_quadrants":
+        line = bench_adjoint2d(args, data="quadrants")
     else:
         line = bench_troubled1d(args)
     if line is not None:

@@ -21,8 +21,11 @@
 //      stage, the troubled count and the status bits.
 // The reconstruction arithmetic is the generated straight-line code of
 // hweno2d_coef.cuh (square cells).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "hweno1d_recon.cuh"
 #include "hweno2d_common.cuh"
@@ -36,13 +39,19 @@ namespace {
 constexpr int TX = kTile2DX, TY = kTile2DY;
 constexpr int NT = kThreads2D;
 constexpr int NW = NT / 32;
-constexpr int RX = TX + 6, RY = TY + 6;  // raw tile, 3-cell halo
+// raw tile: a 3-cell halo, and in x one more column on the left so that the
+// tile's first column bx0 - 4 is 16-byte aligned (TMA); own-tile cell (ci, cj)
+// is raw (ci + OXR, cj + OYR)
+constexpr int RX = TX + 8, RY = TY + 6;
+constexpr int OXR = 4, OYR = 3;
 constexpr int LX = TX + 4, LY = TY + 4;  // flags and modified moments, 2-cell halo
+constexpr unsigned kTmaPolls = 1u << 20;  // mbarrier polls before a tile copy is given up
 static_assert(TX * TY == NT, "one own cell per thread");
 
 template <typename R, int C, int NG>
 struct Smem2D {
-  R u[C][3][RY][RX];            // stage input
+  static constexpr int kPadX = 1;  // raw index of flag-grid column lx: lx + 2
+  alignas(128) R u[C][3][RY][RX];  // stage input (the TMA box)
   R vl[C][LY][LX];              // modified x-moments
   R wl[C][LY][LX];              // modified y-moments
   R xf[C][2 * NG][TY][TX + 2];  // x-face values (left NG, right NG) of cells -1..TX
@@ -51,6 +60,10 @@ struct Smem2D {
   R red[2][NW];
   int cnt[NW];
   R amax[2][NW];
+  unsigned long long bar;                        // mbarrier of the tile copy
+  int ntb, nhw;                                  // lengths of the two work lists
+  unsigned short tbl[LX * LY];                   // troubled cells (Euler limiter)
+  unsigned short hwl[TX * TY + 2 * TX + 2 * TY]; // interface items with HWENO
 };
 
 // --------------------------------------------------------- KXRCF (2D)
@@ -125,7 +138,7 @@ __device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0,
 template <typename S, typename R>
 __device__ __forceinline__ void gather19(const S& sm, int c, int ci, int cj, R* d) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) d[k] = sm.u[c][0][cj + 3 + k / 3 - 1][ci + 3 + k % 3 - 1];
+  for (int k = 0; k < 9; ++k) d[k] = sm.u[c][0][cj + OYR + k / 3 - 1][ci + OXR + k % 3 - 1];
   const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
@@ -156,7 +169,7 @@ __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo
   const R gam[5] = {g0, g1, g2, g3, g4};  // by value: no caller array on the stack
   R Uc[4];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) Uc[c] = sm.u[c][0][cj + 3][ci + 3];
+  for (int c = 0; c < 4; ++c) Uc[c] = sm.u[c][0][cj + OYR][ci + OXR];
   // one eigen-system per direction (the cell average), or with mean_eigen one
   // per face (the mean of the averages on its two sides): "parts" of the
   // direction's 2 NG points
@@ -174,7 +187,7 @@ __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo
     } else {
       const int dx = dir == 0 ? 2 * side - 1 : 0, dy = dir == 1 ? 2 * side - 1 : 0;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) U[c] = R(0.5) * (Uc[c] + sm.u[c][0][cj + 3 + dy][ci + 3 + dx]);
+      for (int c = 0; c < 4; ++c) U[c] = R(0.5) * (Uc[c] + sm.u[c][0][cj + OYR + dy][ci + OXR + dx]);
     }
     R Rm[4][4], Lm[4][4];
     Euler2D<R>::eigen(gas, U, dir, Rm, Lm);
@@ -211,8 +224,9 @@ __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo
 }
 
 template <typename R, int C, int NG>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(Stage2DArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
+    stage2d_kernel(Stage2DArgs a, const __grid_constant__ CUtensorMap tile_map) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem2D<R, C, NG>& sm = *reinterpret_cast<Smem2D<R, C, NG>*>(smem_raw);
   constexpr int NF = 4 * NG, NI = NG * NG;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -222,6 +236,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
   const R* __restrict__ w = static_cast<const R*>(a.w);
 
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // Tiles whose halo lies inside the grid are copied by one TMA box (all 3 C
+  // planes, RX x RY cells from (bx0 - 4, by0 - 3)); the others (periodic or
+  // wall ghosts) by the threads, through the boundary map.
+  const bool tma = a.tma && bx0 >= OXR && bx0 - OXR + RX <= nx && by0 >= OYR &&
+                   by0 - OYR + RY <= ny;
+  if (tma && threadIdx.x == 0) {
+    mbar_init(&sm.bar, 1);
+    mbar_expect_tx(&sm.bar, (unsigned)sizeof(sm.u));
+    tma_load_3d(&sm.u[0][0][0][0], &tile_map, &sm.bar, bx0 - OXR, by0 - OYR, 0);
+  }
 
   R gam[5], eps, gas, inv_dx, inv_dy;
   if constexpr (sizeof(R) == 4) {
@@ -255,14 +279,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
 #pragma unroll
       for (int m = 0; m < 3; ++m) u0c[c][m] = u0[(3 * c + m) * plane + (size_t)gj * nx + gi];
   }
-  for (int k = tid; k < RX * RY; k += NT) {
-    const int rx = k % RX, ry = k / RX;
-    const int si = bc_map(bx0 - 3 + rx, nx, a.bc), sj = bc_map(by0 - 3 + ry, ny, a.bc);
-    const size_t s = (size_t)sj * nx + si;
+  if (!tma) {
+    for (int k = tid; k < RX * RY; k += NT) {
+      const int rx = k % RX, ry = k / RX;
+      const int si = bc_map(bx0 - OXR + rx, nx, a.bc), sj = bc_map(by0 - OYR + ry, ny, a.bc);
+      const size_t s = (size_t)sj * nx + si;
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+      for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+        for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     ax = fmax(ax, __shfl_xor_sync(0xffffffffu, ax, o));
@@ -272,7 +298,15 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
     sm.amax[0][warp] = ax;
     sm.amax[1][warp] = ay;
   }
+  if (tid == 0) sm.ntb = sm.nhw = 0;
   __syncthreads();
+  if (tma && !mbar_wait_bounded(&sm.bar, 0, kTmaPolls)) {
+    // the copy did not land: flag the stage (the host reports
+    // HWENO_ERR_TIMEOUT) and give the copy, which writes this CTA's shared
+    // memory, a second bounded wait; no thread leaves the common path
+    atomicOr(&a.sc->status, ST_TIMEOUT);
+    mbar_wait_bounded(&sm.bar, 0, kTmaPolls);
+  }
   asm volatile("griddepcontrol.launch_dependents;");
   R alx = sm.amax[0][0], aly = sm.amax[1][0];
 #pragma unroll
@@ -304,7 +338,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
   // ---- 2. Step 4 on the tile plus 2 halo cells
   for (int k = tid; k < LX * LY; k += NT) {
     const int lx = k % LX, ly = k / LX;
-    const int rx = lx + 1, ry = ly + 1;  // raw index of the cell
+    const int rx = lx + 1 + Smem2D<R, C, NG>::kPadX, ry = ly + 1;  // raw index of the cell
     int flag;
     if (a.mode == 1) {
       flag = 1;
@@ -343,50 +377,80 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
       sm.wl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx],
                                             sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
                                             sm.u[0][2][ry + 1][rx], gam, eps);
-    } else {
-      limit_euler2d(sm, lx, ly, gam[0], gam[1], gam[2], gam[3], gam[4], eps, gas);
     }
+    // Euler: the troubled cells are listed and limited by consecutive threads
+    // below, so a warp holding one or two of them does not run the
+    // characteristic limiter for its other lanes' sake
+    if constexpr (C == 4) list_append(&sm.ntb, sm.tbl, k, flag != 0, LX * LY);
   }
   __syncthreads();
+  if constexpr (C == 4) {
+    if (sm.ntb > 0) {  // uniform over the CTA
+      for (int q = tid; q < sm.ntb; q += NT) {
+        const int k = sm.tbl[q];
+        limit_euler2d(sm, k % LX, k / LX, gam[0], gam[1], gam[2], gam[3], gam[4], eps, gas);
+      }
+      __syncthreads();
+    }
+  }
 
   // ---- 3. interface values of the own cells (all faces) and of the cross
   //         halo (left column: right face, right column: left face, bottom
   //         row: top face, top row: bottom face)
-  for (int item = tid; item < TX * TY + 2 * TX + 2 * TY; item += NT) {
-    int ci, cj, p_lo, p_hi;  // own-tile coordinates of the cell, point range
-    if (item < TX * TY) {
+  //         by linear p0; the items whose stencil holds a troubled cell are
+  //         listed and reconstructed by HWENO on consecutive threads below
+  //         (the same arithmetic, fewer warps diverging on it)
+  auto item_of = [](int item, int& ci, int& cj, int& p_lo, int& p_hi) {
+    if (item < TX * TY) {  // own cell: every interface point
       ci = item % TX; cj = item / TX; p_lo = 0; p_hi = NF;
-    } else {
+    } else {               // cross halo: the one face shared with the tile
       const int h = item - TX * TY;
       if (h < TY) { ci = -1; cj = h; p_lo = NG; p_hi = 2 * NG; }
       else if (h < 2 * TY) { ci = TX; cj = h - TY; p_lo = 0; p_hi = NG; }
       else if (h < 2 * TY + TX) { ci = h - 2 * TY; cj = -1; p_lo = 3 * NG; p_hi = 4 * NG; }
       else { ci = h - 2 * TY - TX; cj = TY; p_lo = 2 * NG; p_hi = 3 * NG; }
     }
+  };
+  for (int item = tid; item < TX * TY + 2 * TX + 2 * TY; item += NT) {
+    int ci, cj, p_lo, p_hi;  // own-tile coordinates of the cell, point range
+    item_of(item, ci, cj, p_lo, p_hi);
     bool hw = false;
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
       for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 2 + dj][ci + 2 + di] != 0;
-    if (!hw || C == 1) {
+    if (!hw) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         R d[19], v[NF];
         gather19(sm, c, ci, cj, d);
-        if (!hw)
-          p0_faces<NG>(d, v);
-        else
-          hweno2d_faces<NG>(d, gam, eps, p_lo, p_hi, v);
+        p0_faces<NG>(d, v);
 #pragma unroll
         for (int p = 0; p < NF; ++p)
           if (p >= p_lo && p < p_hi) store_point(sm, c, p, ci, cj, v[p]);
       }
-    } else if constexpr (C == 4) {
-      hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam[0], gam[1], gam[2], gam[3], gam[4],
-                              eps, gas, (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
     }
+    list_append(&sm.nhw, sm.hwl, item, hw, TX * TY + 2 * TX + 2 * TY);
   }
   __syncthreads();
+  if (sm.nhw > 0) {  // uniform over the CTA
+    for (int q = tid; q < sm.nhw; q += NT) {
+      int ci, cj, p_lo, p_hi;
+      item_of(sm.hwl[q], ci, cj, p_lo, p_hi);
+      if constexpr (C == 1) {
+        R d[19], v[NF];
+        gather19(sm, 0, ci, cj, d);
+        hweno2d_faces<NG>(d, gam, eps, p_lo, p_hi, v);
+#pragma unroll
+        for (int p = 0; p < NF; ++p)
+          if (p >= p_lo && p < p_hi) store_point(sm, 0, p, ci, cj, v[p]);
+      } else {
+        hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam[0], gam[1], gam[2], gam[3], gam[4],
+                                eps, gas, (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
+      }
+    }
+    __syncthreads();
+  }
 
   // ---- 4. own cells: interior points, fluxes, Eq. (ode2), Eq. (RK)
   constexpr double r15 = 0.38729833462074168852;  // sqrt(15)/10
@@ -476,9 +540,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) stage2d_kernel(S
       // the stage input the combination uses: first moments as modified by
       // Step 4 (stored, the default), or unmodified (variant)
       const bool raw = (a.variant & HWENO_VARIANT_RAW_COMBINE) != 0;
-      const R W[3] = {sm.u[c][0][cj + 3][ci + 3],
-                      raw ? sm.u[c][1][cj + 3][ci + 3] : sm.vl[c][cj + 2][ci + 2],
-                      raw ? sm.u[c][2][cj + 3][ci + 3] : sm.wl[c][cj + 2][ci + 2]};
+      const R W[3] = {sm.u[c][0][cj + OYR][ci + OXR],
+                      raw ? sm.u[c][1][cj + OYR][ci + OXR] : sm.vl[c][cj + 2][ci + 2],
+                      raw ? sm.u[c][2][cj + OYR][ci + OXR] : sm.wl[c][cj + 2][ci + 2]};
       const R Lm[3] = {L0, L1, L2};
       R o[3];
 #pragma unroll
@@ -647,8 +711,39 @@ __global__ void __launch_bounds__(NT) alpha2d_kernel(const R* __restrict__ w, R*
   }
 }
 
+// The tensor map of a stage input (3 C planes of ny x nx values of R, x
+// fastest) with the raw tile as its box; false when the state cannot be
+// copied by TMA (rows not a multiple of 16 bytes, a grid smaller than the
+// box, no encoder in the driver): the kernel then loads every tile itself.
+bool encode_tile_map(const void* w, int nx, int ny, int planes, int esize, CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  memset(map, 0, sizeof(*map));
+  if (!encode || ((size_t)nx * esize) % 16 != 0 || ((uintptr_t)w) % 16 != 0 || nx < RX ||
+      ny < RY)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * ny * esize};
+  const cuuint32_t box[3] = {(cuuint32_t)RX, (cuuint32_t)RY, (cuuint32_t)planes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                3, const_cast<void*>(w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename R, int C, int NG>
-cudaError_t launch_stage2d_t(const Stage2DArgs& a, cudaStream_t s) {
+cudaError_t launch_stage2d_t(const Stage2DArgs& a0, cudaStream_t s) {
+  Stage2DArgs a = a0;
+  CUtensorMap map;
+  a.tma = encode_tile_map(a.w, a.nx, a.ny, 3 * C, (int)sizeof(R), &map) ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
   cfg.blockDim = dim3(NT);
@@ -659,7 +754,7 @@ cudaError_t launch_stage2d_t(const Stage2DArgs& a, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, stage2d_kernel<R, C, NG>, a);
+  return cudaLaunchKernelEx(&cfg, stage2d_kernel<R, C, NG>, a, map);
 }
 
 template <typename R, int C, int NG>

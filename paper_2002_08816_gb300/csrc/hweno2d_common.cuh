@@ -185,7 +185,7 @@ template <typename S, typename R>
 __device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, R g0, R g1, R g2, R g3, R g4,
                                            R eps, R gas) {
   const R gam[5] = {g0, g1, g2, g3, g4};  // by value: no caller array on the stack
-  const int rx = lx + 1, ry = ly + 1;
+  const int rx = lx + 1 + S::kPadX, ry = ly + 1;  // raw index of the cell
   R U[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) U[c] = sm.u[c][0][ry][rx];

@@ -99,6 +99,72 @@ __device__ __forceinline__ float mirror_sign(int c, int m) {
   return m == 0 ? s : -s;
 }
 
+// Tensor-memory-accelerator (TMA) copies of a tile into shared memory,
+// completed on an mbarrier (PTX ISA: cp.async.bulk.tensor, mbarrier).  One
+// thread initialises the barrier, announces the bytes and issues the copy;
+// every thread waits on phase 0 with a bounded number of polls.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  // the initialised barrier, visible to the copy engine
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// box of the 3D tensor map at element coordinates (x, y, z): x * element size
+// must be a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, unsigned long long* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once phase `parity` completed, false after `polls` unsuccessful polls
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Appends `item` to a shared-memory work list when `need`: the converged
+// threads of the warp vote (ballot), one of them reserves the warp's entries
+// with a single shared atomic, and each voter writes its entry at its rank
+// among the voters.  Called by every thread of the loop iteration; returns
+// the entry's index (-1 without an entry).  Entries past `cap` are counted
+// but not written.
+__device__ __forceinline__ int list_append(int* count, unsigned short* list, int item, bool need,
+                                           int cap) {
+  const unsigned act = __activemask();
+  const unsigned vote = __ballot_sync(act, need);
+  if (!vote) return -1;
+  const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(vote));
+  base = __shfl_sync(act, base, leader);
+  if (!need) return -1;
+  const int q = base + __popc(vote & ((1u << lane) - 1u));
+  if (q < cap) list[q] = (unsigned short)item;
+  return q;
+}
+
 template <int NT>
 __device__ __forceinline__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

@@ -114,6 +114,7 @@ struct Stage2DArgs {
   const void* dt_in;     // nullable: stage 1 takes this dt (replay of a recorded step)
   int nx, ny, stage, bc, mode, system, fp64, ng;
   int variant;            // HWENO_VARIANT_* bits
+  int tma;                // set by the launcher: interior tiles copied by TMA
   double dx, dy, cfl, eps, thr, gas;
   double gam[5];
   double inv_dx, inv_dy;  // derived

@@ -5,6 +5,7 @@
                                                   [--dim 1|2] [--n-gauss 2|3]
                                                   [--adjoint EVERY] [--threads 128|256|512]
                                                   [--persistent | --resident] [--batch N]
+                                                  [--quadrants]
 
 Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
 --dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
@@ -14,7 +15,9 @@ EVERY (2D) the steps are recorded with a checkpoint every EVERY steps and the
 gradient of sum(rho^2) is taken (hweno_backward: recomputed stages, then two
 adjoint kernels per stage).  With --batch N it runs N independent 1D Euler
 instances in shared launches (hweno_create_batch).  --persistent and
---resident select the 1D launch kinds with one launch per run.
+--resident select the 1D launch kinds with one launch per run.  --quadrants
+(2D) replaces the vortex by four constant quadrants drawn from the seed (shocks
+along the quadrant lines: the troubled-cell paths).
 """
 
 import argparse
@@ -47,6 +50,8 @@ def main():
                     help="1D: one persistent launch with grid barriers instead of per-stage graphs")
     ap.add_argument("--resident", action="store_true",
                     help="1D FP32: one resident launch (tiles kept on chip) per run")
+    ap.add_argument("--quadrants", action="store_true",
+                    help="2D Euler: four constant quadrants drawn from the seed instead of the vortex")
     ap.add_argument("--batch", type=int, default=0,
                     help="1D Euler: this many instances, cells log-uniform in [256, 16384], "
                          "two-state data (the batched workload's recipe, seed 77)")
@@ -55,7 +60,10 @@ def main():
     prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
     if args.dim == 2:
         # 2D Euler, nx x nx periodic on [0, 10]^2, vortex plus density modes
-        u = W.euler_vortex_modes_2d(args.nx, args.nx, seed=args.seed, npts=2)
+        if args.quadrants:
+            u = W.euler_quadrants_2d(args.nx, args.nx, seed=args.seed)
+        else:
+            u = W.euler_vortex_modes_2d(args.nx, args.nx, seed=args.seed, npts=2)
         cfg = H.make_config(2, H.HWENO_EULER, args.nx, args.nx, x0=0.0, x1=10.0, y0=0.0,
                             y1=10.0, cfl=0.5, precision=prec, n_gauss=args.n_gauss)
     elif args.batch > 0:
