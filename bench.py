@@ -46,7 +46,7 @@ UNIT = "cell-stages/s"
 # algorithmic bytes per cell-stage: stage 1 reads u^n and writes u^(1) (2S),
 # stages 2 and 3 read u^n and u^(k) and write (3S); mean 8S/3 with
 # S = 3 components x 2 moments x sizeof(real)
-BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3}
+BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3, "fp32c": 8 * 36 / 3}
 # DRAM bytes (read + write) per stage from ncu captures of the current kernels,
 # summarised under profiles/ (None where no capture of the current build exists):
 # the resident launch reads the state once per launch (2000 steps = 6000 stages)
@@ -286,18 +286,21 @@ def run_1d(H, s, stream, u0, prec, steps, warmup, flush, sampler=None, autotune=
     cfg = H.make_config(1, H.HWENO_EULER, NX, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=CFL,
                         precision=prec)
     h = H.hweno_create(cfg, s)
-    dt = torch.float32 if prec == H.HWENO_FP32 else torch.float64
+    # the state's element type: FP32 for both FP32 precisions (HWENO_FP32C then
+    # starts from zero low parts: the same input the FP32 path and the oracle see)
+    sdt = H.HWENO_FP64 if prec == H.HWENO_FP64 else H.HWENO_FP32
+    dt = torch.float64 if sdt == H.HWENO_FP64 else torch.float32
     dev_in = torch.from_numpy(u0).to("cuda", dt).contiguous()
     host_in = torch.from_numpy(u0).to(dt).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
 
     def one_step():
-        H.hweno_set_state(h, dev_in.data_ptr(), prec, True)
+        H.hweno_set_state(h, dev_in.data_ptr(), sdt, True)
         H.hweno_step(h, RK_STEPS, -1.0, wait=False)
 
     # the library's autotuner picks threads per CTA and the launch kind for
     # this workload (untimed)
-    H.hweno_set_state(h, dev_in.data_ptr(), prec, True)
+    H.hweno_set_state(h, dev_in.data_ptr(), sdt, True)
     choice = H.hweno_autotune(h, 100) if autotune else (256, 0)
     for _ in range(warmup):
         one_step()
@@ -326,9 +329,9 @@ def run_1d(H, s, stream, u0, prec, steps, warmup, flush, sampler=None, autotune=
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        H.hweno_set_state(h, host_in.data_ptr(), prec, False)
+        H.hweno_set_state(h, host_in.data_ptr(), sdt, False)
         H.hweno_step(h, RK_STEPS, -1.0, wait=False)
-        H.hweno_get_state(h, host_out.data_ptr(), prec, False)
+        H.hweno_get_state(h, host_out.data_ptr(), sdt, False)
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
@@ -363,10 +366,10 @@ def bench_hweno(args):
 
     cells = NX * 3 * RK_STEPS
     res = {}
-    for name, prec in (("fp32", H.HWENO_FP32), ("fp64", H.HWENO_FP64)):
+    for name, prec in (("fp32", H.HWENO_FP32), ("fp32c", H.HWENO_FP32C), ("fp64", H.HWENO_FP64)):
         barrier()
         sampler = ClockSampler(local) if name == "fp32" else None
-        r = run_1d(H, s, stream, u0r if name == "fp32" else u0, prec, args.steps, args.warmup,
+        r = run_1d(H, s, stream, u0 if name == "fp64" else u0r, prec, args.steps, args.warmup,
                    flush, sampler)
         tot_s = max_over_ranks(sum(r["ms"]) / 1e3)
         e2e_s = max_over_ranks(sum(r["e2e_ms"]) / 1e3)
@@ -400,6 +403,18 @@ def bench_hweno(args):
         "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"],
                  "stage_us": res["fp64"]["stage_us"], "e2e": res["fp64"]["e2e"],
                  "execution": res["fp64"]["execution"]},
+        # FP32 arithmetic with float-pair averages (HWENO_FP32C), same input
+        "fp32c": {"value": res["fp32c"]["value"], "ms_per_step": res["fp32c"]["ms_per_step"],
+                  "stage_us": res["fp32c"]["stage_us"], "e2e": res["fp32c"]["e2e"],
+                  "execution": res["fp32c"]["execution"],
+                  "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak,
+                               "achieved": BYTES_PER_CELL_STAGE["fp32c"] * NX
+                               / (res["fp32c"]["stage_us"] * 1e-6) / 1e9,
+                               "frac": BYTES_PER_CELL_STAGE["fp32c"] * NX
+                               / (res["fp32c"]["stage_us"] * 1e-6) / 1e9 / peak,
+                               "traffic": None,
+                               "note": "algorithmic 96 B per cell-stage (the averages as float "
+                                       "pairs: 36 B per cell) x 65536 cells per stage"}},
         "troubled_frac": r["stats"]["troubled"] / float(cells),
         "execution": r["execution"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -428,11 +443,14 @@ def bench_hweno(args):
         line["fp32_vs_oracle"]["note"] = (
             "after the 2000 shocked steps, same FP32-rounded input; rel_L1 per field and the "
             "first moments' L1 over the averages' L1 / 4")
+        line["fp32c_vs_oracle"] = field_errors(res["fp32c"]["final"], ref)
+        line["fp32c_vs_oracle"]["note"] = "HWENO_FP32C, same input and reference as fp32_vs_oracle"
         # conditioning: the FP64 GPU path from the unrounded input against the
         # oracle from the FP32-rounded one (one rounding of the input, no FP32
         # arithmetic)
         line["fp64_unrounded_vs_oracle"] = field_errors(res["fp64"]["final"], ref)
-        line["time_vs_oracle"] = {"fp32": abs(r["stats"]["t"] - t_ref) / t_ref}
+        line["time_vs_oracle"] = {"fp32": abs(r["stats"]["t"] - t_ref) / t_ref,
+                                  "fp32c": abs(res["fp32c"]["stats"]["t"] - t_ref) / t_ref}
     if ws > 1:
         dist.destroy_process_group()
     return line

@@ -36,7 +36,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "hweno1d_stage.cuh"
+#include "hweno1d_comp.cuh"
 
 namespace hw {
 namespace {
@@ -117,9 +117,13 @@ __device__ __forceinline__ bool poll_word(const u64* p, unsigned tag, u64* out, 
   return false;
 }
 
-template <typename R, int C, int NTH>
+template <typename R, int C, int NTH, bool COMP>
 struct SmemRes {
   Smem1D<R, C, NTH> w;  // the stage's working arrays (as the per-stage kernel)
+  // float-pair averages (COMP): low parts of the stage input's averages (sm.u
+  // slots) and the flux increments f(hi_{e+1}) - f(hi_e) (sm.fm slots)
+  R ulo[COMP ? C : 1][COMP ? NTH : 1];
+  R fb[COMP ? C : 1][COMP ? NTH : 1];
   int abort;            // a wait ran out: every thread leaves
   unsigned red_max[2];  // the CTA's maximum wave speed (bits), per stage parity
   unsigned arrived[2];  // warps that have folded theirs in
@@ -152,10 +156,10 @@ __device__ __forceinline__ HaloSrc halo_source(int j, int base, int Tq, int T, i
   return h;
 }
 
-template <typename R, int C, int NTH>
+template <typename R, int C, int NTH, bool COMP>
 __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kernel(Resident1DArgs r) {
   static_assert(sizeof(R) == 4, "the exchange words carry FP32 values");
-  __shared__ SmemRes<R, C, NTH> S;
+  __shared__ SmemRes<R, C, NTH, COMP> S;
   Smem1D<R, C, NTH>& sm = S.w;
   const Stage1DArgs& a = r.a;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -163,8 +167,10 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
   const int T = r.tile, n = a.n, ncta = gridDim.x, q = blockIdx.x;
   const int base = q * T;
   const int Tq = min(T, n - base);  // this CTA's cells (the last tile may be short)
-  u64* const hal = r.halo;                 // [cta][parity][6 slots][C][2]
-  constexpr int HS = 6 * C * 2;            // values of one CTA's published cells
+  u64* const hal = r.halo;                 // [cta][parity][6 slots][C][NV]
+  constexpr int NV = COMP ? 3 : 2;         // words per cell and component: average, first
+                                           // moment (, low part of the average)
+  constexpr int HS = 6 * C * NV;           // values of one CTA's published cells
 
   if (tid == 0) {
     S.abort = 0;
@@ -296,8 +302,9 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
   const bool own = tid < Tq;
   const int i = base + tid;
   // this thread's cell between stages: the stage output, and u^n as limited
-  // by stage 1 (the Runge-Kutta combination's u^n)
-  R cur[C][2], u0c[C][2];
+  // by stage 1 (the Runge-Kutta combination's u^n); COMP: the low parts of
+  // their averages
+  R cur[C][2], u0c[C][2], curl[C], u0l[C];
   // the first stage input: tile and halo from global memory
   {
     const R* w = static_cast<const R*>(a.w);
@@ -309,6 +316,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         for (int c = 0; c < C; ++c) {
           sm.u[c][0][tid] = w[(2 * c + 0) * n + g] * (mir ? R(mirror_sign(c, 0)) : R(1));
           sm.u[c][1][tid] = w[(2 * c + 1) * n + g] * (mir ? R(mirror_sign(c, 1)) : R(1));
+          if constexpr (COMP) S.ulo[c][tid] = r.lo[c * n + g] * (mir ? R(mirror_sign(c, 0)) : R(1));
         }
       } else {
         const int g = bc_map(base - H + tid, n, a.bc);
@@ -316,6 +324,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         for (int c = 0; c < C; ++c) {
           sm.u[c][0][tid] = w[(2 * c + 0) * n + g];
           sm.u[c][1][tid] = w[(2 * c + 1) * n + g];
+          if constexpr (COMP) S.ulo[c][tid] = r.lo[c * n + g];
         }
       }
     }
@@ -338,21 +347,22 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         for (int c = 0; c < C; ++c) {
           sm.u[c][0][tid + H] = cur[c][0];
           sm.u[c][1][tid + H] = cur[c][1];
+          if constexpr (COMP) S.ulo[c][tid + H] = curl[c];
         }
       }
       if (hj >= 0) {
-        const u64* src = hal + ((size_t)hs.cta * 2 + ((s - 1) & 1)) * HS + hs.slot * (C * 2);
-        u64 w[C * 2];
+        const u64* src = hal + ((size_t)hs.cta * 2 + ((s - 1) & 1)) * HS + hs.slot * (C * NV);
+        u64 w[C * NV];
 #pragma unroll
-        for (int j = 0; j < C * 2; ++j) w[j] = 0ull;
+        for (int j = 0; j < C * NV; ++j) w[j] = 0ull;
         bool got = false;
         for (unsigned it = 0; it < r.polls && !got; ++it) {
           got = true;
 #pragma unroll
-          for (int j = 0; j < C * 2; ++j)
+          for (int j = 0; j < C * NV; ++j)
             if (tag_of(w[j]) != (unsigned)s) w[j] = ld_relaxed(src + j);
 #pragma unroll
-          for (int j = 0; j < C * 2; ++j)
+          for (int j = 0; j < C * NV; ++j)
             if (tag_of(w[j]) != (unsigned)s) got = false;
         }
         if (!got) {
@@ -362,8 +372,10 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
           const int e = hj < 3 ? hj : Tq + hj;
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            sm.u[c][0][e] = R(value_of(w[2 * c + 0])) * (hs.mirror ? R(mirror_sign(c, 0)) : R(1));
-            sm.u[c][1][e] = R(value_of(w[2 * c + 1])) * (hs.mirror ? R(mirror_sign(c, 1)) : R(1));
+            const R s0 = hs.mirror ? R(mirror_sign(c, 0)) : R(1);
+            sm.u[c][0][e] = R(value_of(w[NV * c + 0])) * s0;
+            sm.u[c][1][e] = R(value_of(w[NV * c + 1])) * (hs.mirror ? R(mirror_sign(c, 1)) : R(1));
+            if constexpr (COMP) S.ulo[c][e] = R(value_of(w[NV * c + 2])) * s0;
           }
         }
       }
@@ -375,6 +387,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
       for (int c = 0; c < C; ++c) {
         cur[c][0] = sm.u[c][0][tid + H];
         cur[c][1] = sm.u[c][1][tid + H];
+        curl[c] = COMP ? S.ulo[c][tid + H] : R(0);
       }
     }
 
@@ -422,16 +435,42 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
     bar_sync(kBarCells, NT);
 
     // Step 2: interface values and their physical fluxes, cells base-1 .. base+Tq
-    if (tid < Tq + 2) s1d::faces_of_cell<R, C, NTH>(sm, tid, gas, gam, eps, a.variant);
+    // (COMP: their increments over the cell's hi)
+    if (tid < Tq + 2) {
+      if constexpr (COMP)
+        c1d::faces_of_cell_inc<C, NTH>(sm, S.ulo, S.fb, tid, gas, gam, eps, a.variant);
+      else
+        s1d::faces_of_cell<R, C, NTH>(sm, tid, gas, gam, eps, a.variant);
+    }
     bar_sync(kBarCells, NT);
 
-    // own cells: Eq. (odeH) up to its alpha-linear part, before alpha is known
+    // own cells: Eq. (odeH) up to its alpha-linear part, before alpha is known;
+    // COMP: also the alpha-independent part of the averages' combination
     int myflag = 0;
     R speed = R(0);
-    R L0u[C], Du[C], L0v[C], Dv[C];
+    R L0u[C], Du[C], L0v[C], Dv[C], bh[C], bl[C];
     if (own) {
       myflag = sm.fl[tid + 2];
-      s1d::rhs_parts_of_cell<R, C, NTH>(sm, tid, gas, inv_dx, L0u, Du, L0v, Dv);
+      if constexpr (COMP) {
+        c1d::rhs_parts_inc<C, NTH>(sm, S.ulo, S.fb, tid, gas, inv_dx, L0u, Du, L0v, Dv);
+        // 1/3 and 2/3 as float pairs
+        constexpr float t1h = 1.0f / 3.0f, t2h = 2.0f / 3.0f;
+        constexpr float t1l = (float)(1.0 / 3.0 - (double)t1h), t2l = (float)(2.0 / 3.0 - (double)t2h);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const R wh = cur[c][0], wl = curl[c];
+          if (stage == 1) {
+            bh[c] = wh;
+            bl[c] = wl;
+          } else if (stage == 2) {
+            c1d::pair_axpby(0.75f, 0.0f, u0c[c][0], u0l[c], 0.25f, 0.0f, wh, wl, bh[c], bl[c]);
+          } else {
+            c1d::pair_axpby(t1h, t1l, u0c[c][0], u0l[c], t2h, t2l, wh, wl, bh[c], bl[c]);
+          }
+        }
+      } else {
+        s1d::rhs_parts_of_cell<R, C, NTH>(sm, tid, gas, inv_dx, L0u, Du, L0v, Dv);
+      }
     }
     // alpha and dt from the scalar warp
     bar_sync(kBarAll, NT + 32);
@@ -454,6 +493,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         if (stage == 1) {
           u0c[c][0] = wu;
           u0c[c][1] = wv;
+          if constexpr (COMP) u0l[c] = curl[c];
           ou = su;
           ov = sv;
         } else {
@@ -461,6 +501,11 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
           const R cb = stage == 2 ? R(0.25) : R(2.0 / 3.0);
           ou = ca * u0c[c][0] + cb * su;
           ov = ca * u0c[c][1] + cb * sv;
+        }
+        if constexpr (COMP) {
+          // the averages: the pair formed before alpha plus the stage's increment
+          const R cb = stage == 1 ? R(1) : stage == 2 ? R(0.25) : R(2.0 / 3.0);
+          c1d::pair_add(bh[c], bl[c], (cb * dt) * Lu, ou, curl[c]);
         }
         cur[c][0] = ou;
         cur[c][1] = ov;
@@ -475,11 +520,12 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
       // publish the first and last three cells (the neighbours' halo)
       const int pslot = tid < 3 ? tid : (tid >= Tq - 3 ? 3 + tid - (Tq - 3) : -1);
       if (pslot >= 0) {
-        u64* dst = hal + ((size_t)q * 2 + (s & 1)) * HS + pslot * (C * 2);
+        u64* dst = hal + ((size_t)q * 2 + (s & 1)) * HS + pslot * (C * NV);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          st_relaxed(dst + 2 * c + 0, tagged((unsigned)(s + 1), float(cur[c][0])));
-          st_relaxed(dst + 2 * c + 1, tagged((unsigned)(s + 1), float(cur[c][1])));
+          st_relaxed(dst + NV * c + 0, tagged((unsigned)(s + 1), float(cur[c][0])));
+          st_relaxed(dst + NV * c + 1, tagged((unsigned)(s + 1), float(cur[c][1])));
+          if constexpr (COMP) st_relaxed(dst + NV * c + 2, tagged((unsigned)(s + 1), float(curl[c])));
         }
       }
     }
@@ -512,6 +558,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
     for (int c = 0; c < C; ++c) {
       out[(2 * c + 0) * n + i] = cur[c][0];
       out[(2 * c + 1) * n + i] = cur[c][1];
+      if constexpr (COMP) r.lo[c * n + i] = curl[c];
     }
   }
   if (bad) atomicOr(&a.sc->status, bad);
@@ -519,43 +566,90 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
   if (tid == 0 && S.trb) atomicAdd(&a.sc->troubled, (unsigned long long)S.trb);
 }
 
-template <typename R, int C, int NTH>
+template <typename R, int C, int NTH, bool COMP>
 cudaError_t resident_occupancy(int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, resident1d_kernel<R, C, NTH>,
-                                                       NTH + 32, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      per_sm, resident1d_kernel<R, C, NTH, COMP>, NTH + 32, 0);
 }
 
-template <typename R, int C, int NTH>
+template <typename R, int C, int NTH, bool COMP>
 cudaError_t resident_launch(const Resident1DArgs& r, int ncta, cudaStream_t s) {
   Resident1DArgs rc = r;
   void* args[] = {&rc};
-  return cudaLaunchCooperativeKernel((const void*)resident1d_kernel<R, C, NTH>, dim3(ncta),
+  return cudaLaunchCooperativeKernel((const void*)resident1d_kernel<R, C, NTH, COMP>, dim3(ncta),
                                      dim3(NTH + 32), args, 0, s);
 }
 
-template <typename R, int C>
+template <typename R, int C, bool COMP>
 cudaError_t resident_c(int nth, const Resident1DArgs* r, int ncta, cudaStream_t s, int* per) {
-  if (r) return nth == 512 ? resident_launch<R, C, 512>(*r, ncta, s)
-                           : resident_launch<R, C, 256>(*r, ncta, s);
-  return nth == 512 ? resident_occupancy<R, C, 512>(per) : resident_occupancy<R, C, 256>(per);
+  if (r) return nth == 512 ? resident_launch<R, C, 512, COMP>(*r, ncta, s)
+                           : resident_launch<R, C, 256, COMP>(*r, ncta, s);
+  return nth == 512 ? resident_occupancy<R, C, 512, COMP>(per)
+                    : resident_occupancy<R, C, 256, COMP>(per);
 }
 
-cudaError_t resident_dispatch(int system, int nth, const Resident1DArgs* r, int ncta,
+// comp: the float-pair averages (HWENO_FP32C)
+cudaError_t resident_dispatch(int system, int nth, bool comp, const Resident1DArgs* r, int ncta,
                               cudaStream_t s, int* per) {
-  return system == 0 ? resident_c<float, 1>(nth, r, ncta, s, per)
-                     : resident_c<float, 3>(nth, r, ncta, s, per);
+  if (comp)
+    return system == 0 ? resident_c<float, 1, true>(nth, r, ncta, s, per)
+                       : resident_c<float, 3, true>(nth, r, ncta, s, per);
+  return system == 0 ? resident_c<float, 1, false>(nth, r, ncta, s, per)
+                     : resident_c<float, 3, false>(nth, r, ncta, s, per);
+}
+
+// HWENO_FP32C state conversions: an FP64 state [C][2][n] into hi (the state
+// in FP32) and the low parts of its averages [C][n]; and back, hi + lo.
+__global__ void split_pairs_kernel(const double* __restrict__ src, float* __restrict__ hi,
+                                   float* __restrict__ lo, int C, int n) {
+  const size_t total = (size_t)C * 2 * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[k];
+    const float h = (float)x;
+    hi[k] = h;
+    const size_t c = k / (2 * (size_t)n), m = (k / n) % 2, i = k % n;
+    if (m == 0) lo[c * n + i] = (float)(x - (double)h);
+  }
+}
+__global__ void join_pairs_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
+                                  double* __restrict__ out, int C, int n) {
+  const size_t total = (size_t)C * 2 * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = k / (2 * (size_t)n), m = (k / n) % 2, i = k % n;
+    out[k] = (double)hi[k] + (m == 0 ? (double)lo[c * n + i] : 0.0);
+  }
 }
 
 }  // namespace
 
-cudaError_t resident1d_geometry(int system, int nth, int n, int* tile, int* ncta) {
+cudaError_t launch_split_pairs(const void* src, void* hi, float* lo, int C, int n, cudaStream_t s) {
+  const size_t total = (size_t)C * 2 * n;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  split_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const double*>(src),
+                                                      static_cast<float*>(hi), lo, C, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_join_pairs(const void* hi, const float* lo, double* out, int C, int n,
+                              cudaStream_t s) {
+  const size_t total = (size_t)C * 2 * n;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  join_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float*>(hi), lo, out, C, n);
+  return cudaGetLastError();
+}
+
+cudaError_t resident1d_geometry(int system, int nth, bool comp, int n, int* tile, int* ncta) {
   *tile = 0;
   *ncta = 0;
   if (nth != 256 && nth != 512) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = resident_dispatch(system, nth, nullptr, 0, nullptr, &per);
+  if (e == cudaSuccess) e = resident_dispatch(system, nth, comp, nullptr, 0, nullptr, &per);
   if (e != cudaSuccess) return e;
   if (per < 1 || n < 6) return cudaSuccess;  // not possible: *tile = 0
   // the fewest cells per CTA with all CTAs co-resident; every tile (the
@@ -578,13 +672,17 @@ cudaError_t resident1d_geometry(int system, int nth, int n, int* tile, int* ncta
 
 size_t resident1d_entry_words(int ncta) { return (size_t)2 * ncta * kEntStride + 2; }
 
+size_t resident1d_halo_words(int system, int ncta) {
+  return (size_t)ncta * 2 * 6 * (system == 0 ? 1 : 3) * 3;
+}
+
 cudaError_t launch_resident1d(const Resident1DArgs& r, int nth, int ncta, cudaStream_t s) {
-  const int C = r.a.system == 0 ? 1 : 3;
-  cudaError_t e = cudaMemsetAsync(r.halo, 0, sizeof(unsigned long long) * (size_t)ncta * 2 * 6 * C * 2, s);
+  cudaError_t e = cudaMemsetAsync(r.halo, 0,
+                                  sizeof(unsigned long long) * resident1d_halo_words(r.a.system, ncta), s);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(r.entries, 0, sizeof(unsigned long long) * resident1d_entry_words(ncta), s);
   if (e != cudaSuccess) return e;
-  return resident_dispatch(r.a.system, nth, &r, ncta, s, nullptr);
+  return resident_dispatch(r.a.system, nth, r.lo != nullptr, &r, ncta, s, nullptr);
 }
 
 }  // namespace hw

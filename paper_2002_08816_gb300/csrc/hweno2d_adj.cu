@@ -42,32 +42,16 @@ constexpr int AX = TX + 4, AY = TY + 4;  // raw input, 2-cell halo
 constexpr int BX = TX + 2, BY = TY + 2;  // 1-cell halo
 static_assert(TX * TY == NT, "one own cell per thread");
 
-// Own cells of a tile whose stencil holds a troubled cell, handled on
-// consecutive threads when there are at most this many (Euler).
-constexpr int kHwCap = 64;
-static_assert(kHwCap <= NT, "one listed cell per thread");
-
-// The listed cells' buffers reuse arrays that are idle while they live: their
-// interface values (then the adjoints of these) the tile-sum buffer g, which
-// is first written after them; their stencil adjoints the raw input u, which
-// the Euler kernel no longer reads once they are formed.
 template <typename R, int C>
 struct SmemA {
   static constexpr int kPadX = 0;  // raw index of flag-grid column lx: lx + 1
-  static constexpr int kH = C == 4 ? kHwCap : 1;
   R u[C][3][AY][AX];    // raw stage input
   R lam[C][3][BY][BX];  // b dt lam (the adjoint of L)
   R vl[C][BY][BX];      // Step 4 moments
   R wl[C][BY][BX];
   R g[19][TY][TX];      // one component's stencil adjoints of the own cells
-  int nhw;
-  unsigned short hwl[kH];
   uint8_t fl[BY][BX];
-  __device__ R (*hwv())[12][kH] { return reinterpret_cast<R (*)[12][kH]>(&g[0][0][0]); }
-  __device__ R (*hwg())[19][kH] { return reinterpret_cast<R (*)[19][kH]>(&u[0][0][0][0]); }
 };
-static_assert(sizeof(float) * 4 * 12 * kHwCap <= sizeof(float) * 19 * TY * TX, "hwv fits g");
-static_assert(sizeof(float) * 4 * 19 * kHwCap <= sizeof(float) * 4 * 3 * AY * AX, "hwg fits u");
 
 // Offsets of the 19 stencil data (Fig. 1): averages of cells 1..9, then the
 // x- and the y-moments of cells 2, 4, 5, 6, 8.
@@ -320,7 +304,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
   const R ax = static_cast<const R*>(a.alpha)[0], ay = static_cast<const R*>(a.alpha)[1];
   const R scale = a.stage == 0 ? R(1) : stage_b<R>(a.stage) * *static_cast<const R*>(a.dt);
 
-  if (tid == 0) sm.nhw = 0;
   for (int k = tid; k < AX * AY; k += NT) {
     const int rx = k % AX, ry = k / AX;
     const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 2 + rx, nx, 0);
@@ -340,9 +323,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
     sm.fl[ly][lx] = a.flags[s] != 0;
     ring_troubled |= sm.fl[ly][lx];
   }
-  // a troubled cell in the ring: kernel C's work, and (Euler) HWENO cells
-  const bool tile_troubled = __syncthreads_or(ring_troubled) != 0;
-  if (tile_troubled && tid == 0) {  // kernel C's work list
+  if (__syncthreads_or(ring_troubled) && tid == 0) {  // kernel C's work list
     const int q = atomicAdd(a.tile_list, 1);
     a.tile_list[1 + q] = blockIdx.y * gridDim.x + blockIdx.x;
   }
@@ -380,15 +361,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
 #pragma unroll
     for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 1 + dj][ci + 1 + di] != 0;
 
-  // Euler: own cells whose stencil holds a troubled cell are listed; when
-  // they fit the shared buffers (packed), their characteristic HWENO values
-  // and adjoints run on consecutive threads, so that a warp with a few such
-  // cells does not carry the others through it
-  int myq = -1;
-  if constexpr (C == 4) {
-    if (tile_troubled) myq = list_append(&sm.nhw, sm.hwl, tid, own && hw, kHwCap);
-  }
-
   // point values (the forward's)
   R P[C][NP];
 #pragma unroll
@@ -401,34 +373,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
       if (hw) hweno2d_faces<NG>(d, P_.gam, P_.eps, 0, NF, P[c]);
     }
   }
-  bool packed = false;
-  int nhw = 0;
   if constexpr (C == 4) {
-    if (tile_troubled) {  // uniform over the CTA
-      __syncthreads();
-      nhw = sm.nhw;
-    }
-    packed = nhw <= kHwCap;
-    if (packed && nhw > 0) {
-      R (*hwv)[12][SmemA<R, C>::kH] = sm.hwv();
-      for (int q = tid; q < nhw; q += NT) {
-        const int cell = sm.hwl[q];
-        R hv[4][NF];
-        hw_faces_euler_vals<NG>(sm, cell % TX, cell / TX, P_.gam[0], P_.gam[1], P_.gam[2],
-                                P_.gam[3], P_.gam[4], P_.eps, P_.gas, hv);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int p = 0; p < NF; ++p) hwv[c][p][q] = hv[c][p];
-      }
-      __syncthreads();
-      if (myq >= 0) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int p = 0; p < NF; ++p) P[c][p] = hwv[c][p][myq];
-      }
-    } else if (!packed && hw) {
+    if (hw) {
       R hv[4][NF];
       hw_faces_euler_vals<NG>(sm, ci, cj, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4],
                               P_.eps, P_.gas, hv);
@@ -516,40 +462,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
   // adjoints of the 19 data, summed per target cell over the tile's own cells
   R Gl[C == 4 ? 4 : 1][19];
   if constexpr (C == 4) {
-    if (packed && nhw > 0) {
-      R (*hwv)[12][SmemA<R, C>::kH] = sm.hwv();
-      if (myq >= 0) {  // the own entry only: no other thread reads it before the barrier
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int p = 0; p < NF; ++p) hwv[c][p][myq] = P[c][p];
-      }
-      __syncthreads();
-      // nhw <= kHwCap < NT: one listed cell per thread at most
-      R G[4][19];
-      if (tid < nhw) {
-        const int cell = sm.hwl[tid];
-        R lamF[4][NF];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-#pragma unroll
-          for (int p = 0; p < NF; ++p) lamF[c][p] = hwv[c][p][tid];
-#pragma unroll
-          for (int k = 0; k < 19; ++k) G[c][k] = R(0);
-        }
-        hw_faces_euler_vjp<NG>(sm, cell % TX, cell / TX, P_.gam[0], P_.gam[1], P_.gam[2],
-                               P_.gam[3], P_.gam[4], P_.eps, P_.gas, lamF, G);
-      }
-      __syncthreads();  // every read of u done: the stencil adjoints take its place
-      if (tid < nhw) {
-        R (*hwg)[19][SmemA<R, C>::kH] = sm.hwg();
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int k = 0; k < 19; ++k) hwg[c][k][tid] = G[c][k];
-      }
-      __syncthreads();
-    } else if (!packed && own && hw) {
+    if (own && hw) {
       R lamF[4][NF];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -575,9 +488,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
         R d[19];
         gather19a(sm, c, ci, cj, d);
         hweno2d_faces_vjp<NG>(d, P_.gam, P_.eps, P[c], g);
-      } else if (packed) {
-#pragma unroll
-        for (int k = 0; k < 19; ++k) g[k] = sm.hwg()[c][k][myq];
       } else {
 #pragma unroll
         for (int k = 0; k < 19; ++k) g[k] = Gl[c][k];

@@ -37,6 +37,10 @@ struct hweno_ctx {
   int res_tile = 0, res_ncta = 0, res_cap = 0;
   unsigned long long* res_halo = nullptr;     // tagged exchange words of the halos
   unsigned long long* res_entries = nullptr;  // and of the per-CTA maxima
+  // HWENO_FP32C: the low parts of the averages ([C][n] floats beside U[0]);
+  // every step runs as the resident launch
+  bool comp = false;
+  float* Ulo = nullptr;
   int ntile_alpha = 0;               // CTAs of the 1D wave-speed kernels (kTile1D cells each)
   unsigned* bar = nullptr;           // grid barrier of the persistent kernel
   std::vector<int> batch_nx;         // cells of each batch instance
@@ -248,10 +252,10 @@ cudaError_t enqueue_run1d(hweno_ctx* h, int nsteps, cudaStream_t s) {
 // and its buffers.
 cudaError_t prepare_resident(hweno_ctx* h) {
   h->res_tile = h->res_ncta = 0;
-  if (h->dim != 1 || h->n_batch > 0 || h->cfg.precision != HWENO_FP32) return cudaSuccess;
+  if (h->dim != 1 || h->n_batch > 0 || h->cfg.precision == HWENO_FP64) return cudaSuccess;
   if (h->nth1d != 256 && h->nth1d != 512) return cudaSuccess;
   int tile = 0, ncta = 0;
-  cudaError_t e = hw::resident1d_geometry(h->cfg.system, h->nth1d, h->n, &tile, &ncta);
+  cudaError_t e = hw::resident1d_geometry(h->cfg.system, h->nth1d, h->comp, h->n, &tile, &ncta);
   if (e != cudaSuccess || tile == 0) return e;
   if (ncta > h->res_cap) {
     if (h->res_halo) cudaFree(h->res_halo);
@@ -259,7 +263,7 @@ cudaError_t prepare_resident(hweno_ctx* h) {
     h->res_halo = nullptr;
     h->res_entries = nullptr;
     h->res_cap = 0;
-    e = cudaMalloc(&h->res_halo, (size_t)ncta * 2 * 6 * h->C * 2 * sizeof(unsigned long long));
+    e = cudaMalloc(&h->res_halo, hw::resident1d_halo_words(h->cfg.system, ncta) * sizeof(unsigned long long));
     if (e == cudaSuccess)
       e = cudaMalloc(&h->res_entries, sizeof(unsigned long long) * hw::resident1d_entry_words(ncta));
     if (e != cudaSuccess) return e;
@@ -289,6 +293,7 @@ cudaError_t enqueue_resident1d(hweno_ctx* h, int nsteps, cudaStream_t s, int sil
   r.alpha_word = h->res_entries + hw::resident1d_entry_words(h->res_ncta) - 2;
   r.polls = polls;
   r.silent_cta = silent_cta;
+  r.lo = h->comp ? h->Ulo : nullptr;
   return hw::launch_resident1d(r, h->nth1d, h->res_ncta, s);
 }
 
@@ -379,8 +384,10 @@ hweno_status validate(const hweno_config* c) {
   if (!(c->eps > 0.0)) return fail(nullptr, HWENO_ERR_ARG, "eps must be positive");
   if (!(c->kxrcf_threshold >= 0.0)) return fail(nullptr, HWENO_ERR_ARG, "threshold must be >= 0");
   if (c->troubled_mode < 0 || c->troubled_mode > 2) return fail(nullptr, HWENO_ERR_ARG, "unknown troubled_mode");
-  if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64)
+  if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64 && c->precision != HWENO_FP32C)
     return fail(nullptr, HWENO_ERR_ARG, "unknown precision");
+  if (c->precision == HWENO_FP32C && c->dim != 1)
+    return fail(nullptr, HWENO_ERR_ARG, "HWENO_FP32C is available for 1D");
   if (c->variant & ~(HWENO_VARIANT_RAW_COMBINE | HWENO_VARIANT_MEAN_EIGEN))
     return fail(nullptr, HWENO_ERR_ARG, "unknown variant bits");
   return HWENO_OK;
@@ -555,8 +562,10 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
   }
   h->elems = (size_t)h->C * h->M * h->n;
   h->esize = cfg->precision == HWENO_FP64 ? 8 : 4;
+  h->comp = cfg->precision == HWENO_FP32C;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->U[k], h->elems * h->esize);
+  if (e == cudaSuccess && h->comp) e = cudaMalloc(&h->Ulo, sizeof(float) * h->C * h->n);
   if (e == cudaSuccess) e = cudaMalloc(&h->U0, h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_buf, h->elems * 8);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * 2 * hw::kAlphaSlots);
@@ -574,6 +583,17 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
     std::string msg = std::string("allocation: ") + cudaGetErrorString(e);
     hweno_destroy(h);
     return fail(nullptr, HWENO_ERR_CUDA, msg);
+  }
+  if (h->comp) {  // the resident launch only
+    h->persist1d = 2;
+    e = prepare_resident(h);
+    if (e != cudaSuccess || h->res_tile == 0) {
+      std::string msg = e != cudaSuccess ? std::string("resident launch: ") + cudaGetErrorString(e)
+                                         : std::string("HWENO_FP32C runs as the resident launch, "
+                                                       "and this grid does not fit on the GPU at once");
+      hweno_destroy(h);
+      return fail(nullptr, e != cudaSuccess ? HWENO_ERR_CUDA : HWENO_ERR_ARG, msg);
+    }
   }
   *out = h;
   return HWENO_OK;
@@ -595,7 +615,16 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
       src = h->stage_buf;
     }
   }
-  if (src) HW_CUDA(h, hw::launch_convert(src, src64, h->U[0], dst64, h->elems, h->stream));
+  if (h->comp) {
+    // hi into the state, the low parts of the averages beside it
+    if (src64) HW_CUDA(h, hw::launch_split_pairs(src ? src : h->U[0], h->U[0], h->Ulo, h->C, h->n, h->stream));
+    else {
+      if (src) HW_CUDA(h, hw::launch_convert(src, 0, h->U[0], 0, h->elems, h->stream));
+      HW_CUDA(h, cudaMemsetAsync(h->Ulo, 0, sizeof(float) * h->C * h->n, h->stream));
+    }
+  } else if (src) {
+    HW_CUDA(h, hw::launch_convert(src, src64, h->U[0], dst64, h->elems, h->stream));
+  }
   HW_CUDA(h, hw::launch_set_scalars(h->sc, 1, -1.0, h->stream));
   const size_t nslot = h->n_batch > 2 * hw::kAlphaSlots ? (size_t)h->n_batch : 2 * hw::kAlphaSlots;
   for (int k = 0; k < 3; ++k)
@@ -704,6 +733,14 @@ hweno_status hweno_get_state(hweno_handle h, void* out, int dtype, int on_device
   if (dtype != HWENO_FP32 && dtype != HWENO_FP64) return fail(h, HWENO_ERR_ARG, "unknown dtype");
   const int dst64 = dtype == HWENO_FP64, src64 = h->cfg.precision == HWENO_FP64;
   const size_t dbytes = h->elems * (dst64 ? 8 : 4);
+  if (h->comp && dst64) {  // hi + lo of the averages
+    void* dst = on_device ? out : h->stage_buf;
+    HW_CUDA(h, hw::launch_join_pairs(h->U[0], h->Ulo, static_cast<double*>(dst), h->C, h->n, h->stream));
+    if (on_device) return HWENO_OK;
+    HW_CUDA(h, cudaMemcpyAsync(out, h->stage_buf, dbytes, cudaMemcpyDeviceToHost, h->stream));
+    HW_CUDA(h, cudaStreamSynchronize(h->stream));
+    return HWENO_OK;
+  }
   if (on_device) {
     HW_CUDA(h, hw::launch_convert(h->U[0], src64, out, dst64, h->elems, h->stream));
     return HWENO_OK;
@@ -753,6 +790,7 @@ void hweno_destroy(hweno_handle h) {
   if (h->bar) cudaFree(h->bar);
   if (h->res_halo) cudaFree(h->res_halo);
   if (h->res_entries) cudaFree(h->res_entries);
+  if (h->Ulo) cudaFree(h->Ulo);
   if (h->tot_buf) cudaFree(h->tot_buf);
   if (h->d_tile_inst) cudaFree(h->d_tile_inst);
   if (h->d_tile_base) cudaFree(h->d_tile_base);
@@ -767,6 +805,8 @@ hweno_status hweno_create_batch(const hweno_config* cfg, int n_batch, const int*
                                 void* cuda_stream, hweno_handle* out) {
   if (!out) return fail(nullptr, HWENO_ERR_ARG, "out is NULL");
   if (!cfg || cfg->dim != 1) return fail(nullptr, HWENO_ERR_ARG, "batches are of 1D instances");
+  if (cfg->precision == HWENO_FP32C)
+    return fail(nullptr, HWENO_ERR_ARG, "batches take HWENO_FP32 or HWENO_FP64");
   if (n_batch < 1 || !nx) return fail(nullptr, HWENO_ERR_ARG, "n_batch must be >= 1 with sizes");
   hweno_config c = *cfg;
   long long total = 0;
@@ -1032,10 +1072,15 @@ hweno_status hweno_totals(hweno_handle h, double* totals) {
     const long long stride = (long long)h->M * n;  // [c][m][cells]: component c's averages
     HW_CUDA(h, hw::launch_totals(byte_off(h->U[0], (size_t)off * h->esize), fp64, stride, C, n, part,
                                  kBlocks, out, h->stream));
-    double sums[8];
+    double sums[8], lows[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     HW_CUDA(h, cudaMemcpyAsync(sums, out, sizeof(double) * C, cudaMemcpyDeviceToHost, h->stream));
+    if (h->comp) {  // the averages' low parts, [c][cells]
+      HW_CUDA(h, cudaStreamSynchronize(h->stream));
+      HW_CUDA(h, hw::launch_totals(h->Ulo, 0, n, C, n, part, kBlocks, out, h->stream));
+      HW_CUDA(h, cudaMemcpyAsync(lows, out, sizeof(double) * C, cudaMemcpyDeviceToHost, h->stream));
+    }
     HW_CUDA(h, cudaStreamSynchronize(h->stream));
-    for (int c = 0; c < C; ++c) totals[(size_t)b * C + c] = sums[c] * cell;
+    for (int c = 0; c < C; ++c) totals[(size_t)b * C + c] = (sums[c] + lows[c]) * cell;
   }
   return HWENO_OK;
 }
@@ -1046,6 +1091,8 @@ hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent) {
   if (threads != 128 && threads != 256 && threads != 512)
     return fail(h, HWENO_ERR_ARG, "threads must be 128, 256 or 512");
   if (persistent < 0 || persistent > 2) return fail(h, HWENO_ERR_ARG, "persistent must be 0, 1 or 2");
+  if (h->comp && (persistent != 2 || threads == 128))
+    return fail(h, HWENO_ERR_ARG, "HWENO_FP32C runs as the resident launch (2) with 256 or 512 threads");
   HW_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->g_many) cudaGraphExecDestroy(h->g_many);
   if (h->g_one) cudaGraphExecDestroy(h->g_one);
@@ -1078,13 +1125,15 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
   const size_t nslot = h->n_batch > 2 * hw::kAlphaSlots ? (size_t)h->n_batch : 2 * hw::kAlphaSlots;
   const size_t pbytes = sizeof(double) * nslot;
   const size_t bbytes = sizeof(hw::BatchScalars) * (size_t)h->n_batch;
+  const size_t lbytes = h->comp ? sizeof(float) * h->C * h->n : 0;
   // everything a run changes, saved on the device and put back before each trial
   char* save = nullptr;
-  HW_CUDA(h, cudaMalloc(&save, sbytes + 3 * pbytes + sizeof(hw::DevScalars) + bbytes));
+  HW_CUDA(h, cudaMalloc(&save, sbytes + 3 * pbytes + sizeof(hw::DevScalars) + bbytes + lbytes));
   char* sv_u = save;
   char* sv_p = save + sbytes;
   char* sv_sc = sv_p + 3 * pbytes;
   char* sv_b = sv_sc + sizeof(hw::DevScalars);
+  char* sv_l = sv_b + bbytes;
   cudaStream_t s = h->stream;
   auto copy_all = [&](bool to_save) -> cudaError_t {
     cudaError_t e = cudaMemcpyAsync(to_save ? sv_u : h->U[0], to_save ? h->U[0] : sv_u, sbytes,
@@ -1099,6 +1148,9 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
     if (e == cudaSuccess && bbytes)
       e = cudaMemcpyAsync(to_save ? sv_b : (char*)h->d_bsc, to_save ? (char*)h->d_bsc : sv_b,
                           bbytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && lbytes)
+      e = cudaMemcpyAsync(to_save ? sv_l : (char*)h->Ulo, to_save ? (char*)h->Ulo : sv_l, lbytes,
+                          cudaMemcpyDeviceToDevice, s);
     return e;
   };
   auto configure = [&](int nth, int persist) -> cudaError_t {
@@ -1119,8 +1171,8 @@ hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  for (int persist = 0; persist < 3 && e == cudaSuccess; ++persist)
-    for (int ci = 0; ci < 3 && e == cudaSuccess; ++ci) {
+  for (int persist = h->comp ? 2 : 0; persist < 3 && e == cudaSuccess; ++persist)
+    for (int ci = h->comp ? 1 : 0; ci < 3 && e == cudaSuccess; ++ci) {
       e = configure(cand_nth[ci], persist);
       if (e != cudaSuccess) break;
       if (persist == 2 && h->res_tile == 0) continue;  // not available here

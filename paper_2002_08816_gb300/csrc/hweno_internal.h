@@ -199,12 +199,23 @@ struct Resident1DArgs {
   unsigned long long* alpha_word;
   unsigned polls;     // bound of every wait (2^21 polls: about a second)
   int silent_cta;     // self-test: this CTA never publishes its maximum (-1: none)
+  float* lo;          // HWENO_FP32C: low parts of the averages [C][n] (read at the
+                      // start, rewritten at the end); nullptr: FP32 averages
 };
 // Words of the entries buffer (entries and the two alpha words) for ncta CTAs.
 size_t resident1d_entry_words(int ncta);
+// Words of the halo buffer for ncta CTAs (room for the float-pair launch's three
+// words per cell and component).
+size_t resident1d_halo_words(int system, int ncta);
 // Cells per CTA and CTAs of the resident launch with nth + 32 threads for n
-// cells; *tile = 0 when the grid does not fit on the GPU at once.
-cudaError_t resident1d_geometry(int system, int nth, int n, int* tile, int* ncta);
+// cells (comp: the float-pair averages of HWENO_FP32C); *tile = 0 when the
+// grid does not fit on the GPU at once.
+cudaError_t resident1d_geometry(int system, int nth, bool comp, int n, int* tile, int* ncta);
+// HWENO_FP32C states: an FP64 state into hi (FP32, the state layout) and the
+// averages' low parts [C][n]; and hi + lo back into an FP64 state.
+cudaError_t launch_split_pairs(const void* src, void* hi, float* lo, int C, int n, cudaStream_t s);
+cudaError_t launch_join_pairs(const void* hi, const float* lo, double* out, int C, int n,
+                              cudaStream_t s);
 // Zeroes the exchange words, then launches.
 cudaError_t launch_resident1d(const Resident1DArgs& r, int nth, int ncta, cudaStream_t s);
 

@@ -21,7 +21,7 @@ HWENO_BC_PERIODIC, HWENO_BC_OUTFLOW, HWENO_BC_REFLECTIVE = 0, 1, 2
 HWENO_VARIANT_RAW_COMBINE = 1  # the RK combination uses the unmodified first moments
 HWENO_VARIANT_MEAN_EIGEN = 2  # characteristic fields of each interface's mean state
 HWENO_TROUBLED_HYBRID, HWENO_TROUBLED_ALL, HWENO_TROUBLED_NONE = 0, 1, 2
-HWENO_FP32, HWENO_FP64 = 0, 1
+HWENO_FP32, HWENO_FP64, HWENO_FP32C = 0, 1, 2
 
 _D, _I, _VP = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
 

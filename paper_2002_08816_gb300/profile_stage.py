@@ -1,7 +1,7 @@
 """Short run of the 1D stage kernels for profilers (ncu).
 
   python -m paper_2002_08816_gb300.profile_stage [--nx 65536] [--rk-steps 10]
-                                                  [--precision fp32|fp64] [--system euler|burgers]
+                                                  [--precision fp32|fp32c|fp64] [--system euler|burgers]
                                                   [--dim 1|2] [--n-gauss 2|3]
                                                   [--adjoint EVERY] [--threads 128|256|512]
                                                   [--persistent | --resident] [--batch N]
@@ -38,7 +38,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nx", type=int, default=65536)
     ap.add_argument("--rk-steps", type=int, default=10)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64"],
+                    help="fp32c: FP32 with float-pair averages (1D, the resident launch)")
     ap.add_argument("--system", default="euler", choices=["euler", "burgers"])
     ap.add_argument("--seed", type=int, default=20250)
     ap.add_argument("--dim", type=int, default=1, choices=[1, 2])
@@ -57,7 +58,8 @@ def main():
                          "two-state data (the batched workload's recipe, seed 77)")
     args = ap.parse_args()
     B.build()
-    prec = H.HWENO_FP32 if args.precision == "fp32" else H.HWENO_FP64
+    prec = {"fp32": H.HWENO_FP32, "fp32c": H.HWENO_FP32C, "fp64": H.HWENO_FP64}[args.precision]
+    sdt = H.HWENO_FP64 if prec == H.HWENO_FP64 else H.HWENO_FP32  # the state's element type
     if args.dim == 2:
         # 2D Euler, nx x nx periodic on [0, 10]^2, vortex plus density modes
         if args.quadrants:
@@ -79,7 +81,7 @@ def main():
     else:
         u = W.burgers_sine_1d(args.nx)
         cfg = H.make_config(1, H.HWENO_BURGERS, args.nx, x0=-1.0, x1=1.0, cfl=0.5, precision=prec)
-    dt = torch.float32 if prec == H.HWENO_FP32 else torch.float64
+    dt = torch.float64 if sdt == H.HWENO_FP64 else torch.float32
     dev = torch.from_numpy(u).to("cuda", dt).contiguous()
     if args.batch > 0:
         h = H.hweno_create_batch(cfg, sizes, torch.cuda.current_stream().cuda_stream)
@@ -87,17 +89,18 @@ def main():
         h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
         if (args.threads or args.persistent or args.resident) and args.dim == 1:
+            resident = args.resident or prec == H.HWENO_FP32C  # fp32c: always resident
             H.hweno_set_execution(h, args.threads or 256,
-                                  2 if args.resident else (1 if args.persistent else 0))
-        H.hweno_set_state(h, dev.data_ptr(), prec, True)
+                                  2 if resident else (1 if args.persistent else 0))
+        H.hweno_set_state(h, dev.data_ptr(), sdt, True)
         if args.adjoint > 0:
             t = H.hweno_record(h, args.rk_steps, args.adjoint)
             out = torch.empty_like(dev)
-            H.hweno_get_state(h, out.data_ptr(), prec, True)
+            H.hweno_get_state(h, out.data_ptr(), sdt, True)
             seed = torch.zeros_like(dev)
             seed[0, 0] = 2.0 * out[0, 0]
             grad = torch.empty_like(dev)
-            H.hweno_backward(h, seed.data_ptr(), grad.data_ptr(), prec, True)
+            H.hweno_backward(h, seed.data_ptr(), grad.data_ptr(), sdt, True)
             print("gradient norm %.6g" % float(grad.double().norm()))
         else:
             t = H.hweno_step(h, args.rk_steps)
