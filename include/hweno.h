@@ -159,14 +159,14 @@ hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* st
  * (every boundary condition, variant and precision hweno_create accepts for
  * 1D) and cuda_stream is the stream to run on (NULL: legacy default stream).
  * in, out, flags_out and ulim_out mean exactly what they mean for hweno_rhs
- * (caller-owned device buffers in cfg->precision; flags_out and ulim_out
+ * (caller-owned device buffers in cfg->precision, FP32 for HWENO_FP32C;
+ * flags_out and ulim_out
  * nullable; no overlap), and the result is the same L(in).
  * Scratch: a file-scope __device__ array inside the library, which every GPU
  * that loads the library holds until the process exits.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and caches it for the life of the process; make that first
- * call before any stream capture begins, and do not use the library across a
- * cudaDeviceReset (the cached address would be stale).  Every call shares the
+ * device current) and caches it for the life of the process; do not use the
+ * library across a cudaDeviceReset (the cached address would be stale).  Every call shares the
  * one array and each call resets the part that must start at zero, so calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.

@@ -711,39 +711,11 @@ __global__ void __launch_bounds__(NT) alpha2d_kernel(const R* __restrict__ w, R*
   }
 }
 
-// The tensor map of a stage input (3 C planes of ny x nx values of R, x
-// fastest) with the raw tile as its box; false when the state cannot be
-// copied by TMA (rows not a multiple of 16 bytes, a grid smaller than the
-// box, no encoder in the driver): the kernel then loads every tile itself.
-bool encode_tile_map(const void* w, int nx, int ny, int planes, int esize, CUtensorMap* map) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      fn = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }();
-  memset(map, 0, sizeof(*map));
-  if (!encode || ((size_t)nx * esize) % 16 != 0 || ((uintptr_t)w) % 16 != 0 || nx < RX ||
-      ny < RY)
-    return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
-  const cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * ny * esize};
-  const cuuint32_t box[3] = {(cuuint32_t)RX, (cuuint32_t)RY, (cuuint32_t)planes};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return encode(map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                3, const_cast<void*>(w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <typename R, int C, int NG>
 cudaError_t launch_stage2d_t(const Stage2DArgs& a0, cudaStream_t s) {
   Stage2DArgs a = a0;
   CUtensorMap map;
-  a.tma = encode_tile_map(a.w, a.nx, a.ny, 3 * C, (int)sizeof(R), &map) ? 1 : 0;
+  a.tma = encode_box_map(a.w, a.nx, a.ny, 3 * C, (int)sizeof(R), RX, RY, &map) ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
   cfg.blockDim = dim3(NT);
@@ -768,6 +740,31 @@ cudaError_t prepare_t() {
 }
 
 }  // namespace
+
+bool encode_box_map(const void* w, int nx, int ny, int planes, int esize, int box_x, int box_y,
+                    CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  memset(map, 0, sizeof(*map));
+  if (!encode || !w || ((size_t)nx * esize) % 16 != 0 || ((uintptr_t)w) % 16 != 0 || nx < box_x ||
+      ny < box_y || ((size_t)box_x * esize) % 16 != 0 || box_x > 256 || box_y > 256 || planes > 256)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * ny * esize};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)planes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                3, const_cast<void*>(w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 void finish_stage2d_args(Stage2DArgs& a) {
   a.inv_dx = 1.0 / a.dx;

@@ -40,17 +40,24 @@ constexpr int TX = kTile2DX, TY = kTile2DY;
 constexpr int NT = kThreads2D;
 constexpr int AX = TX + 4, AY = TY + 4;  // raw input, 2-cell halo
 constexpr int BX = TX + 2, BY = TY + 2;  // 1-cell halo
+// kernel A's tiles start 16-byte aligned in x (TMA): its raw input from x =
+// bx0 - 4 (two columns more than the 2-cell halo needs), its lambda from x =
+// bx0 - 4 (three more than the 1-cell halo), both TX + 8 wide
+constexpr int AXA = TX + 8, LXA = TX + 8;
+constexpr unsigned kTmaPollsA = 1u << 20;
 static_assert(TX * TY == NT, "one own cell per thread");
 
 template <typename R, int C>
 struct SmemA {
-  static constexpr int kPadX = 0;  // raw index of flag-grid column lx: lx + 1
-  R u[C][3][AY][AX];    // raw stage input
-  R lam[C][3][BY][BX];  // b dt lam (the adjoint of L)
+  static constexpr int kPadX = 2;  // raw index of flag-grid column lx: lx + 1 + 2
+  alignas(128) R u[C][3][AY][AXA];   // raw stage input (a TMA box)
+  alignas(128) R lam[C][3][BY][LXA]; // lam, the adjoint of the stage output (a TMA box;
+                                     // b dt is applied where it is used)
   R vl[C][BY][BX];      // Step 4 moments
   R wl[C][BY][BX];
   R g[19][TY][TX];      // one component's stencil adjoints of the own cells
   uint8_t fl[BY][BX];
+  unsigned long long bar;  // mbarrier of the tile copies
 };
 
 // Offsets of the 19 stencil data (Fig. 1): averages of cells 1..9, then the
@@ -119,7 +126,7 @@ __device__ __forceinline__ R stage_b(int stage) {
 template <typename S, typename R>
 __device__ __forceinline__ void gather19a(const S& sm, int c, int ci, int cj, R* d) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) d[k] = sm.u[c][0][cj + 2 + k / 3 - 1][ci + 2 + k % 3 - 1];
+  for (int k = 0; k < 9; ++k) d[k] = sm.u[c][0][cj + 2 + k / 3 - 1][ci + 2 + S::kPadX + k % 3 - 1];
   const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
@@ -290,8 +297,10 @@ __device__ __noinline__ void limit_euler2d_vjp(S& sm, int lx, int ly, R g0, R g1
 // ------------------------------------------------------------- kernel A
 
 template <typename R, int C, int NG>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_kernel(Adj2DArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
+    adj2d_points_kernel(Adj2DArgs a, const __grid_constant__ CUtensorMap u_map,
+                        const __grid_constant__ CUtensorMap lam_map) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   SmemA<R, C>& sm = *reinterpret_cast<SmemA<R, C>*>(smem_raw);
   constexpr int NF = 4 * NG, NI = NG * NG, NP = NF + NI;
   const int tid = threadIdx.x;
@@ -304,22 +313,38 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
   const R ax = static_cast<const R*>(a.alpha)[0], ay = static_cast<const R*>(a.alpha)[1];
   const R scale = a.stage == 0 ? R(1) : stage_b<R>(a.stage) * *static_cast<const R*>(a.dt);
 
-  for (int k = tid; k < AX * AY; k += NT) {
-    const int rx = k % AX, ry = k / AX;
-    const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 2 + rx, nx, 0);
+  // interior tiles: the raw input and lambda as two TMA boxes (all 3 C
+  // planes each) on one mbarrier; the outermost ring of tiles (periodic
+  // wrap) through the boundary map
+  const bool tma = a.tma && bx0 >= 4 && bx0 - 4 + AXA <= nx && by0 >= 2 && by0 - 2 + AY <= ny;
+  if (tma && tid == 0) {
+    mbar_init(&sm.bar, 1);
+    mbar_expect_tx(&sm.bar, (unsigned)(sizeof(sm.u) + sizeof(sm.lam)));
+    tma_load_3d(&sm.u[0][0][0][0], &u_map, &sm.bar, bx0 - 4, by0 - 2, 0);
+    tma_load_3d(&sm.lam[0][0][0][0], &lam_map, &sm.bar, bx0 - 4, by0 - 1, 0);
+  }
+  if (!tma) {
+    for (int k = tid; k < AXA * AY; k += NT) {
+      const int rx = k % AXA, ry = k / AXA;
+      const size_t s = (size_t)bc_map(by0 - 2 + ry, ny, 0) * nx + bc_map(bx0 - 4 + rx, nx, 0);
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+      for (int c = 0; c < C; ++c)
 #pragma unroll
-      for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+        for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+    }
+    for (int k = tid; k < LXA * BY; k += NT) {
+      const int lx = k % LXA, ly = k / LXA;
+      const size_t s = (size_t)bc_map(by0 - 1 + ly, ny, 0) * nx + bc_map(bx0 - 4 + lx, nx, 0);
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) sm.lam[c][m][ly][lx] = lam[(3 * c + m) * plane + s];
+    }
   }
   int ring_troubled = 0;
   for (int k = tid; k < BX * BY; k += NT) {
     const int lx = k % BX, ly = k / BX;
     const size_t s = (size_t)bc_map(by0 - 1 + ly, ny, 0) * nx + bc_map(bx0 - 1 + lx, nx, 0);
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) sm.lam[c][m][ly][lx] = scale * lam[(3 * c + m) * plane + s];
     sm.fl[ly][lx] = a.flags[s] != 0;
     ring_troubled |= sm.fl[ly][lx];
   }
@@ -327,11 +352,17 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
     const int q = atomicAdd(a.tile_list, 1);
     a.tile_list[1 + q] = blockIdx.y * gridDim.x + blockIdx.x;
   }
+  if (tma && !mbar_wait_bounded(&sm.bar, 0, kTmaPollsA)) {
+    // the copies did not land: flag it and give them a second bounded wait
+    // (they write this CTA's shared memory); no thread leaves the common path
+    if (a.sc) atomicOr(&a.sc->status, ST_TIMEOUT);
+    mbar_wait_bounded(&sm.bar, 0, kTmaPollsA);
+  }
 
   // Step 4 on the tile and its 1-cell halo (the forward values)
   for (int k = tid; k < BX * BY; k += NT) {
     const int lx = k % BX, ly = k / BX;
-    const int rx = lx + 1, ry = ly + 1;
+    const int rx = lx + 1 + SmemA<R, C>::kPadX, ry = ly + 1;
     if (!sm.fl[ly][lx]) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
@@ -392,10 +423,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
   const R gx[3] = {NG == 3 ? R(-r15) : R(-r3), NG == 3 ? R(0) : R(r3), R(r15)};
   const R hax = R(0.5) * ax, hay = R(0.5) * ay;
   const int lx = ci + 1, ly = cj + 1;
-#define LAM(c, m, di, dj) sm.lam[c][m][ly + (dj)][lx + (di)]
+  // sm.lam holds lambda itself (from x = bx0 - 4); b dt enters the weights
+#define LAM(c, m, di, dj) sm.lam[c][m][ly + (dj)][lx + 3 + (di)]
 #pragma unroll
   for (int k = 0; k < NG; ++k) {
-    const R wxk = gw[k] * P_.inv_dx, wyk = gw[k] * P_.inv_dy;
+    const R wxk = gw[k] * P_.inv_dx * scale, wyk = gw[k] * P_.inv_dy * scale;
     R lf[C], U[C], o[C];
     // x_{i-1/2}: own left point k is u^+
 #pragma unroll
@@ -449,8 +481,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) adj2d_points_ker
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         U[c] = P[c][p];
-        l1[c] = wk * P_.inv_dx * LAM(c, 1, 0, 0);
-        l2[c] = wk * P_.inv_dy * LAM(c, 2, 0, 0);
+        l1[c] = wk * P_.inv_dx * scale * LAM(c, 1, 0, 0);
+        l2[c] = wk * P_.inv_dy * scale * LAM(c, 2, 0, 0);
       }
       flux_jt2<R, C>(P_.gas, U, 0, l1, o1);
       flux_jt2<R, C>(P_.gas, U, 1, l2, o2);
@@ -698,7 +730,11 @@ cudaError_t launch_t(const Adj2DArgs& a, cudaStream_t s) {
   const dim3 grid((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
   cudaError_t e = cudaMemsetAsync(a.tile_list, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  adj2d_points_kernel<R, C, NG><<<grid, NT, sizeof(SmemA<R, C>), s>>>(a);
+  Adj2DArgs b = a;
+  CUtensorMap um, lm;
+  b.tma = encode_box_map(a.w, a.nx, a.ny, 3 * C, (int)sizeof(R), AXA, AY, &um) &&
+          encode_box_map(a.lam, a.nx, a.ny, 3 * C, (int)sizeof(R), LXA, BY, &lm);
+  adj2d_points_kernel<R, C, NG><<<grid, NT, sizeof(SmemA<R, C>), s>>>(b, um, lm);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adj2d_pass_kernel<R, C><<<grid, NT, 0, s>>>(a);

@@ -472,6 +472,7 @@ hw::Adj2DArgs base_adj_args(const hweno_ctx* h) {
   for (int k = 0; k < 5; ++k) a.gam[k] = c.lin_w[k];
   a.G = h->tape.G;
   a.tile_list = h->tape.tile_list;
+  a.sc = h->tape.sc;
   hw::finish_adj2d_args(a);
   return a;
 }
@@ -1038,9 +1039,10 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
   a.dt = h->tape.aux;
   a.lam = lam;
   a.lam_in = grad;
+  HW_CUDA(h, hw::launch_set_scalars(h->tape.sc, 1, -1.0, h->stream));
   HW_CUDA(h, hw::launch_adj2d(a, h->stream));
-  HW_CUDA(h, cudaStreamSynchronize(h->stream));
-  return HWENO_OK;
+  hw::DevScalars sc;
+  return check_scalars(h, h->tape.sc, &sc);
 }
 
 hweno_status hweno_totals(hweno_handle h, double* totals) {

@@ -2,6 +2,7 @@
 // units (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,6 +127,13 @@ constexpr int kTile2DX = 32, kTile2DY = 8;  // cells per CTA of the 2D kernels (
 constexpr int kThreads2D = 256;
 
 void finish_stage2d_args(Stage2DArgs& a);
+// The tensor map of a 2D state (planes planes of ny x nx values of esize
+// bytes, x fastest) with a box_x x box_y x planes box, for TMA copies of a tile
+// and its halo; false when the state cannot be copied that way (a row not a
+// multiple of 16 bytes, an unaligned base, a grid smaller than the box, no
+// encoder in the driver): the kernels then load every tile themselves.
+bool encode_box_map(const void* w, int nx, int ny, int planes, int esize, int box_x, int box_y,
+                    CUtensorMap* map);
 // Allows the 2D stage kernel of this configuration its dynamic shared memory.
 cudaError_t prepare_stage2d(int system, int fp64, int ng);
 cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s);
@@ -153,6 +161,8 @@ struct Adj2DArgs {
   void* acc;              // adjoint of W0
   void* lam_in;           // out: adjoint of the stage input
   int* tile_list;         // scratch, 1 + tiles ints: count, then the tiles kernel C visits
+  DevScalars* sc;         // status word (a tile copy that did not land: ST_TIMEOUT)
+  int tma;                // set by the launcher: kernel A's interior tiles copied by TMA
   int stage, nx, ny, system, fp64, ng;
   double dx, dy, eps, gas;
   double gam[5];

@@ -5,7 +5,7 @@
                                                   [--dim 1|2] [--n-gauss 2|3]
                                                   [--adjoint EVERY] [--threads 128|256|512]
                                                   [--persistent | --resident] [--batch N]
-                                                  [--quadrants]
+                                                  [--quadrants] [--lax-tiles]
 
 Sets the seeded two-state 1D Euler state (or the Burgers sine wave; with
 --dim 2 the nx x nx vortex-plus-modes 2D Euler state), runs the
@@ -17,7 +17,9 @@ adjoint kernels per stage).  With --batch N it runs N independent 1D Euler
 instances in shared launches (hweno_create_batch).  --persistent and
 --resident select the 1D launch kinds with one launch per run.  --quadrants
 (2D) replaces the vortex by four constant quadrants drawn from the seed (shocks
-along the quadrant lines: the troubled-cell paths).
+along the quadrant lines: the troubled-cell paths); --lax-tiles (1D Euler)
+replaces the two-state data by Lax's Riemann problem repeated every 800 cells
+(10-14 % of the cell-stages troubled).
 """
 
 import argparse
@@ -53,6 +55,8 @@ def main():
                     help="1D FP32: one resident launch (tiles kept on chip) per run")
     ap.add_argument("--quadrants", action="store_true",
                     help="2D Euler: four constant quadrants drawn from the seed instead of the vortex")
+    ap.add_argument("--lax-tiles", action="store_true",
+                    help="1D Euler: Lax's problem repeated every 800 cells, periodic")
     ap.add_argument("--batch", type=int, default=0,
                     help="1D Euler: this many instances, cells log-uniform in [256, 16384], "
                          "two-state data (the batched workload's recipe, seed 77)")
@@ -73,6 +77,10 @@ def main():
         u = np.concatenate([W.euler_two_state_1d(n, seed=77 + b).reshape(-1)
                             for b, n in enumerate(sizes)])
         cfg = H.make_config(1, H.HWENO_EULER, 4, x0=0.0, x1=1.0, bc=H.HWENO_BC_OUTFLOW, cfl=0.5,
+                            precision=prec)
+    elif args.system == "euler" and args.lax_tiles:
+        u = W.euler_lax_tiled_1d(args.nx)
+        cfg = H.make_config(1, H.HWENO_EULER, args.nx, x0=0.0, x1=1.0, bc=H.HWENO_BC_PERIODIC, cfl=0.5,
                             precision=prec)
     elif args.system == "euler":
         u = W.euler_two_state_1d(args.nx, args.seed)
