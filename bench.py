@@ -464,20 +464,32 @@ SEED_2D = 2026
 CFL_2D = 0.5
 
 
-def flops_per_cell_stage_2d(ng, ncomp=4):
-    """FP32 operations of one smooth 2D cell-stage, counted on the operations
-    the method needs (halo recomputation excluded): the linear p0 maps at the
-    4 ng interface and ng^2 interior points of every component, counted from
-    the nonzero coefficients of the oracle's own point-value maps (Step 5.2 /
-    5.3; one multiply-add = 2 flops), the Lax-Friedrichs flux of each of the
-    cell's own 2 ng interface points (Euler: two fluxes of 15 flops and 16 for
-    the combination; Burgers: two u^2/2 and 4), f and g at the interior points
-    (Euler 2 x 15 + 16; Burgers 2 + 4), the right-hand-side sums (6 per
-    quadrature point and component plus 10) and the Runge-Kutta combination
-    (4 per moment)."""
-    from oracle import oracle as O
-    W = O.linear_weights2d(ng)
-    nnz = int((np.abs(W) > 1e-14).sum())
+FLOP_COUNTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle", "flop_counts.json")
+
+
+def oracle_flops(path):
+    """Algorithmic flops of one cell-stage on a path ("2d_euler_ng2_smooth",
+    "1d_euler_troubled", ...): the oracle's operation count of that path (its
+    sources compiled with a counting scalar), as stored in the table that
+    oracle/count_flops.py writes (a data file: nothing of the oracle runs)."""
+    with open(FLOP_COUNTS) as f:
+        return json.load(f)["paths"][path]["cell_stage"]
+
+
+def kernel_flops_per_cell_stage_2d(ng, ncomp=4):
+    """The same count for the kernel's own formulation of a smooth 2D
+    cell-stage (halo recomputation excluded): the linear p0 maps at the 4 ng
+    interface and ng^2 interior points of every component (the nonzero
+    coefficients of the generated maps over the 19 data: 228 for 2 Gauss
+    points, 353 for 3; one multiply-add = 2 flops), the
+    Lax-Friedrichs flux of each of the cell's own 2 ng interface points (Euler:
+    two fluxes of 15 flops and 16 for the combination; Burgers: two u^2/2 and
+    4), f and g at the interior points (Euler 2 x 15 + 16; Burgers 2 + 4), the
+    right-hand-side sums (6 per quadrature point and component plus 10) and
+    the Runge-Kutta combination (4 per moment).  Lower than the oracle's count
+    (which also has the wave speeds, the KXRCF indicator and general
+    polynomial evaluations); reported beside it."""
+    nnz = 228 if ng == 2 else 353
     pt = 46 if ncomp == 4 else 8
     return (2 * ncomp * nnz + 2 * ng * pt + ng * ng * pt + ncomp * (6 * 3 * ng + 10)
             + 4 * 3 * ncomp)
@@ -567,7 +579,8 @@ def bench_euler2d(args, ngs=None, fp32_tflops=None):
             H.hweno_destroy(h)
         tot = sum(ms)
         stage_s = tot / (args.steps * 3 * RK_STEPS_2D)
-        fpc = flops_per_cell_stage_2d(ng, ncomp)
+        fpc = oracle_flops("2d_%s_ng%d_smooth" % ("burgers" if burgers else "euler", ng))
+        fpk = kernel_flops_per_cell_stage_2d(ng, ncomp)
         flops = fpc * NX2 * NX2
         byts = (8 * 3 * 4 * ncomp / 3) * NX2 * NX2  # 8S/3, S = 3 moments x ncomp x 4 B
         t_alu = flops / (fp32_tflops * 1e12)
@@ -576,8 +589,11 @@ def bench_euler2d(args, ngs=None, fp32_tflops=None):
         if t_alu >= t_hbm:
             roof = {"bound": "alu", "achieved": flops / stage_s / 1e12, "peak": fp32_tflops,
                     "unit": "TFLOP/s", "frac": t_alu / stage_s, "traffic": traffic,
-                    "note": "peak = measured FP32 FMA throughput (hweno_fma_peak); %d flops per "
-                            "smooth cell-stage" % fpc}
+                    "flops_per_cell_stage": fpc,
+                    "frac_kernel_count": fpk * NX2 * NX2 / (fp32_tflops * 1e12) / stage_s,
+                    "note": "peak = measured FP32 FMA throughput (hweno_fma_peak); %.0f flops per "
+                            "smooth cell-stage counted on the oracle (oracle/flop_counts.json); "
+                            "frac_kernel_count: the kernel's own %d" % (fpc, fpk)}
         else:
             roof = {"bound": "hbm", "achieved": byts / stage_s / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": t_hbm / stage_s, "traffic": traffic, "note": "peak %s" % peak_kind}
@@ -832,24 +848,6 @@ def bench_batch1d(args):
 RK_STEPS_TROUBLED = 200
 
 
-def flops_per_cell_stage_1d_euler():
-    """FP32 operations of one 1D Euler cell-stage as the method defines it,
-    smooth and troubled (halo recomputation excluded): the linear p0 values at
-    the 4 Gauss-Lobatto points (6 data each: 2 x 6 per point and component),
-    4 physical fluxes (12 each), 2 Lax-Friedrichs combinations (5 per
-    component), F_i and Eq. (odeH) (8 per component), the RK combination (6
-    per moment), the wave speed (8) and the KXRCF test (2 x 8).  A troubled
-    cell adds the limiter of Step 1 in characteristic fields (eigen-system 40,
-    5 projections and 1 back-projection of 3 x 3, 3 scalar limiters of ~70)
-    and the HWENO interface values of Step 2.1 (eigen-system 40, 6 projections
-    and 2 back-projections, 3 scalar reconstructions of ~120, 2 fluxes); its
-    two neighbours redo the interface values (~2 x 500)."""
-    smooth = 4 * 3 * 12 + 4 * 12 + 2 * 3 * 5 + 3 * 8 + 6 * 6 + 8 + 16
-    limiter = 40 + 6 * 18 + 3 * 70
-    faces = 40 + 8 * 18 + 3 * 120 + 24
-    return smooth, limiter + 3 * faces
-
-
 def bench_troubled1d(args):
     """The headline kernel on data with a paper-like share of troubled cells:
     the Lax problem's states repeated every 800 cells over 65536 cells
@@ -898,7 +896,7 @@ def bench_troubled1d(args):
     stage_s = tot / (args.steps * 3 * RK_STEPS_TROUBLED)
     hbm, peak_kind = peaks()
     achieved = BYTES_PER_CELL_STAGE["fp32"] * NX / stage_s / 1e9
-    smooth, extra = flops_per_cell_stage_1d_euler()
+    smooth, troubled = oracle_flops("1d_euler_smooth"), oracle_flops("1d_euler_troubled")
     launch = LAUNCH_KIND[choice[1]]
     return {
         "metric": METRIC, "value": cells * args.steps / tot, "unit": UNIT, "steps": args.steps,
@@ -915,10 +913,11 @@ def bench_troubled1d(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "kernel": "%s<float,3,%d threads>" % (KERNEL_OF_LAUNCH[launch], choice[0]),
-                     "flops_per_cell_stage": smooth + frac * extra,
-                     "note": "64 B per cell-stage; flops: %d smooth + the troubled share x %d "
-                             "(limiter and characteristic HWENO); peak %s"
-                             % (smooth, extra, peak_kind)},
+                     "flops_per_cell_stage": smooth + frac * (troubled - smooth),
+                     "note": "64 B per cell-stage; flops counted on the oracle "
+                             "(oracle/flop_counts.json): %.0f per smooth and %.0f per troubled "
+                             "cell-stage at the measured share; peak %s"
+                             % (smooth, troubled, peak_kind)},
         "gpu_launches": args.steps * ((3 * RK_STEPS_TROUBLED if launch == "per-stage graphs" else 1) + 4),
         "clocks": sampler.summary(),
     }

@@ -16,6 +16,8 @@ _LIB_PATH = os.path.join(_HERE, "libhweno_oracle.so")
 # the same sources built with OpenMP: the per-cell loops run on all cores,
 # the arithmetic of every cell unchanged
 _LIB_OMP_PATH = os.path.join(_HERE, "libhweno_oracle_omp.so")
+# the same sources compiled as C++ with a counting scalar (opcount.cpp)
+_LIB_OPC_PATH = os.path.join(_HERE, "libhweno_oracle_opcount.so")
 
 BURGERS, EULER = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECTIVE = 0, 1, 2
@@ -98,19 +100,62 @@ def _build_one(path, extra, force):
     return path
 
 
+def _build_opcount(force):
+    srcs = [os.path.join(_HERE, f) for f in ("opcount.cpp", "opcount_1d.cpp", "opcount_2d.cpp")]
+    deps = srcs + sorted(glob.glob(os.path.join(_HERE, "*.c"))) + glob.glob(os.path.join(_HERE, "*.h"))
+    if not force and os.path.exists(_LIB_OPC_PATH):
+        if os.path.getmtime(_LIB_OPC_PATH) >= max(os.path.getmtime(p) for p in deps):
+            return
+    tmp = _LIB_OPC_PATH + ".tmp%d" % os.getpid()
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + _HERE,
+                    "-o", tmp] + srcs, check=True)
+    os.replace(tmp, _LIB_OPC_PATH)
+
+
 def build(force=False):
     """Compile the C oracle with gcc (no FMA contraction, so x86 and Arm agree),
-    plain and with OpenMP (the second build is skipped where gcc has none)."""
+    plain and with OpenMP (the second build is skipped where gcc has none), and
+    the op-counting build of the same sources with g++."""
     _build_one(_LIB_PATH, [], force)
     try:
         _build_one(_LIB_OMP_PATH, ["-fopenmp"], force)
     except (subprocess.CalledProcessError, OSError):
         pass
+    _build_opcount(force)
     return _LIB_PATH
 
 
 _lib = None
 _lib_omp = None
+_lib_opc = None
+
+
+def lib_opcount():
+    """The op-counting build: the oracle's functions, plus hwo_opcount_read /
+    hwo_opcount_reset (counts of add/sub, mul, div, sqrt, pow)."""
+    global _lib_opc
+    if _lib_opc is None:
+        build()
+        L = _setup(ctypes.CDLL(_LIB_OPC_PATH))
+        L.hwo_opcount_read.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+        L.hwo_opcount_read.restype = None
+        L.hwo_opcount_reset.argtypes = []
+        L.hwo_opcount_reset.restype = None
+        _lib_opc = L
+    return _lib_opc
+
+
+def count_ops(call):
+    """The floating-point operations [add/sub, mul, div, sqrt, pow] the
+    op-counting build performs in call(L) (L: that library), after one
+    untimed warm-up call that builds the oracle's coefficient tables."""
+    L = lib_opcount()
+    call(L)
+    L.hwo_opcount_reset()
+    call(L)
+    out = (ctypes.c_ulonglong * 5)()
+    L.hwo_opcount_read(out)
+    return [int(v) for v in out]
 
 
 def lib_omp():
