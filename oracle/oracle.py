@@ -121,7 +121,10 @@ def build(force=False):
         _build_one(_LIB_OMP_PATH, ["-fopenmp"], force)
     except (subprocess.CalledProcessError, OSError):
         pass
-    _build_opcount(force)
+    try:
+        _build_opcount(force)
+    except (subprocess.CalledProcessError, OSError):
+        pass  # measurement only: lib_opcount() then fails, the oracle itself does not
     return _LIB_PATH
 
 
@@ -136,6 +139,8 @@ def lib_opcount():
     global _lib_opc
     if _lib_opc is None:
         build()
+        if not os.path.exists(_LIB_OPC_PATH):
+            raise OSError("the op-counting build of the oracle (g++) is not available")
         L = _setup(ctypes.CDLL(_LIB_OPC_PATH))
         L.hwo_opcount_read.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
         L.hwo_opcount_read.restype = None
