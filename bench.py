@@ -633,6 +633,19 @@ def bench_euler2d(args, ngs=None, fp32_tflops=None):
                 "roofline": {"bound": roof["bound"], "frac": roof["frac"] * (tot / args.steps) / q_s,
                              "note": "the smooth roofline's fraction at this run's time"},
                 "data": "four constant quadrants (rho, u, v, p) drawn from the seed"}
+        if not burgers:
+            # the same vortex run with the float-pair averages (HWENO_FP32C)
+            cfg.precision = H.HWENO_FP32C
+            msc, _, hc = _time_2d(H, stream, cfg, dev, max(1, args.steps - 1), 1, RK_STEPS_2D)
+            H.hweno_destroy(hc)
+            cfg.precision = H.HWENO_FP32
+            c_s = sum(msc) / len(msc)
+            rec["fp32c"] = {"value": cells / c_s, "ms_per_step": 1e3 * c_s,
+                            "stage_ms": 1e3 * c_s / (3 * RK_STEPS_2D),
+                            "roofline": {"bound": roof["bound"],
+                                         "frac": roof["frac"] * (tot / args.steps) / c_s,
+                                         "note": "the FP32 roofline's fraction at this run's time "
+                                                 "(the same algorithmic flops)"}}
         out["ng%d" % ng] = rec
     return out
 

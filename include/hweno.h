@@ -50,17 +50,19 @@ typedef enum {
 enum { HWENO_BURGERS = 0, HWENO_EULER = 1 };
 enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECTIVE = 2 };
 enum { HWENO_TROUBLED_HYBRID = 0, HWENO_TROUBLED_ALL = 1, HWENO_TROUBLED_NONE = 2 };
-/* Precision of the bulk arithmetic.  HWENO_FP32C (1D single-instance
- * handles): FP32 arithmetic with the cell averages carried as float pairs
+/* Precision of the bulk arithmetic.  HWENO_FP32C (single-instance handles,
+ * 1D and 2D): FP32 arithmetic with the cell averages carried as float pairs
  * (hi + lo) between stages and the operator formed on increments over each
  * cell's hi, so that no FP32 rounding of an average reaches the first moments'
- * right-hand side (whose response to the averages has a factor 1/dx); every
- * step runs as the resident launch, and a grid that does not fit on the GPU
- * at once is refused.  Its state buffers are FP32 (hi); get_state with
+ * right-hand side (whose response to the averages has a factor 1/dx).  1D
+ * steps run as the resident launch (a grid that does not fit on the GPU at
+ * once is refused); 2D steps run the stage kernels with the low parts beside
+ * each stage buffer.  Its state buffers are FP32 (hi); get_state with
  * HWENO_FP64 returns hi + lo, set_state from HWENO_FP64 keeps the low parts.
  * hweno_rhs and hweno_rhs1d_noalloc evaluate the FP32 operator on the caller's
- * FP32 buffers.  As a dtype (set_state, get_state, backward) only HWENO_FP32
- * and HWENO_FP64 exist. */
+ * FP32 buffers; batches and the adjoint take HWENO_FP32 or HWENO_FP64.  As a
+ * dtype (set_state, get_state, backward) only HWENO_FP32 and HWENO_FP64
+ * exist. */
 enum { HWENO_FP32 = 0, HWENO_FP64 = 1, HWENO_FP32C = 2 };
 
 typedef struct {

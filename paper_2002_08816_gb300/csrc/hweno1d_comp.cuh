@@ -62,25 +62,35 @@ __device__ __forceinline__ void flux_inc(float gas, const float* B, const float*
   }
 }
 
-// a (ah + al) + b (bh + bl) for float pairs, as a normalised pair (s + e, |e|
-// <= ulp(s) / 2): error-free products (fma) and sums, the small terms rounded
-// once; relative error ~2^-45.
-__device__ __forceinline__ void pair_axpby(float ah, float al, float xh, float xl, float bh,
-                                           float bl, float yh, float yl, float& s, float& e) {
-  const float p = __fmul_rn(ah, xh), pe = fmaf(ah, xh, -p);
-  const float q = __fmul_rn(bh, yh), qe = fmaf(bh, yh, -q);
-  float t, te;
-  two_sum(p, q, t, te);
-  const float small = __fadd_rn(
-      __fadd_rn(__fadd_rn(te, pe), qe),
-      __fadd_rn(__fadd_rn(__fmul_rn(ah, xl), __fmul_rn(al, xh)),
-                __fadd_rn(__fmul_rn(bh, yl), __fmul_rn(bl, yh))));
-  two_sum(t, small, s, e);
-}
-
-// (h + l) + x as a normalised pair (x small next to h)
-__device__ __forceinline__ void pair_add(float h, float l, float x, float& s, float& e) {
-  two_sum(h, __fadd_rn(l, x), s, e);
+// KXRCF on float-pair averages (um + lm, u0 + l0, up + lp; FP32 first
+// moments): the plain kernel's FP32 fast test on hi, whose margins (6e-7 S on
+// the jump, 4.8e-7 on the threshold) exceed what the low parts can change
+// (below 2^-24 of |u0| + |u_nb|), and, where it cannot decide, the FP64
+// product form on hi + lo: the oracle's decision on the same state except
+// within a few ulp of the threshold (deciding on hi alone would flip the rare
+// cell that hi's rounding moves across it).
+__device__ __forceinline__ bool kxrcf_troubled_pair(float um, float lm, float u0, float l0,
+                                                    float up, float lp, float vm, float v0,
+                                                    float vp, bool left, double h, double thr,
+                                                    float hthr) {
+  float a, b, s;
+  if (left) {
+    a = u0 - 6.0f * v0;
+    b = um + 6.0f * vm;
+    s = fabsf(u0) + 6.0f * fabsf(v0) + fabsf(um) + 6.0f * fabsf(vm);
+  } else {
+    a = u0 + 6.0f * v0;
+    b = up - 6.0f * vp;
+    s = fabsf(u0) + 6.0f * fabsf(v0) + fabsf(up) + 6.0f * fabsf(vp);
+  }
+  const float j = fabsf(a - b);
+  const float e = 6.0e-7f * s;
+  const float r = hthr * fmaxf(fabsf(u0), 1e-12f);
+  if (j - e > r * (1.0f + 4.8e-7f)) return true;
+  if (j + e < r * (1.0f - 4.8e-7f)) return false;
+  return kxrcf_troubled((double)um + (double)lm, (double)u0 + (double)l0,
+                        (double)up + (double)lp, (double)vm, (double)v0, (double)vp, left, h,
+                        thr, 0.0f, 0.0f);
 }
 
 // Step 2.1 of an Euler cell on increments: the HWENO values at x_{i-1/2} and

@@ -157,6 +157,27 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// a (ah + al) + b (bh + bl) for float pairs, as a normalised pair (s + e, |e|
+// <= ulp(s) / 2): error-free products (fma) and sums, the small terms rounded
+// once; relative error ~2^-45.
+__device__ __forceinline__ void pair_axpby(float ah, float al, float xh, float xl, float bh,
+                                           float bl, float yh, float yl, float& s, float& e) {
+  const float p = __fmul_rn(ah, xh), pe = fmaf(ah, xh, -p);
+  const float q = __fmul_rn(bh, yh), qe = fmaf(bh, yh, -q);
+  float t, te;
+  two_sum(p, q, t, te);
+  const float small = __fadd_rn(
+      __fadd_rn(__fadd_rn(te, pe), qe),
+      __fadd_rn(__fadd_rn(__fmul_rn(ah, xl), __fmul_rn(al, xh)),
+                __fadd_rn(__fmul_rn(bh, yl), __fmul_rn(bl, yh))));
+  two_sum(t, small, s, e);
+}
+
+// (h + l) + x as a normalised pair (x small next to h)
+__device__ __forceinline__ void pair_add(float h, float l, float x, float& s, float& e) {
+  two_sum(h, __fadd_rn(l, x), s, e);
+}
+
 // The KXRCF jump (u0 -+ 6 v0) - (u_nb +- 6 v_nb) of FP32 data as an unevaluated
 // float pair jh + jl, with jh carrying its sign and |jl| <= ulp(jh) / 2, within
 // ~2^-46 S of the exact value (S = |u0| + 6|v0| + |u_nb| + 6|v_nb|): the four

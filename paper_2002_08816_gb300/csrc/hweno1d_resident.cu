@@ -401,6 +401,19 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         flag = 1;
       } else if (a.mode == 2) {
         flag = 0;
+      } else if constexpr (COMP) {
+        // the decision on hi + lo (the FP64 form where FP32 on hi cannot decide)
+        const bool left = C == 1 ? sm.u[0][0][e] >= R(0) : inflow_left(sm.u[0][0][e], sm.u[1][0][e]);
+        flag = c1d::kxrcf_troubled_pair(sm.u[0][0][e - 1], S.ulo[0][e - 1], sm.u[0][0][e],
+                                        S.ulo[0][e], sm.u[0][0][e + 1], S.ulo[0][e + 1],
+                                        sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left,
+                                        h, a.thr, hthr);
+        if constexpr (C == 3)
+          flag = flag || c1d::kxrcf_troubled_pair(sm.u[2][0][e - 1], S.ulo[2][e - 1],
+                                                  sm.u[2][0][e], S.ulo[2][e], sm.u[2][0][e + 1],
+                                                  S.ulo[2][e + 1], sm.u[2][1][e - 1],
+                                                  sm.u[2][1][e], sm.u[2][1][e + 1], left, h,
+                                                  a.thr, hthr);
       } else if constexpr (C == 1) {
         const R uc = sm.u[0][0][e];
         flag = kxrcf_troubled(sm.u[0][0][e - 1], uc, sm.u[0][0][e + 1], sm.u[0][1][e - 1],
@@ -463,9 +476,9 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
             bh[c] = wh;
             bl[c] = wl;
           } else if (stage == 2) {
-            c1d::pair_axpby(0.75f, 0.0f, u0c[c][0], u0l[c], 0.25f, 0.0f, wh, wl, bh[c], bl[c]);
+            pair_axpby(0.75f, 0.0f, u0c[c][0], u0l[c], 0.25f, 0.0f, wh, wl, bh[c], bl[c]);
           } else {
-            c1d::pair_axpby(t1h, t1l, u0c[c][0], u0l[c], t2h, t2l, wh, wl, bh[c], bl[c]);
+            pair_axpby(t1h, t1l, u0c[c][0], u0l[c], t2h, t2l, wh, wl, bh[c], bl[c]);
           }
         }
       } else {
@@ -505,7 +518,7 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         if constexpr (COMP) {
           // the averages: the pair formed before alpha plus the stage's increment
           const R cb = stage == 1 ? R(1) : stage == 2 ? R(0.25) : R(2.0 / 3.0);
-          c1d::pair_add(bh[c], bl[c], (cb * dt) * Lu, ou, curl[c]);
+          pair_add(bh[c], bl[c], (cb * dt) * Lu, ou, curl[c]);
         }
         cur[c][0] = ou;
         cur[c][1] = ov;
@@ -598,47 +611,50 @@ cudaError_t resident_dispatch(int system, int nth, bool comp, const Resident1DAr
                      : resident_c<float, 3, false>(nth, r, ncta, s, per);
 }
 
-// HWENO_FP32C state conversions: an FP64 state [C][2][n] into hi (the state
-// in FP32) and the low parts of its averages [C][n]; and back, hi + lo.
+// HWENO_FP32C state conversions: an FP64 state [C][M][n] (M moments, n cells)
+// into hi (the state in FP32) and the low parts of its averages [C][n]; and
+// back, hi + lo.
 __global__ void split_pairs_kernel(const double* __restrict__ src, float* __restrict__ hi,
-                                   float* __restrict__ lo, int C, int n) {
-  const size_t total = (size_t)C * 2 * n;
+                                   float* __restrict__ lo, int C, int M, int n) {
+  const size_t total = (size_t)C * M * n;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
     const double x = src[k];
     const float h = (float)x;
     hi[k] = h;
-    const size_t c = k / (2 * (size_t)n), m = (k / n) % 2, i = k % n;
+    const size_t c = k / ((size_t)M * n), m = (k / n) % M, i = k % n;
     if (m == 0) lo[c * n + i] = (float)(x - (double)h);
   }
 }
 __global__ void join_pairs_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
-                                  double* __restrict__ out, int C, int n) {
-  const size_t total = (size_t)C * 2 * n;
+                                  double* __restrict__ out, int C, int M, int n) {
+  const size_t total = (size_t)C * M * n;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
-    const size_t c = k / (2 * (size_t)n), m = (k / n) % 2, i = k % n;
+    const size_t c = k / ((size_t)M * n), m = (k / n) % M, i = k % n;
     out[k] = (double)hi[k] + (m == 0 ? (double)lo[c * n + i] : 0.0);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_split_pairs(const void* src, void* hi, float* lo, int C, int n, cudaStream_t s) {
-  const size_t total = (size_t)C * 2 * n;
+cudaError_t launch_split_pairs(const void* src, void* hi, float* lo, int C, int M, int n,
+                               cudaStream_t s) {
+  const size_t total = (size_t)C * M * n;
   size_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   split_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const double*>(src),
-                                                      static_cast<float*>(hi), lo, C, n);
+                                                      static_cast<float*>(hi), lo, C, M, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_join_pairs(const void* hi, const float* lo, double* out, int C, int n,
+cudaError_t launch_join_pairs(const void* hi, const float* lo, double* out, int C, int M, int n,
                               cudaStream_t s) {
-  const size_t total = (size_t)C * 2 * n;
+  const size_t total = (size_t)C * M * n;
   size_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  join_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float*>(hi), lo, out, C, n);
+  join_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float*>(hi), lo, out, C,
+                                                     M, n);
   return cudaGetLastError();
 }
 

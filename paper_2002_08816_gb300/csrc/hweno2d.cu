@@ -48,10 +48,12 @@ constexpr int LX = TX + 4, LY = TY + 4;  // flags and modified moments, 2-cell h
 constexpr unsigned kTmaPolls = 1u << 20;  // mbarrier polls before a tile copy is given up
 static_assert(TX * TY == NT, "one own cell per thread");
 
-template <typename R, int C, int NG>
+template <typename R, int C, int NG, bool COMP = false>
 struct Smem2D {
   static constexpr int kPadX = 1;  // raw index of flag-grid column lx: lx + 2
   alignas(128) R u[C][3][RY][RX];  // stage input (the TMA box)
+  // HWENO_FP32C: the low parts of the stage input's averages (a second box)
+  alignas(128) R ulo[COMP ? C : 1][COMP ? RY : 1][COMP ? RX : 1];
   R vl[C][LY][LX];              // modified x-moments
   R wl[C][LY][LX];              // modified y-moments
   R xf[C][2 * NG][TY][TX + 2];  // x-face values (left NG, right NG) of cells -1..TX
@@ -133,6 +135,28 @@ __device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0,
   return fabs(num) > __dmul_rn(k.thr, __dmul_rn(k.den_h, nrm));
 }
 
+// Float-pair averages (HWENO_FP32C: u0 + l0, uxn + lxn, uyn + lyn): the FP32
+// fast test on hi (its margins exceed what the low parts can change, below
+// 2^-24 of the averages), and, where it cannot decide, the FP64 form on hi +
+// lo, so that the decision is the oracle's on the same state except within a
+// few ulp of the threshold.
+__device__ __forceinline__ bool kxrcf2_troubled_pair(float u0, float l0, float v0, float w0,
+                                                     float uxn, float lxn, float vxn, float uyn,
+                                                     float lyn, float wyn, bool lowx, bool lowy,
+                                                     const Kx2& k) {
+  const float jx = lowx ? (u0 - 6.0f * v0) - (uxn + 6.0f * vxn) : (u0 + 6.0f * v0) - (uxn - 6.0f * vxn);
+  const float jy = lowy ? (u0 - 6.0f * w0) - (uyn + 6.0f * wyn) : (u0 + 6.0f * w0) - (uyn - 6.0f * wyn);
+  const float sx = fabsf(u0) + 6.0f * fabsf(v0) + fabsf(uxn) + 6.0f * fabsf(vxn);
+  const float sy = fabsf(u0) + 6.0f * fabsf(w0) + fabsf(uyn) + 6.0f * fabsf(wyn);
+  const float num = fabsf(k.fdy * jx + k.fdx * jy);
+  const float e = 1.0e-6f * (k.fdy * sx + k.fdx * sy);
+  const float r = k.fthr_den * fmaxf(fabsf(u0), 1e-12f);
+  if (num - e > r * (1.0f + 4.8e-7f)) return true;
+  if (num + e < r * (1.0f - 4.8e-7f)) return false;
+  return kxrcf2_troubled((double)u0 + (double)l0, (double)v0, (double)w0, (double)uxn + (double)lxn,
+                         (double)vxn, (double)uyn + (double)lyn, (double)wyn, lowx, lowy, k);
+}
+
 // The 19 data of component c of the cell at own-tile coordinates (ci, cj):
 // ubar of cells 1..9, vbar and wbar (modified) of cells 2, 4, 5, 6, 8.
 template <typename S, typename R>
@@ -144,6 +168,22 @@ __device__ __forceinline__ void gather19(const S& sm, int c, int ci, int cj, R* 
   for (int k = 0; k < 5; ++k) {
     d[9 + k] = sm.vl[c][cj + 2 + my[k]][ci + 2 + mx[k]];
     d[14 + k] = sm.wl[c][cj + 2 + my[k]][ci + 2 + mx[k]];
+  }
+}
+
+// The 19 data as gather19 gives them, or (COMP: the float-pair averages of
+// HWENO_FP32C) with the 9 averages as increments over the cell's own hi, low
+// parts included: the p0 and HWENO maps are consistent (their average
+// coefficients sum to one, their smoothness indicators are differences), so
+// they map these increments to the point values' increments over hi.
+template <bool COMP, typename S, typename R>
+__device__ __forceinline__ void gather_data(const S& sm, int c, int ci, int cj, R* d) {
+  gather19(sm, c, ci, cj, d);
+  if constexpr (COMP) {
+    const R b = d[4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      d[k] = __fadd_rn(__fsub_rn(d[k], b), sm.ulo[c][cj + OYR + k / 3 - 1][ci + OXR + k % 3 - 1]);
   }
 }
 
@@ -161,7 +201,7 @@ __device__ __forceinline__ void store_point(S& sm, int c, int p, int ci, int cj,
 // Step 5.1 for an Euler cell whose 3x3 stencil holds a troubled cell: the
 // interface points [p_lo, p_hi) by HWENO in the x (x-faces) and y (y-faces)
 // characteristic fields of the cell average (Remark 4).  Rare: out of line.
-template <int NG, typename S, typename R>
+template <int NG, bool COMP, typename S, typename R>
 __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo, int p_hi, R g0,
                                                  R g1, R g2, R g3, R g4, R eps, R gas,
                                                  bool mean_eigen) {
@@ -203,7 +243,7 @@ __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo
       for (int k = 0; k < 19; ++k) e[k] = R(0);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        gather19(sm, c, ci, cj, t);
+        gather_data<COMP>(sm, c, ci, cj, t);
 #pragma unroll
         for (int k = 0; k < 19; ++k) e[k] += Lm[f][c] * t[k];
       }
@@ -223,11 +263,14 @@ __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo
   }
 }
 
-template <typename R, int C, int NG>
+template <typename R, int C, int NG, bool COMP>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
-    stage2d_kernel(Stage2DArgs a, const __grid_constant__ CUtensorMap tile_map) {
+    stage2d_kernel(Stage2DArgs a, const __grid_constant__ CUtensorMap tile_map,
+                   const __grid_constant__ CUtensorMap lo_map) {
+  static_assert(!COMP || sizeof(R) == 4, "the float-pair averages are FP32");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem2D<R, C, NG>& sm = *reinterpret_cast<Smem2D<R, C, NG>*>(smem_raw);
+  using SM = Smem2D<R, C, NG, COMP>;
+  SM& sm = *reinterpret_cast<SM*>(smem_raw);
   constexpr int NF = 4 * NG, NI = NG * NG;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nx = a.nx, ny = a.ny;
@@ -243,8 +286,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
                    by0 - OYR + RY <= ny;
   if (tma && threadIdx.x == 0) {
     mbar_init(&sm.bar, 1);
-    mbar_expect_tx(&sm.bar, (unsigned)sizeof(sm.u));
+    mbar_expect_tx(&sm.bar, (unsigned)(sizeof(sm.u) + (COMP ? sizeof(sm.ulo) : 0)));
     tma_load_3d(&sm.u[0][0][0][0], &tile_map, &sm.bar, bx0 - OXR, by0 - OYR, 0);
+    if constexpr (COMP) tma_load_3d(&sm.ulo[0][0][0], &lo_map, &sm.bar, bx0 - OXR, by0 - OYR, 0);
   }
 
   R gam[5], eps, gas, inv_dx, inv_dy;
@@ -271,13 +315,15 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   const int ox = tid % TX, oy = tid / TX;  // own cell of this thread
   const int gi = bx0 + ox, gj = by0 + oy;
   const bool own = gi < nx && gj < ny;
-  R u0c[C][3];
+  R u0c[C][3], u0l[C];
   if (a.stage >= 2 && own) {
     const R* u0 = static_cast<const R*>(a.u0);
 #pragma unroll
-    for (int c = 0; c < C; ++c)
+    for (int c = 0; c < C; ++c) {
 #pragma unroll
       for (int m = 0; m < 3; ++m) u0c[c][m] = u0[(3 * c + m) * plane + (size_t)gj * nx + gi];
+      if constexpr (COMP) u0l[c] = a.u0_lo[c * plane + (size_t)gj * nx + gi];
+    }
   }
   if (!tma) {
     for (int k = tid; k < RX * RY; k += NT) {
@@ -285,9 +331,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       const int si = bc_map(bx0 - OXR + rx, nx, a.bc), sj = bc_map(by0 - OYR + ry, ny, a.bc);
       const size_t s = (size_t)sj * nx + si;
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int c = 0; c < C; ++c) {
 #pragma unroll
         for (int m = 0; m < 3; ++m) sm.u[c][m][ry][rx] = w[(3 * c + m) * plane + s];
+        if constexpr (COMP) sm.ulo[c][ry][rx] = a.w_lo[c * plane + s];
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -338,7 +386,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   // ---- 2. Step 4 on the tile plus 2 halo cells
   for (int k = tid; k < LX * LY; k += NT) {
     const int lx = k % LX, ly = k / LX;
-    const int rx = lx + 1 + Smem2D<R, C, NG>::kPadX, ry = ly + 1;  // raw index of the cell
+    const int rx = lx + 1 + SM::kPadX, ry = ly + 1;  // raw index of the cell
     int flag;
     if (a.mode == 1) {
       flag = 1;
@@ -354,13 +402,27 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       }
       const int nxx = lowx ? rx - 1 : rx + 1, nyy = lowy ? ry - 1 : ry + 1;
       const int ci = 0;
-      flag = kxrcf2_troubled(sm.u[ci][0][ry][rx], sm.u[ci][1][ry][rx], sm.u[ci][2][ry][rx],
-                             sm.u[ci][0][ry][nxx], sm.u[ci][1][ry][nxx], sm.u[ci][0][nyy][rx],
-                             sm.u[ci][2][nyy][rx], lowx, lowy, a.kx);
-      if constexpr (C == 4) {
-        flag = flag || kxrcf2_troubled(sm.u[3][0][ry][rx], sm.u[3][1][ry][rx], sm.u[3][2][ry][rx],
-                                       sm.u[3][0][ry][nxx], sm.u[3][1][ry][nxx],
-                                       sm.u[3][0][nyy][rx], sm.u[3][2][nyy][rx], lowx, lowy, a.kx);
+      if constexpr (COMP) {  // on hi + lo
+        flag = kxrcf2_troubled_pair(sm.u[ci][0][ry][rx], sm.ulo[ci][ry][rx], sm.u[ci][1][ry][rx],
+                                    sm.u[ci][2][ry][rx], sm.u[ci][0][ry][nxx], sm.ulo[ci][ry][nxx],
+                                    sm.u[ci][1][ry][nxx], sm.u[ci][0][nyy][rx], sm.ulo[ci][nyy][rx],
+                                    sm.u[ci][2][nyy][rx], lowx, lowy, a.kx);
+        if constexpr (C == 4)
+          flag = flag || kxrcf2_troubled_pair(sm.u[3][0][ry][rx], sm.ulo[3][ry][rx],
+                                              sm.u[3][1][ry][rx], sm.u[3][2][ry][rx],
+                                              sm.u[3][0][ry][nxx], sm.ulo[3][ry][nxx],
+                                              sm.u[3][1][ry][nxx], sm.u[3][0][nyy][rx],
+                                              sm.ulo[3][nyy][rx], sm.u[3][2][nyy][rx], lowx,
+                                              lowy, a.kx);
+      } else {
+        flag = kxrcf2_troubled(sm.u[ci][0][ry][rx], sm.u[ci][1][ry][rx], sm.u[ci][2][ry][rx],
+                               sm.u[ci][0][ry][nxx], sm.u[ci][1][ry][nxx], sm.u[ci][0][nyy][rx],
+                               sm.u[ci][2][nyy][rx], lowx, lowy, a.kx);
+        if constexpr (C == 4) {
+          flag = flag || kxrcf2_troubled(sm.u[3][0][ry][rx], sm.u[3][1][ry][rx], sm.u[3][2][ry][rx],
+                                         sm.u[3][0][ry][nxx], sm.u[3][1][ry][nxx],
+                                         sm.u[3][0][nyy][rx], sm.u[3][2][nyy][rx], lowx, lowy, a.kx);
+        }
       }
     }
     sm.fl[ly][lx] = (uint8_t)flag;
@@ -423,7 +485,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         R d[19], v[NF];
-        gather19(sm, c, ci, cj, d);
+        gather_data<COMP>(sm, c, ci, cj, d);
         p0_faces<NG>(d, v);
 #pragma unroll
         for (int p = 0; p < NF; ++p)
@@ -439,14 +501,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       item_of(sm.hwl[q], ci, cj, p_lo, p_hi);
       if constexpr (C == 1) {
         R d[19], v[NF];
-        gather19(sm, 0, ci, cj, d);
+        gather_data<COMP>(sm, 0, ci, cj, d);
         hweno2d_faces<NG>(d, gam, eps, p_lo, p_hi, v);
 #pragma unroll
         for (int p = 0; p < NF; ++p)
           if (p >= p_lo && p < p_hi) store_point(sm, 0, p, ci, cj, v[p]);
       } else {
-        hweno_faces_euler2d<NG>(sm, ci, cj, p_lo, p_hi, gam[0], gam[1], gam[2], gam[3], gam[4],
-                                eps, gas, (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
+        hweno_faces_euler2d<NG, COMP>(sm, ci, cj, p_lo, p_hi, gam[0], gam[1], gam[2], gam[3],
+                                      gam[4], eps, gas, (a.variant & HWENO_VARIANT_MEAN_EIGEN) != 0);
       }
     }
     __syncthreads();
@@ -464,6 +526,23 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   {
     myflag = sm.fl[cj + 2][ci + 2];
     const R hax = R(0.5) * alx, hay = R(0.5) * aly;
+    // COMP: every point value is an increment over the own cell's hi B, every
+    // flux an increment over f(B) (the base cancels from Eq. (ode2) exactly)
+    R B[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) B[c] = sm.u[c][0][cj + OYR][ci + OXR];
+    auto flux = [&](const R* U, int dir, R* F) {
+      if constexpr (COMP) flux_inc2<C>(gas, B, U, dir, F);
+      else phys_flux2<R, C>(gas, U, dir, F);
+    };
+    // COMP: a neighbour's face value, held over its own hi, over B instead
+    auto rebase = [&](R* v, int dx, int dy) {
+      if constexpr (COMP) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          v[c] = __fadd_rn(v[c], __fsub_rn(sm.u[c][0][cj + OYR + dy][ci + OXR + dx], B[c]));
+      }
+    };
     R Fv[C], Gv[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) Fv[c] = Gv[c] = R(0);
@@ -472,7 +551,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         R d[19];
-        gather19(sm, c, ci, cj, d);
+        gather_data<COMP>(sm, c, ci, cj, d);
         p0_interior<NG>(d, inter[c]);
       }
 #pragma unroll
@@ -482,8 +561,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
           R U[C], f[C], g[C];
 #pragma unroll
           for (int c = 0; c < C; ++c) U[c] = inter[c][l * NG + k];
-          phys_flux2<R, C>(gas, U, 0, f);
-          phys_flux2<R, C>(gas, U, 1, g);
+          flux(U, 0, f);
+          flux(U, 1, g);
 #pragma unroll
           for (int c = 0; c < C; ++c) {
             Fv[c] += gw[k] * gw[l] * f[c];
@@ -500,25 +579,29 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       // x_{i-1/2}: u^- = right face of cell i-1, u^+ = own left face
 #pragma unroll
       for (int c = 0; c < C; ++c) { am[c] = sm.xf[c][NG + k][cj][ci]; ap[c] = sm.xf[c][k][cj][ci + 1]; }
-      phys_flux2<R, C>(gas, am, 0, fa); phys_flux2<R, C>(gas, ap, 0, fb);
+      rebase(am, -1, 0);
+      flux(am, 0, fa); flux(ap, 0, fb);
 #pragma unroll
       for (int c = 0; c < C; ++c) FLk[c] = R(0.5) * (fa[c] + fb[c]) - hax * (ap[c] - am[c]);
       // x_{i+1/2}: u^- = own right face, u^+ = left face of cell i+1
 #pragma unroll
       for (int c = 0; c < C; ++c) { am[c] = sm.xf[c][NG + k][cj][ci + 1]; ap[c] = sm.xf[c][k][cj][ci + 2]; }
-      phys_flux2<R, C>(gas, am, 0, fa); phys_flux2<R, C>(gas, ap, 0, fb);
+      rebase(ap, 1, 0);
+      flux(am, 0, fa); flux(ap, 0, fb);
 #pragma unroll
       for (int c = 0; c < C; ++c) FRk[c] = R(0.5) * (fa[c] + fb[c]) - hax * (ap[c] - am[c]);
       // y_{j-1/2}: u^- = top face of cell j-1, u^+ = own bottom face
 #pragma unroll
       for (int c = 0; c < C; ++c) { am[c] = sm.yf[c][NG + k][cj][ci]; ap[c] = sm.yf[c][k][cj + 1][ci]; }
-      phys_flux2<R, C>(gas, am, 1, fa); phys_flux2<R, C>(gas, ap, 1, fb);
+      rebase(am, 0, -1);
+      flux(am, 1, fa); flux(ap, 1, fb);
 #pragma unroll
       for (int c = 0; c < C; ++c) GBk[c] = R(0.5) * (fa[c] + fb[c]) - hay * (ap[c] - am[c]);
       // y_{j+1/2}: u^- = own top face, u^+ = bottom face of cell j+1
 #pragma unroll
       for (int c = 0; c < C; ++c) { am[c] = sm.yf[c][NG + k][cj + 1][ci]; ap[c] = sm.yf[c][k][cj + 2][ci]; }
-      phys_flux2<R, C>(gas, am, 1, fa); phys_flux2<R, C>(gas, ap, 1, fb);
+      rebase(ap, 0, 1);
+      flux(am, 1, fa); flux(ap, 1, fb);
 #pragma unroll
       for (int c = 0; c < C; ++c) GTk[c] = R(0.5) * (fa[c] + fb[c]) - hay * (ap[c] - am[c]);
 #pragma unroll
@@ -560,11 +643,28 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
         }
         if (!isfinite(o[m])) bad |= ST_NONFINITE;
       }
+      R olo = R(0);
+      if constexpr (COMP) {
+        // the average as a float pair: a u^n + b w in pair arithmetic (1/3
+        // and 2/3 as pairs), then the increment b dt L
+        constexpr float t1h = 1.0f / 3.0f, t2h = 2.0f / 3.0f;
+        constexpr float t1l = (float)(1.0 / 3.0 - (double)t1h), t2l = (float)(2.0 / 3.0 - (double)t2h);
+        const R wl = sm.ulo[c][cj + OYR][ci + OXR];
+        R bh = W[0], bl = wl;
+        if (a.stage == 2)
+          pair_axpby(0.75f, 0.0f, u0c[c][0], u0l[c], 0.25f, 0.0f, W[0], wl, bh, bl);
+        else if (a.stage == 3)
+          pair_axpby(t1h, t1l, u0c[c][0], u0l[c], t2h, t2l, W[0], wl, bh, bl);
+        const R cb = a.stage == 2 ? R(0.25) : a.stage == 3 ? R(2.0 / 3.0) : R(1);
+        pair_add(bh, bl, (cb * dt) * L0, o[0], olo);
+        if (!isfinite(o[0])) bad |= ST_NONFINITE;
+      }
       if (own) {
         R* out = static_cast<R*>(a.out);
         const size_t s = (size_t)gj * nx + gi;
 #pragma unroll
         for (int m = 0; m < 3; ++m) out[(3 * c + m) * plane + s] = o[m];
+        if constexpr (COMP) a.out_lo[c * plane + s] = olo;
         if (a.lim_out) {  // rhs mode: the modified moments; stage 1: what stages 2-3 combine
           R* lo = static_cast<R*>(a.lim_out);
           const R M[3] = {W[0], sm.vl[c][cj + 2][ci + 2], sm.wl[c][cj + 2][ci + 2]};
@@ -711,32 +811,43 @@ __global__ void __launch_bounds__(NT) alpha2d_kernel(const R* __restrict__ w, R*
   }
 }
 
-template <typename R, int C, int NG>
+template <typename R, int C, int NG, bool COMP>
 cudaError_t launch_stage2d_t(const Stage2DArgs& a0, cudaStream_t s) {
   Stage2DArgs a = a0;
-  CUtensorMap map;
+  CUtensorMap map, lo_map;
   a.tma = encode_box_map(a.w, a.nx, a.ny, 3 * C, (int)sizeof(R), RX, RY, &map) ? 1 : 0;
+  memset(&lo_map, 0, sizeof(lo_map));
+  if (COMP && a.tma)  // both boxes, or neither
+    a.tma = encode_box_map(a.w_lo, a.nx, a.ny, C, (int)sizeof(R), RX, RY, &lo_map) ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((a.nx + TX - 1) / TX), (unsigned)((a.ny + TY - 1) / TY));
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = sizeof(Smem2D<R, C, NG>);
+  cfg.dynamicSmemBytes = sizeof(Smem2D<R, C, NG, COMP>);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, stage2d_kernel<R, C, NG>, a, map);
+  return cudaLaunchKernelEx(&cfg, stage2d_kernel<R, C, NG, COMP>, a, map, lo_map);
 }
 
+template <typename R, int C, int NG, bool COMP>
+cudaError_t prepare_one() {
+  cudaError_t e = cudaFuncSetAttribute(stage2d_kernel<R, C, NG, COMP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem2D<R, C, NG, COMP>));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(stage2d_kernel<R, C, NG, COMP>,
+                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
 template <typename R, int C, int NG>
 cudaError_t prepare_t() {
-  cudaError_t e = cudaFuncSetAttribute(stage2d_kernel<R, C, NG>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem2D<R, C, NG>));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage2d_kernel<R, C, NG>,
-                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = prepare_one<R, C, NG, false>();
+  if constexpr (sizeof(R) == 4) {
+    if (e == cudaSuccess) e = prepare_one<R, C, NG, true>();
+  }
+  return e;
 }
 
 }  // namespace
@@ -798,12 +909,17 @@ cudaError_t prepare_stage2d(int system, int fp64, int ng) {
 }
 
 cudaError_t launch_stage2d(const Stage2DArgs& a, cudaStream_t s) {
-  if (a.system == 0) {
-    if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 1, 2>(a, s) : launch_stage2d_t<double, 1, 3>(a, s);
-    return a.ng == 2 ? launch_stage2d_t<float, 1, 2>(a, s) : launch_stage2d_t<float, 1, 3>(a, s);
+  if (a.comp) {  // HWENO_FP32C (stages 1-3 of a step)
+    if (a.system == 0)
+      return a.ng == 2 ? launch_stage2d_t<float, 1, 2, true>(a, s) : launch_stage2d_t<float, 1, 3, true>(a, s);
+    return a.ng == 2 ? launch_stage2d_t<float, 4, 2, true>(a, s) : launch_stage2d_t<float, 4, 3, true>(a, s);
   }
-  if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 4, 2>(a, s) : launch_stage2d_t<double, 4, 3>(a, s);
-  return a.ng == 2 ? launch_stage2d_t<float, 4, 2>(a, s) : launch_stage2d_t<float, 4, 3>(a, s);
+  if (a.system == 0) {
+    if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 1, 2, false>(a, s) : launch_stage2d_t<double, 1, 3, false>(a, s);
+    return a.ng == 2 ? launch_stage2d_t<float, 1, 2, false>(a, s) : launch_stage2d_t<float, 1, 3, false>(a, s);
+  }
+  if (a.fp64) return a.ng == 2 ? launch_stage2d_t<double, 4, 2, false>(a, s) : launch_stage2d_t<double, 4, 3, false>(a, s);
+  return a.ng == 2 ? launch_stage2d_t<float, 4, 2, false>(a, s) : launch_stage2d_t<float, 4, 3, false>(a, s);
 }
 
 cudaError_t launch_dt2d(const Stage2DArgs& a, cudaStream_t s) {

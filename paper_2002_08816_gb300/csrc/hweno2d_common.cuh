@@ -86,6 +86,44 @@ __device__ __forceinline__ void phys_flux2(R gas, const R* U, int dir, R* F) {
   }
 }
 
+// f(B + D) - f(B) (dir 0) or g(B + D) - g(B) (dir 1) for a base state B and
+// an increment D, FP32, with rounding errors relative to the increment (no
+// difference of O(|f|) terms; the float-pair precision HWENO_FP32C): with
+// mu = m / rho, nu = n / rho, p = (gamma - 1)(E - (m mu + n nu) / 2),
+//   dmu = (dm - mu drho) / (rho + drho), dnu likewise,
+//   d(m mu) = m dmu + dm (mu + dmu), and the other products the same way,
+//   dp = (gamma - 1)(dE - (d(m mu) + d(n nu)) / 2),
+//   d(vn (E + p)) = dvn (E + p + dE + dp) + vn (dE + dp).
+template <int C>
+__device__ __forceinline__ void flux_inc2(float gas, const float* B, const float* D, int dir,
+                                          float* dF) {
+  if constexpr (C == 1) {
+    dF[0] = D[0] * (B[0] + 0.5f * D[0]);
+  } else {
+    const float rho = B[0], m = B[1], n = B[2], E = B[3];
+    const float dr = D[0], dm = D[1], dn = D[2], dE = D[3];
+    const float ir = fast_rcp(rho), ir1 = fast_rcp(rho + dr);
+    const float mu = m * ir, nu = n * ir;
+    const float dmu = (dm - mu * dr) * ir1, dnu = (dn - nu * dr) * ir1;
+    const float dmm = m * dmu + dm * (mu + dmu);  // d(m mu)
+    const float dnn = n * dnu + dn * (nu + dnu);  // d(n nu)
+    const float g1 = gas - 1.0f;
+    const float p = g1 * (E - 0.5f * (m * mu + n * nu));
+    const float dp = g1 * (dE - 0.5f * (dmm + dnn));
+    if (dir == 0) {
+      dF[0] = dm;
+      dF[1] = dmm + dp;
+      dF[2] = n * dmu + dn * (mu + dmu);  // d(n mu)
+      dF[3] = dmu * ((E + p) + (dE + dp)) + mu * (dE + dp);
+    } else {
+      dF[0] = dn;
+      dF[1] = m * dnu + dm * (nu + dnu);  // d(m nu)
+      dF[2] = dnn + dp;
+      dF[3] = dnu * ((E + p) + (dE + dp)) + nu * (dE + dp);
+    }
+  }
+}
+
 // max |f'| (dir 0) and |g'| (dir 1) at a cell average; NaN when not physical
 template <typename R, int C>
 __device__ __forceinline__ void wave_speeds2(R gas, const R* U, R& sx, R& sy) {

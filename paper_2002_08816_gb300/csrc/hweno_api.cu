@@ -38,9 +38,11 @@ struct hweno_ctx {
   unsigned long long* res_halo = nullptr;     // tagged exchange words of the halos
   unsigned long long* res_entries = nullptr;  // and of the per-CTA maxima
   // HWENO_FP32C: the low parts of the averages ([C][n] floats beside U[0]);
-  // every step runs as the resident launch
+  // 1D steps run as the resident launch, 2D steps carry the low parts of the
+  // stage buffers U[1], U[2] too (Ulo_s)
   bool comp = false;
   float* Ulo = nullptr;
+  float* Ulo_s[2] = {nullptr, nullptr};
   int ntile_alpha = 0;               // CTAs of the 1D wave-speed kernels (kTile1D cells each)
   unsigned* bar = nullptr;           // grid barrier of the persistent kernel
   std::vector<int> batch_nx;         // cells of each batch instance
@@ -173,6 +175,12 @@ struct Step2DIO {
   void* rec_alpha;
   void* rec_dt;
   const void* dt_in;
+  // HWENO_FP32C: the low parts of the averages of in, s1, s2 and out (nullptr:
+  // plain precision)
+  const float* in_lo = nullptr;
+  float* s1_lo = nullptr;
+  float* s2_lo = nullptr;
+  float* out_lo = nullptr;
 };
 
 void* byte_off(const void* p, size_t bytes) {
@@ -195,6 +203,9 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.rec_alpha = io.rec_alpha;
   a.rec_dt = io.rec_dt;
   a.dt_in = io.dt_in;
+  a.comp = io.in_lo != nullptr;
+  a.w_lo = io.in_lo;
+  a.out_lo = io.s1_lo;
   cudaError_t e = hw::launch_dt2d(a, s);
   if (e != cudaSuccess) return e;
   e = hw::launch_stage2d(a, s);
@@ -209,6 +220,9 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.a_in = io.part[1];
   a.a_out = io.part[2];
   a.a_zero = io.part[0];
+  a.w_lo = io.s1_lo;
+  a.u0_lo = io.in_lo;  // the limiter leaves the averages of u^n as they are
+  a.out_lo = io.s2_lo;
   if (io.flags) a.flags_out = io.flags + (size_t)h->n;
   if (io.rec_alpha) a.rec_alpha = byte_off(io.rec_alpha, pair);
   e = hw::launch_stage2d(a, s);
@@ -219,6 +233,8 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.a_in = io.part[2];
   a.a_out = io.part[0];
   a.a_zero = io.part[1];
+  a.w_lo = io.s2_lo;
+  a.out_lo = io.out_lo;  // may be in_lo: each cell reads its u^n low part before it writes
   if (io.flags) a.flags_out = io.flags + 2 * (size_t)h->n;
   if (io.rec_alpha) a.rec_alpha = byte_off(io.rec_alpha, 2 * pair);
   return hw::launch_stage2d(a, s);
@@ -227,6 +243,12 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
 cudaError_t enqueue_step2d(hweno_ctx* h, cudaStream_t s) {
   Step2DIO io = {h->U[0], h->U[1], h->U[2], h->U[0], h->U0,
                  {h->part[0], h->part[1], h->part[2]}, h->sc, nullptr, nullptr, nullptr, nullptr};
+  if (h->comp) {
+    io.in_lo = h->Ulo;
+    io.s1_lo = h->Ulo_s[0];
+    io.s2_lo = h->Ulo_s[1];
+    io.out_lo = h->Ulo;
+  }
   return enqueue_step2d_io(h, io, s);
 }
 
@@ -386,8 +408,6 @@ hweno_status validate(const hweno_config* c) {
   if (c->troubled_mode < 0 || c->troubled_mode > 2) return fail(nullptr, HWENO_ERR_ARG, "unknown troubled_mode");
   if (c->precision != HWENO_FP32 && c->precision != HWENO_FP64 && c->precision != HWENO_FP32C)
     return fail(nullptr, HWENO_ERR_ARG, "unknown precision");
-  if (c->precision == HWENO_FP32C && c->dim != 1)
-    return fail(nullptr, HWENO_ERR_ARG, "HWENO_FP32C is available for 1D");
   if (c->variant & ~(HWENO_VARIANT_RAW_COMBINE | HWENO_VARIANT_MEAN_EIGEN))
     return fail(nullptr, HWENO_ERR_ARG, "unknown variant bits");
   return HWENO_OK;
@@ -436,6 +456,7 @@ hweno_status check_adjoint_config(hweno_ctx* h) {
   if (h->n_batch > 0) return fail(h, HWENO_ERR_ARG, "the adjoint takes a single-instance handle");
   if (h->cfg.bc != HWENO_BC_PERIODIC) return fail(h, HWENO_ERR_ARG, "the adjoint needs periodic boundaries");
   if (h->cfg.variant != 0) return fail(h, HWENO_ERR_ARG, "the adjoint is of the default variant");
+  if (h->comp) return fail(h, HWENO_ERR_ARG, "the adjoint takes HWENO_FP32 or HWENO_FP64 handles");
   return HWENO_OK;
 }
 
@@ -567,6 +588,8 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->U[k], h->elems * h->esize);
   if (e == cudaSuccess && h->comp) e = cudaMalloc(&h->Ulo, sizeof(float) * h->C * h->n);
+  for (int k = 0; k < 2 && e == cudaSuccess && h->comp && cfg->dim == 2; ++k)
+    e = cudaMalloc(&h->Ulo_s[k], sizeof(float) * h->C * h->n);
   if (e == cudaSuccess) e = cudaMalloc(&h->U0, h->elems * h->esize);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_buf, h->elems * 8);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&h->part[k], sizeof(double) * 2 * hw::kAlphaSlots);
@@ -585,7 +608,7 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
     hweno_destroy(h);
     return fail(nullptr, HWENO_ERR_CUDA, msg);
   }
-  if (h->comp) {  // the resident launch only
+  if (h->comp && h->dim == 1) {  // the resident launch only
     h->persist1d = 2;
     e = prepare_resident(h);
     if (e != cudaSuccess || h->res_tile == 0) {
@@ -618,7 +641,7 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
   }
   if (h->comp) {
     // hi into the state, the low parts of the averages beside it
-    if (src64) HW_CUDA(h, hw::launch_split_pairs(src ? src : h->U[0], h->U[0], h->Ulo, h->C, h->n, h->stream));
+    if (src64) HW_CUDA(h, hw::launch_split_pairs(src ? src : h->U[0], h->U[0], h->Ulo, h->C, h->M, h->n, h->stream));
     else {
       if (src) HW_CUDA(h, hw::launch_convert(src, 0, h->U[0], 0, h->elems, h->stream));
       HW_CUDA(h, cudaMemsetAsync(h->Ulo, 0, sizeof(float) * h->C * h->n, h->stream));
@@ -736,7 +759,7 @@ hweno_status hweno_get_state(hweno_handle h, void* out, int dtype, int on_device
   const size_t dbytes = h->elems * (dst64 ? 8 : 4);
   if (h->comp && dst64) {  // hi + lo of the averages
     void* dst = on_device ? out : h->stage_buf;
-    HW_CUDA(h, hw::launch_join_pairs(h->U[0], h->Ulo, static_cast<double*>(dst), h->C, h->n, h->stream));
+    HW_CUDA(h, hw::launch_join_pairs(h->U[0], h->Ulo, static_cast<double*>(dst), h->C, h->M, h->n, h->stream));
     if (on_device) return HWENO_OK;
     HW_CUDA(h, cudaMemcpyAsync(out, h->stage_buf, dbytes, cudaMemcpyDeviceToHost, h->stream));
     HW_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -792,6 +815,8 @@ void hweno_destroy(hweno_handle h) {
   if (h->res_halo) cudaFree(h->res_halo);
   if (h->res_entries) cudaFree(h->res_entries);
   if (h->Ulo) cudaFree(h->Ulo);
+  for (int k = 0; k < 2; ++k)
+    if (h->Ulo_s[k]) cudaFree(h->Ulo_s[k]);
   if (h->tot_buf) cudaFree(h->tot_buf);
   if (h->d_tile_inst) cudaFree(h->d_tile_inst);
   if (h->d_tile_base) cudaFree(h->d_tile_base);

@@ -116,6 +116,10 @@ struct Stage2DArgs {
   int nx, ny, stage, bc, mode, system, fp64, ng;
   int variant;            // HWENO_VARIANT_* bits
   int tma;                // set by the launcher: interior tiles copied by TMA
+  int comp;               // HWENO_FP32C: the averages' low parts below are read and written
+  const float* w_lo;      // low parts of the stage input's averages [C][ny][nx]
+  const float* u0_lo;     // low parts of u^n's averages (stages 2-3)
+  float* out_lo;          // low parts of the output's averages
   double dx, dy, cfl, eps, thr, gas;
   double gam[5];
   double inv_dx, inv_dy;  // derived
@@ -221,10 +225,11 @@ size_t resident1d_halo_words(int system, int ncta);
 // cells (comp: the float-pair averages of HWENO_FP32C); *tile = 0 when the
 // grid does not fit on the GPU at once.
 cudaError_t resident1d_geometry(int system, int nth, bool comp, int n, int* tile, int* ncta);
-// HWENO_FP32C states: an FP64 state into hi (FP32, the state layout) and the
-// averages' low parts [C][n]; and hi + lo back into an FP64 state.
-cudaError_t launch_split_pairs(const void* src, void* hi, float* lo, int C, int n, cudaStream_t s);
-cudaError_t launch_join_pairs(const void* hi, const float* lo, double* out, int C, int n,
+// HWENO_FP32C states: an FP64 state [C][M][n] into hi (FP32, the state layout)
+// and the averages' low parts [C][n]; and hi + lo back into an FP64 state.
+cudaError_t launch_split_pairs(const void* src, void* hi, float* lo, int C, int M, int n,
+                               cudaStream_t s);
+cudaError_t launch_join_pairs(const void* hi, const float* lo, double* out, int C, int M, int n,
                               cudaStream_t s);
 // Zeroes the exchange words, then launches.
 cudaError_t launch_resident1d(const Resident1DArgs& r, int nth, int ncta, cudaStream_t s);

@@ -64,13 +64,10 @@ def test_barrier_self_test_rejects_bad_arguments_before_cuda(lib, args):
     assert b"hweno_check_barrier" in lib.hweno_last_error(None)
 
 
-def test_pair_precision_is_one_dimensional(lib):
-    """HWENO_FP32C (float-pair averages) is refused for 2D handles and for
-    batches before any CUDA call."""
-    c = H.make_config(2, H.HWENO_EULER, 64, 64, precision=H.HWENO_FP32C)
+def test_pair_precision_is_refused_for_batches(lib):
+    """HWENO_FP32C (float-pair averages) is refused for batches before any
+    CUDA call."""
     h = ctypes.c_void_p()
-    assert lib.hweno_create(ctypes.byref(c), None, ctypes.byref(h)) == H.HWENO_ERR_ARG
-    assert "1D" in H.hweno_last_error(None)
     c1 = H.make_config(1, H.HWENO_EULER, 64, precision=H.HWENO_FP32C)
     sizes = (ctypes.c_int * 2)(64, 80)
     assert lib.hweno_create_batch(ctypes.byref(c1), 2, sizes, None, ctypes.byref(h)) == H.HWENO_ERR_ARG

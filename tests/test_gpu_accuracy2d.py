@@ -1,11 +1,20 @@
-"""2D Euler, FP32 and FP64 against the FP64 oracle over 100 RK steps from the
-same input, per field (component x moment): the 128 x 128 vortex-plus-modes
-data (smooth) and four constant quadrants (shocked), 2 Gauss points, CFL
-0.5.  The cell averages meet the 1e-5 (smooth) / 1e-4 (shocked) relative L1
-targets in FP32; the first moments carry the FP32 rounding of the averages
-amplified by 1/dx (measured 3e-5 - 7e-5 on the smooth data: an FP64 run of
-the oracle's own operator that rounds the state to FP32 every stage gives the
-same 3e-5 - 6e-5), so the test holds them to 2e-4 and FP64 to 1e-10."""
+"""2D Euler, FP32, HWENO_FP32C and FP64 against the FP64 oracle over 100 RK
+steps from the same input, per field (component x moment): the 128 x 128
+vortex-plus-modes data (smooth) and four constant quadrants (shocked), 2
+Gauss points, CFL 0.5.  FP32: the cell averages meet the 1e-5 (smooth) /
+1e-4 (shocked) relative L1 targets; the first moments carry the FP32 rounding
+of the averages amplified by 1/dx (measured 5e-5 - 1e-4 on the smooth data:
+an FP64 run of the oracle's own operator that rounds the state to FP32 every
+stage gives 3e-5 - 6e-5), held to 2e-4.  HWENO_FP32C (float-pair averages,
+the operator on increments): averages within 1e-7 and first moments within
+1e-5, the targets met with margin (measured 3e-9 - 4e-8 and 3.5e-7 - 7e-7).
+FP64 within 1e-10.  The shocked run uses the KXRCF threshold 1.0001 in every
+run: at 1.0, one cell of this run reaches the threshold within the band that
+the runs' own differences cover (the indicator's jump is a difference of
+O(|u|) terms, so a 5e-7 difference of the state moves it by ~2e-5) around
+step 85, and the float-pair run takes the other decision there (its first
+moments then differ by 1e-3 locally as a limited cell's do); at 1.0001 no
+decision is that close."""
 
 import numpy as np
 import pytest
@@ -31,9 +40,9 @@ def _gpu(cfg, u, prec):
     import torch
     h = H.hweno_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
-        dt = np.float64 if prec == H.HWENO_FP64 else np.float32
-        host = np.ascontiguousarray(u, dtype=dt)
-        H.hweno_set_state(h, host.ctypes.data, prec, False)
+        sdt = H.HWENO_FP32 if prec == H.HWENO_FP32 else H.HWENO_FP64  # FP32C: keep the pairs
+        host = np.ascontiguousarray(u, dtype=np.float64 if sdt == H.HWENO_FP64 else np.float32)
+        H.hweno_set_state(h, host.ctypes.data, sdt, False)
         t = H.hweno_step(h, STEPS)
         out = np.empty(u.shape, dtype=np.float64)
         H.hweno_get_state(h, out.ctypes.data, H.HWENO_FP64, False)
@@ -49,21 +58,30 @@ def test_per_field_errors_against_the_oracle(data):
     else:
         u = W.euler_quadrants_2d(N, N, seed=2026)
     u = u.astype(np.float32).astype(np.float64)  # the input every run sees
+    thr = 1.0 if data == "vortex" else 1.0001
     cfg = H.make_config(2, H.HWENO_EULER, N, N, x0=0.0, x1=10.0, y0=0.0, y1=10.0,
-                        bc=H.HWENO_BC_PERIODIC, cfl=0.5, precision=H.HWENO_FP32, n_gauss=2)
-    ocfg = O.Cfg2D.make(O.EULER, N, N, 0.0, 10.0, 0.0, 10.0, O.BC_PERIODIC, n_gauss=2)
+                        bc=H.HWENO_BC_PERIODIC, cfl=0.5, precision=H.HWENO_FP32, n_gauss=2,
+                        threshold=thr)
+    ocfg = O.Cfg2D.make(O.EULER, N, N, 0.0, 10.0, 0.0, 10.0, O.BC_PERIODIC, n_gauss=2,
+                        threshold=thr)
     ref, t_ref, _ = O.run2d(ocfg, u, nsteps=STEPS, cfl=0.5, omp=True)
     ref = ref.reshape(u.shape)
     got32, t32 = _gpu(cfg, u, H.HWENO_FP32)
+    cfg.precision = H.HWENO_FP32C
+    got32c, t32c = _gpu(cfg, u, H.HWENO_FP32C)
     cfg.precision = H.HWENO_FP64
     got64, t64 = _gpu(cfg, u, H.HWENO_FP64)
-    for got, prec in ((got32, "fp32"), (got64, "fp64")):
+    for got, prec in ((got32, "fp32"), (got32c, "fp32c"), (got64, "fp64")):
         err = np.abs(got - ref).sum(axis=(2, 3)) / np.abs(ref).sum(axis=(2, 3))  # [C][3]
         print("2D %s %s rel L1 [rho, m, n, E] x [avg, x-moment, y-moment]: %s"
               % (data, prec, np.array2string(err, precision=2).replace("\n", "")))
         if prec == "fp64":
             assert (err <= 1e-10).all(), err
+        elif prec == "fp32c":
+            assert (err[:, 0] <= 1e-7).all(), err
+            assert (err[:, 1:] <= 1e-5).all(), err
         else:
             assert (err[:, 0] <= (1e-5 if data == "vortex" else 1e-4)).all(), err
             assert (err[:, 1:] <= 2e-4).all(), err
     assert abs(t32 - t_ref) <= 1e-6 * t_ref and abs(t64 - t_ref) <= 1e-12 * t_ref
+    assert abs(t32c - t_ref) <= 1e-6 * t_ref
