@@ -128,7 +128,8 @@ hweno_status hweno_set_state(hweno_handle h, const void* moments, int dtype, int
 hweno_status hweno_step(hweno_handle h, int nsteps, double t_final, double* t_out);
 
 /* One evaluation of the right-hand side L of Eq. (odeH)/(ode2) on caller
- * device buffers in the configured precision and the state layout: out =
+ * device buffers in the configured precision (FP32 for HWENO_FP32C) and the
+ * state layout: out =
  * L(in) with alpha from in.  flags_out (nullable, nx*ny bytes) receives the
  * troubled-cell flags (1 = troubled); ulim_out (nullable, state layout)
  * receives in with the first moments of troubled cells modified (Step 1/4).
@@ -249,8 +250,10 @@ hweno_status hweno_rhs_vjp(hweno_handle h, const void* in, const uint8_t* flags,
  * contract a few multiply-adds differently).  The paper has no counterpart (it
  * fixes no hardware mapping).  choice_out (nullable, 2 ints) receives the
  * threads per CTA and the launch kind (0 graphs, 1 persistent, 2 resident).
- * New handles start with 256 threads and per-stage graphs.  Waits for the
- * stream; HWENO_ERR_ARG for 2D handles, HWENO_ERR_STATE before set_state. */
+ * New handles start with 256 threads and per-stage graphs (HWENO_FP32C: the
+ * resident launch, the only one it has; its autotuner times 256 and 512
+ * threads).  Waits for the stream; HWENO_ERR_ARG for 2D handles,
+ * HWENO_ERR_STATE before set_state. */
 hweno_status hweno_autotune(hweno_handle h, int nsteps_trial, int* choice_out);
 
 /* Failure-detection self-test of the grid barrier the persistent launch uses
@@ -288,9 +291,9 @@ hweno_status hweno_check_resident(hweno_handle h, int nsteps, int silent_cta, un
  * resident launch per hweno_step in which every CTA keeps its tile of the
  * state in shared memory for the whole run (FP32 single-instance handles, 256
  * or 512 threads, grids small enough for every tile to be on the GPU at once;
- * HWENO_ERR_ARG otherwise).  1D handles only; waits for the stream.  All
- * choices compute the same scheme; results agree to rounding (the per-stage
- * choices bit for bit). */
+ * HWENO_ERR_ARG otherwise; HWENO_FP32C handles take only this kind).  1D
+ * handles only; waits for the stream.  All choices compute the same scheme;
+ * results agree to rounding (the per-stage choices bit for bit). */
 hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent);
 
 /* The conserved totals of the current state: totals[c] = the sum over cells
