@@ -49,16 +49,18 @@ UNIT = "cell-stages/s"
 BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3, "fp32c": 8 * 36 / 3}
 # DRAM bytes (read + write) per stage from ncu captures of the current kernels,
 # summarised under profiles/ (None where no capture of the current build exists):
-# the resident launch reads the state once per launch (2000 steps = 6000 stages)
-TRAFFIC_1D_FP32 = {(256, "resident"): (2340608 + 57856) / 6000}
+# the resident launch reads the state once per launch: a 2000-step (6000-stage)
+# capture over its stages; FP32C also reads the averages' low parts
+TRAFFIC_1D_FP32 = {(256, "resident"): (1915136 + 73472) / 6000}
+TRAFFIC_1D_FP32C = {(256, "resident"): (2937856 + 55808) / 6000}
 # the batched workload, 128-thread per-stage launches: the mean of the three
 # stages of one step, cold L2
 TRAFFIC_BATCH_FP32 = {(128, "per-stage graphs"): (48920064 + 43554304 + 96720384 + 22503424
                                                   + 96724480 + 21628160) / 3}
 # 2D, 2 Gauss points: a 2048^2 capture (the three stages of one step) scaled
 # by the cell count to 4096^2 (the bytes per cell do not depend on the grid)
-TRAFFIC_2D_NG2 = 4 * (213615872 + 353926144 + 403311616 + 174973952 + 403310592
-                      + 175929856) / 3
+TRAFFIC_2D_NG2 = 4 * (212943104 + 351479552 + 403683840 + 174359296 + 403575808
+                      + 175461120) / 3
 L2_FLUSH_BYTES = 512 << 20
 # hweno_autotune's launch kinds and the kernel each one times
 LAUNCH_KIND = {0: "per-stage graphs", 1: "persistent", 2: "resident"}
@@ -412,7 +414,9 @@ def bench_hweno(args):
                                / (res["fp32c"]["stage_us"] * 1e-6) / 1e9,
                                "frac": BYTES_PER_CELL_STAGE["fp32c"] * NX
                                / (res["fp32c"]["stage_us"] * 1e-6) / 1e9 / peak,
-                               "traffic": None,
+                               "traffic": TRAFFIC_1D_FP32C.get(
+                                   (res["fp32c"]["execution"]["threads_per_cta"],
+                                    res["fp32c"]["execution"]["launch"])),
                                "note": "algorithmic 96 B per cell-stage (the averages as float "
                                        "pairs: 36 B per cell) x 65536 cells per stage"}},
         "troubled_frac": r["stats"]["troubled"] / float(cells),

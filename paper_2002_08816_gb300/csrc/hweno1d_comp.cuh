@@ -63,16 +63,22 @@ __device__ __forceinline__ void flux_inc(float gas, const float* B, const float*
 }
 
 // KXRCF on float-pair averages (um + lm, u0 + l0, up + lp; FP32 first
-// moments): the plain kernel's FP32 fast test on hi, whose margins (6e-7 S on
-// the jump, 4.8e-7 on the threshold) exceed what the low parts can change
-// (below 2^-24 of |u0| + |u_nb|), and, where it cannot decide, the FP64
-// product form on hi + lo: the oracle's decision on the same state except
-// within a few ulp of the threshold (deciding on hi alone would flip the rare
-// cell that hi's rounding moves across it).
+// moments), in three tiers: the plain kernel's FP32 fast test on hi, whose
+// margins (6e-7 S on the jump, 4.8e-7 on the threshold) exceed what the low
+// parts can change (below 2^-24 of |u0| + |u_nb|); where it cannot decide (on
+// fine grids, where the threshold h^(3/2) |u0| falls below the jump's rounding
+// bound, that is most cells), the jump and the threshold as unevaluated float
+// pairs with the low parts added in (jump_pair_lo: within ~2^-45 S of the
+// exact jump of hi + lo; r = |u0 + l0| (hthr + hthr_lo) within ~2^-46 r),
+// decided when their difference clears 1e-12 (S + r), far above those
+// bounds; and only inside that margin the FP64 product form on hi + lo.  The
+// decision is the oracle's on the same state except within a few FP64 ulp of
+// the threshold (deciding on hi alone would flip the rare cell that hi's
+// rounding moves across it).
 __device__ __forceinline__ bool kxrcf_troubled_pair(float um, float lm, float u0, float l0,
                                                     float up, float lp, float vm, float v0,
                                                     float vp, bool left, double h, double thr,
-                                                    float hthr) {
+                                                    float hthr, float hthr_lo) {
   float a, b, s;
   if (left) {
     a = u0 - 6.0f * v0;
@@ -88,6 +94,23 @@ __device__ __forceinline__ bool kxrcf_troubled_pair(float um, float lm, float u0
   const float r = hthr * fmaxf(fabsf(u0), 1e-12f);
   if (j - e > r * (1.0f + 4.8e-7f)) return true;
   if (j + e < r * (1.0f - 4.8e-7f)) return false;
+  float jh, jl;
+  jump_pair_lo(u0, l0, v0, left ? um : up, left ? lm : lp, left ? vm : vp, left, jh, jl);
+  if (jh < 0.0f) {
+    jh = -jh;
+    jl = -jl;
+  }
+  // |u0 + l0| as a pair: a normalised pair's hi carries the sign
+  float nh = fabsf(u0), nl = u0 < 0.0f ? -l0 : l0;
+  if (nh < 1e-12f) {
+    nh = 1e-12f;
+    nl = 0.0f;
+  }
+  const float rh = __fmul_rn(nh, hthr);
+  const float rl = __fadd_rn(fmaf(nh, hthr, -rh),
+                             __fadd_rn(__fmul_rn(nh, hthr_lo), __fmul_rn(nl, hthr)));
+  const float d = __fadd_rn(__fsub_rn(jh, rh), __fsub_rn(jl, rl));
+  if (fabsf(d) > 1e-12f * (s + r)) return d > 0.0f;
   return kxrcf_troubled((double)um + (double)lm, (double)u0 + (double)l0,
                         (double)up + (double)lp, (double)vm, (double)v0, (double)vp, left, h,
                         thr, 0.0f, 0.0f);

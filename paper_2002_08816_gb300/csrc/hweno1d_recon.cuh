@@ -197,6 +197,16 @@ __device__ __forceinline__ void jump_pair(float u0, float v0, float unb, float v
   two_sum(s3, __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), t3), sv * __fadd_rn(e0, e1)), jh, jl);
 }
 
+// jump_pair of float-pair averages u0 + l0 and u_nb + l_nb (FP32 first
+// moments): the hi parts' jump plus l0 - l_nb, renormalised; within ~2^-45 S
+// of the exact jump of hi + lo (each low part is below 2^-24 of its hi, so
+// their difference and its addition round at ~2^-48 S and ~2^-46 S).
+__device__ __forceinline__ void jump_pair_lo(float u0, float l0, float v0, float unb, float lnb,
+                                             float vnb, bool low, float& jh, float& jl) {
+  jump_pair(u0, v0, unb, vnb, low, jh, jl);
+  two_sum(jh, __fadd_rn(jl, __fsub_rn(l0, lnb)), jh, jl);
+}
+
 // FP32 inputs: decide in FP32 when the rounding-error bound allows, else
 // evaluate the jump and the threshold as unevaluated float pairs (error-free
 // sums and products), so that the decision equals the FP64 one away from the

@@ -407,13 +407,13 @@ __global__ void __launch_bounds__(NTH + 32, NTH == 256 ? 2 : 1) resident1d_kerne
         flag = c1d::kxrcf_troubled_pair(sm.u[0][0][e - 1], S.ulo[0][e - 1], sm.u[0][0][e],
                                         S.ulo[0][e], sm.u[0][0][e + 1], S.ulo[0][e + 1],
                                         sm.u[0][1][e - 1], sm.u[0][1][e], sm.u[0][1][e + 1], left,
-                                        h, a.thr, hthr);
+                                        h, a.thr, hthr, hthr_lo);
         if constexpr (C == 3)
           flag = flag || c1d::kxrcf_troubled_pair(sm.u[2][0][e - 1], S.ulo[2][e - 1],
                                                   sm.u[2][0][e], S.ulo[2][e], sm.u[2][0][e + 1],
                                                   S.ulo[2][e + 1], sm.u[2][1][e - 1],
                                                   sm.u[2][1][e], sm.u[2][1][e + 1], left, h,
-                                                  a.thr, hthr);
+                                                  a.thr, hthr, hthr_lo);
       } else if constexpr (C == 1) {
         const R uc = sm.u[0][0][e];
         flag = kxrcf_troubled(sm.u[0][0][e - 1], uc, sm.u[0][0][e + 1], sm.u[0][1][e - 1],

@@ -135,11 +135,14 @@ __device__ __forceinline__ bool kxrcf2_troubled(double u0, double v0, double w0,
   return fabs(num) > __dmul_rn(k.thr, __dmul_rn(k.den_h, nrm));
 }
 
-// Float-pair averages (HWENO_FP32C: u0 + l0, uxn + lxn, uyn + lyn): the FP32
-// fast test on hi (its margins exceed what the low parts can change, below
-// 2^-24 of the averages), and, where it cannot decide, the FP64 form on hi +
-// lo, so that the decision is the oracle's on the same state except within a
-// few ulp of the threshold.
+// Float-pair averages (HWENO_FP32C: u0 + l0, uxn + lxn, uyn + lyn), in three
+// tiers: the FP32 fast test on hi (its margins exceed what the low parts can
+// change, below 2^-24 of the averages); where it cannot decide, the float-pair
+// form of the FP32 kernel with the low parts added in (jump_pair_lo; the norm
+// |u0 + l0| as a pair), decided when the difference clears 1e-12 (dy S_x + dx
+// S_y + r), far above its rounding bound; and only inside that margin the FP64
+// form on hi + lo.  The decision is the oracle's on the same state except
+// within a few FP64 ulp of the threshold.
 __device__ __forceinline__ bool kxrcf2_troubled_pair(float u0, float l0, float v0, float w0,
                                                      float uxn, float lxn, float vxn, float uyn,
                                                      float lyn, float wyn, bool lowx, bool lowy,
@@ -153,6 +156,32 @@ __device__ __forceinline__ bool kxrcf2_troubled_pair(float u0, float l0, float v
   const float r = k.fthr_den * fmaxf(fabsf(u0), 1e-12f);
   if (num - e > r * (1.0f + 4.8e-7f)) return true;
   if (num + e < r * (1.0f - 4.8e-7f)) return false;
+  float jxh, jxl, jyh, jyl;
+  jump_pair_lo(u0, l0, v0, uxn, lxn, vxn, lowx, jxh, jxl);
+  jump_pair_lo(u0, l0, w0, uyn, lyn, wyn, lowy, jyh, jyl);
+  const float p1h = __fmul_rn(k.fdy, jxh);
+  const float p1l = __fadd_rn(fmaf(k.fdy, jxh, -p1h),
+                              __fadd_rn(__fmul_rn(k.fdy, jxl), __fmul_rn(k.fdy_lo, jxh)));
+  const float p2h = __fmul_rn(k.fdx, jyh);
+  const float p2l = __fadd_rn(fmaf(k.fdx, jyh, -p2h),
+                              __fadd_rn(__fmul_rn(k.fdx, jyl), __fmul_rn(k.fdx_lo, jyh)));
+  float mh, ml, t;
+  two_sum(p1h, p2h, mh, t);
+  two_sum(mh, __fadd_rn(t, __fadd_rn(p1l, p2l)), mh, ml);
+  if (mh < 0.0f) {
+    mh = -mh;
+    ml = -ml;
+  }
+  float nh = fabsf(u0), nl = u0 < 0.0f ? -l0 : l0;
+  if (nh < 1e-12f) {
+    nh = 1e-12f;
+    nl = 0.0f;
+  }
+  const float rh = __fmul_rn(nh, k.fthr_den);
+  const float rl = __fadd_rn(fmaf(nh, k.fthr_den, -rh),
+                             __fadd_rn(__fmul_rn(nh, k.fthr_den_lo), __fmul_rn(nl, k.fthr_den)));
+  const float d = __fadd_rn(__fsub_rn(mh, rh), __fsub_rn(ml, rl));
+  if (fabsf(d) > 1e-12f * (k.fdy * sx + k.fdx * sy + r)) return d > 0.0f;
   return kxrcf2_troubled((double)u0 + (double)l0, (double)v0, (double)w0, (double)uxn + (double)lxn,
                          (double)vxn, (double)uyn + (double)lyn, (double)wyn, lowx, lowy, k);
 }
