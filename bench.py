@@ -968,6 +968,20 @@ def main():
             sub.steps, sub.warmup = max(1, min(args.steps, 2)), 1
             ap_ = alu_peaks()
             line["alu_peaks"] = ap_
+            # the FP64 path is bound by GB300's FP64 pipe (1/64 of FP32): its
+            # arithmetic roofline, the oracle's flops per cell-stage at the
+            # run's troubled share over the measured FP64 FMA peak
+            tf = line["troubled_frac"]
+            fl64 = ((1.0 - tf) * oracle_flops("1d_euler_smooth")
+                    + tf * oracle_flops("1d_euler_troubled"))
+            ach64 = line["fp64"]["value"] * fl64 / 1e12
+            line["fp64"]["roofline"] = {
+                "bound": "alu", "unit": "TFLOP/s", "peak": ap_["fp64_tflops"], "achieved": ach64,
+                "frac": ach64 / ap_["fp64_tflops"], "traffic": None,
+                "flops_per_cell_stage": fl64,
+                "note": "oracle op count per cell-stage (oracle/flop_counts.json) at the FP32 "
+                        "run's troubled share x cell-stages/s; peak = measured FP64 FMA "
+                        "throughput (hweno_fma_peak)"}
             wl = {}
 
             def sub_record(name, fn, *a, **k):
