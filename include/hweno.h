@@ -166,11 +166,9 @@ hweno_status hweno_stats(hweno_handle h, double* t, double* last_dt, int64_t* st
  * flags_out and ulim_out
  * nullable; no overlap), and the result is the same L(in).
  * Scratch: a file-scope __device__ array inside the library, which every GPU
- * that loads the library holds until the process exits.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and caches it for the life of the process; do not use the
- * library across a cudaDeviceReset (the cached address would be stale).  Every call shares the
- * one array and each call resets the part that must start at zero, so calls
+ * that loads the library holds until the process exits; every call looks up
+ * its device address on the current device (cudaGetSymbolAddress), so a
+ * device reset leaves nothing stale behind.  Every call shares the one array and each call resets the part that must start at zero, so calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.
  * Returns HWENO_ERR_TOO_LARGE when cfg->nx > HWENO_NOALLOC_MAX_CELLS,

@@ -20,8 +20,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "hweno.h"
 #include "hweno_internal.h"
 
@@ -45,27 +43,14 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchDoubles
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, looked up once per
-// device (with that device current) and cached for the life of the process:
-// after cudaDeviceReset the cached address is stale, so the library must not
-// be used across a device reset.
+// Device address of the scratch on the current device, looked up on every
+// call (cheap next to the call's stream synchronisation), so that a device
+// reset or a re-created context never leaves a stale address behind.
 hweno_status scratch_on_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return HWENO_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return HWENO_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return HWENO_ERR_CUDA;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return HWENO_ERR_CUDA;
+  *out = static_cast<double*>(p);
   return HWENO_OK;
 }
 
