@@ -168,6 +168,32 @@ def emit_map(name, rows, nd_in="d", out="o"):
     return "\n".join(lines)
 
 
+def emit_map_x2(name, rows):
+    """The same map on pairs of FP32 data (two components of one cell), in
+    packed FP32 arithmetic: each coefficient is a broadcast pair and every
+    term one packed fma, so a pair of values costs the instructions of one;
+    the terms run in the order of emit_map's, the first a product."""
+    lines = ["__device__ __forceinline__ void %s(const float2* d, float2* o) {" % name,
+             "  float2 a;"]
+    for p, row in enumerate(rows):
+        first = True
+        for j, v in enumerate(row):
+            s = lit(v)
+            if s is None:
+                continue
+            c = "hw2_pair(%s)" % s[2:-1]
+            if first:
+                lines.append("  a = __fmul2_rn(%s, d[%d]);" % (c, j))
+                first = False
+            else:
+                lines.append("  a = __ffma2_rn(%s, d[%d], a);" % (c, j))
+        if first:
+            lines.append("  a = make_float2(0.0f, 0.0f);")
+        lines.append("  o[%d] = a;" % p)
+    lines.append("}")
+    return "\n".join(lines)
+
+
 def emit_beta(name, D, forms):
     lines = ["template <typename R>",
              "__device__ __forceinline__ R %s(const R* d) {" % name,
@@ -254,6 +280,10 @@ def main():
     M0 = p0_map()
     MQ = {n: quad_map(n) for n in (1, 2, 3, 4)}
     B4, B2 = gram(4), gram(2)
+    out.append("// a coefficient as a broadcast pair of FP32 values (the packed maps below)\n"
+               "__device__ __forceinline__ float2 hw2_pair(double c) {\n"
+               "  return make_float2((float)c, (float)c);\n"
+               "}")
     for ng in (2, 3):
         pts = points(ng)
         nf = 4 * ng
@@ -261,6 +291,8 @@ def main():
                    (ng, nf, ng * ng))
         out.append(emit_map("p0_faces_ng%d" % ng, value_map(M0, 4, pts[:nf])))
         out.append(emit_map("p0_interior_ng%d" % ng, value_map(M0, 4, pts[nf:])))
+        out.append(emit_map_x2("p0_faces_ng%d_x2" % ng, value_map(M0, 4, pts[:nf])))
+        out.append(emit_map_x2("p0_interior_ng%d_x2" % ng, value_map(M0, 4, pts[nf:])))
         for n in (1, 2, 3, 4):
             out.append(emit_map("q%d_faces_ng%d" % (n, ng), value_map(MQ[n], 2, pts[:nf])))
     D0, F0 = ldl_forms(B4, M0)

@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   using SM = Smem2D<R, C, NG, COMP>;
   SM& sm = *reinterpret_cast<SM*>(smem_raw);
   constexpr int NF = 4 * NG, NI = NG * NG;
+  // FP32 Euler: the linear p0 maps take two components at once (packed FP32)
+  constexpr bool kPacked = C == 4 && sizeof(R) == 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nx = a.nx, ny = a.ny;
   const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
@@ -511,14 +513,34 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
       for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 2 + dj][ci + 2 + di] != 0;
     if (!hw) {
+      if constexpr (kPacked) {
+        // FP32 Euler: components (0, 1) and (2, 3) through the packed map
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        R d[19], v[NF];
-        gather_data<COMP>(sm, c, ci, cj, d);
-        p0_faces<NG>(d, v);
+        for (int c = 0; c < C; c += 2) {
+          R da[19], db[19];
+          gather_data<COMP>(sm, c, ci, cj, da);
+          gather_data<COMP>(sm, c + 1, ci, cj, db);
+          float2 d2[19], v2[NF];
 #pragma unroll
-        for (int p = 0; p < NF; ++p)
-          if (p >= p_lo && p < p_hi) store_point(sm, c, p, ci, cj, v[p]);
+          for (int k = 0; k < 19; ++k) d2[k] = make_float2(da[k], db[k]);
+          p0_faces_x2<NG>(d2, v2);
+#pragma unroll
+          for (int p = 0; p < NF; ++p)
+            if (p >= p_lo && p < p_hi) {
+              store_point(sm, c, p, ci, cj, v2[p].x);
+              store_point(sm, c + 1, p, ci, cj, v2[p].y);
+            }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          R d[19], v[NF];
+          gather_data<COMP>(sm, c, ci, cj, d);
+          p0_faces<NG>(d, v);
+#pragma unroll
+          for (int p = 0; p < NF; ++p)
+            if (p >= p_lo && p < p_hi) store_point(sm, c, p, ci, cj, v[p]);
+        }
       }
     }
     list_append(&sm.nhw, sm.hwl, item, hw, TX * TY + 2 * TX + 2 * TY);
@@ -577,11 +599,29 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     for (int c = 0; c < C; ++c) Fv[c] = Gv[c] = R(0);
     {
       R inter[C][NI];
+      if constexpr (kPacked) {
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        R d[19];
-        gather_data<COMP>(sm, c, ci, cj, d);
-        p0_interior<NG>(d, inter[c]);
+        for (int c = 0; c < C; c += 2) {
+          R da[19], db[19];
+          gather_data<COMP>(sm, c, ci, cj, da);
+          gather_data<COMP>(sm, c + 1, ci, cj, db);
+          float2 d2[19], i2[NI];
+#pragma unroll
+          for (int k = 0; k < 19; ++k) d2[k] = make_float2(da[k], db[k]);
+          p0_interior_x2<NG>(d2, i2);
+#pragma unroll
+          for (int l = 0; l < NI; ++l) {
+            inter[c][l] = i2[l].x;
+            inter[c + 1][l] = i2[l].y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          R d[19];
+          gather_data<COMP>(sm, c, ci, cj, d);
+          p0_interior<NG>(d, inter[c]);
+        }
       }
 #pragma unroll
       for (int l = 0; l < NG; ++l)

@@ -159,6 +159,15 @@ template <int NG, typename R>
 __device__ __forceinline__ void p0_interior(const R* d, R* o) {
   if constexpr (NG == 3) hw2::p0_interior_ng3(d, o); else hw2::p0_interior_ng2(d, o);
 }
+// The same two maps on two components of a cell at once (packed FP32).
+template <int NG>
+__device__ __forceinline__ void p0_faces_x2(const float2* d, float2* o) {
+  if constexpr (NG == 3) hw2::p0_faces_ng3_x2(d, o); else hw2::p0_faces_ng2_x2(d, o);
+}
+template <int NG>
+__device__ __forceinline__ void p0_interior_x2(const float2* d, float2* o) {
+  if constexpr (NG == 3) hw2::p0_interior_ng3_x2(d, o); else hw2::p0_interior_ng2_x2(d, o);
+}
 template <int NG, typename R>
 __device__ __forceinline__ void q_faces(int n, const R* d, R* o) {
   if constexpr (NG == 3) {

@@ -41,7 +41,7 @@ def main():
     ap.add_argument("--nx", type=int, default=65536)
     ap.add_argument("--rk-steps", type=int, default=10)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32c", "fp64"],
-                    help="fp32c: FP32 with float-pair averages (1D, the resident launch)")
+                    help="fp32c: FP32 with float-pair averages (1D: the resident launch)")
     ap.add_argument("--system", default="euler", choices=["euler", "burgers"])
     ap.add_argument("--seed", type=int, default=20250)
     ap.add_argument("--dim", type=int, default=1, choices=[1, 2])

@@ -69,3 +69,30 @@ def test_generated_maps_match_the_oracle(ng):
         got = [sum(w * sum(c * d[j] for j, c in f.items()) ** 2 for w, f in BETAS[name])
                for name in ("beta_p0", "beta_q1", "beta_q2", "beta_q3", "beta_q4")]
         np.testing.assert_allclose(got, beta, rtol=1e-11)
+
+
+def _parse_x2():
+    """The packed (two components at once) copies of the p0 maps: {name of
+    the scalar map: {point: {datum: coefficient}}}."""
+    txt = open(HDR).read()
+    maps = {}
+    for m in re.finditer(r"void (\w+)_x2\(const float2\* d, float2\* o\) \{(.*?)\n\}", txt, re.S):
+        rows, cur = {}, {}
+        for line in m.group(2).splitlines():
+            t = re.match(r"\s*a = __f(?:mul|fma)2_rn\(hw2_pair\(([-0-9.eE+]+)\), d\[(\d+)\]", line)
+            if t:
+                cur[int(t.group(2))] = float(t.group(1))
+                continue
+            o = re.match(r"\s*o\[(\d+)\] = a;", line)
+            if o:
+                rows[int(o.group(1))] = cur
+                cur = {}
+        maps[m.group(1)] = rows
+    return maps
+
+
+def test_packed_maps_are_the_scalar_maps():
+    x2 = _parse_x2()
+    assert set(x2) == {"p0_faces_ng2", "p0_interior_ng2", "p0_faces_ng3", "p0_interior_ng3"}
+    for name, rows in x2.items():
+        assert rows == MAPS[name], name
