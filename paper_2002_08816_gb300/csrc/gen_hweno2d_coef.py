@@ -228,6 +228,29 @@ def emit_map_T(name, rows):
     return "\n".join(lines)
 
 
+def emit_map_T_x2(name, rows):
+    """emit_map_T on pairs of FP32 data (two components), in packed FP32: the
+    sum of each row formed as in emit_map_x2, then added to g."""
+    lines = ["__device__ __forceinline__ void %s(const float2* l, float2* g) {" % name,
+             "  float2 a;"]
+    for j in range(19):
+        first = True
+        for p, row in enumerate(rows):
+            s = lit(row[j])
+            if s is None:
+                continue
+            c = "hw2_pair(%s)" % s[2:-1]
+            if first:
+                lines.append("  a = __fmul2_rn(%s, l[%d]);" % (c, p))
+                first = False
+            else:
+                lines.append("  a = __ffma2_rn(%s, l[%d], a);" % (c, p))
+        if not first:
+            lines.append("  g[%d] = __fadd2_rn(g[%d], a);" % (j, j))
+    lines.append("}")
+    return "\n".join(lines)
+
+
 def emit_beta_grad(name, D, forms):
     lines = ["template <typename R>",
              "__device__ __forceinline__ void %s(const R* d, R s, R* g) {" % name,
@@ -249,6 +272,7 @@ def main_adjoint():
            "// Zhao & Qiu, arXiv:2002.08816, Sec. 2.2 Step 5: transposed point maps and\n"
            "// smoothness-indicator gradients.  Do not edit: rerun the generator.\n"
            "#pragma once\n"
+           "#include \"hweno2d_coef.cuh\"  // hw2_pair\n"
            "namespace hw2 {"]
     M0 = p0_map()
     MQ = {n: quad_map(n) for n in (1, 2, 3, 4)}
@@ -259,6 +283,8 @@ def main_adjoint():
         out.append("// ---- %d Gauss points per direction" % ng)
         out.append(emit_map_T("p0_faces_ng%d_T" % ng, value_map(M0, 4, pts[:nf])))
         out.append(emit_map_T("p0_interior_ng%d_T" % ng, value_map(M0, 4, pts[nf:])))
+        out.append(emit_map_T_x2("p0_faces_ng%d_T_x2" % ng, value_map(M0, 4, pts[:nf])))
+        out.append(emit_map_T_x2("p0_interior_ng%d_T_x2" % ng, value_map(M0, 4, pts[nf:])))
         for n in (1, 2, 3, 4):
             out.append(emit_map_T("q%d_faces_ng%d_T" % (n, ng), value_map(MQ[n], 2, pts[:nf])))
     D0, F0 = ldl_forms(B4, M0)

@@ -392,16 +392,37 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
     for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 1 + dj][ci + 1 + di] != 0;
 
-  // point values (the forward's)
+  // point values (the forward's); FP32 Euler: the linear maps on pairs of
+  // components in packed FP32, as the forward stage kernel
+  constexpr bool kPacked = C == 4 && sizeof(R) == 4;
   R P[C][NP];
+  if constexpr (kPacked) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    R d[19];
-    gather19a(sm, c, ci, cj, d);
-    p0_faces<NG>(d, P[c]);
-    p0_interior<NG>(d, &P[c][NF]);
-    if constexpr (C == 1) {
-      if (hw) hweno2d_faces<NG>(d, P_.gam, P_.eps, 0, NF, P[c]);
+    for (int c = 0; c < C; c += 2) {
+      R da[19], db[19];
+      gather19a(sm, c, ci, cj, da);
+      gather19a(sm, c + 1, ci, cj, db);
+      float2 d2[19], v2[NP];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) d2[k] = make_float2(da[k], db[k]);
+      p0_faces_x2<NG>(d2, v2);
+      p0_interior_x2<NG>(d2, &v2[NF]);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        P[c][p] = v2[p].x;
+        P[c + 1][p] = v2[p].y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      R d[19];
+      gather19a(sm, c, ci, cj, d);
+      p0_faces<NG>(d, P[c]);
+      p0_interior<NG>(d, &P[c][NF]);
+      if constexpr (C == 1) {
+        if (hw) hweno2d_faces<NG>(d, P_.gam, P_.eps, 0, NF, P[c]);
+      }
     }
   }
   if constexpr (C == 4) {
@@ -508,24 +529,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     }
   }
   R* __restrict__ part = static_cast<R*>(a.G) + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (C * 3 * BX * BY);
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    R g[19];
-#pragma unroll
-    for (int k = 0; k < 19; ++k) g[k] = R(0);
-    if (own) {
-      if (!hw) {
-        p0_faces_T<NG>(P[c], g);
-      } else if constexpr (C == 1) {
-        R d[19];
-        gather19a(sm, c, ci, cj, d);
-        hweno2d_faces_vjp<NG>(d, P_.gam, P_.eps, P[c], g);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 19; ++k) g[k] = Gl[c][k];
-      }
-      p0_interior_T<NG>(&P[c][NF], g);
-    }
+  // the tile's sums of its cells' stencil adjoints g for component c, in a
+  // fixed order (deterministic)
+  auto exchange = [&](int c, const R* g) {
 #pragma unroll
     for (int k = 0; k < 19; ++k) sm.g[k][cj][ci] = g[k];
     __syncthreads();
@@ -541,6 +547,54 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       for (int q = 0; q < 3; ++q) part[(c * 3 + q) * (BX * BY) + t] = m[q];
     }
     __syncthreads();
+  };
+  if constexpr (kPacked) {
+#pragma unroll
+    for (int c = 0; c < C; c += 2) {
+      float2 g2[19];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) g2[k] = make_float2(0.0f, 0.0f);
+      if (own) {
+        float2 l2[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) l2[p] = make_float2(P[c][p], P[c + 1][p]);
+        if (!hw) {
+          p0_faces_T_x2<NG>(l2, g2);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 19; ++k) g2[k] = make_float2(Gl[c][k], Gl[c + 1][k]);
+        }
+        p0_interior_T_x2<NG>(&l2[NF], g2);
+      }
+      R g[19];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) g[k] = g2[k].x;
+      exchange(c, g);
+#pragma unroll
+      for (int k = 0; k < 19; ++k) g[k] = g2[k].y;
+      exchange(c + 1, g);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      R g[19];
+#pragma unroll
+      for (int k = 0; k < 19; ++k) g[k] = R(0);
+      if (own) {
+        if (!hw) {
+          p0_faces_T<NG>(P[c], g);
+        } else if constexpr (C == 1) {
+          R d[19];
+          gather19a(sm, c, ci, cj, d);
+          hweno2d_faces_vjp<NG>(d, P_.gam, P_.eps, P[c], g);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 19; ++k) g[k] = Gl[c][k];
+        }
+        p0_interior_T<NG>(&P[c][NF], g);
+      }
+      exchange(c, g);
+    }
   }
 }
 

@@ -121,6 +121,15 @@ template <int NG, typename R>
 __device__ __forceinline__ void p0_interior_T(const R* l, R* g) {
   if constexpr (NG == 3) hw2::p0_interior_ng3_T(l, g); else hw2::p0_interior_ng2_T(l, g);
 }
+// The same two transposes on two components at once (packed FP32).
+template <int NG>
+__device__ __forceinline__ void p0_faces_T_x2(const float2* l, float2* g) {
+  if constexpr (NG == 3) hw2::p0_faces_ng3_T_x2(l, g); else hw2::p0_faces_ng2_T_x2(l, g);
+}
+template <int NG>
+__device__ __forceinline__ void p0_interior_T_x2(const float2* l, float2* g) {
+  if constexpr (NG == 3) hw2::p0_interior_ng3_T_x2(l, g); else hw2::p0_interior_ng2_T_x2(l, g);
+}
 template <int NG, typename R>
 __device__ __forceinline__ void q_faces_T(int n, const R* l, R* g) {
   if constexpr (NG == 3) {

@@ -96,3 +96,36 @@ def test_packed_maps_are_the_scalar_maps():
     assert set(x2) == {"p0_faces_ng2", "p0_interior_ng2", "p0_faces_ng3", "p0_interior_ng3"}
     for name, rows in x2.items():
         assert rows == MAPS[name], name
+
+
+ADJ = os.path.join(os.path.dirname(HDR), "hweno2d_adj_coef.cuh")
+
+
+def test_packed_transposes_are_the_scalar_transposes():
+    """The adjoint's packed transposed p0 maps hold the coefficients of its
+    scalar ones (which the GPU adjoint tests hold to the oracle's gradient)."""
+    txt = open(ADJ).read()
+    scalar, packed = {}, {}
+    for m in re.finditer(r"void (p0_\w+_T)\(const R\* l, R\* g\) \{(.*?)\n\}", txt, re.S):
+        rows = {}
+        for line in m.group(2).strip().splitlines():
+            mm = re.match(r"\s*g\[(\d+)\] \+= (.*);", line)
+            rows[int(mm.group(1))] = {int(p): float(c) for c, p in
+                                      re.findall(r"R\(([-0-9.eE+]+)\) \* l\[(\d+)\]", mm.group(2))}
+        scalar[m.group(1)] = rows
+    for m in re.finditer(r"void (p0_\w+_T)_x2\(const float2\* l, float2\* g\) \{(.*?)\n\}", txt, re.S):
+        rows, cur = {}, {}
+        for line in m.group(2).splitlines():
+            t = re.match(r"\s*a = __f(?:mul|fma)2_rn\(hw2_pair\(([-0-9.eE+]+)\), l\[(\d+)\]", line)
+            if t:
+                cur[int(t.group(2))] = float(t.group(1))
+                continue
+            o = re.match(r"\s*g\[(\d+)\] = __fadd2_rn\(g\[\d+\], a\);", line)
+            if o:
+                rows[int(o.group(1))] = cur
+                cur = {}
+        packed[m.group(1)] = rows
+    assert set(packed) == set(scalar) == {"p0_faces_ng2_T", "p0_interior_ng2_T",
+                                          "p0_faces_ng3_T", "p0_interior_ng3_T"}
+    for name in scalar:
+        assert packed[name] == scalar[name], name
