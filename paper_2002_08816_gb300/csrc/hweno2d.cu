@@ -597,53 +597,51 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     R Fv[C], Gv[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) Fv[c] = Gv[c] = R(0);
-    {
-      R inter[C][NI];
-      if constexpr (kPacked) {
+    R inter[C][NI];
+    if constexpr (kPacked) {
 #pragma unroll
-        for (int c = 0; c < C; c += 2) {
-          R da[19], db[19];
-          gather_data<COMP>(sm, c, ci, cj, da);
-          gather_data<COMP>(sm, c + 1, ci, cj, db);
-          float2 d2[19], i2[NI];
+      for (int c = 0; c < C; c += 2) {
+        R da[19], db[19];
+        gather_data<COMP>(sm, c, ci, cj, da);
+        gather_data<COMP>(sm, c + 1, ci, cj, db);
+        float2 d2[19], i2[NI];
 #pragma unroll
-          for (int k = 0; k < 19; ++k) d2[k] = make_float2(da[k], db[k]);
-          p0_interior_x2<NG>(d2, i2);
+        for (int k = 0; k < 19; ++k) d2[k] = make_float2(da[k], db[k]);
+        p0_interior_x2<NG>(d2, i2);
 #pragma unroll
-          for (int l = 0; l < NI; ++l) {
-            inter[c][l] = i2[l].x;
-            inter[c + 1][l] = i2[l].y;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          R d[19];
-          gather_data<COMP>(sm, c, ci, cj, d);
-          p0_interior<NG>(d, inter[c]);
+        for (int l = 0; l < NI; ++l) {
+          inter[c][l] = i2[l].x;
+          inter[c + 1][l] = i2[l].y;
         }
       }
+    } else {
 #pragma unroll
-      for (int l = 0; l < NG; ++l)
-#pragma unroll
-        for (int k = 0; k < NG; ++k) {
-          R U[C], f[C], g[C];
-#pragma unroll
-          for (int c = 0; c < C; ++c) U[c] = inter[c][l * NG + k];
-          flux(U, 0, f);
-          flux(U, 1, g);
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            Fv[c] += gw[k] * gw[l] * f[c];
-            Gv[c] += gw[k] * gw[l] * g[c];
-          }
-        }
+      for (int c = 0; c < C; ++c) {
+        R d[19];
+        gather_data<COMP>(sm, c, ci, cj, d);
+        p0_interior<NG>(d, inter[c]);
+      }
     }
+    // the volume integrals of Eq. (ode2) at interior point p (weight
+    // gw[p % NG] gw[p / NG])
+    auto interior_point = [&](int p) {
+      R U[C], f[C], g[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) U[c] = inter[c][p];
+      flux(U, 0, f);
+      flux(U, 1, g);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        Fv[c] += gw[p % NG] * gw[p / NG] * f[c];
+        Gv[c] += gw[p % NG] * gw[p / NG] * g[c];
+      }
+    };
     R sfx[C], sfs[C], sfxe[C], sgy[C], sgs[C], sgyx[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) sfx[c] = sfs[c] = sfxe[c] = sgy[c] = sgs[c] = sgyx[c] = R(0);
-#pragma unroll
-    for (int k = 0; k < NG; ++k) {
+    // the Lax-Friedrichs fluxes of the four faces at Gauss point k and their
+    // weighted sums
+    auto face_point = [&](int k) {
       R am[C], ap[C], fa[C], fb[C], FLk[C], FRk[C], GBk[C], GTk[C];
       // x_{i-1/2}: u^- = right face of cell i-1, u^+ = own left face
 #pragma unroll
@@ -682,6 +680,102 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
         sgs[c] += gw[k] * (GBk[c] + GTk[c]);
         sgyx[c] += gw[k] * gx[k] * (GTk[c] - GBk[c]);
       }
+    };
+    if constexpr (kPacked && !COMP) {
+      // FP32 Euler: points in pairs, (interior p, p + 1) and (Gauss k, k + 1)
+      // of every face, each flux, Lax-Friedrichs flux and weighted sum in
+      // packed FP32; the pairs' halves are added at the end and an odd last
+      // point (3 Gauss points) runs alone
+      float2 Fv2[C], Gv2[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) Fv2[c] = Gv2[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int p = 0; p + 1 < NI; p += 2) {
+        float2 U2[C], f2[C], g2[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) U2[c] = make_float2(inter[c][p], inter[c][p + 1]);
+        euler_flux_x2(gas, U2, 0, f2);
+        euler_flux_x2(gas, U2, 1, g2);
+        const float2 w2 = make_float2(gw[p % NG] * gw[p / NG], gw[(p + 1) % NG] * gw[(p + 1) / NG]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          Fv2[c] = __ffma2_rn(w2, f2[c], Fv2[c]);
+          Gv2[c] = __ffma2_rn(w2, g2[c], Gv2[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        Fv[c] = Fv2[c].x + Fv2[c].y;
+        Gv[c] = Gv2[c].x + Gv2[c].y;
+      }
+      if constexpr (NI % 2 == 1) interior_point(NI - 1);
+      float2 sfx2[C], sfs2[C], sfxe2[C], sgy2[C], sgs2[C], sgyx2[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        sfx2[c] = sfs2[c] = sfxe2[c] = sgy2[c] = sgs2[c] = sgyx2[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k + 1 < NG; k += 2) {
+        const float2 gw2 = make_float2(gw[k], gw[k + 1]);
+        const float2 gwx2 = make_float2(gw[k] * gx[k], gw[k + 1] * gx[k + 1]);
+        float2 am[C], ap[C], fa[C], fb[C], FL[C], FR[C], GB[C], GT[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          am[c] = make_float2(sm.xf[c][NG + k][cj][ci], sm.xf[c][NG + k + 1][cj][ci]);
+          ap[c] = make_float2(sm.xf[c][k][cj][ci + 1], sm.xf[c][k + 1][cj][ci + 1]);
+        }
+        euler_flux_x2(gas, am, 0, fa); euler_flux_x2(gas, ap, 0, fb);
+#pragma unroll
+        for (int c = 0; c < C; ++c) FL[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hax);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          am[c] = make_float2(sm.xf[c][NG + k][cj][ci + 1], sm.xf[c][NG + k + 1][cj][ci + 1]);
+          ap[c] = make_float2(sm.xf[c][k][cj][ci + 2], sm.xf[c][k + 1][cj][ci + 2]);
+        }
+        euler_flux_x2(gas, am, 0, fa); euler_flux_x2(gas, ap, 0, fb);
+#pragma unroll
+        for (int c = 0; c < C; ++c) FR[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hax);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          am[c] = make_float2(sm.yf[c][NG + k][cj][ci], sm.yf[c][NG + k + 1][cj][ci]);
+          ap[c] = make_float2(sm.yf[c][k][cj + 1][ci], sm.yf[c][k + 1][cj + 1][ci]);
+        }
+        euler_flux_x2(gas, am, 1, fa); euler_flux_x2(gas, ap, 1, fb);
+#pragma unroll
+        for (int c = 0; c < C; ++c) GB[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hay);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          am[c] = make_float2(sm.yf[c][NG + k][cj + 1][ci], sm.yf[c][NG + k + 1][cj + 1][ci]);
+          ap[c] = make_float2(sm.yf[c][k][cj + 2][ci], sm.yf[c][k + 1][cj + 2][ci]);
+        }
+        euler_flux_x2(gas, am, 1, fa); euler_flux_x2(gas, ap, 1, fb);
+#pragma unroll
+        for (int c = 0; c < C; ++c) GT[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hay);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float2 dx = sub2(FR[c], FL[c]), dy = sub2(GT[c], GB[c]);
+          sfx2[c] = __ffma2_rn(gw2, dx, sfx2[c]);
+          sfs2[c] = __ffma2_rn(gw2, __fadd2_rn(FL[c], FR[c]), sfs2[c]);
+          sfxe2[c] = __ffma2_rn(gwx2, dx, sfxe2[c]);
+          sgy2[c] = __ffma2_rn(gw2, dy, sgy2[c]);
+          sgs2[c] = __ffma2_rn(gw2, __fadd2_rn(GB[c], GT[c]), sgs2[c]);
+          sgyx2[c] = __ffma2_rn(gwx2, dy, sgyx2[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        sfx[c] = sfx2[c].x + sfx2[c].y;
+        sfs[c] = sfs2[c].x + sfs2[c].y;
+        sfxe[c] = sfxe2[c].x + sfxe2[c].y;
+        sgy[c] = sgy2[c].x + sgy2[c].y;
+        sgs[c] = sgs2[c].x + sgs2[c].y;
+        sgyx[c] = sgyx2[c].x + sgyx2[c].y;
+      }
+      if constexpr (NG % 2 == 1) face_point(NG - 1);
+    } else {
+#pragma unroll
+      for (int p = 0; p < NI; ++p) interior_point(p);
+#pragma unroll
+      for (int k = 0; k < NG; ++k) face_point(k);
     }
     R Uo[C];
 #pragma unroll

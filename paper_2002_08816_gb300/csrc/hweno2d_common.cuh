@@ -86,6 +86,32 @@ __device__ __forceinline__ void phys_flux2(R gas, const R* U, int dir, R* F) {
   }
 }
 
+// ------------------------------------------------ packed FP32 (pairs of points)
+
+__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+// a - b (one rounding, as the subtraction)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(bcast2(-1.0f), b, a);
+}
+// The Euler flux f (dir 0) or g (dir 1) of two states at once (each component
+// a pair), the arithmetic of Euler2D<float>::flux in packed FP32.
+__device__ __forceinline__ void euler_flux_x2(float gas, const float2* U, int dir, float2* F) {
+  const float2 rho = U[0], m = U[1], n = U[2], E = U[3];
+  const float2 ir = make_float2(fast_rcp(rho.x), fast_rcp(rho.y));
+  const float2 mu = __fmul2_rn(m, ir), nu = __fmul2_rn(n, ir);
+  const float2 q = __ffma2_rn(n, nu, __fmul2_rn(m, mu));  // m mu + n nu
+  const float2 p = __fmul2_rn(bcast2(gas - 1.0f), __ffma2_rn(bcast2(-0.5f), q, E));
+  const float2 vn = dir == 0 ? mu : nu;
+  F[0] = dir == 0 ? m : n;
+  F[1] = dir == 0 ? __ffma2_rn(m, vn, p) : __fmul2_rn(m, vn);
+  F[2] = dir == 1 ? __ffma2_rn(n, vn, p) : __fmul2_rn(n, vn);
+  F[3] = __fmul2_rn(vn, __fadd2_rn(E, p));
+}
+// The Lax-Friedrichs flux (f(u^-) + f(u^+)) / 2 - h (u^+ - u^-) of two points.
+__device__ __forceinline__ float2 lf_x2(float2 fm, float2 fp, float2 um, float2 up, float h) {
+  return __ffma2_rn(bcast2(-h), sub2(up, um), __fmul2_rn(bcast2(0.5f), __fadd2_rn(fm, fp)));
+}
+
 // f(B + D) - f(B) (dir 0) or g(B + D) - g(B) (dir 1) for a base state B and
 // an increment D, FP32, with rounding errors relative to the increment (no
 // difference of O(|f|) terms; the float-pair precision HWENO_FP32C): with
