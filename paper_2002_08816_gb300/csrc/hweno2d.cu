@@ -51,11 +51,15 @@ static_assert(TX * TY == NT, "one own cell per thread");
 template <typename R, int C, int NG, bool COMP = false>
 struct Smem2D {
   static constexpr int kPadX = 1;  // raw index of flag-grid column lx: lx + 2
-  alignas(128) R u[C][3][RY][RX];  // stage input (the TMA box)
+  // the limiter's results go to `lim` by work-list slot (and are written into
+  // u once every cell's flag and limiter has read the raw moments)
+  static constexpr bool kLimList = true;
+  // stage input (the TMA box); after Step 4 its first moments are the
+  // modified ones
+  alignas(128) R u[C][3][RY][RX];
   // HWENO_FP32C: the low parts of the stage input's averages (a second box)
   alignas(128) R ulo[COMP ? C : 1][COMP ? RY : 1][COMP ? RX : 1];
-  R vl[C][LY][LX];              // modified x-moments
-  R wl[C][LY][LX];              // modified y-moments
+  R lim[C == 4 ? LX * LY : 1][C][2];  // Euler: modified x-, y-moments by list slot
   R xf[C][2 * NG][TY][TX + 2];  // x-face values (left NG, right NG) of cells -1..TX
   R yf[C][2 * NG][TY + 2][TX];  // y-face values (bottom NG, top NG) of cells -1..TY
   uint8_t fl[LY][LX];
@@ -187,7 +191,8 @@ __device__ __forceinline__ bool kxrcf2_troubled_pair(float u0, float l0, float v
 }
 
 // The 19 data of component c of the cell at own-tile coordinates (ci, cj):
-// ubar of cells 1..9, vbar and wbar (modified) of cells 2, 4, 5, 6, 8.
+// ubar of cells 1..9, vbar and wbar (modified: read after Step 4) of cells
+// 2, 4, 5, 6, 8.
 template <typename S, typename R>
 __device__ __forceinline__ void gather19(const S& sm, int c, int ci, int cj, R* d) {
 #pragma unroll
@@ -195,8 +200,8 @@ __device__ __forceinline__ void gather19(const S& sm, int c, int ci, int cj, R* 
   const int mx[5] = {0, -1, 0, 1, 0}, my[5] = {-1, 0, 0, 0, 1};
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    d[9 + k] = sm.vl[c][cj + 2 + my[k]][ci + 2 + mx[k]];
-    d[14 + k] = sm.wl[c][cj + 2 + my[k]][ci + 2 + mx[k]];
+    d[9 + k] = sm.u[c][1][cj + OYR + my[k]][ci + OXR + mx[k]];
+    d[14 + k] = sm.u[c][2][cj + OYR + my[k]][ci + OXR + mx[k]];
   }
 }
 
@@ -414,8 +419,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   if (a.a_zero && blockIdx.x == 0 && blockIdx.y == 0 && tid < 2 * kAlphaSlots)
     static_cast<R*>(a.a_zero)[tid] = R(0);
 
-  // ---- 2. Step 4 on the tile plus 2 halo cells
-  for (int k = tid; k < LX * LY; k += NT) {
+  // ---- 2. Step 4 on the tile plus 2 halo cells; the modified first moments
+  // of the troubled cells replace the raw ones in the tile only after every
+  // flag and limiter has read the raw ones
+  static_assert(LX * LY <= 2 * NT, "two cells of Step 4 per thread at most");
+  R hv[2][2];       // Burgers: the modified moments of this thread's troubled cells
+  int hk[2] = {-1, -1};
+  int it = 0;
+  for (int k = tid; k < LX * LY; k += NT, ++it) {
     const int lx = k % LX, ly = k / LX;
     const int rx = lx + 1 + SM::kPadX, ry = ly + 1;  // raw index of the cell
     int flag;
@@ -457,31 +468,49 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       }
     }
     sm.fl[ly][lx] = (uint8_t)flag;
-    if (!flag) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        sm.vl[c][ly][lx] = sm.u[c][1][ry][rx];
-        sm.wl[c][ly][lx] = sm.u[c][2][ry][rx];
+    if constexpr (C == 1) {
+      if (flag) {
+        hk[it] = k;
+        hv[it][0] = limit_first_moment(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx],
+                                       sm.u[0][0][ry][rx + 1], sm.u[0][1][ry][rx - 1],
+                                       sm.u[0][1][ry][rx + 1], gam, eps);
+        hv[it][1] = limit_first_moment(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx],
+                                       sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
+                                       sm.u[0][2][ry + 1][rx], gam, eps);
       }
-    } else if constexpr (C == 1) {
-      sm.vl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry][rx - 1], sm.u[0][0][ry][rx],
-                                            sm.u[0][0][ry][rx + 1], sm.u[0][1][ry][rx - 1],
-                                            sm.u[0][1][ry][rx + 1], gam, eps);
-      sm.wl[0][ly][lx] = limit_first_moment(sm.u[0][0][ry - 1][rx], sm.u[0][0][ry][rx],
-                                            sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
-                                            sm.u[0][2][ry + 1][rx], gam, eps);
     }
     // Euler: the troubled cells are listed and limited by consecutive threads
     // below, so a warp holding one or two of them does not run the
     // characteristic limiter for its other lanes' sake
     if constexpr (C == 4) list_append(&sm.ntb, sm.tbl, k, flag != 0, LX * LY);
   }
-  __syncthreads();
-  if constexpr (C == 4) {
+  if constexpr (C == 1) {
+    if (__syncthreads_or(hk[0] >= 0 || hk[1] >= 0)) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (hk[j] >= 0) {
+          const int rx = hk[j] % LX + 1 + SM::kPadX, ry = hk[j] / LX + 1;
+          sm.u[0][1][ry][rx] = hv[j][0];
+          sm.u[0][2][ry][rx] = hv[j][1];
+        }
+      __syncthreads();
+    }
+  } else {
+    __syncthreads();
     if (sm.ntb > 0) {  // uniform over the CTA
       for (int q = tid; q < sm.ntb; q += NT) {
         const int k = sm.tbl[q];
-        limit_euler2d(sm, k % LX, k / LX, gam[0], gam[1], gam[2], gam[3], gam[4], eps, gas);
+        limit_euler2d(sm, k % LX, k / LX, q, gam[0], gam[1], gam[2], gam[3], gam[4], eps, gas);
+      }
+      __syncthreads();
+      for (int q = tid; q < sm.ntb; q += NT) {
+        const int k = sm.tbl[q];
+        const int rx = k % LX + 1 + SM::kPadX, ry = k / LX + 1;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          sm.u[c][1][ry][rx] = sm.lim[q][c][0];
+          sm.u[c][2][ry][rx] = sm.lim[q][c][1];
+        }
       }
       __syncthreads();
     }
@@ -785,10 +814,13 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
       const R L2 = -sfxe[c] * inv_dx - R(0.5) * sgs[c] * inv_dy + Gv[c] * inv_dy;
       // the stage input the combination uses: first moments as modified by
       // Step 4 (stored, the default), or unmodified (variant)
+      // (the tile holds the modified ones; the raw ones of an own cell are
+      // read back from the stage input)
       const bool raw = (a.variant & HWENO_VARIANT_RAW_COMBINE) != 0;
+      const size_t sw = (size_t)gj * nx + gi;
       const R W[3] = {sm.u[c][0][cj + OYR][ci + OXR],
-                      raw ? sm.u[c][1][cj + OYR][ci + OXR] : sm.vl[c][cj + 2][ci + 2],
-                      raw ? sm.u[c][2][cj + OYR][ci + OXR] : sm.wl[c][cj + 2][ci + 2]};
+                      raw ? (own ? w[(3 * c + 1) * plane + sw] : R(0)) : sm.u[c][1][cj + OYR][ci + OXR],
+                      raw ? (own ? w[(3 * c + 2) * plane + sw] : R(0)) : sm.u[c][2][cj + OYR][ci + OXR]};
       const R Lm[3] = {L0, L1, L2};
       R o[3];
 #pragma unroll
@@ -830,7 +862,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
         if constexpr (COMP) a.out_lo[c * plane + s] = olo;
         if (a.lim_out) {  // rhs mode: the modified moments; stage 1: what stages 2-3 combine
           R* lo = static_cast<R*>(a.lim_out);
-          const R M[3] = {W[0], sm.vl[c][cj + 2][ci + 2], sm.wl[c][cj + 2][ci + 2]};
+          const R M[3] = {W[0], sm.u[c][1][cj + OYR][ci + OXR], sm.u[c][2][cj + OYR][ci + OXR]};
 #pragma unroll
           for (int m = 0; m < 3; ++m) lo[(3 * c + m) * plane + s] = a.stage == 0 ? M[m] : W[m];
         }

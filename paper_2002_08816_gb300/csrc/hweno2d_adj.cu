@@ -50,6 +50,7 @@ static_assert(TX * TY == NT, "one own cell per thread");
 template <typename R, int C>
 struct SmemA {
   static constexpr int kPadX = 2;  // raw index of flag-grid column lx: lx + 1 + 2
+  static constexpr bool kLimList = false;  // the limiter writes vl / wl
   alignas(128) R u[C][3][AY][AXA];   // raw stage input (a TMA box)
   alignas(128) R lam[C][3][BY][LXA]; // lam, the adjoint of the stage output (a TMA box;
                                      // b dt is applied where it is used)
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
                                             sm.u[0][0][ry + 1][rx], sm.u[0][2][ry - 1][rx],
                                             sm.u[0][2][ry + 1][rx], P_.gam, P_.eps);
     } else {
-      limit_euler2d(sm, lx, ly, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4], P_.eps,
+      limit_euler2d(sm, lx, ly, 0, P_.gam[0], P_.gam[1], P_.gam[2], P_.gam[3], P_.gam[4], P_.eps,
                     P_.gas);
     }
   }

@@ -252,11 +252,12 @@ __device__ __forceinline__ void hweno2d_faces(const R* d, const R* gam, R eps, i
 
 // Step 4 for a troubled Euler cell (lx, ly) of the flag grid: vbar from the
 // x-neighbours in the x characteristic fields, wbar from the y-neighbours in
-// the y fields, with the 1D Step 1 formula.  Rare: kept out of line so that
+// the y fields, with the 1D Step 1 formula, written to sm.lim[slot] (S with
+// kLimList) or to sm.vl / sm.wl at (lx, ly).  Rare: kept out of line so that
 // its registers do not weigh on the common path.
 template <typename S, typename R>
-__device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, R g0, R g1, R g2, R g3, R g4,
-                                           R eps, R gas) {
+__device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, int slot, R g0, R g1, R g2,
+                                           R g3, R g4, R eps, R gas) {
   const R gam[5] = {g0, g1, g2, g3, g4};  // by value: no caller array on the stack
   const int rx = lx + 1 + S::kPadX, ry = ly + 1;  // raw index of the cell
   R U[4];
@@ -290,7 +291,9 @@ __device__ __noinline__ void limit_euler2d(S& sm, int lx, int ly, R g0, R g1, R 
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const R v = Rm[c][0] * q[0] + Rm[c][1] * q[1] + Rm[c][2] * q[2] + Rm[c][3] * q[3];
-      if (dir == 0) sm.vl[c][ly][lx] = v; else sm.wl[c][ly][lx] = v;
+      if constexpr (S::kLimList) sm.lim[slot][c][dir] = v;
+      else if (dir == 0) sm.vl[c][ly][lx] = v;
+      else sm.wl[c][ly][lx] = v;
     }
   }
 }
