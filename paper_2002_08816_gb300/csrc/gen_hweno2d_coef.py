@@ -213,6 +213,34 @@ def emit_beta(name, D, forms):
     return "\n".join(lines)
 
 
+def emit_beta_x2(name, D, forms):
+    """emit_beta on pairs of FP32 data (two characteristic fields), in packed
+    FP32: each linear form as in emit_map_x2, then b += D t t."""
+    lines = ["__device__ __forceinline__ float2 %s(const float2* d) {" % name,
+             "  float2 b = make_float2(0.0f, 0.0f), t;"]
+    for k in range(forms.shape[0]):
+        terms = [(j, lit(forms[k, j])) for j in range(19)]
+        terms = [(j, c) for j, c in terms if c is not None]
+        if not terms:
+            continue
+        for i, (j, c) in enumerate(terms):
+            cc = "hw2_pair(%s)" % c[2:-1]
+            if i == 0:
+                if forms[k, j] == 1:
+                    lines.append("  t = d[%d];" % j)
+                else:
+                    lines.append("  t = __fmul2_rn(%s, d[%d]);" % (cc, j))
+            else:
+                lines.append("  t = __ffma2_rn(%s, d[%d], t);" % (cc, j))
+        if D[k] == 1:
+            lines.append("  b = __ffma2_rn(t, t, b);")
+        else:
+            lines.append("  b = __ffma2_rn(__fmul2_rn(hw2_pair(%s), t), t, b);" % lit(D[k])[2:-1])
+    lines.append("  return b;")
+    lines.append("}")
+    return "\n".join(lines)
+
+
 def emit_map_T(name, rows):
     lines = ["template <typename R>",
              "__device__ __forceinline__ void %s(const R* l, R* g) {" % name]
@@ -321,12 +349,18 @@ def main():
         out.append(emit_map_x2("p0_interior_ng%d_x2" % ng, value_map(M0, 4, pts[nf:])))
         for n in (1, 2, 3, 4):
             out.append(emit_map("q%d_faces_ng%d" % (n, ng), value_map(MQ[n], 2, pts[:nf])))
+        for n in (1, 2, 3, 4):
+            out.append(emit_map_x2("q%d_faces_ng%d_x2" % (n, ng), value_map(MQ[n], 2, pts[:nf])))
     D0, F0 = ldl_forms(B4, M0)
     out.append("// smoothness indicators of Eq. (2dGHYZ), dx = dy")
     out.append(emit_beta("beta_p0", D0, F0))
     for n in (1, 2, 3, 4):
         Dn, Fn = ldl_forms(B2, MQ[n])
         out.append(emit_beta("beta_q%d" % n, Dn, Fn))
+    out.append(emit_beta_x2("beta_p0_x2", D0, F0))
+    for n in (1, 2, 3, 4):
+        Dn, Fn = ldl_forms(B2, MQ[n])
+        out.append(emit_beta_x2("beta_q%d_x2" % n, Dn, Fn))
     out.append("}  // namespace hw2")
     sys.stdout.write("\n\n".join(out) + "\n")
 

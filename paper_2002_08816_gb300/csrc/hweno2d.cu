@@ -270,24 +270,53 @@ __device__ __noinline__ void hweno_faces_euler2d(S& sm, int ci, int cj, int p_lo
     for (int c = 0; c < 4; ++c)
 #pragma unroll
       for (int p = 0; p < NF; ++p) acc[c][p] = R(0);
+    if constexpr (sizeof(R) == 4) {
+      // FP32: the fields in pairs (f, f + 1) through the packed HWENO
+      // helpers, the stencil data of each component gathered once per pair
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      R e[19], t[19];
+      for (int f = 0; f < 4; f += 2) {
+        float2 e2[19];
 #pragma unroll
-      for (int k = 0; k < 19; ++k) e[k] = R(0);
+        for (int k = 0; k < 19; ++k) e2[k] = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        gather_data<COMP>(sm, c, ci, cj, t);
+        for (int c = 0; c < 4; ++c) {
+          R t[19];
+          gather_data<COMP>(sm, c, ci, cj, t);
 #pragma unroll
-        for (int k = 0; k < 19; ++k) e[k] += Lm[f][c] * t[k];
+          for (int k = 0; k < 19; ++k) {
+            e2[k].x += Lm[f][c] * t[k];
+            e2[k].y += Lm[f + 1][c] * t[k];
+          }
+        }
+        float2 chv2[NF];
+        hweno2d_faces_x2<NG>(e2, gam, eps, plo, phi, chv2);
+#pragma unroll
+        for (int p = 0; p < NF; ++p)
+          if (p >= plo && p < phi)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              acc[c][p] += Rm[c][f] * chv2[p].x + Rm[c][f + 1] * chv2[p].y;
       }
-      R chv[NF];
-      hweno2d_faces<NG>(e, gam, eps, plo, phi, chv);
+    } else {
 #pragma unroll
-      for (int p = 0; p < NF; ++p)
-        if (p >= plo && p < phi)
+      for (int f = 0; f < 4; ++f) {
+        R e[19], t[19];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[c][p] += Rm[c][f] * chv[p];
+        for (int k = 0; k < 19; ++k) e[k] = R(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          gather_data<COMP>(sm, c, ci, cj, t);
+#pragma unroll
+          for (int k = 0; k < 19; ++k) e[k] += Lm[f][c] * t[k];
+        }
+        R chv[NF];
+        hweno2d_faces<NG>(e, gam, eps, plo, phi, chv);
+#pragma unroll
+        for (int p = 0; p < NF; ++p)
+          if (p >= plo && p < phi)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c][p] += Rm[c][f] * chv[p];
+      }
     }
 #pragma unroll
     for (int p = 0; p < NF; ++p)
@@ -351,14 +380,17 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   const int ox = tid % TX, oy = tid / TX;  // own cell of this thread
   const int gi = bx0 + ox, gj = by0 + oy;
   const bool own = gi < nx && gj < ny;
-  R u0c[C][3], u0l[C];
+  // u^n of the own cell (stages 2 and 3): brought into L2 now and loaded in
+  // phase 4, so that no registers hold it through phases 2 and 3
   if (a.stage >= 2 && own) {
     const R* u0 = static_cast<const R*>(a.u0);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) u0c[c][m] = u0[(3 * c + m) * plane + (size_t)gj * nx + gi];
-      if constexpr (COMP) u0l[c] = a.u0_lo[c * plane + (size_t)gj * nx + gi];
+      for (int m = 0; m < 3; ++m)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(u0 + (3 * c + m) * plane + (size_t)gj * nx + gi));
+      if constexpr (COMP)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u0_lo + c * plane + (size_t)gj * nx + gi));
     }
   }
   if (!tma) {
@@ -604,6 +636,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   R spx = R(0), spy = R(0);
   unsigned bad = 0;
   {
+    R u0c[C][3], u0l[C];
+    if (a.stage >= 2 && own) {
+      const R* u0 = static_cast<const R*>(a.u0);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) u0c[c][m] = u0[(3 * c + m) * plane + (size_t)gj * nx + gi];
+        if constexpr (COMP) u0l[c] = a.u0_lo[c * plane + (size_t)gj * nx + gi];
+      }
+    }
     myflag = sm.fl[cj + 2][ci + 2];
     const R hax = R(0.5) * alx, hay = R(0.5) * aly;
     // COMP: every point value is an increment over the own cell's hi B, every

@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   const int lx = ci + 1, ly = cj + 1;
   // sm.lam holds lambda itself (from x = bx0 - 4); b dt enters the weights
 #define LAM(c, m, di, dj) sm.lam[c][m][ly + (dj)][lx + 3 + (di)]
-#pragma unroll
-  for (int k = 0; k < NG; ++k) {
+  // the adjoints of the four faces' point values at Gauss point k
+  auto face_point = [&](int k) {
     const R wxk = gw[k] * P_.inv_dx * scale, wyk = gw[k] * P_.inv_dy * scale;
     R lf[C], U[C], o[C];
     // x_{i-1/2}: own left point k is u^+
@@ -491,26 +491,88 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     flux_jt2<R, C>(P_.gas, U, 1, lf, o);
 #pragma unroll
     for (int c = 0; c < C; ++c) P[c][3 * NG + k] = R(0.5) * o[c] + hay * lf[c];
-  }
-  // interior points: the volume integrals of Eq. (ode2)'s moment equations
+  };
+  // interior point p: the volume integrals of Eq. (ode2)'s moment equations
+  auto interior_point = [&](int p) {
+    const int k = (p - NF) % NG, l = (p - NF) / NG;
+    const R wk = gw[k] * gw[l];
+    R U[C], l1[C], l2[C], o1[C], o2[C];
 #pragma unroll
-  for (int l = 0; l < NG; ++l)
+    for (int c = 0; c < C; ++c) {
+      U[c] = P[c][p];
+      l1[c] = wk * P_.inv_dx * scale * LAM(c, 1, 0, 0);
+      l2[c] = wk * P_.inv_dy * scale * LAM(c, 2, 0, 0);
+    }
+    flux_jt2<R, C>(P_.gas, U, 0, l1, o1);
+    flux_jt2<R, C>(P_.gas, U, 1, l2, o2);
 #pragma unroll
-    for (int k = 0; k < NG; ++k) {
-      const int p = NF + l * NG + k;
-      const R wk = gw[k] * gw[l];
-      R U[C], l1[C], l2[C], o1[C], o2[C];
+    for (int c = 0; c < C; ++c) P[c][p] = o1[c] + o2[c];
+  };
+  if constexpr (kPacked) {
+    // FP32 Euler: points in pairs (Gauss k, k + 1 of each face; interior p,
+    // p + 1) through the packed Jacobian transposes; a face's lambda
+    // combination is A + gx_k B with A and B formed once for both points
+#pragma unroll
+    for (int k = 0; k + 1 < NG; k += 2) {
+      const float2 wx2 = make_float2(gw[k] * P_.inv_dx * scale, gw[k + 1] * P_.inv_dx * scale);
+      const float2 wy2 = make_float2(gw[k] * P_.inv_dy * scale, gw[k + 1] * P_.inv_dy * scale);
+      const float2 gx2 = make_float2(gx[k], gx[k + 1]);
+      // one face: sign s of the own cell's side (-1: u^+ at the low face, +1:
+      // u^- at the high face), the neighbour's offset, the moment m1 that
+      // carries 1/2 and m2 that carries gx; writes the points p0, p0 + 1
+      auto face_pair = [&](int p0, int dir, float sgn, int di, int dj, int m1, int m2) {
+        float2 lf[C], U2[C], o2[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          // -s (own - nb) terms: A = -s (L0 - L0nb) - (L1 + L1nb) / 2 (m1), B = -s (L2 - L2nb) (m2)
+          const float A = -sgn * (LAM(c, 0, 0, 0) - LAM(c, 0, di, dj)) -
+                          0.5f * (LAM(c, m1, 0, 0) + LAM(c, m1, di, dj));
+          const float B = -sgn * (LAM(c, m2, 0, 0) - LAM(c, m2, di, dj));
+          lf[c] = __fmul2_rn(dir == 0 ? wx2 : wy2, __ffma2_rn(gx2, bcast2(B), bcast2(A)));
+          U2[c] = make_float2(P[c][p0], P[c][p0 + 1]);
+        }
+        flux_jt2_x2(P_.gas, U2, dir, lf, o2);
+        const float h = dir == 0 ? hax : hay;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float2 r = __ffma2_rn(bcast2(sgn * h), lf[c], __fmul2_rn(bcast2(0.5f), o2[c]));
+          P[c][p0] = r.x;
+          P[c][p0 + 1] = r.y;
+        }
+      };
+      face_pair(k, 0, -1.0f, -1, 0, 1, 2);           // x_{i-1/2}
+      face_pair(NG + k, 0, 1.0f, 1, 0, 1, 2);        // x_{i+1/2}
+      face_pair(2 * NG + k, 1, -1.0f, 0, -1, 2, 1);  // y_{j-1/2}
+      face_pair(3 * NG + k, 1, 1.0f, 0, 1, 2, 1);    // y_{j+1/2}
+    }
+    if constexpr (NG % 2 == 1) face_point(NG - 1);
+#pragma unroll
+    for (int p = NF; p + 1 < NP; p += 2) {
+      const int k0 = (p - NF) % NG, l0 = (p - NF) / NG, k1 = (p + 1 - NF) % NG, l1i = (p + 1 - NF) / NG;
+      const float2 w2 = make_float2(gw[k0] * gw[l0], gw[k1] * gw[l1i]);
+      float2 U2[C], la[C], lb[C], oa[C], ob[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        U[c] = P[c][p];
-        l1[c] = wk * P_.inv_dx * scale * LAM(c, 1, 0, 0);
-        l2[c] = wk * P_.inv_dy * scale * LAM(c, 2, 0, 0);
+        U2[c] = make_float2(P[c][p], P[c][p + 1]);
+        la[c] = __fmul2_rn(w2, bcast2(P_.inv_dx * scale * LAM(c, 1, 0, 0)));
+        lb[c] = __fmul2_rn(w2, bcast2(P_.inv_dy * scale * LAM(c, 2, 0, 0)));
       }
-      flux_jt2<R, C>(P_.gas, U, 0, l1, o1);
-      flux_jt2<R, C>(P_.gas, U, 1, l2, o2);
+      flux_jt2_x2(P_.gas, U2, 0, la, oa);
+      flux_jt2_x2(P_.gas, U2, 1, lb, ob);
 #pragma unroll
-      for (int c = 0; c < C; ++c) P[c][p] = o1[c] + o2[c];
+      for (int c = 0; c < C; ++c) {
+        const float2 r = __fadd2_rn(oa[c], ob[c]);
+        P[c][p] = r.x;
+        P[c][p + 1] = r.y;
+      }
     }
+    if constexpr (NI % 2 == 1) interior_point(NP - 1);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NG; ++k) face_point(k);
+#pragma unroll
+    for (int p = NF; p < NP; ++p) interior_point(p);
+  }
 #undef LAM
 
   // adjoints of the 19 data, summed per target cell over the tile's own cells

@@ -250,6 +250,66 @@ __device__ __forceinline__ void hweno2d_faces(const R* d, const R* gam, R eps, i
   }
 }
 
+// The same on two fields at once (packed FP32: the smoothness indicators and
+// the candidates' values in pairs, the weights of each field in scalar FP32).
+template <int NG>
+__device__ __forceinline__ void q_faces_x2(int n, const float2* d, float2* o) {
+  if constexpr (NG == 3) {
+    if (n == 1) hw2::q1_faces_ng3_x2(d, o);
+    else if (n == 2) hw2::q2_faces_ng3_x2(d, o);
+    else if (n == 3) hw2::q3_faces_ng3_x2(d, o);
+    else hw2::q4_faces_ng3_x2(d, o);
+  } else {
+    if (n == 1) hw2::q1_faces_ng2_x2(d, o);
+    else if (n == 2) hw2::q2_faces_ng2_x2(d, o);
+    else if (n == 3) hw2::q3_faces_ng2_x2(d, o);
+    else hw2::q4_faces_ng2_x2(d, o);
+  }
+}
+template <int NG>
+__device__ __forceinline__ void hweno2d_faces_x2(const float2* d, const float* gam, float eps,
+                                                 int p_lo, int p_hi, float2* out) {
+  constexpr int NF = 4 * NG;
+  const float2 b2[5] = {hw2::beta_p0_x2(d), hw2::beta_q1_x2(d), hw2::beta_q2_x2(d),
+                        hw2::beta_q3_x2(d), hw2::beta_q4_x2(d)};
+  float2 c02, cn2[4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float b[5];
+#pragma unroll
+    for (int n = 0; n < 5; ++n) b[n] = h ? b2[n].y : b2[n].x;
+    const float s = 0.25f * (fabsf(b[0] - b[1]) + fabsf(b[0] - b[2]) + fabsf(b[0] - b[3]) +
+                             fabsf(b[0] - b[4]));
+    const float tau = s * s;
+    float a[5], sum = 0.0f;
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+      a[n] = gam[n] * (1.0f + tau * fast_rcp(b[n] + eps));
+      sum += a[n];
+    }
+    const float inv = fast_rcp(sum);
+    const float c0 = a[0] * inv * fast_rcp(gam[0]);
+    if (h) c02.y = c0; else c02.x = c0;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const float cn = a[n + 1] * inv - c0 * gam[n + 1];
+      if (h) cn2[n].y = cn; else cn2[n].x = cn;
+    }
+  }
+  float2 tmp[NF];
+  p0_faces_x2<NG>(d, tmp);
+#pragma unroll
+  for (int p = 0; p < NF; ++p)
+    if (p >= p_lo && p < p_hi) out[p] = __fmul2_rn(c02, tmp[p]);
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    q_faces_x2<NG>(n + 1, d, tmp);
+#pragma unroll
+    for (int p = 0; p < NF; ++p)
+      if (p >= p_lo && p < p_hi) out[p] = __ffma2_rn(cn2[n], tmp[p], out[p]);
+  }
+}
+
 // Step 4 for a troubled Euler cell (lx, ly) of the flag grid: vbar from the
 // x-neighbours in the x characteristic fields, wbar from the y-neighbours in
 // the y fields, with the 1D Step 1 formula, written to sm.lim[slot] (S with

@@ -212,6 +212,46 @@ __device__ __forceinline__ void flux_jt2(R gas, const R* U, int dir, const R* l,
   }
 }
 
+// flux_jt2 (Euler) of two points at once: each component a pair, the same
+// arithmetic in packed FP32 (one approximate reciprocal per point).
+__device__ __forceinline__ void flux_jt2_x2(float gas, const float2* U, int dir, const float2* l,
+                                            float2* o) {
+  const float2 ir = make_float2(fast_rcp(U[0].x), fast_rcp(U[0].y));
+  const float2 u = __fmul2_rn(U[1], ir), v = __fmul2_rn(U[2], ir);
+  const float g1 = gas - 1.0f;
+  const float2 kq = __fmul2_rn(bcast2(g1 * 0.5f), __ffma2_rn(v, v, __fmul2_rn(u, u)));
+  const float2 p = __ffma2_rn(bcast2(-1.0f), __fmul2_rn(U[0], kq), __fmul2_rn(bcast2(g1), U[3]));
+  const float2 H = __fmul2_rn(__fadd2_rn(U[3], p), ir);
+  const float2 uv = __fmul2_rn(u, v);
+  if (dir == 0) {
+    const float2 uu = __fmul2_rn(u, u);
+    // l1 (kq - u u) - l2 u v + l3 u (kq - H)
+    o[0] = __ffma2_rn(l[3], __fmul2_rn(u, sub2(kq, H)),
+                      __ffma2_rn(l[1], sub2(kq, uu), __fmul2_rn(bcast2(-1.0f), __fmul2_rn(l[2], uv))));
+    // l0 + l1 (3 - gamma) u + l2 v + l3 (H - g1 u u)
+    o[1] = __ffma2_rn(l[3], __ffma2_rn(bcast2(-g1), uu, H),
+                      __ffma2_rn(l[2], v, __ffma2_rn(__fmul2_rn(l[1], bcast2(3.0f - gas)), u, l[0])));
+    // -l1 g1 v + l2 u - l3 g1 u v
+    o[2] = __ffma2_rn(__fmul2_rn(l[3], bcast2(-g1)), uv,
+                      __ffma2_rn(l[2], u, __fmul2_rn(__fmul2_rn(l[1], bcast2(-g1)), v)));
+    // l1 g1 + l3 gamma u
+    o[3] = __ffma2_rn(__fmul2_rn(l[3], bcast2(gas)), u, __fmul2_rn(l[1], bcast2(g1)));
+  } else {
+    const float2 vv = __fmul2_rn(v, v);
+    // -l1 u v + l2 (kq - v v) + l3 v (kq - H)
+    o[0] = __ffma2_rn(l[3], __fmul2_rn(v, sub2(kq, H)),
+                      __ffma2_rn(l[2], sub2(kq, vv), __fmul2_rn(bcast2(-1.0f), __fmul2_rn(l[1], uv))));
+    // l1 v - l2 g1 u - l3 g1 u v
+    o[1] = __ffma2_rn(__fmul2_rn(l[3], bcast2(-g1)), uv,
+                      __ffma2_rn(l[1], v, __fmul2_rn(__fmul2_rn(l[2], bcast2(-g1)), u)));
+    // l0 + l1 u + l2 (3 - gamma) v + l3 (H - g1 v v)
+    o[2] = __ffma2_rn(l[3], __ffma2_rn(bcast2(-g1), vv, H),
+                      __ffma2_rn(__fmul2_rn(l[2], bcast2(3.0f - gas)), v, __ffma2_rn(l[1], u, l[0])));
+    // l2 g1 + l3 gamma v
+    o[3] = __ffma2_rn(__fmul2_rn(l[3], bcast2(gas)), v, __fmul2_rn(l[2], bcast2(g1)));
+  }
+}
+
 // A number with four tangents (forward mode), for the derivatives of the
 // eigen-system with respect to the cell average.
 template <typename R>

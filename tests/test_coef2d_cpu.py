@@ -93,9 +93,39 @@ def _parse_x2():
 
 def test_packed_maps_are_the_scalar_maps():
     x2 = _parse_x2()
-    assert set(x2) == {"p0_faces_ng2", "p0_interior_ng2", "p0_faces_ng3", "p0_interior_ng3"}
+    names = {"p0_faces_ng2", "p0_interior_ng2", "p0_faces_ng3", "p0_interior_ng3"}
+    names |= {"q%d_faces_ng%d" % (n, ng) for n in (1, 2, 3, 4) for ng in (2, 3)}
+    assert set(x2) == names
     for name, rows in x2.items():
         assert rows == MAPS[name], name
+
+
+def test_packed_smoothness_indicators_are_the_scalar_ones():
+    """beta_*_x2 (two characteristic fields at once) hold the weights and
+    linear forms of the scalar indicators, in the same order."""
+    txt = open(HDR).read()
+    packed = {}
+    for m in re.finditer(r"float2 (beta_\w+)_x2\(const float2\* d\) \{(.*?)\n\}", txt, re.S):
+        terms, cur = [], {}
+        for line in m.group(2).splitlines():
+            t0 = re.match(r"\s*t = d\[(\d+)\];", line)
+            t = re.match(r"\s*t = __f(?:mul|fma)2_rn\(hw2_pair\(([-0-9.eE+]+)\), d\[(\d+)\]", line)
+            if t0:
+                cur = {int(t0.group(1)): 1.0}
+            elif t:
+                if "__fmul2_rn" in line:
+                    cur = {}
+                cur[int(t.group(2))] = float(t.group(1))
+            elif re.match(r"\s*b = __ffma2_rn\(t, t, b\);", line):
+                terms.append((1.0, cur))
+            else:
+                w = re.match(r"\s*b = __ffma2_rn\(__fmul2_rn\(hw2_pair\(([-0-9.eE+]+)\), t\), t, b\);", line)
+                if w:
+                    terms.append((float(w.group(1)), cur))
+        packed[m.group(1)] = terms
+    assert set(packed) == set(BETAS) == {"beta_p0", "beta_q1", "beta_q2", "beta_q3", "beta_q4"}
+    for name in BETAS:
+        assert packed[name] == BETAS[name], name
 
 
 ADJ = os.path.join(os.path.dirname(HDR), "hweno2d_adj_coef.cuh")

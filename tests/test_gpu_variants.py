@@ -126,3 +126,22 @@ def test_adjoint_rejects_variants():
         assert ei.value.status == H.HWENO_ERR_ARG
     finally:
         H.hweno_destroy(h)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("ng", [2, 3])
+def test_run2d_variant_fp32(ng, variant):
+    """FP32 runs (the packed-FP32 Euler path; with the raw combination the
+    stage reads an own cell's unmodified moments back from its input) over 5
+    steps against the oracle, relative L1 1e-4."""
+    nx, ny = 40, 24
+    dom = square_domain(nx, ny)
+    u = round_to(H.HWENO_FP32, mixed_euler2d(nx, ny, dom, 7))
+    cfg = H.make_config(2, H.HWENO_EULER, nx, ny, x0=dom[0], x1=dom[1], y0=dom[2], y1=dom[3],
+                        bc=H.HWENO_BC_PERIODIC, lin_w=(0.96, 0.01, 0.01, 0.01, 0.01), cfl=0.4,
+                        precision=H.HWENO_FP32, n_gauss=ng, variant=variant)
+    ocfg = O.Cfg2D.make(O.EULER, nx, ny, *dom, O.BC_PERIODIC, n_gauss=ng, **_okw(variant))
+    got, t, _ = gpu_run1d(cfg, u, 5)
+    ref, t_o, _ = O.run2d(ocfg, u, nsteps=5, cfl=0.4)
+    assert np.abs(got - ref).sum() / np.abs(ref).sum() <= 1e-4
+    assert abs(t - t_o) <= 1e-6 * t_o
