@@ -965,7 +965,9 @@ def main():
         ws, _, _ = dist_env()
         if line is not None and ws == 1 and not args.headline_only:
             sub = copy.copy(args)
-            sub.steps, sub.warmup = max(1, min(args.steps, 2)), 1
+            # every sub-record takes the command's warm-up count (>= 3) and up
+            # to 2 timed steps
+            sub.steps, sub.warmup = max(1, min(args.steps, 2)), max(3, args.warmup)
             ap_ = alu_peaks()
             line["alu_peaks"] = ap_
             # the FP64 path is bound by GB300's FP64 pipe (1/64 of FP32): its
