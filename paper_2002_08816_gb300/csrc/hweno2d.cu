@@ -430,6 +430,10 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     alx = fmax(alx, sm.amax[0][k]);
     aly = fmax(aly, sm.amax[1][k]);
   }
+  if (a.alpha_in) {  // replay: the recorded values (what the reduction gave)
+    alx = static_cast<const R*>(a.alpha_in)[0];
+    aly = static_cast<const R*>(a.alpha_in)[1];
+  }
   R dt = dt_prev;
   if (a.stage == 1) {
     if (a.dt_in) {  // replay of a recorded step
@@ -462,7 +466,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     const int lx = k % LX, ly = k / LX;
     const int rx = lx + 1 + SM::kPadX, ry = ly + 1;  // raw index of the cell
     int flag;
-    if (a.mode == 1) {
+    if (a.flags_in) {  // replay: the recorded decision (periodic: a ghost's is its image's)
+      flag = a.flags_in[(size_t)bc_map(by0 - 2 + ly, ny, a.bc) * nx + bc_map(bx0 - 2 + lx, nx, a.bc)] != 0;
+    } else if (a.mode == 1) {
       flag = 1;
     } else if (a.mode == 2) {
       flag = 0;
@@ -913,7 +919,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     }
     if (own) {
       if (a.flags_out) a.flags_out[(size_t)gj * nx + gi] = (uint8_t)myflag;
-      if (a.stage > 0) {
+      if (a.stage > 0 && a.a_out) {  // (a replayed stage needs no maxima)
         wave_speeds2<R, C>(gas, Uo, spx, spy);
         if (!(spx == spx) || !(spy == spy)) {
           bad |= ST_NONPHYSICAL;

@@ -162,7 +162,8 @@ hw::Stage2DArgs base_args2d(const hweno_ctx* h) {
 // The buffers of one 2D Runge-Kutta step: in -> s1 -> s2 -> out, the limited
 // u^n in w0, alpha carried through part[0..2]; optional recording of the
 // switches (flags: 3 planes; rec_alpha: 3 pairs; rec_dt) or replay of a
-// recorded dt (dt_in).
+// recorded step (dt_in; alpha_in: its 3 pairs, flags_in: its 3 planes, which
+// spare the replayed stages their wave-speed maxima and KXRCF tests).
 struct Step2DIO {
   const void* in;
   void* s1;
@@ -181,6 +182,8 @@ struct Step2DIO {
   float* s1_lo = nullptr;
   float* s2_lo = nullptr;
   float* out_lo = nullptr;
+  const uint8_t* flags_in = nullptr;
+  const void* alpha_in = nullptr;
 };
 
 void* byte_off(const void* p, size_t bytes) {
@@ -206,7 +209,11 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.comp = io.in_lo != nullptr;
   a.w_lo = io.in_lo;
   a.out_lo = io.s1_lo;
-  cudaError_t e = hw::launch_dt2d(a, s);
+  const bool replay = io.alpha_in != nullptr;
+  a.flags_in = io.flags_in;
+  a.alpha_in = io.alpha_in;
+  if (replay) a.a_out = nullptr;
+  cudaError_t e = replay ? cudaSuccess : hw::launch_dt2d(a, s);
   if (e != cudaSuccess) return e;
   e = hw::launch_stage2d(a, s);
   if (e != cudaSuccess) return e;
@@ -225,6 +232,11 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.out_lo = io.s2_lo;
   if (io.flags) a.flags_out = io.flags + (size_t)h->n;
   if (io.rec_alpha) a.rec_alpha = byte_off(io.rec_alpha, pair);
+  if (io.flags_in) a.flags_in = io.flags_in + (size_t)h->n;
+  if (replay) {
+    a.alpha_in = byte_off(io.alpha_in, pair);
+    a.a_out = nullptr;
+  }
   e = hw::launch_stage2d(a, s);
   if (e != cudaSuccess) return e;
   a.stage = 3;
@@ -237,6 +249,11 @@ cudaError_t enqueue_step2d_io(hweno_ctx* h, const Step2DIO& io, cudaStream_t s) 
   a.out_lo = io.out_lo;  // may be in_lo: each cell reads its u^n low part before it writes
   if (io.flags) a.flags_out = io.flags + 2 * (size_t)h->n;
   if (io.rec_alpha) a.rec_alpha = byte_off(io.rec_alpha, 2 * pair);
+  if (io.flags_in) a.flags_in = io.flags_in + 2 * (size_t)h->n;
+  if (replay) {
+    a.alpha_in = byte_off(io.alpha_in, 2 * pair);
+    a.a_out = nullptr;
+  }
   return hw::launch_stage2d(a, s);
 }
 
@@ -986,10 +1003,9 @@ hweno_status hweno_backward(hweno_handle h, const void* grad_out, void* grad_in,
     // recompute the segment's stage inputs from its checkpoint
     HW_CUDA(h, cudaMemcpyAsync(t.seg, byte_off(t.ck, sbytes * seg), sbytes, cudaMemcpyDeviceToDevice,
                                h->stream));
-    HW_CUDA(h, cudaMemsetAsync(t.slots, 0, sizeof(double) * 6 * hw::kAlphaSlots, h->stream));
+    // (each stage takes its recorded alpha and flags: the stage inputs are
+    // bitwise those of the recorded run, and no alpha slots are needed)
     double* sl[3] = {t.slots, t.slots + 2 * hw::kAlphaSlots, t.slots + 4 * hw::kAlphaSlots};
-    HW_CUDA(h, hw::launch_alpha2d(t.seg, sl[0], h->cfg.nx, h->cfg.ny, h->cfg.system, k64,
-                                  h->cfg.gas_gamma, t.sc, 1, h->stream));
     for (int n = n0; n < n1; ++n) {
       if (!(t.dt_host[n] > 0.0)) break;  // past t_final: the remaining steps did nothing
       const size_t m = (size_t)(n - n0);
@@ -997,6 +1013,8 @@ hweno_status hweno_backward(hweno_handle h, const void* grad_out, void* grad_in,
                      byte_off(t.seg, sbytes * (3 * m + 2)), byte_off(t.seg, sbytes * (3 * m + 3)),
                      t.w0, {sl[0], sl[1], sl[2]}, t.sc, nullptr, nullptr, nullptr,
                      byte_off(t.dt, (size_t)n * h->esize)};
+      io.flags_in = t.flags + (size_t)3 * n * h->n;
+      io.alpha_in = byte_off(t.alpha, (size_t)6 * n * h->esize);
       HW_CUDA(h, enqueue_step2d_io(h, io, h->stream));
     }
     // the adjoint stages, last step first

@@ -113,6 +113,11 @@ struct Stage2DArgs {
   void* rec_alpha;       // nullable: (alpha_x, alpha_y) of the stage, kernel precision
   void* rec_dt;          // nullable: dt of the step (stage 1), kernel precision
   const void* dt_in;     // nullable: stage 1 takes this dt (replay of a recorded step)
+  // replay of a recorded stage (nullable): its troubled flags (one byte per
+  // cell; periodic grids) and its (alpha_x, alpha_y) in the kernel precision;
+  // with alpha_in the stage computes no wave-speed maxima (a_out unused)
+  const uint8_t* flags_in;
+  const void* alpha_in;
   int nx, ny, stage, bc, mode, system, fp64, ng;
   int variant;            // HWENO_VARIANT_* bits
   int tma;                // set by the launcher: interior tiles copied by TMA
