@@ -303,16 +303,18 @@ hweno_status hweno_set_execution(hweno_handle h, int threads, int persistent);
  * stream. */
 hweno_status hweno_totals(hweno_handle h, double* totals);
 
-/* Measures the fused multiply-add throughput of the current device (FP32 when
- * fp64 = 0, FP64 otherwise) for the arithmetic roofline of the stage kernels
- * (no counterpart in the paper, which names no hardware): a kernel of eight
- * independent FMA chains per thread on a grid that fills every SM, each
- * thread doing iters x 128 FMAs, timed with CUDA events after one untimed
- * launch on a private stream; *flops_per_s = 2 x FMAs / time, at whatever SM
- * clock the GPU runs.  Allocates and frees a small buffer; waits for
- * completion.  HWENO_ERR_ARG unless 1 <= iters <= 2^24 and flops_per_s is
- * non-NULL. */
-hweno_status hweno_fma_peak(int fp64, int iters, double* flops_per_s);
+/* Measures the fused multiply-add throughput of the current device for the
+ * arithmetic roofline of the stage kernels (no counterpart in the paper, which
+ * names no hardware): kind 0 FP32, 1 FP64, 2 packed FP32 (fma.rn.f32x2, two
+ * FMAs per instruction; it shows whether the packed form used by the 2D
+ * kernels raises the FP32 flop rate).  A kernel of eight independent FMA
+ * chains per thread (kind 2: eight chains of pairs) on a grid that fills every
+ * SM, each thread doing iters x 128 FMAs (kind 2: iters x 256), timed with
+ * CUDA events after one untimed launch on a private stream; *flops_per_s =
+ * 2 x FMAs / time, at whatever SM clock the GPU runs.  Allocates and frees a
+ * small buffer; waits for completion.  HWENO_ERR_ARG unless 0 <= kind <= 2,
+ * 1 <= iters <= 2^24 and flops_per_s is non-NULL. */
+hweno_status hweno_fma_peak(int kind, int iters, double* flops_per_s);
 
 /* Frees every device buffer of the handle; NULL is ignored. */
 void hweno_destroy(hweno_handle h);

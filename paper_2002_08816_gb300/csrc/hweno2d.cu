@@ -36,7 +36,7 @@
 namespace hw {
 namespace {
 
-constexpr int TX = kTile2DX, TY = kTile2DY;
+constexpr int TX = 32, TY = 8;  // cells per CTA of the stage and wave-speed kernels (a warp per row)
 constexpr int NT = kThreads2D;
 constexpr int NW = NT / 32;
 // raw tile: a 3-cell halo, and in x one more column on the left so that the
@@ -1094,6 +1094,8 @@ cudaError_t prepare_t() {
 }
 
 }  // namespace
+
+int stage2d_tiles(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
 
 bool encode_box_map(const void* w, int nx, int ny, int planes, int esize, int box_x, int box_y,
                     CUtensorMap* map) {

@@ -43,7 +43,7 @@ struct hweno_ctx {
   bool comp = false;
   float* Ulo = nullptr;
   float* Ulo_s[2] = {nullptr, nullptr};
-  int ntile_alpha = 0;               // CTAs of the 1D wave-speed kernels (kTile1D cells each)
+  int ntile_alpha = 0;               // CTAs of the wave-speed kernels (1D: kTile1D cells each; 2D: the stage tiles)
   unsigned* bar = nullptr;           // grid barrier of the persistent kernel
   std::vector<int> batch_nx;         // cells of each batch instance
   std::vector<hw::BatchInst> batch_inst;
@@ -591,7 +591,10 @@ hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_hand
     h->C = cfg->system == HWENO_EULER ? 4 : 1;
     h->M = 3;
     h->n = cfg->nx * cfg->ny;
+    // ntile: the adjoint kernels' tiles; ntile_alpha: the stage and wave-speed
+    // kernels' (the per-tile maxima of hweno_rhs)
     h->ntile = ((cfg->nx + hw::kTile2DX - 1) / hw::kTile2DX) * ((cfg->ny + hw::kTile2DY - 1) / hw::kTile2DY);
+    h->ntile_alpha = hw::stage2d_tiles(cfg->nx, cfg->ny);
   } else {
     h->C = cfg->system == HWENO_EULER ? 3 : 1;
     h->M = 2;
@@ -742,7 +745,7 @@ hweno_status hweno_rhs(hweno_handle h, const void* in, void* out, uint8_t* flags
     a.out = out;
     a.lim_out = ulim_out;
     a.a_in = h->part_rhs;
-    a.nin = h->ntile;
+    a.nin = h->ntile_alpha;
     a.sc = h->sc_rhs;
     a.flags_out = flags_out;
     HW_CUDA(h, hw::launch_stage2d(a, h->stream));

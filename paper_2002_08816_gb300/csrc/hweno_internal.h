@@ -132,7 +132,9 @@ struct Stage2DArgs {
   float f32[10];          // FP32 copies: gamma_0..4, eps, gas, 1/dx, 1/dy, cfl
 };
 
-constexpr int kTile2DX = 32, kTile2DY = 8;  // cells per CTA of the 2D kernels (a warp per row)
+constexpr int kTile2DX = 32, kTile2DY = 8;  // cells per CTA of the 2D adjoint kernels
+// CTAs of the 2D stage and wave-speed kernels (their own tile) for nx x ny cells
+int stage2d_tiles(int nx, int ny);
 constexpr int kThreads2D = 256;
 
 void finish_stage2d_args(Stage2DArgs& a);

@@ -204,10 +204,11 @@ def hweno_check_barrier(ctas, meetings, missing, polls):
     return st
 
 
-def hweno_fma_peak(fp64, iters):
-    """Measured FMA throughput of the current device, flops per second."""
+def hweno_fma_peak(kind, iters):
+    """Measured FMA throughput of the current device, flops per second (kind:
+    0 or False FP32, 1 or True FP64, 2 packed FP32)."""
     out = _D()
-    _check(lib().hweno_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(out)))
+    _check(lib().hweno_fma_peak(int(kind), int(iters), ctypes.byref(out)))
     return out.value
 
 

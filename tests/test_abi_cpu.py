@@ -97,3 +97,5 @@ def test_fma_peak_rejects_bad_arguments_before_any_cuda_call(lib):
     assert lib.hweno_fma_peak(0, 0, ctypes.byref(out)) == H.HWENO_ERR_ARG
     assert lib.hweno_fma_peak(1, (1 << 24) + 1, ctypes.byref(out)) == H.HWENO_ERR_ARG
     assert lib.hweno_fma_peak(0, 10, None) == H.HWENO_ERR_ARG
+    assert lib.hweno_fma_peak(3, 10, ctypes.byref(out)) == H.HWENO_ERR_ARG
+    assert lib.hweno_fma_peak(-1, 10, ctypes.byref(out)) == H.HWENO_ERR_ARG

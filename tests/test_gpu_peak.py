@@ -25,3 +25,6 @@ def test_fma_peak_is_plausible():
     f64 = H.hweno_fma_peak(True, 100)
     assert 1e12 < f32 <= 2 * 128 * sms * 2.5e9
     assert 0 < f64 < f32
+    # packed FP32 (two FMAs per instruction) within the same lane-rate bound
+    f32x2 = H.hweno_fma_peak(2, 1000)
+    assert 1e12 < f32x2 <= 2 * 128 * sms * 2.5e9
