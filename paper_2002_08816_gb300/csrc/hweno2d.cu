@@ -7,10 +7,12 @@
 //      (global Lax-Friedrichs fluxes); stage 1 turns them into
 //      dt = CFL / (alpha_x/dx + alpha_y/dy), clipped to t_final;
 //   2. Step 4 for the tile and 2 halo cells: KXRCF flags (FP32 kernels decide
-//      in FP32 when the rounding-error bound allows, else in FP64) and the
+//      in FP32 when the rounding-error bound allows, else with float pairs;
+//      a replayed stage of the adjoint takes its recorded flags) and the
 //      first moments of troubled cells modified dimension by dimension with
 //      the 1D Step 1 formula (Euler: characteristic fields of the x- and of
-//      the y-Jacobian at the cell average);
+//      the y-Jacobian at the cell average), written back into the tile once
+//      every flag and limiter has read the raw ones;
 //   3. Step 5.1/5.2 at the interface Gauss points of the tile's cells and of
 //      the one-cell cross halo: linear p0 (the quartic on the 3x3 stencil),
 //      or HWENO when the 3x3 stencil holds a troubled cell (Euler: x-faces in
@@ -20,7 +22,9 @@
 //   5. the tile's wave-speed maxima (x and y) into the slots for the next
 //      stage, the troubled count and the status bits.
 // The reconstruction arithmetic is the generated straight-line code of
-// hweno2d_coef.cuh (square cells).
+// hweno2d_coef.cuh (square cells); the FP32 Euler kernel runs it, the fluxes
+// and the HWENO helpers on pairs (two components, two points or two
+// characteristic fields) in packed FP32 (fma.rn.f32x2).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -522,8 +526,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     // characteristic limiter for its other lanes' sake
     if constexpr (C == 4) list_append(&sm.ntb, sm.tbl, k, flag != 0, LX * LY);
   }
+  // the tile's flag grid holds a troubled cell (uniform over the CTA): else
+  // no interface item of the tile needs HWENO and none tests its stencil
+  bool tile_troubled;
   if constexpr (C == 1) {
-    if (__syncthreads_or(hk[0] >= 0 || hk[1] >= 0)) {
+    tile_troubled = __syncthreads_or(hk[0] >= 0 || hk[1] >= 0);
+    if (tile_troubled) {
 #pragma unroll
       for (int j = 0; j < 2; ++j)
         if (hk[j] >= 0) {
@@ -535,7 +543,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     }
   } else {
     __syncthreads();
-    if (sm.ntb > 0) {  // uniform over the CTA
+    tile_troubled = sm.ntb > 0;
+    if (tile_troubled) {
       for (int q = tid; q < sm.ntb; q += NT) {
         const int k = sm.tbl[q];
         limit_euler2d(sm, k % LX, k / LX, q, gam[0], gam[1], gam[2], gam[3], gam[4], eps, gas);
@@ -575,10 +584,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     int ci, cj, p_lo, p_hi;  // own-tile coordinates of the cell, point range
     item_of(item, ci, cj, p_lo, p_hi);
     bool hw = false;
+    if (tile_troubled) {
 #pragma unroll
-    for (int dj = -1; dj <= 1; ++dj)
+      for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
-      for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 2 + dj][ci + 2 + di] != 0;
+        for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 2 + dj][ci + 2 + di] != 0;
+    }
     if (!hw) {
       if constexpr (kPacked) {
         // FP32 Euler: components (0, 1) and (2, 3) through the packed map

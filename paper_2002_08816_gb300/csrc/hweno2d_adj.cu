@@ -349,7 +349,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     sm.fl[ly][lx] = a.flags[s] != 0;
     ring_troubled |= sm.fl[ly][lx];
   }
-  if (__syncthreads_or(ring_troubled) && tid == 0) {  // kernel C's work list
+  const bool tile_troubled = __syncthreads_or(ring_troubled);  // uniform over the CTA
+  if (tile_troubled && tid == 0) {  // kernel C's work list
     const int q = atomicAdd(a.tile_list, 1);
     a.tile_list[1 + q] = blockIdx.y * gridDim.x + blockIdx.x;
   }
@@ -387,11 +388,13 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
   const int ci = tid % TX, cj = tid / TX;
   const int gi = bx0 + ci, gj = by0 + cj;
   const bool own = gi < nx && gj < ny;
-  bool hw = false;
+  bool hw = false;  // the cell's 3x3 stencil holds a troubled cell
+  if (tile_troubled) {
 #pragma unroll
-  for (int dj = -1; dj <= 1; ++dj)
+    for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
-    for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 1 + dj][ci + 1 + di] != 0;
+      for (int di = -1; di <= 1; ++di) hw |= sm.fl[cj + 1 + dj][ci + 1 + di] != 0;
+  }
 
   // point values (the forward's); FP32 Euler: the linear maps on pairs of
   // components in packed FP32, as the forward stage kernel
