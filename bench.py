@@ -53,6 +53,8 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3, "fp32c": 8 * 36 
 # capture over its stages; FP32C also reads the averages' low parts
 TRAFFIC_1D_FP32 = {(256, "resident"): (1915136 + 73472) / 6000}
 TRAFFIC_1D_FP32C = {(256, "resident"): (2937856 + 55808) / 6000}
+# the troubled-share workload's resident launch: a 200-step (600-stage) capture
+TRAFFIC_TROUBLED_1D = {(256, "resident"): (1784320 + 39936) / 600}
 # the batched workload, 128-thread per-stage launches: the mean of the three
 # stages of one step, cold L2
 TRAFFIC_BATCH_FP32 = {(128, "per-stage graphs"): (48920064 + 43554304 + 96720384 + 22503424
@@ -933,7 +935,8 @@ def bench_troubled1d(args):
         "execution": {"threads_per_cta": choice[0], "launch": launch,
                       "chosen_by": "hweno_autotune"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": TRAFFIC_TROUBLED_1D.get((choice[0], launch)),
                      "kernel": "%s<float,3,%d threads>" % (KERNEL_OF_LAUNCH[launch], choice[0]),
                      "flops_per_cell_stage": smooth + frac * (troubled - smooth),
                      "note": "64 B per cell-stage; flops counted on the oracle "
