@@ -769,11 +769,23 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
         sgyx[c] += gw[k] * gx[k] * (GTk[c] - GBk[c]);
       }
     };
-    if constexpr (kPacked && !COMP) {
+    if constexpr (kPacked) {
       // FP32 Euler: points in pairs, (interior p, p + 1) and (Gauss k, k + 1)
       // of every face, each flux, Lax-Friedrichs flux and weighted sum in
       // packed FP32; the pairs' halves are added at the end and an odd last
-      // point (3 Gauss points) runs alone
+      // point (3 Gauss points) runs alone.  COMP: the fluxes are increments
+      // over f(B), a neighbour's face values moved onto B by one broadcast add
+      auto flux_x2 = [&](const float2* U, int dir, float2* F) {
+        if constexpr (COMP) flux_inc2_x2(gas, B, U, dir, F);
+        else euler_flux_x2(gas, U, dir, F);
+      };
+      auto rebase_x2 = [&](float2* v, int dx, int dy) {
+        if constexpr (COMP) {
+#pragma unroll
+          for (int c = 0; c < C; ++c)
+            v[c] = __fadd2_rn(v[c], bcast2(__fsub_rn(sm.u[c][0][cj + OYR + dy][ci + OXR + dx], B[c])));
+        }
+      };
       float2 Fv2[C], Gv2[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) Fv2[c] = Gv2[c] = make_float2(0.0f, 0.0f);
@@ -782,8 +794,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
         float2 U2[C], f2[C], g2[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) U2[c] = make_float2(inter[c][p], inter[c][p + 1]);
-        euler_flux_x2(gas, U2, 0, f2);
-        euler_flux_x2(gas, U2, 1, g2);
+        flux_x2(U2, 0, f2);
+        flux_x2(U2, 1, g2);
         const float2 w2 = make_float2(gw[p % NG] * gw[p / NG], gw[(p + 1) % NG] * gw[(p + 1) / NG]);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -811,7 +823,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
           am[c] = make_float2(sm.xf[c][NG + k][cj][ci], sm.xf[c][NG + k + 1][cj][ci]);
           ap[c] = make_float2(sm.xf[c][k][cj][ci + 1], sm.xf[c][k + 1][cj][ci + 1]);
         }
-        euler_flux_x2(gas, am, 0, fa); euler_flux_x2(gas, ap, 0, fb);
+        rebase_x2(am, -1, 0);
+        flux_x2(am, 0, fa); flux_x2(ap, 0, fb);
 #pragma unroll
         for (int c = 0; c < C; ++c) FL[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hax);
 #pragma unroll
@@ -819,7 +832,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
           am[c] = make_float2(sm.xf[c][NG + k][cj][ci + 1], sm.xf[c][NG + k + 1][cj][ci + 1]);
           ap[c] = make_float2(sm.xf[c][k][cj][ci + 2], sm.xf[c][k + 1][cj][ci + 2]);
         }
-        euler_flux_x2(gas, am, 0, fa); euler_flux_x2(gas, ap, 0, fb);
+        rebase_x2(ap, 1, 0);
+        flux_x2(am, 0, fa); flux_x2(ap, 0, fb);
 #pragma unroll
         for (int c = 0; c < C; ++c) FR[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hax);
 #pragma unroll
@@ -827,7 +841,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
           am[c] = make_float2(sm.yf[c][NG + k][cj][ci], sm.yf[c][NG + k + 1][cj][ci]);
           ap[c] = make_float2(sm.yf[c][k][cj + 1][ci], sm.yf[c][k + 1][cj + 1][ci]);
         }
-        euler_flux_x2(gas, am, 1, fa); euler_flux_x2(gas, ap, 1, fb);
+        rebase_x2(am, 0, -1);
+        flux_x2(am, 1, fa); flux_x2(ap, 1, fb);
 #pragma unroll
         for (int c = 0; c < C; ++c) GB[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hay);
 #pragma unroll
@@ -835,7 +850,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
           am[c] = make_float2(sm.yf[c][NG + k][cj + 1][ci], sm.yf[c][NG + k + 1][cj + 1][ci]);
           ap[c] = make_float2(sm.yf[c][k][cj + 2][ci], sm.yf[c][k + 1][cj + 2][ci]);
         }
-        euler_flux_x2(gas, am, 1, fa); euler_flux_x2(gas, ap, 1, fb);
+        rebase_x2(ap, 0, 1);
+        flux_x2(am, 1, fa); flux_x2(ap, 1, fb);
 #pragma unroll
         for (int c = 0; c < C; ++c) GT[c] = lf_x2(fa[c], fb[c], am[c], ap[c], hay);
 #pragma unroll

@@ -150,6 +150,37 @@ __device__ __forceinline__ void flux_inc2(float gas, const float* B, const float
   }
 }
 
+// flux_inc2 (Euler) for two increments D over one base B at once (each
+// increment component a pair), the same arithmetic in packed FP32.
+__device__ __forceinline__ void flux_inc2_x2(float gas, const float* B, const float2* D, int dir,
+                                             float2* dF) {
+  const float rho = B[0], m = B[1], n = B[2], E = B[3];
+  const float2 dr = D[0], dm = D[1], dn = D[2], dE = D[3];
+  const float ir = fast_rcp(rho);
+  const float2 ir1 = make_float2(fast_rcp(rho + dr.x), fast_rcp(rho + dr.y));
+  const float mu = m * ir, nu = n * ir;
+  const float2 dmu = __fmul2_rn(__ffma2_rn(bcast2(-mu), dr, dm), ir1);
+  const float2 dnu = __fmul2_rn(__ffma2_rn(bcast2(-nu), dr, dn), ir1);
+  // d(m mu), d(n nu)
+  const float2 dmm = __ffma2_rn(bcast2(m), dmu, __fmul2_rn(dm, __fadd2_rn(bcast2(mu), dmu)));
+  const float2 dnn = __ffma2_rn(bcast2(n), dnu, __fmul2_rn(dn, __fadd2_rn(bcast2(nu), dnu)));
+  const float g1 = gas - 1.0f;
+  const float p = g1 * (E - 0.5f * (m * mu + n * nu));
+  const float2 dp = __fmul2_rn(bcast2(g1), __ffma2_rn(bcast2(-0.5f), __fadd2_rn(dmm, dnn), dE));
+  const float2 sE = __fadd2_rn(dE, dp);  // d(E + p)
+  if (dir == 0) {
+    dF[0] = dm;
+    dF[1] = __fadd2_rn(dmm, dp);
+    dF[2] = __ffma2_rn(bcast2(n), dmu, __fmul2_rn(dn, __fadd2_rn(bcast2(mu), dmu)));  // d(n mu)
+    dF[3] = __ffma2_rn(dmu, __fadd2_rn(bcast2(E + p), sE), __fmul2_rn(bcast2(mu), sE));
+  } else {
+    dF[0] = dn;
+    dF[1] = __ffma2_rn(bcast2(m), dnu, __fmul2_rn(dm, __fadd2_rn(bcast2(nu), dnu)));  // d(m nu)
+    dF[2] = __fadd2_rn(dnn, dp);
+    dF[3] = __ffma2_rn(dnu, __fadd2_rn(bcast2(E + p), sE), __fmul2_rn(bcast2(nu), sE));
+  }
+}
+
 // max |f'| (dir 0) and |g'| (dir 1) at a cell average; NaN when not physical
 template <typename R, int C>
 __device__ __forceinline__ void wave_speeds2(R gas, const R* U, R& sx, R& sy) {
