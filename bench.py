@@ -61,8 +61,8 @@ TRAFFIC_BATCH_FP32 = {(128, "per-stage graphs"): (48920064 + 43554304 + 96720384
                                                   + 96724480 + 21628160) / 3}
 # 2D, 2 Gauss points: a 2048^2 capture (the three stages of one step) scaled
 # by the cell count to 4096^2 (the bytes per cell do not depend on the grid)
-TRAFFIC_2D_NG2 = 4 * (202501376 + 350601216 + 403324160 + 173975552 + 403563264
-                      + 175034112) / 3
+TRAFFIC_2D_NG2 = 4 * (202326016 + 350454528 + 403358976 + 173675008 + 403536384
+                      + 175169536) / 3
 L2_FLUSH_BYTES = 512 << 20
 # hweno_autotune's launch kinds and the kernel each one times
 LAUNCH_KIND = {0: "per-stage graphs", 1: "persistent", 2: "resident"}
