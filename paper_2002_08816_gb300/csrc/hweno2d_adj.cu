@@ -56,7 +56,11 @@ struct SmemA {
                                      // b dt is applied where it is used)
   R vl[C][BY][BX];      // Step 4 moments
   R wl[C][BY][BX];
-  R g[19][TY][TX];      // one component's stencil adjoints of the own cells
+  // stencil adjoints of the own cells: one component's, or (FP32 Euler) a
+  // pair of components' at once
+  static constexpr bool kPairs = C == 4 && sizeof(R) == 4;
+  R g[kPairs ? 1 : 19][TY][TX];
+  float2 g2[kPairs ? 19 : 1][TY][TX];
   uint8_t fl[BY][BX];
   unsigned long long bar;  // mbarrier of the tile copies
 };
@@ -595,25 +599,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
     }
   }
   R* __restrict__ part = static_cast<R*>(a.G) + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (C * 3 * BX * BY);
-  // the tile's sums of its cells' stencil adjoints g for component c, in a
-  // fixed order (deterministic)
-  auto exchange = [&](int c, const R* g) {
-#pragma unroll
-    for (int k = 0; k < 19; ++k) sm.g[k][cj][ci] = g[k];
-    __syncthreads();
-    for (int t = tid; t < BX * BY; t += NT) {
-      const int tx = t % BX - 1, ty = t / BX - 1;  // tile coordinates of the target
-      R m[3] = {R(0), R(0), R(0)};
-#pragma unroll
-      for (int k = 0; k < 19; ++k) {
-        const int sx = tx - data_dx(k), sy = ty - data_dy(k);
-        if (sx >= 0 && sx < TX && sy >= 0 && sy < TY) m[k < 9 ? 0 : (k < 14 ? 1 : 2)] += sm.g[k][sy][sx];
-      }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) part[(c * 3 + q) * (BX * BY) + t] = m[q];
-    }
-    __syncthreads();
-  };
   if constexpr (kPacked) {
 #pragma unroll
     for (int c = 0; c < C; c += 2) {
@@ -632,15 +617,50 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1))
         }
         p0_interior_T_x2<NG>(&l2[NF], g2);
       }
-      R g[19];
+      // both components' tile sums at once (each in the fixed order of the
+      // single-component exchange)
 #pragma unroll
-      for (int k = 0; k < 19; ++k) g[k] = g2[k].x;
-      exchange(c, g);
+      for (int k = 0; k < 19; ++k) sm.g2[k][cj][ci] = g2[k];
+      __syncthreads();
+      for (int t = tid; t < BX * BY; t += NT) {
+        const int tx = t % BX - 1, ty = t / BX - 1;  // tile coordinates of the target
+        float2 m[3] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
-      for (int k = 0; k < 19; ++k) g[k] = g2[k].y;
-      exchange(c + 1, g);
+        for (int k = 0; k < 19; ++k) {
+          const int sx = tx - data_dx(k), sy = ty - data_dy(k);
+          if (sx >= 0 && sx < TX && sy >= 0 && sy < TY) {
+            const int q = k < 9 ? 0 : (k < 14 ? 1 : 2);
+            m[q] = __fadd2_rn(m[q], sm.g2[k][sy][sx]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          part[(c * 3 + q) * (BX * BY) + t] = m[q].x;
+          part[((c + 1) * 3 + q) * (BX * BY) + t] = m[q].y;
+        }
+      }
+      __syncthreads();
     }
   } else {
+    // the tile's sums of its cells' stencil adjoints g for component c, in a
+    // fixed order (deterministic)
+    auto exchange = [&](int c, const R* g) {
+#pragma unroll
+      for (int k = 0; k < 19; ++k) sm.g[k][cj][ci] = g[k];
+      __syncthreads();
+      for (int t = tid; t < BX * BY; t += NT) {
+        const int tx = t % BX - 1, ty = t / BX - 1;  // tile coordinates of the target
+        R m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+          const int sx = tx - data_dx(k), sy = ty - data_dy(k);
+          if (sx >= 0 && sx < TX && sy >= 0 && sy < TY) m[k < 9 ? 0 : (k < 14 ? 1 : 2)] += sm.g[k][sy][sx];
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) part[(c * 3 + q) * (BX * BY) + t] = m[q];
+      }
+      __syncthreads();
+    };
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       R g[19];
