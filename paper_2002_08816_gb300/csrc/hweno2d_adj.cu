@@ -727,7 +727,7 @@ __device__ __forceinline__ void mu_at(const Adj2DArgs& a, int gi, int gj, R (*m)
 
 // Kernel B, one cell per thread: the adjoint of the stage input where Step 4
 // changed nothing (mu itself; zero for the first moments of a troubled cell),
-// and the adjoint of W0 (stage 3 sets it to lam / 3, stage 2 adds 3 lam / 4).
+// and the adjoint of W0 (formed at stage 2: lam3 / 3 + 3 lam2 / 4; stage 1 adds it).
 template <typename R, int C>
 __global__ void __launch_bounds__(NT) adj2d_pass_kernel(Adj2DArgs a) {
   const int gi = blockIdx.x * TX + threadIdx.x % TX, gj = blockIdx.y * TY + threadIdx.x / TX;
@@ -737,14 +737,17 @@ __global__ void __launch_bounds__(NT) adj2d_pass_kernel(Adj2DArgs a) {
   R* __restrict__ out = static_cast<R*>(a.lam_in);
   const R* __restrict__ lam = static_cast<const R*>(a.lam);
   R* __restrict__ acc = static_cast<R*>(a.acc);
-  // every load first, then the stores
+  // every load first, then the stores.  av: stage 1 the adjoint of W0 that
+  // stage 2 left; stage 2 lam3 / 3, lam3 (the adjoint of stage 3's output)
+  // still being in this kernel's output buffer, which stage 3 only read
   R lv[C][3], m[C][3], av[C][3];
 #pragma unroll
   for (int c = 0; c < C; ++c)
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       lv[c][q] = lam[(3 * c + q) * plane + s];
-      av[c][q] = a.stage == 1 || a.stage == 2 ? acc[(3 * c + q) * plane + s] : R(0);
+      av[c][q] = a.stage == 1 ? acc[(3 * c + q) * plane + s]
+                 : a.stage == 2 ? R(1.0 / 3.0) * out[(3 * c + q) * plane + s] : R(0);
     }
   const R bco = stage_b<R>(a.stage);
 #pragma unroll
@@ -757,11 +760,9 @@ __global__ void __launch_bounds__(NT) adj2d_pass_kernel(Adj2DArgs a) {
     out[(3 * c) * plane + s] = m[c][0];
     out[(3 * c + 1) * plane + s] = t0 ? R(0) : m[c][1];
     out[(3 * c + 2) * plane + s] = t0 ? R(0) : m[c][2];
-    if (a.stage >= 2) {
+    if (a.stage == 2) {
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-        acc[(3 * c + q) * plane + s] =
-            a.stage == 3 ? R(1.0 / 3.0) * lv[c][q] : av[c][q] + R(0.75) * lv[c][q];
+      for (int q = 0; q < 3; ++q) acc[(3 * c + q) * plane + s] = av[c][q] + R(0.75) * lv[c][q];
     }
   }
 }
