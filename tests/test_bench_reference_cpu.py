@@ -1,7 +1,8 @@
 """bench.py's reference arm (`--impl reference`: the oracle's OpenMP build timed on
 the host cores on bounded samples of the 65536-cell workload) needs no GPU: it
 prints one JSON line with the contract's keys, and a rank other than 0 of a
-multi-rank launch prints nothing and exits 0."""
+multi-rank launch prints nothing and exits 0; and the per-field error figures of
+the bench line on a case computed by hand."""
 
 import json
 import os
@@ -42,3 +43,25 @@ def test_reference_arm_other_ranks_are_silent():
     p = _run({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_field_errors_by_hand():
+    """The per-field figures of the bench line on a hand-made case: one cell of
+    one field off by 0.5 out of sums of 4 (averages) and 2 (first moments)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    ref = np.zeros((3, 2, 4))
+    ref[:, 0] = 1.0   # averages: sum 4 per component
+    ref[:, 1] = 0.5   # first moments: sum 2
+    a = ref.copy()
+    a[1, 1, 2] += 0.5  # m first moment, one cell
+    a[2, 0, 0] -= 0.25  # E average, one cell
+    e = bench.field_errors(a, ref)
+    assert e["rho_average"] == {"L1": 0.0, "Linf": 0.0, "rel_L1": 0.0}
+    assert e["m_first_moment"]["L1"] == 0.125 and e["m_first_moment"]["Linf"] == 0.5
+    assert e["m_first_moment"]["rel_L1"] == 0.25
+    assert e["m_first_moment"]["L1_over_avg_scale"] == 0.5  # 0.5 / (4 / 4)
+    assert e["E_average"]["rel_L1"] == 0.0625 and e["E_average"]["Linf"] == 0.25
+    assert set(e) == {"%s_%s" % (n, m) for n in ("rho", "m", "E")
+                      for m in ("average", "first_moment")}
