@@ -83,6 +83,28 @@ __device__ __forceinline__ void linear_faces(R um, R u0, R up, R vm, R v0, R vp,
           R(241.0 / 54.0) * v0 - R(28.0 / 27.0) * vp;
 }
 
+// Packed FP32 (two values per instruction, fma.rn.f32x2): a broadcast pair
+// and a - b in one rounding.
+__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(bcast2(-1.0f), b, a);
+}
+
+// linear_faces of two components at once (each argument a pair), the same
+// terms in packed FP32.
+__device__ __forceinline__ void linear_faces_x2(float2 um, float2 u0, float2 up, float2 vm,
+                                                float2 v0, float2 vp, float2& left, float2& right) {
+  auto k = [](double c) { return bcast2((float)c); };
+  left = __ffma2_rn(k(-25.0 / 54.0), vp,
+         __ffma2_rn(k(-241.0 / 54.0), v0,
+         __ffma2_rn(k(28.0 / 27.0), vm,
+         __ffma2_rn(k(13.0 / 108.0), up, __ffma2_rn(k(7.0 / 12.0), u0, __fmul2_rn(k(8.0 / 27.0), um))))));
+  right = __ffma2_rn(k(-28.0 / 27.0), vp,
+          __ffma2_rn(k(241.0 / 54.0), v0,
+          __ffma2_rn(k(25.0 / 54.0), vm,
+          __ffma2_rn(k(8.0 / 27.0), up, __ffma2_rn(k(7.0 / 12.0), u0, __fmul2_rn(k(13.0 / 108.0), um))))));
+}
+
 // Step 2.3: linear p0 at x_{i-sqrt5/10} (gm) and x_{i+sqrt5/10} (gp).
 template <typename R>
 __device__ __forceinline__ void linear_interior(R um, R u0, R up, R vm, R v0, R vp, R& gm,
@@ -94,6 +116,23 @@ __device__ __forceinline__ void linear_interior(R um, R u0, R up, R vm, R v0, R 
        R(c - d) * vp;
   gp = R(a - b) * um + R(13.0 / 12.0) * u0 - R(a + b) * up + R(d - c) * vm + R(e) * v0 +
        R(c + d) * vp;
+}
+
+// linear_interior of two components at once, in packed FP32.
+__device__ __forceinline__ void linear_interior_x2(float2 um, float2 u0, float2 up, float2 vm,
+                                                   float2 v0, float2 vp, float2& gm, float2& gp) {
+  constexpr double r5 = 2.2360679774997896964;
+  constexpr double a = 101.0 / 5400.0 * r5, b = 1.0 / 24.0;
+  constexpr double c = 3.0 / 20.0, d = 841.0 / 13500.0 * r5, e = 10289.0 / 6750.0 * r5;
+  auto k = [](double x) { return bcast2((float)x); };
+  gm = __ffma2_rn(k(c - d), vp,
+       __ffma2_rn(k(-e), v0,
+       __ffma2_rn(k(-(c + d)), vm,
+       __ffma2_rn(k(a - b), up, __ffma2_rn(k(13.0 / 12.0), u0, __fmul2_rn(k(-(a + b)), um))))));
+  gp = __ffma2_rn(k(c + d), vp,
+       __ffma2_rn(k(e), v0,
+       __ffma2_rn(k(d - c), vm,
+       __ffma2_rn(k(-(a + b)), up, __ffma2_rn(k(13.0 / 12.0), u0, __fmul2_rn(k(a - b), um))))));
 }
 
 // Step 2.1: HWENO values at x_{i-1/2} (left) and x_{i+1/2} (right); one set of

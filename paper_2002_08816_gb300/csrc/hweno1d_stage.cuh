@@ -195,10 +195,22 @@ __device__ __forceinline__ void faces_of_cell(Smem1D<R, C, NTH>& sm, int k, R ga
   R L[C], Rt[C], fL[C], fR[C];
   if (!hw || C == 1) {
     if (!hw) {
+      if constexpr (C == 3 && sizeof(R) == 4) {
+        // FP32 Euler: density and momentum as a pair through the packed map
+        float2 l2, r2;
+        auto p2 = [&](int m, int j) { return make_float2(m == 0 ? sm.u[0][0][j] : sm.vl[0][j],
+                                                         m == 0 ? sm.u[1][0][j] : sm.vl[1][j]); };
+        linear_faces_x2(p2(0, e - 1), p2(0, e), p2(0, e + 1), p2(1, e - 2), p2(1, e - 1),
+                        p2(1, e), l2, r2);
+        L[0] = l2.x; L[1] = l2.y; Rt[0] = r2.x; Rt[1] = r2.y;
+        linear_faces(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1], sm.vl[2][e - 2],
+                     sm.vl[2][e - 1], sm.vl[2][e], L[2], Rt[2]);
+      } else {
 #pragma unroll
-      for (int c = 0; c < C; ++c)
-        linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                     sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
+        for (int c = 0; c < C; ++c)
+          linear_faces(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                       sm.vl[c][e - 1], sm.vl[c][e], L[c], Rt[c]);
+      }
     } else {
       hweno_faces(sm.u[0][0][e - 1], sm.u[0][0][e], sm.u[0][0][e + 1], sm.vl[0][e - 2],
                   sm.vl[0][e - 1], sm.vl[0][e], gam, eps, L[0], Rt[0]);
@@ -245,6 +257,27 @@ __device__ __forceinline__ void faces_of_cell(Smem1D<R, C, NTH>& sm, int k, R ga
   }
 }
 
+// Step 2.3 of the cell in sm.u slot e (FP32 Euler: density and momentum as a
+// pair through the packed map).
+template <typename R, int C, int NTH>
+__device__ __forceinline__ void interior_values(const Smem1D<R, C, NTH>& sm, int e, R* gm, R* gp) {
+  if constexpr (C == 3 && sizeof(R) == 4) {
+    auto p2 = [&](int m, int j) { return make_float2(m == 0 ? sm.u[0][0][j] : sm.vl[0][j],
+                                                     m == 0 ? sm.u[1][0][j] : sm.vl[1][j]); };
+    float2 m2, q2;
+    linear_interior_x2(p2(0, e - 1), p2(0, e), p2(0, e + 1), p2(1, e - 2), p2(1, e - 1), p2(1, e),
+                       m2, q2);
+    gm[0] = m2.x; gm[1] = m2.y; gp[0] = q2.x; gp[1] = q2.y;
+    linear_interior(sm.u[2][0][e - 1], sm.u[2][0][e], sm.u[2][0][e + 1], sm.vl[2][e - 2],
+                    sm.vl[2][e - 1], sm.vl[2][e], gm[2], gp[2]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+      linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
+                      sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
+  }
+}
+
 // Eq. (odeH) for the own cell of thread tid (sm.u slot e = tid + 3): the
 // interior Gauss-Lobatto values (Step 2.3) and their fluxes, the
 // Lax-Friedrichs fluxes at x_{i-+1/2} (each from the traces and trace fluxes
@@ -259,10 +292,7 @@ __device__ __forceinline__ void rhs_of_cell(const Smem1D<R, C, NTH>& sm, int tid
   const int e = tid + H, k = tid + 1;  // sm.u slot; sm.fm/fp slot of the cell
   const R half_alpha = R(0.5) * alpha;
   R gm[C], gp[C], f2[C], f3[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-    linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                    sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
+  interior_values<R, C, NTH>(sm, e, gm, gp);
   phys_flux<R, C>(gas, gm, f2);
   phys_flux<R, C>(gas, gp, f3);
 #pragma unroll
@@ -287,10 +317,7 @@ __device__ __forceinline__ void rhs_parts_of_cell(const Smem1D<R, C, NTH>& sm, i
                                                   R inv_dx, R* L0u, R* Du, R* L0v, R* Dv) {
   const int e = tid + H, k = tid + 1;  // sm.u slot; sm.fm/fp slot of the cell
   R gm[C], gp[C], f2[C], f3[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-    linear_interior(sm.u[c][0][e - 1], sm.u[c][0][e], sm.u[c][0][e + 1], sm.vl[c][e - 2],
-                    sm.vl[c][e - 1], sm.vl[c][e], gm[c], gp[c]);
+  interior_values<R, C, NTH>(sm, e, gm, gp);
   phys_flux<R, C>(gas, gm, f2);
   phys_flux<R, C>(gas, gp, f3);
 #pragma unroll

@@ -88,11 +88,7 @@ __device__ __forceinline__ void phys_flux2(R gas, const R* U, int dir, R* F) {
 
 // ------------------------------------------------ packed FP32 (pairs of points)
 
-__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
-// a - b (one rounding, as the subtraction)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __ffma2_rn(bcast2(-1.0f), b, a);
-}
+// (bcast2 and sub2: hweno1d_recon.cuh)
 // The Euler flux f (dir 0) or g (dir 1) of two states at once (each component
 // a pair), the arithmetic of Euler2D<float>::flux in packed FP32.
 __device__ __forceinline__ void euler_flux_x2(float gas, const float2* U, int dir, float2* F) {
