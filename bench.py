@@ -51,14 +51,14 @@ BYTES_PER_CELL_STAGE = {"fp32": 8 * 24 / 3, "fp64": 8 * 48 / 3, "fp32c": 8 * 36 
 # summarised under profiles/ (None where no capture of the current build exists):
 # the resident launch reads the state once per launch: a 2000-step (6000-stage)
 # capture over its stages; FP32C also reads the averages' low parts
-TRAFFIC_1D_FP32 = {(256, "resident"): (1915136 + 73472) / 6000}
+TRAFFIC_1D_FP32 = {(256, "resident"): (2069504 + 63488) / 6000}
 TRAFFIC_1D_FP32C = {(256, "resident"): (2937856 + 55808) / 6000}
 # the troubled-share workload's resident launch: a 200-step (600-stage) capture
-TRAFFIC_TROUBLED_1D = {(256, "resident"): (1784320 + 39936) / 600}
+TRAFFIC_TROUBLED_1D = {(256, "resident"): (1767936 + 53248) / 600}
 # the batched workload, 128-thread per-stage launches: the mean of the three
 # stages of one step, cold L2
-TRAFFIC_BATCH_FP32 = {(128, "per-stage graphs"): (48920064 + 43554304 + 96720384 + 22503424
-                                                  + 96724480 + 21628160) / 3}
+TRAFFIC_BATCH_FP32 = {(128, "per-stage graphs"): (48942336 + 43494656 + 96712960 + 22568192
+                                                  + 96711424 + 21799936) / 3}
 # 2D, 2 Gauss points: a 2048^2 capture (the three stages of one step) scaled
 # by the cell count to 4096^2 (the bytes per cell do not depend on the grid)
 TRAFFIC_2D_NG2 = 4 * (202326016 + 350454528 + 403358976 + 173675008 + 403536384
